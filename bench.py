@@ -1,0 +1,372 @@
+"""Benchmark: coupled Gibbs nonzero-updates/s on the pedigree workload.
+
+Workload "pedigree50k": pedigree-shaped real non-symmetric C, n = 50,000, about
+7 nnz per row, K = 1024 chains, FP32 sweeps; estimates = the full diagonal of
+C^-1 and the 512-column block C^-1[:, 0:512] (BF16 tensor-core accumulation).
+A step = one sampling batch: B cycles of the coupled sweep (Eqs. 4/5) with
+the fused diagonal partials, one block contraction over the batch, and the FP64
+folds.  value = nnz(C) * K * cycles / seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+With N > 1 (torchrun) every rank runs its own K chains (disjoint chain ids):
+chains are independent, so there is no exchange on the data path ("weak").
+The reference arm is the FP64 CPU oracle on the host cores, timed on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled Gibbs nonzero-updates/s"
+UNIT = "nonzero-updates/s"
+WORKLOAD = "pedigree50k"
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "mine" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_from_profiles(kernel_file, units_per_launch):
+    """DRAM bytes per launch of the sweep from the committed ncu summary, if the
+    summary was taken on the current source of the kernel (matching hash)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(p):
+        return None
+    src = open(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", "sweep.cu"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    per_unit, ok = None, False
+    for line in open(p):
+        if line.startswith("source_sha256_16:"):
+            ok = line.split(":", 1)[1].strip() == digest
+        if line.startswith("dram_bytes_per_unit:"):
+            per_unit = float(line.split(":", 1)[1])
+    if ok and per_unit is not None:
+        return per_unit * units_per_launch
+    return None
+
+
+def run_mine(args, world, rank, local):
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    from paper_cs_0412107_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    w = wl.WORKLOADS[WORKLOAD]
+    csr = w.build()
+    K = args.chains
+    acc = mcinv.MCINV_ACC_BF16_TC if args.acc == "tc" else mcinv.MCINV_ACC_FP32_SIMT
+    S = np.arange(512)
+    R = np.arange(csr.n)
+    stream = torch.cuda.current_stream()
+    h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=acc,
+                              batch_cycles=args.batch, block_rows=R, block_cols=S,
+                              chains_per_cta=args.W, threads_per_cta=args.threads)
+    info0 = mcinv.mcinv_info(h)
+    B = info0["batch_cycles"]
+    mcinv.mcinv_burnin(h, args.burnin)
+    for _ in range(args.warmup):
+        mcinv.mcinv_sample(h, B)
+    mcinv.mcinv_sync(h)
+    launches0 = mcinv.mcinv_info(h)["kernel_launches"]
+    mcinv.mcinv_profile(h, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            mcinv.mcinv_sample(h, B)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    mcinv.mcinv_sync(h)
+    ms = ev0.elapsed_time(ev1)
+    prof = {mcinv.KERNEL_NAMES[k]: mcinv.mcinv_profile_read(h, k) for k in range(5)}
+    mcinv.mcinv_profile(h, False)
+    launches = mcinv.mcinv_info(h)["kernel_launches"] - launches0
+    ms_max = max_over_ranks(ms, world)
+    cycles = args.steps * B
+    updates = float(csr.nnz) * K * cycles * world
+    value = updates / (ms_max / 1e3)
+
+    hbm, bf16, bf16_sus, peak_kind = read_peaks()
+    sw_launches, sw_ms = prof["sweep"]
+    units_per_launch = csr.n * K * B  # (row, chain) coupled updates per sweep launch
+    alg_bytes = 16.0 * units_per_launch  # read + write z and w, FP32
+    achieved = alg_bytes / (sw_ms / sw_launches / 1e3) / 1e9 if sw_launches else None
+    nnz_off = csr.nnz - csr.n
+    gather_bytes = (4.0 * (2 * nnz_off + 2 * csr.n)) * K * B  # every stored c_ij gathers z_j and w_j
+    bl_launches, bl_ms = prof["block"]
+    gemm_flops = 2.0 * csr.n * 512 * K * B  # one contraction per batch
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded pedigree-shaped matrix, Philox noise)",
+        "config": {"workload": WORKLOAD, "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
+                   "cycles_per_step": B, "estimates": "diagonal + C^-1[:, 0:512]",
+                   "block_accumulation": "bf16 tensor cores" if acc else "fp32 simt",
+                   "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"],
+                   "levels": info0["levels"],
+                   "l2": "inputs larger than L2 (z, w double-buffered: %.0f MB)" % (4 * 4 * csr.n * K / 1e6),
+                   "parallelism": f"replicas x{world} (disjoint chains)"},
+        "roofline": {"kernel": "cc_sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
+                     "traffic": traffic_from_profiles("cc_sweep_pedigree50k.txt", units_per_launch),
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "gather_inclusive_bytes_per_launch": gather_bytes,
+                     "gather_inclusive_gbs": gather_bytes / (sw_ms / sw_launches / 1e3) / 1e9 if sw_launches else None},
+        "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "block_tflops": (gemm_flops * bl_launches / (bl_ms / 1e3) / 1e12 / max(bl_launches, 1) * 1) if bl_launches and acc else None,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    mcinv.mcinv_destroy(h)
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = run_e2e(args, csr, K, acc, rank)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(csr, K, args.cpu_seconds)
+    return result
+
+
+def run_e2e(args, csr, K, acc, rank):
+    """The same metric through the public C ABI from host buffers: one job =
+    mcinv_create from a pinned host CSR (H2D), burn-in, sampling, the diagonal
+    and block estimates read back to pinned host memory (D2H), destroy."""
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    rp = torch.from_numpy(csr.row_ptr).pin_memory()
+    col = torch.from_numpy(csr.col).pin_memory()
+    val = torch.from_numpy(np.ascontiguousarray(csr.val)).pin_memory()
+    S = np.arange(512)
+    R = np.arange(csr.n)
+    burn, samp = args.e2e_burnin, args.e2e_samples
+    h2d = rp.numel() * 8 + col.numel() * 4 + val.numel() * 8
+    d2h = csr.n * 8 * 2 + csr.n * 512 * 8 * 2
+    out_d = torch.empty(csr.n, dtype=torch.float64).pin_memory()
+    se_d = torch.empty(csr.n, dtype=torch.float64).pin_memory()
+    out_b = torch.empty(csr.n * 512, dtype=torch.float64).pin_memory()
+    se_b = torch.empty(csr.n * 512, dtype=torch.float64).pin_memory()
+    L = mcinv.lib()
+    import ctypes
+
+    def job():
+        opt = mcinv.mcinv_default_options(K=K, seed=args.seed + 1, chain_base=rank * K, acc=acc,
+                                          batch_cycles=args.batch)
+        opt.stream = mcinv.current_stream()
+        Ra = np.ascontiguousarray(R, dtype=np.int64)
+        Sa = np.ascontiguousarray(S, dtype=np.int64)
+        opt.block_rows = Ra.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        opt.block_cols = Sa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        opt.n_block_rows, opt.n_block_cols = len(Ra), len(Sa)
+        hp = ctypes.c_void_p()
+        mcinv._check(L.mcinv_create(ctypes.byref(hp), csr.n, ctypes.c_void_p(rp.data_ptr()),
+                                    ctypes.c_void_p(col.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                    mcinv.MCINV_REAL64, ctypes.byref(opt)))
+        mcinv._check(L.mcinv_burnin(hp, burn), hp)
+        mcinv._check(L.mcinv_sample(hp, samp), hp)
+        mcinv._check(L.mcinv_estimate(hp, mcinv.MCINV_EST_DIAG, None, ctypes.c_void_p(out_d.data_ptr()),
+                                      ctypes.c_void_p(se_d.data_ptr())), hp)
+        mcinv._check(L.mcinv_estimate(hp, mcinv.MCINV_EST_BLOCK, None, ctypes.c_void_p(out_b.data_ptr()),
+                                      ctypes.c_void_p(se_b.data_ptr())), hp)
+        L.mcinv_destroy(hp)
+
+    job()  # warm-up (allocator, module load)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_jobs):
+        job()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.e2e_jobs
+    return {"value": float(csr.nnz) * K * (burn + samp) / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "step": f"one job: create + {burn} burn-in + {samp} sampling cycles + diag and block readback",
+            "seconds_per_job": dt}
+
+
+def cpu_baseline(csr, K, seconds):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    `chains` chains (one OpenMP thread per chain group) for `cycles` cycles."""
+    import oracle
+    threads = os.cpu_count() or 1
+    chains = threads
+    t0 = time.perf_counter()
+    oracle.run(csr, chains, seed=0, ncycles=1, cpg=1, diag=False, threads=threads)
+    one = time.perf_counter() - t0
+    cycles = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(csr, chains, seed=0, ncycles=cycles, cpg=1, diag=False, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": float(csr.nnz) * chains * cycles / dt, "unit": UNIT, "cores": threads,
+            "kind": "oracle", "sample": f"{chains} chains x {cycles} cycles of {WORKLOAD} (of K={K})",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 CPU oracle (there is no upstream code), one
+    bounded sample of the workload per step, on rank 0 only."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_cs_0412107_gb300 import workloads as wl
+    csr = wl.WORKLOADS[WORKLOAD].build()
+    threads = os.cpu_count() or 1
+    chains = threads
+    st = None
+    for k in range(args.warmup):
+        st, _, _ = oracle.run(csr, chains, seed=0, cycle0=k, ncycles=1, cpg=1, diag=False, threads=threads, state=st)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        st, _, _ = oracle.run(csr, chains, seed=0, cycle0=args.warmup + k, ncycles=1, cpg=1, diag=False,
+                              threads=threads, state=st)
+    dt = time.perf_counter() - t0
+    value = float(csr.nnz) * chains * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded pedigree-shaped matrix, Philox noise)",
+            "config": {"workload": WORKLOAD, "n": csr.n, "nnz": csr.nnz, "K": args.chains},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{chains} chains x 1 cycle per step of {WORKLOAD}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--acc", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--chains", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--burnin", type=int, default=20)
+    ap.add_argument("--W", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--e2e-burnin", type=int, default=500)
+    ap.add_argument("--e2e-samples", type=int, default=5000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_mine(args, world, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * mcinv.h -- C ABI of a GB300 (sm_103a) implementation of the correlated-chains
+ * (CC) Monte Carlo inverse of Garcia-Cortes & Cabrillo, "A Monte Carlo
+ * algorithm for efficient large matrix inversion".
+ *
+ * Method (Sec. 2): two vectors z and w are advanced by noisy Gauss-Seidel
+ * sweeps that share their noise phi,
+ *     Eq. 4:  z_i <- phi_i / sqrt(c_ii) - (1/c_ii)  sum_{j != i} c_ij  z_j
+ *     Eq. 5:  w_i <- phi_i / sqrt(c*_ii) - (1/c*_ii) sum_{j != i} c*_ji w_j
+ * with rows i ascending and in-place semantics (j < i sees the current
+ * cycle, j > i the previous one).  After burn-in, the average of z w^dagger
+ * estimates C^-1 (Eq. 1/C); its diagonal, a block of it, and tr(Q C^-1) for a
+ * diagonal Q (Eq. tr) are the estimates this library returns.
+ *
+ * Conventions for every function below
+ *  - Host pointers are plain host memory owned by the caller; the library
+ *    copies what it needs and never keeps a caller pointer after returning.
+ *  - Device memory is owned by the handle and freed by mcinv_destroy.
+ *  - All GPU work is ordered on the stream given in mcinv_options.stream
+ *    (NULL = the legacy default stream).  mcinv_burnin and mcinv_sample only
+ *    enqueue work; mcinv_estimate, mcinv_get_state and mcinv_sync wait for it.
+ *  - Every function returns an mcinv_status; nothing aborts or traps.  On
+ *    error, mcinv_last_error(h) describes it.  After any error the handle can
+ *    still be destroyed.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef MCINV_H
+#define MCINV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcinv_ctx *mcinv_t;
+
+typedef enum {
+    MCINV_OK = 0,
+    MCINV_E_ARG = 1,           /* invalid argument or malformed CSR */
+    MCINV_E_SINGULAR_DIAG = 2, /* a c_ii is missing, zero or non-finite (D must be
+                                  non-singular, Sec. 2.2) */
+    MCINV_E_DIVERGED = 3,      /* a chain went non-finite or beyond 1e30: the sweep
+                                  does not converge (sp(T) >= 1 or sp(S) >= 1, Sec. 2.2) */
+    MCINV_E_NOMEM = 4,         /* device memory could not be allocated */
+    MCINV_E_CUDA = 5,          /* a CUDA runtime error; see mcinv_last_error */
+    MCINV_E_TIMEOUT = 6,       /* a bounded device-side wait expired */
+    MCINV_E_STATE = 7,         /* call not valid in the handle's current state */
+    MCINV_E_UNSUPPORTED = 8    /* option not supported on this device/build */
+} mcinv_status;
+
+/* Value type of the host CSR given to mcinv_create. */
+typedef enum {
+    MCINV_REAL64 = 0,    /* val: double[nnz]; the sweep runs in FP32 */
+    MCINV_COMPLEX128 = 1 /* val: double[2*nnz] interleaved re,im; the sweep runs in complex64 */
+} mcinv_dtype;
+
+/* How the block estimate accumulates z w^dagger. */
+typedef enum {
+    MCINV_ACC_FP32_SIMT = 0, /* FP32 CUDA-core contraction after every cycle */
+    MCINV_ACC_BF16_TC = 1    /* BF16 operands on the tensor cores (tcgen05), FP32 accumulate,
+                                over a batch of cycles at once */
+} mcinv_acc;
+
+typedef enum {
+    MCINV_EST_BLOCK = 0, /* (C^-1)_{R[a], S[b]}: out [nR][nS] */
+    MCINV_EST_DIAG = 1,  /* (C^-1)_{ii}: out [n] */
+    MCINV_EST_TRACE = 2  /* tr(Q C^-1), Q = diag(q): out [1] */
+} mcinv_kind;
+
+typedef struct {
+    int64_t K;              /* chains advanced in lockstep (>= 1) */
+    uint64_t seed;          /* Philox key */
+    int64_t chain_base;     /* global id of chain 0 (disjoint ranges shard work across GPUs) */
+    uint32_t matrix_id;     /* Philox counter word 3; distinct per matrix in a batch */
+    int32_t groups;         /* SE replicates G for diag/trace (chain groups); 0 = 32 */
+    int32_t batch_cycles;   /* cycles per sweep launch / per block contraction; 0 = 8 */
+    int32_t acc;            /* mcinv_acc for the block estimate */
+    int32_t chains_per_cta; /* chain-slice width W (1,2,4,8,16,32); 0 = chosen by the library */
+    int32_t threads_per_cta;/* 0 = chosen by the library (multiple of 32, <= 1024) */
+    int32_t flags;          /* MCINV_F_* bits */
+    void *stream;           /* cudaStream_t; NULL = legacy default stream */
+    const int64_t *block_rows; /* R (row indices of C^-1), may be NULL when n_block_rows = 0 */
+    int64_t n_block_rows;
+    const int64_t *block_cols; /* S (column indices of C^-1) */
+    int64_t n_block_cols;
+} mcinv_options;
+
+#define MCINV_F_NO_DIAG 1 /* do not accumulate the diagonal (and trace) */
+
+/* Fill *opt with defaults (K = 1024, seed = 0, everything else automatic). */
+void mcinv_default_options(mcinv_options *opt);
+
+/*
+ * Create a sampler for the n x n sparse matrix C given in CSR form.
+ *   row_ptr : int64[n+1], row_ptr[0] = 0, non-decreasing.
+ *   col     : int32[nnz], strictly increasing within each row, in [0, n).
+ *   val     : see mcinv_dtype.  Every row must hold its diagonal entry.
+ * Validates the CSR on the host (MCINV_E_ARG), checks that D is non-singular
+ * (MCINV_E_SINGULAR_DIAG), builds C^dagger and the Gauss-Seidel dependency
+ * levels, uploads everything, and sets z = w = 0 for every chain (Algorithm 1,
+ * step 1).  The per-row reciprocals 1/c_ii, 1/sqrt(c_ii) and 1/conj(sqrt(c_ii))
+ * are formed on the GPU in FP64 and rounded once to the sweep precision.
+ * On success *out is a new handle; on failure *out = NULL.
+ */
+mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                          const double *val, mcinv_dtype dt, const mcinv_options *opt);
+
+/* Advance every chain `cycles` CC cycles (Eqs. 4, 5) without accumulating
+ * (burn-in, Algorithm 1 steps 1-5 with a fixed count).  cycles >= 0. */
+mcinv_status mcinv_burnin(mcinv_t h, int64_t cycles);
+
+/* Advance every chain `cycles` cycles and accumulate each cycle's z w^dagger
+ * into the diagonal / block estimates (Eq. 1/C; Algorithm 1 steps 6-9). */
+mcinv_status mcinv_sample(mcinv_t h, int64_t cycles);
+
+/*
+ * Wait for queued work and return the current estimate and its Monte Carlo
+ * standard error (Sec. 2.3) in FP64 host memory.
+ *   DIAG : out[n]; TRACE: out[1] with q_diag = double[n] (Q = diag(q)).
+ *   BLOCK: out[nR*nS] row-major over (R[a], S[b]).
+ *   Complex matrices return interleaved re,im (twice the length); se_out has
+ *   the same shape and holds the SE of the real and imaginary parts.
+ *   se_out may be NULL.  DIAG/TRACE SE comes from independent chain groups,
+ *   BLOCK SE from batch means over sampling batches.
+ * MCINV_E_STATE if nothing was sampled or the estimate was not configured;
+ * MCINV_E_DIVERGED if a chain diverged.
+ */
+mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double *q_diag, double *out,
+                            double *se_out);
+
+/* Wait for queued work; report MCINV_E_DIVERGED / CUDA errors raised since the last check. */
+mcinv_status mcinv_sync(mcinv_t h);
+
+/*
+ * Copy chains [chain0, chain0+nchains) of the current z and w to host memory
+ * as double [n][nchains] (complex: interleaved, [n][nchains][2]); *cycle gets
+ * the number of cycles run so far.  z, w, cycle may each be NULL.
+ */
+mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchains, double *z, double *w,
+                             int64_t *cycle);
+
+/* Overwrite all chains' z and w (same layout as mcinv_get_state with chain0 = 0,
+ * nchains = K) and set the cycle counter; accumulated estimates are cleared.
+ * Resuming from a saved state reproduces the uninterrupted run bit for bit. */
+mcinv_status mcinv_set_state(mcinv_t h, const double *z, const double *w, int64_t cycle);
+
+/* Clear the accumulated estimates (diagonal, trace, block) and the sample count. */
+mcinv_status mcinv_reset_estimates(mcinv_t h);
+
+typedef struct {
+    int64_t n, nnz, K;
+    int32_t is_complex;
+    int32_t chains_per_cta;  /* W */
+    int32_t threads_per_cta;
+    int32_t slices;          /* CTAs per sweep = ceil(K / W) */
+    int32_t groups;          /* G actually used (divides slices) */
+    int32_t levels;          /* Gauss-Seidel dependency levels of C and C^dagger */
+    int32_t batch_cycles;
+    int32_t acc;
+    int64_t cycle;           /* cycles run so far */
+    int64_t samples;         /* cycles accumulated so far */
+    int64_t block_batches;   /* batches folded into the block estimate */
+    int64_t kernel_launches; /* kernels this handle has launched */
+    int64_t device_bytes;    /* device memory held by the handle */
+} mcinv_info_t;
+
+mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info);
+
+/* Kernel classes for per-kernel timing. */
+typedef enum {
+    MCINV_KERNEL_NOISE = 0,    /* Philox noise plane */
+    MCINV_KERNEL_SWEEP = 1,    /* coupled sweep of Eqs. 4/5 (with fused diagonal partials) */
+    MCINV_KERNEL_BLOCK = 2,    /* block contraction z w^dagger (tensor-core or SIMT) */
+    MCINV_KERNEL_FOLD = 3,     /* FP64 folds of the diagonal / block batches */
+    MCINV_KERNEL_ESTIMATE = 4, /* mean / standard-error kernels */
+    MCINV_KERNEL_CLASSES = 5
+} mcinv_kernel;
+
+/*
+ * Per-kernel timing.  mcinv_profile(h, 1) starts bracketing every launch of
+ * the handle with CUDA events on its stream (and clears earlier totals);
+ * mcinv_profile(h, 0) stops.  mcinv_profile_read waits for the stream and
+ * returns, for one kernel class, the launches recorded and the summed
+ * event-to-event time in milliseconds.
+ */
+mcinv_status mcinv_profile(mcinv_t h, int enable);
+mcinv_status mcinv_profile_read(mcinv_t h, mcinv_kernel kernel, int64_t *launches, double *ms);
+
+/* Free everything the handle owns.  NULL is allowed. */
+void mcinv_destroy(mcinv_t h);
+
+/* Description of the last error on h (or of the last failed mcinv_create when
+ * h is NULL, per host thread).  Never NULL. */
+const char *mcinv_last_error(mcinv_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCINV_H */

@@ -1,0 +1,675 @@
+// context.cu -- the C ABI of include/mcinv.h: host-side set-up (CSR
+// validation, C^dagger, Gauss-Seidel dependency levels), device memory, and
+// the orchestration of the sweep / accumulation / estimate kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mcinv.h"
+#include "internal.h"
+#include "tc_gemm.h"
+
+using namespace mcinv;
+
+struct mcinv_ctx {
+    // problem and options
+    int64_t n = 0, nnz = 0, K = 0;
+    int cplx = 0;
+    int W = 0, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
+    uint64_t seed = 0;
+    int64_t chain_base = 0;
+    uint32_t matrix_id = 0;
+    cudaStream_t stream = nullptr;
+    int nlev = 0, nw = 0;
+    // device arrays
+    int *d_lev_ptr = nullptr, *d_perm = nullptr, *d_zptr = nullptr, *d_wptr = nullptr;
+    void *d_zent = nullptr, *d_went = nullptr, *d_cst = nullptr;
+    uint32_t *d_noise = nullptr;
+    void *d_z[2] = {nullptr, nullptr}, *d_w[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *d_diag_part = nullptr;
+    double *d_diag_acc = nullptr, *d_counts = nullptr;
+    std::vector<double> counts;
+    // block estimate
+    int64_t nR = 0, nS = 0;
+    int *d_R = nullptr, *d_S = nullptr, *d_rpos = nullptr, *d_spos = nullptr;
+    float *d_blk = nullptr;
+    double *d_bsum = nullptr, *d_bsq = nullptr;
+    uint16_t *d_zsh = nullptr, *d_wsh = nullptr;
+    long long ldsh = 0, kp = 0;
+    TcGemmPlan *gemm = nullptr;
+    // estimate scratch
+    double *d_mean = nullptr, *d_se = nullptr, *d_q = nullptr;
+    int *d_status = nullptr;
+    // counters
+    int64_t cycle = 0, samples = 0, block_batches = 0, block_cycles = 0, launches = 0;
+    int64_t bytes = 0;
+    // per-kernel timing (mcinv_profile)
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    int64_t prof_launches[MCINV_KERNEL_CLASSES] = {};
+    double prof_ms[MCINV_KERNEL_CLASSES] = {};
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static mcinv_status fail(mcinv_ctx *h, mcinv_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(h, call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? MCINV_E_NOMEM : MCINV_E_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static cudaError_t prof_begin(mcinv_ctx *h, int kind, cudaEvent_t *stop)
+{
+    *stop = nullptr;
+    if (!h->profiling) return cudaSuccess;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t a, b;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
+        h->ev_pool.emplace_back(a, b);
+        h->ev_kind.push_back(0);
+    }
+    h->ev_kind[h->ev_used] = kind;
+    *stop = h->ev_pool[h->ev_used].second;
+    return cudaEventRecord(h->ev_pool[h->ev_used++].first, h->stream);
+}
+
+// Launch one kernel through `call`, counting it and (when profiling) timing it.
+#define LAUNCH_K(h, kind, call)                                     \
+    do {                                                            \
+        cudaEvent_t stop_;                                          \
+        CUDA_TRY(h, prof_begin((h), (kind), &stop_));               \
+        CUDA_TRY(h, call);                                          \
+        (h)->launches++;                                            \
+        if (stop_) CUDA_TRY(h, cudaEventRecord(stop_, (h)->stream)); \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(mcinv_ctx *h, T **p, size_t count)
+{
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) { *p = nullptr; return e; }
+    h->allocs.push_back((void *)*p);
+    h->bytes += (int64_t)bytes;
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t upload(mcinv_ctx *h, T **p, const std::vector<T> &v)
+{
+    cudaError_t e = dalloc(h, p, v.size());
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream);
+}
+
+extern "C" void mcinv_default_options(mcinv_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->K = 1024;
+    opt->acc = MCINV_ACC_BF16_TC;
+}
+
+static int choose_W(int64_t K)
+{
+    // Chain-slice width: wide slices make each gathered row segment long
+    // (W x 4 or 8 bytes), narrow slices make more CTAs.  Aim for at least two
+    // slices per SM of a 152-SM part, with segments of at least 16 bytes.
+    int W = 32;
+    while (W > 4 && (K + W - 1) / W < 304) W /= 2;
+    while (W > 1 && W / 2 >= K) W /= 2;
+    return W;
+}
+
+extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr,
+                                     const int32_t *col, const double *val, mcinv_dtype dt,
+                                     const mcinv_options *opt_in)
+{
+    if (!out) return fail(nullptr, MCINV_E_ARG, "out is NULL");
+    *out = nullptr;
+    mcinv_options opt;
+    if (opt_in) opt = *opt_in;
+    else mcinv_default_options(&opt);
+    if (n <= 0 || n > (1LL << 30)) return fail(nullptr, MCINV_E_ARG, "n = %lld out of range", (long long)n);
+    if (!row_ptr || !col || !val) return fail(nullptr, MCINV_E_ARG, "NULL CSR array");
+    if (dt != MCINV_REAL64 && dt != MCINV_COMPLEX128) return fail(nullptr, MCINV_E_ARG, "bad dtype");
+    if (opt.K < 1 || opt.K > (1LL << 24)) return fail(nullptr, MCINV_E_ARG, "K = %lld out of range", (long long)opt.K);
+    if (row_ptr[0] != 0) return fail(nullptr, MCINV_E_ARG, "row_ptr[0] != 0");
+    const int64_t nnz = row_ptr[n];
+    if (nnz < n || nnz > (1LL << 31) - 1) return fail(nullptr, MCINV_E_ARG, "nnz = %lld out of range", (long long)nnz);
+    if ((double)n * (double)opt.K > 4.0e9) return fail(nullptr, MCINV_E_ARG, "n*K too large");
+    const int cplx = dt == MCINV_COMPLEX128;
+    const int NV = cplx ? 2 : 1;
+
+    // ---- host validation: sorted unique columns in range, diagonal present and usable
+    std::vector<double> diag((size_t)n * NV);
+    for (int64_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, MCINV_E_ARG, "row_ptr decreases at row %lld", (long long)i);
+        bool has_diag = false;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int64_t j = col[e];
+            if (j < 0 || j >= n) return fail(nullptr, MCINV_E_ARG, "column %lld out of range in row %lld", (long long)j, (long long)i);
+            if (e > row_ptr[i] && col[e - 1] >= j) return fail(nullptr, MCINV_E_ARG, "columns not strictly increasing in row %lld", (long long)i);
+            for (int v = 0; v < NV; ++v)
+                if (!std::isfinite(val[e * NV + v])) return fail(nullptr, MCINV_E_ARG, "non-finite value in row %lld", (long long)i);
+            if (j == i) {
+                has_diag = true;
+                for (int v = 0; v < NV; ++v) diag[(size_t)i * NV + v] = val[e * NV + v];
+            }
+        }
+        bool zero = true;
+        for (int v = 0; v < NV; ++v) zero &= diag[(size_t)i * NV + v] == 0.0;
+        if (!has_diag || zero)
+            return fail(nullptr, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %lld is %s", (long long)i, has_diag ? "zero" : "missing");
+    }
+
+    mcinv_ctx *h = new (std::nothrow) mcinv_ctx;
+    if (!h) return fail(nullptr, MCINV_E_NOMEM, "host allocation failed");
+    h->n = n; h->nnz = nnz; h->K = opt.K; h->cplx = cplx;
+    h->seed = opt.seed; h->chain_base = opt.chain_base; h->matrix_id = opt.matrix_id;
+    h->stream = (cudaStream_t)opt.stream;
+    h->flags = opt.flags;
+    h->acc = opt.acc;
+    h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
+    h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : choose_W(opt.K);
+    if (h->W != 1 && h->W != 2 && h->W != 4 && h->W != 8 && h->W != 16 && h->W != 32) {
+        delete h;
+        return fail(nullptr, MCINV_E_ARG, "chains_per_cta must be 1,2,4,8,16 or 32");
+    }
+    h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 256;
+    if (h->threads % 32 || h->threads > 1024) {
+        delete h;
+        return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 1024");
+    }
+    h->slices = (int)((opt.K + h->W - 1) / h->W);
+    const int Greq = opt.groups > 0 ? opt.groups : 32;
+    h->G = 1;
+    for (int g = std::min(Greq, h->slices); g >= 1; --g)
+        if (h->slices % g == 0) { h->G = g; break; }
+    h->counts.assign(h->G, 0.0);
+    for (int s = 0; s < h->slices; ++s)
+        h->counts[s / (h->slices / h->G)] += (double)std::min<int64_t>(h->W, opt.K - (int64_t)s * h->W);
+    h->nw = (int)((opt.K + 31) / 32);
+    mcinv_t H = h;
+    auto bail = [&](mcinv_status st) {
+        std::string msg = h->err;
+        mcinv_destroy(H);
+        g_create_error = msg;
+        return st;
+    };
+
+    // ---- C^dagger rows: (C^H)_{j,i} = conj(c_ij), off-diagonal only, columns ascending
+    std::vector<int64_t> wcount(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] != i) wcount[col[e] + 1]++;
+    for (int64_t j = 0; j < n; ++j) wcount[j + 1] += wcount[j];
+    std::vector<int32_t> wcol(wcount[n]);
+    std::vector<double> wval((size_t)wcount[n] * NV);
+    {
+        std::vector<int64_t> fill(wcount.begin(), wcount.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int64_t j = col[e];
+                if (j == i) continue;
+                const int64_t p = fill[j]++;
+                wcol[p] = (int32_t)i;
+                wval[p * NV] = val[e * NV];
+                if (cplx) wval[p * NV + 1] = -val[e * NV + 1];
+            }
+    }
+
+    // ---- dependency levels: row i waits for every j < i it reads this cycle
+    //      through C (Eq. 4) or C^dagger (Eq. 5)
+    std::vector<int32_t> level(n, 0);
+    int nlev = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int lv = 0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1] && col[e] < i; ++e) lv = std::max(lv, level[col[e]] + 1);
+        for (int64_t e = wcount[i]; e < wcount[i + 1] && wcol[e] < i; ++e) lv = std::max(lv, level[wcol[e]] + 1);
+        level[i] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    h->nlev = nlev;
+    std::vector<int32_t> lev_ptr(nlev + 1, 0), perm(n);
+    for (int64_t i = 0; i < n; ++i) lev_ptr[level[i] + 1]++;
+    for (int l = 0; l < nlev; ++l) lev_ptr[l + 1] += lev_ptr[l];
+    {
+        std::vector<int32_t> fill(lev_ptr.begin(), lev_ptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i) perm[fill[level[i]]++] = (int32_t)i;
+    }
+
+    // ---- pack rows by position
+    std::vector<int32_t> zptr(n + 1, 0), wptr(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t i = perm[p];
+        zptr[p + 1] = zptr[p] + (int32_t)(row_ptr[i + 1] - row_ptr[i] - 1);
+        wptr[p + 1] = wptr[p] + (int32_t)(wcount[i + 1] - wcount[i]);
+    }
+    std::vector<double> diag_pos((size_t)n * NV);
+    for (int64_t p = 0; p < n; ++p)
+        for (int v = 0; v < NV; ++v) diag_pos[(size_t)p * NV + v] = diag[(size_t)perm[p] * NV + v];
+    cudaError_t ce = cudaSuccess;
+    if (!cplx) {
+        std::vector<EntR> ze(zptr[n]), we(wptr[n]);
+        for (int64_t p = 0; p < n; ++p) {
+            const int64_t i = perm[p];
+            int64_t q = zptr[p];
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] != i) ze[q++] = EntR{col[e], (float)val[e]};
+            q = wptr[p];
+            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) we[q++] = EntR{wcol[e], (float)wval[e]};
+        }
+        if ((ce = upload(h, (EntR **)&h->d_zent, ze)) != cudaSuccess || (ce = upload(h, (EntR **)&h->d_went, we)) != cudaSuccess) {
+            fail(h, MCINV_E_NOMEM, "upload: %s", cudaGetErrorString(ce));
+            return bail(MCINV_E_NOMEM);
+        }
+        ce = cudaStreamSynchronize(h->stream);
+    } else {
+        std::vector<EntC> ze(zptr[n]), we(wptr[n]);
+        for (int64_t p = 0; p < n; ++p) {
+            const int64_t i = perm[p];
+            int64_t q = zptr[p];
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] != i) ze[q++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
+            q = wptr[p];
+            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e)
+                we[q++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
+        }
+        if ((ce = upload(h, (EntC **)&h->d_zent, ze)) != cudaSuccess || (ce = upload(h, (EntC **)&h->d_went, we)) != cudaSuccess) {
+            fail(h, MCINV_E_NOMEM, "upload: %s", cudaGetErrorString(ce));
+            return bail(MCINV_E_NOMEM);
+        }
+        ce = cudaStreamSynchronize(h->stream);  // host vectors die at scope exit
+    }
+    if (ce != cudaSuccess) { fail(h, MCINV_E_CUDA, "upload: %s", cudaGetErrorString(ce)); return bail(MCINV_E_CUDA); }
+
+    double *d_diag = nullptr;
+    std::vector<int32_t> bad_init(1, 0x7fffffff);
+    int *d_bad = nullptr;
+#define SETUP(call)                                                                               \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            mcinv_status st_ = e_ == cudaErrorMemoryAllocation ? MCINV_E_NOMEM : MCINV_E_CUDA;    \
+            fail(h, st_, "%s: %s", #call, cudaGetErrorString(e_));                                \
+            return bail(st_);                                                                     \
+        }                                                                                         \
+    } while (0)
+    SETUP(upload(h, &h->d_lev_ptr, lev_ptr));
+    SETUP(upload(h, &h->d_perm, perm));
+    SETUP(upload(h, &h->d_zptr, zptr));
+    SETUP(upload(h, &h->d_wptr, wptr));
+    SETUP(upload(h, &d_diag, diag_pos));
+    SETUP(upload(h, &d_bad, bad_init));
+    SETUP(dalloc(h, (char **)&h->d_cst, (size_t)n * (cplx ? sizeof(CstC) : sizeof(CstR))));
+    SETUP(launch_constants((int)n, d_diag, cplx, h->d_cst, d_bad, h->stream));
+    h->launches++;
+    int bad = 0x7fffffff;
+    SETUP(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SETUP(cudaStreamSynchronize(h->stream));
+    if (bad != 0x7fffffff) {
+        fail(h, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %d is not usable", perm[bad]);
+        return bail(MCINV_E_SINGULAR_DIAG);
+    }
+
+    // ---- chain state (Algorithm 1 step 1: z = w = 0), noise plane, accumulators
+    const size_t esz = cplx ? 8 : 4;
+    const size_t state = (size_t)n * (size_t)opt.K;
+    for (int b = 0; b < 2; ++b) {
+        SETUP(dalloc(h, (char **)&h->d_z[b], state * esz));
+        SETUP(dalloc(h, (char **)&h->d_w[b], state * esz));
+        SETUP(cudaMemsetAsync(h->d_z[b], 0, state * esz, h->stream));
+        SETUP(cudaMemsetAsync(h->d_w[b], 0, state * esz, h->stream));
+    }
+    SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
+    SETUP(dalloc(h, &h->d_status, 1));
+    SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    if (!(h->flags & MCINV_F_NO_DIAG)) {
+        SETUP(dalloc(h, (char **)&h->d_diag_part, (size_t)h->slices * n * esz));
+        SETUP(cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->slices * n * esz, h->stream));
+        SETUP(dalloc(h, &h->d_diag_acc, (size_t)h->G * n * NV));
+        SETUP(cudaMemsetAsync(h->d_diag_acc, 0, (size_t)h->G * n * NV * sizeof(double), h->stream));
+        SETUP(upload(h, &h->d_counts, h->counts));
+        SETUP(dalloc(h, &h->d_q, (size_t)n));
+    }
+    size_t est_elems = std::max<size_t>((size_t)n, 2);  // the trace writes mean and SE
+
+    // ---- block estimate
+    if (opt.n_block_rows > 0 && opt.n_block_cols > 0) {
+        if (!opt.block_rows || !opt.block_cols) { fail(h, MCINV_E_ARG, "block index arrays are NULL"); return bail(MCINV_E_ARG); }
+        h->nR = opt.n_block_rows; h->nS = opt.n_block_cols;
+        std::vector<int32_t> R(h->nR), S(h->nS), rpos(n, -1), spos(n, -1);
+        for (int64_t a = 0; a < h->nR; ++a) {
+            if (opt.block_rows[a] < 0 || opt.block_rows[a] >= n) { fail(h, MCINV_E_ARG, "block row out of range"); return bail(MCINV_E_ARG); }
+            R[a] = (int32_t)opt.block_rows[a];
+            if (rpos[R[a]] >= 0) { fail(h, MCINV_E_ARG, "repeated block row %d", R[a]); return bail(MCINV_E_ARG); }
+            rpos[R[a]] = (int32_t)a;
+        }
+        for (int64_t b = 0; b < h->nS; ++b) {
+            if (opt.block_cols[b] < 0 || opt.block_cols[b] >= n) { fail(h, MCINV_E_ARG, "block column out of range"); return bail(MCINV_E_ARG); }
+            S[b] = (int32_t)opt.block_cols[b];
+            if (spos[S[b]] >= 0) { fail(h, MCINV_E_ARG, "repeated block column %d", S[b]); return bail(MCINV_E_ARG); }
+            spos[S[b]] = (int32_t)b;
+        }
+        const size_t elems = (size_t)h->nR * h->nS;
+        est_elems = std::max(est_elems, elems);
+        SETUP(upload(h, &h->d_R, R));
+        SETUP(upload(h, &h->d_S, S));
+        SETUP(dalloc(h, &h->d_blk, elems * NV));
+        SETUP(cudaMemsetAsync(h->d_blk, 0, elems * NV * sizeof(float), h->stream));
+        SETUP(dalloc(h, &h->d_bsum, elems * NV));
+        SETUP(dalloc(h, &h->d_bsq, elems * NV));
+        SETUP(cudaMemsetAsync(h->d_bsum, 0, elems * NV * sizeof(double), h->stream));
+        SETUP(cudaMemsetAsync(h->d_bsq, 0, elems * NV * sizeof(double), h->stream));
+        if (h->acc == MCINV_ACC_BF16_TC) {
+            SETUP(upload(h, &h->d_rpos, rpos));
+            SETUP(upload(h, &h->d_spos, spos));
+            // shadow rows hold B cycle blocks of K chains (x2 for re,im), each block
+            // padded to 64 elements with zeros
+            h->kp = (opt.K * NV + 63) / 64 * 64;
+            h->ldsh = (long long)h->B * h->kp;
+            const size_t zrows = (size_t)((h->nR + 127) / 128 * 128);
+            const size_t wrows = (size_t)(((h->nS * NV) + 255) / 256 * 256);
+            SETUP(dalloc(h, &h->d_zsh, zrows * (size_t)h->ldsh));
+            SETUP(dalloc(h, &h->d_wsh, wrows * (size_t)h->ldsh));
+            SETUP(cudaMemsetAsync(h->d_zsh, 0, zrows * (size_t)h->ldsh * 2, h->stream));
+            SETUP(cudaMemsetAsync(h->d_wsh, 0, wrows * (size_t)h->ldsh * 2, h->stream));
+            std::string why;
+            h->gemm = tc_gemm_plan_create(h->d_zsh, zrows, h->d_wsh, wrows, h->ldsh, h->d_blk,
+                                          h->nR, h->nS * NV, &why);
+            if (!h->gemm) { fail(h, MCINV_E_UNSUPPORTED, "tensor-core block contraction: %s", why.c_str()); return bail(MCINV_E_UNSUPPORTED); }
+        } else if (h->acc != MCINV_ACC_FP32_SIMT) {
+            fail(h, MCINV_E_ARG, "unknown accumulation mode %d", h->acc);
+            return bail(MCINV_E_ARG);
+        }
+    }
+    SETUP(dalloc(h, &h->d_mean, est_elems * NV));
+    SETUP(dalloc(h, &h->d_se, est_elems * NV));
+    SETUP(cudaStreamSynchronize(h->stream));
+    *out = h;
+    return MCINV_OK;
+#undef SETUP
+}
+
+static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumulate, int cyc0_in_batch)
+{
+    SweepArgs a{};
+    a.n = (int)h->n; a.K = (int)h->K; a.nlev = h->nlev; a.nw = h->nw;
+    a.lev_ptr = h->d_lev_ptr; a.perm = h->d_perm;
+    a.zptr = h->d_zptr; a.zent = h->d_zent; a.wptr = h->d_wptr; a.went = h->d_went;
+    a.cst = h->d_cst;
+    a.noise = h->d_noise + (size_t)noise_cyc * h->nw * (size_t)h->n;
+    a.z[0] = h->d_z[0]; a.z[1] = h->d_z[1]; a.w[0] = h->d_w[0]; a.w[1] = h->d_w[1];
+    a.cur = h->cur; a.ncyc = ncyc;
+    a.diag_part = accumulate ? h->d_diag_part : nullptr;
+    if (accumulate && h->gemm) {
+        a.rpos = h->d_rpos; a.spos = h->d_spos;
+        a.zsh = h->d_zsh; a.wsh = h->d_wsh; a.ldsh = h->ldsh; a.kp = h->kp;
+        a.cyc0_in_batch = cyc0_in_batch;
+    }
+    a.status = h->d_status;
+    return a;
+}
+
+static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
+{
+    const bool block = accumulate && h->nR > 0;
+    while (cycles > 0) {
+        const int b = (int)std::min<int64_t>(h->B, cycles);
+        LAUNCH_K(h, MCINV_KERNEL_NOISE, launch_noise(h->seed, h->matrix_id, (uint64_t)h->chain_base, (int)h->K, (int)h->n,
+                               (uint32_t)h->cycle, b, h->d_noise, h->stream));
+        if (block && h->acc == MCINV_ACC_FP32_SIMT) {
+            for (int k = 0; k < b; ++k) {
+                SweepArgs a = sweep_args(h, 1, k, true, 0);
+                LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->W, h->slices, h->threads, h->stream));
+                h->cur ^= 1;
+                LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
+                                            (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
+            }
+        } else {
+            SweepArgs a = sweep_args(h, b, 0, accumulate, 0);
+            LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->W, h->slices, h->threads, h->stream));
+            if (b & 1) h->cur ^= 1;
+            if (block) {
+                const long long inner = (long long)b * h->kp;
+                LAUNCH_K(h, MCINV_KERNEL_BLOCK, tc_gemm_run(h->gemm, inner, h->stream));
+            }
+        }
+        if (block) {
+            const double Kd = (double)h->K;
+            LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_block_fold(h->cplx, (long long)h->nR * h->nS, 1.0 / (Kd * Kd * b), h->d_blk,
+                                        h->d_bsum, h->d_bsq, h->acc == MCINV_ACC_FP32_SIMT, h->stream));
+            h->block_batches++;
+            h->block_cycles += b;
+        }
+        if (accumulate && h->d_diag_part) {
+            LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_diag_fold(h->cplx, (int)h->n, h->slices, h->G, h->d_diag_part, h->d_diag_acc, h->stream));
+        }
+        h->cycle += b;
+        if (accumulate) h->samples += b;
+        cycles -= b;
+    }
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_burnin(mcinv_t h, int64_t cycles)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (cycles < 0) return fail(h, MCINV_E_ARG, "cycles < 0");
+    return run_cycles(h, cycles, false);
+}
+
+extern "C" mcinv_status mcinv_sample(mcinv_t h, int64_t cycles)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (cycles < 0) return fail(h, MCINV_E_ARG, "cycles < 0");
+    return run_cycles(h, cycles, true);
+}
+
+extern "C" mcinv_status mcinv_sync(mcinv_t h)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    int status = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (status & 1) return fail(h, MCINV_E_DIVERGED, "a chain diverged (non-finite or |value| > 1e30): the sweep does not converge for this matrix");
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double *q, double *out, double *se_out)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (!out) return fail(h, MCINV_E_ARG, "out is NULL");
+    mcinv_status st = mcinv_sync(h);
+    if (st != MCINV_OK) return st;
+    const int NV = h->cplx ? 2 : 1;
+    size_t count = 0;
+    if (kind == MCINV_EST_DIAG || kind == MCINV_EST_TRACE) {
+        if (!h->d_diag_acc) return fail(h, MCINV_E_STATE, "diagonal accumulation was disabled");
+        if (h->samples == 0) return fail(h, MCINV_E_STATE, "no cycles sampled yet");
+        if (kind == MCINV_EST_DIAG) {
+            LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_diag_estimate(h->cplx, (int)h->n, h->G, h->d_counts, (double)h->samples,
+                                           h->d_diag_acc, h->d_mean, h->d_se, h->stream));
+            count = (size_t)h->n * NV;
+            CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_se, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            if (!q) return fail(h, MCINV_E_ARG, "q_diag is NULL");
+            CUDA_TRY(h, cudaMemcpyAsync(h->d_q, q, (size_t)h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_trace_estimate(h->cplx, (int)h->n, h->G, h->d_counts, (double)h->samples,
+                                            h->d_diag_acc, h->d_q, h->d_mean, h->stream));
+            CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_mean + NV, NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        }
+    } else if (kind == MCINV_EST_BLOCK) {
+        if (h->nR == 0) return fail(h, MCINV_E_STATE, "no block was configured");
+        if (h->block_batches == 0) return fail(h, MCINV_E_STATE, "no cycles sampled yet");
+        const long long elems = (long long)h->nR * h->nS;
+        LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_block_estimate(h->cplx, elems, (double)h->K, (double)h->block_cycles,
+                                        (double)h->block_batches, h->d_bsum, h->d_bsq, h->d_mean, h->d_se, h->stream));
+        count = (size_t)elems * NV;
+        CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_se, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        return fail(h, MCINV_E_ARG, "unknown estimate kind %d", (int)kind);
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchains, double *z, double *w, int64_t *cycle)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (chain0 < 0 || nchains < 0 || chain0 + nchains > h->K) return fail(h, MCINV_E_ARG, "chain range out of bounds");
+    mcinv_status st = mcinv_sync(h);
+    if (st != MCINV_OK && st != MCINV_E_DIVERGED) return st;
+    const int NV = h->cplx ? 2 : 1;
+    const size_t esz = NV * sizeof(float);
+    std::vector<float> tmp((size_t)h->n * nchains * NV);
+    double *dst[2] = {z, w};
+    void *src[2] = {h->d_z[h->cur], h->d_w[h->cur]};
+    for (int v = 0; v < 2; ++v) {
+        if (!dst[v] || nchains == 0) continue;
+        CUDA_TRY(h, cudaMemcpy2DAsync(tmp.data(), nchains * esz, (char *)src[v] + chain0 * esz, h->K * esz,
+                                      nchains * esz, h->n, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        for (size_t k = 0; k < tmp.size(); ++k) dst[v][k] = (double)tmp[k];
+    }
+    if (cycle) *cycle = h->cycle;
+    return st;
+}
+
+extern "C" mcinv_status mcinv_reset_estimates(mcinv_t h)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    const int NV = h->cplx ? 2 : 1;
+    const size_t esz = NV * sizeof(float);
+    if (h->d_diag_part) {
+        CUDA_TRY(h, cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->slices * h->n * esz, h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_diag_acc, 0, (size_t)h->G * h->n * NV * sizeof(double), h->stream));
+    }
+    if (h->nR) {
+        const size_t elems = (size_t)h->nR * h->nS * NV;
+        CUDA_TRY(h, cudaMemsetAsync(h->d_blk, 0, elems * sizeof(float), h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_bsum, 0, elems * sizeof(double), h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_bsq, 0, elems * sizeof(double), h->stream));
+    }
+    h->samples = 0;
+    h->block_batches = 0;
+    h->block_cycles = 0;
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_set_state(mcinv_t h, const double *z, const double *w, int64_t cycle)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (!z || !w || cycle < 0) return fail(h, MCINV_E_ARG, "bad state arguments");
+    mcinv_status st = mcinv_sync(h);
+    if (st != MCINV_OK && st != MCINV_E_DIVERGED) return st;
+    const int NV = h->cplx ? 2 : 1;
+    const size_t count = (size_t)h->n * h->K * NV;
+    std::vector<float> tmp(count);
+    const double *srcs[2] = {z, w};
+    void *dsts[2] = {h->d_z[h->cur], h->d_w[h->cur]};
+    for (int v = 0; v < 2; ++v) {
+        for (size_t k = 0; k < count; ++k) tmp[k] = (float)srcs[v][k];
+        CUDA_TRY(h, cudaMemcpyAsync(dsts[v], tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    h->cycle = cycle;
+    return mcinv_reset_estimates(h);
+}
+
+extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
+{
+    if (!h || !info) return fail(h, MCINV_E_ARG, "NULL argument");
+    info->n = h->n; info->nnz = h->nnz; info->K = h->K;
+    info->is_complex = h->cplx; info->chains_per_cta = h->W; info->threads_per_cta = h->threads;
+    info->slices = h->slices; info->groups = h->G; info->levels = h->nlev;
+    info->batch_cycles = h->B; info->acc = h->acc;
+    info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
+    info->kernel_launches = h->launches; info->device_bytes = h->bytes;
+    return MCINV_OK;
+}
+
+static mcinv_status prof_collect(mcinv_ctx *h)
+{
+    if (h->ev_used == 0) return MCINV_OK;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k < h->ev_used; ++k) {
+        float ms = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev_pool[k].first, h->ev_pool[k].second));
+        h->prof_ms[h->ev_kind[k]] += ms;
+        h->prof_launches[h->ev_kind[k]]++;
+    }
+    h->ev_used = 0;
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_profile(mcinv_t h, int enable)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    mcinv_status st = prof_collect(h);
+    if (st != MCINV_OK) return st;
+    if (enable) {
+        for (int k = 0; k < MCINV_KERNEL_CLASSES; ++k) { h->prof_ms[k] = 0.0; h->prof_launches[k] = 0; }
+    }
+    h->profiling = enable != 0;
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_profile_read(mcinv_t h, mcinv_kernel kernel, int64_t *launches, double *ms)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if ((int)kernel < 0 || (int)kernel >= MCINV_KERNEL_CLASSES) return fail(h, MCINV_E_ARG, "bad kernel class");
+    mcinv_status st = prof_collect(h);
+    if (st != MCINV_OK) return st;
+    if (launches) *launches = h->prof_launches[kernel];
+    if (ms) *ms = h->prof_ms[kernel];
+    return MCINV_OK;
+}
+
+extern "C" void mcinv_destroy(mcinv_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &e : h->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    if (h->gemm) tc_gemm_plan_destroy(h->gemm);
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+extern "C" const char *mcinv_last_error(mcinv_t h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}

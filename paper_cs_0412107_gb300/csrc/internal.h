@@ -1,0 +1,80 @@
+// internal.h -- declarations shared by the translation units of libmcinv.
+// Not part of the public ABI (that is include/mcinv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcinv {
+
+// One off-diagonal CSR entry as the sweep reads it: a single aligned load.
+struct EntR {
+    int col;
+    float val;
+};
+struct __align__(16) EntC {
+    int col;
+    float re, im;
+    int pad;
+};
+
+// Per-row constants of Eqs. 4/5 in the sweep precision (formed in FP64).
+struct __align__(16) CstR {
+    float alpha, beta, inv_d, pad;  // 1/sqrt(c_ii), 1/conj(sqrt(c_ii)), 1/c_ii
+};
+struct __align__(16) CstC {
+    float2 alpha, beta, inv_d, pad;
+};
+
+// Arguments of the coupled sweep.  Rows are visited in "positions": the rows
+// of Gauss-Seidel dependency level 0, then level 1, ...; within a level rows
+// are independent (no row depends on another row of its level through C or
+// C^dagger), so a CTA may update them concurrently and get exactly the
+// in-place ascending-row result of Eqs. 4/5.
+struct SweepArgs {
+    int n, K, nlev, nw;        // nw = ceil(K/32) noise words per row
+    const int *lev_ptr;        // [nlev+1] positions
+    const int *perm;           // [n] row at position p
+    const int *zptr;           // [n+1] by position: off-diagonal entries of row perm[p] of C
+    const void *zent;          // EntR / EntC
+    const int *wptr;           // [n+1] by position: off-diagonal entries of row perm[p] of C^dagger
+    const void *went;
+    const void *cst;           // [n] by position: CstR / CstC
+    const uint32_t *noise;     // [ncyc][nw][n] Z2 sign bits (bit c%32 of word c/32), 1 -> phi = -1
+    void *z[2], *w[2];         // double-buffered chain state [n][K] (float / float2)
+    int cur;                   // buffer holding the state before the first cycle of this launch
+    int ncyc;                  // cycles this launch runs
+    void *diag_part;           // [slices][n] running sum of z_i conj(w_i) over the slice's chains, or null
+    // BF16 shadows of rows in R (z) and S (w) for the tensor-core block contraction
+    const int *rpos, *spos;    // [n] -> index in R / S, or -1; null disables shadows
+    uint16_t *zsh, *wsh;
+    long long ldsh;            // elements per shadow row (batch_cycles * kp)
+    long long kp;              // elements per cycle block: K (x2 complex) rounded up to 64
+    int cyc0_in_batch;         // shadow column block of this launch's first cycle
+    int *status;               // bit 0: a chain diverged
+};
+
+// Launchers (sweep.cu)
+cudaError_t launch_noise(uint64_t seed, uint32_t matrix, uint64_t chain_base, int K, int n,
+                         uint32_t cycle0, int ncyc, uint32_t *out, cudaStream_t s);
+cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int *bad,
+                             cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs &a, int cplx, int W, int slices, int threads,
+                         cudaStream_t s);
+
+// accumulate.cu
+cudaError_t launch_diag_fold(int cplx, int n, int slices, int G, void *diag_part, double *acc,
+                             cudaStream_t s);
+cudaError_t launch_block_simt(int cplx, int K, const void *z, const void *w, const int *R, int nR,
+                              const int *S, int nS, float *blk, cudaStream_t s);
+cudaError_t launch_block_fold(int cplx, long long elems, double scale_sq, float *blk,
+                              double *sum, double *sq, int zero_blk, cudaStream_t s);
+cudaError_t launch_diag_estimate(int cplx, int n, int G, const double *counts, double samples,
+                                 const double *acc, double *mean, double *se, cudaStream_t s);
+cudaError_t launch_trace_estimate(int cplx, int n, int G, const double *counts, double samples,
+                                  const double *acc, const double *q, double *out, cudaStream_t s);
+cudaError_t launch_block_estimate(int cplx, long long elems, double K, double T, double nb,
+                                  const double *sum, const double *sq, double *mean, double *se,
+                                  cudaStream_t s);
+
+}  // namespace mcinv

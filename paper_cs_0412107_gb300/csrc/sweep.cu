@@ -1,0 +1,334 @@
+// sweep.cu -- the hot path of the correlated-chains sampler on sm_103a:
+//   * the Z2 noise plane (Philox4x32-10, Eqs. 5a/5b),
+//   * the per-row constants of Eqs. 4/5 formed in FP64,
+//   * the coupled noisy Gauss-Seidel sweep of Eqs. 4 and 5 for a slice of
+//     chains per CTA, with the z_i conj(w_i) diagonal partials (Eq. 1/C)
+//     and the BF16 shadows for the tensor-core block contraction fused in.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace mcinv {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
+// multiplies words 0 and 2 by two fixed odd constants, swaps the high halves
+// across (xored with the other words and the round key), and the key is
+// advanced by a Weyl sequence between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k)
+{
+    const uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    const uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kMul0, x.x), lo0 = kMul0 * x.x;
+        const uint32_t hi1 = __umulhi(kMul1, x.z), lo1 = kMul1 * x.z;
+        x = make_uint4(hi1 ^ x.y ^ k.x, lo1, hi0 ^ x.w ^ k.y, lo0);
+        k.x += kWeyl0;
+        k.y += kWeyl1;
+    }
+    return x;
+}
+
+// Noise plane for cycles cycle0 .. cycle0+ncyc-1: out[cyc][cw][row] holds the
+// sign bits of chains 32cw .. 32cw+31 at `row`.  One Philox call yields the
+// 128 bits of rows 128rb .. 128rb+127 of one chain (row r -> bit r%32 of word
+// (r/32)%4); a warp of 32 chains transposes them with ballots so every word
+// is written once, coalesced along rows.
+__global__ void __launch_bounds__(128) noise_kernel(uint64_t seed, uint32_t matrix,
+                                                    uint64_t chain_base, int K, int n, int nw,
+                                                    uint32_t cycle0, uint32_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int cw = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (cw >= nw) return;  // whole warp
+    const int rb = blockIdx.x, cyc = blockIdx.z;
+    const int chain = cw * 32 + lane;
+    const uint4 r = philox4x32_10(
+        make_uint4((uint32_t)rb, (uint32_t)(chain_base + (uint64_t)chain), cycle0 + (uint32_t)cyc, matrix),
+        make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)));
+    const bool valid = chain < K;
+    const uint32_t xs[4] = {r.x, r.y, r.z, r.w};
+    uint32_t *dst = out + ((size_t)cyc * nw + cw) * (size_t)n;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t mine = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, valid && ((xs[q] >> b) & 1u));
+            if (lane == b) mine = bal;
+        }
+        const int row = rb * 128 + q * 32 + lane;
+        if (row < n) dst[row] = mine;
+    }
+}
+
+cudaError_t launch_noise(uint64_t seed, uint32_t matrix, uint64_t chain_base, int K, int n,
+                         uint32_t cycle0, int ncyc, uint32_t *out, cudaStream_t s)
+{
+    const int nw = (K + 31) / 32;
+    dim3 grid((n + 127) / 128, (nw + 3) / 4, ncyc);
+    noise_kernel<<<grid, 128, 0, s>>>(seed, matrix, chain_base, K, n, nw, cycle0, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-row constants in FP64: inv_d = 1/c_ii, alpha = 1/sqrt(c_ii),
+// beta = 1/conj(sqrt(c_ii)) (Eq. 5's 1/sqrt(c*_ii) read so that
+// alpha conj(beta) = 1/c_ii).  Real storage with c_ii < 0 keeps real
+// arithmetic: alpha = 1/sqrt|c|, beta = -1/sqrt|c|.
+// ---------------------------------------------------------------------------
+__device__ inline double2 crecip64(double a, double b)
+{
+    // 1/(a+ib) with the operands scaled by max(|a|,|b|) to avoid overflow
+    const double m = fmax(fabs(a), fabs(b));
+    const double x = a / m, y = b / m;
+    const double den = m * (x * x + y * y);
+    return make_double2(x / den, -y / den);
+}
+
+__device__ inline double2 csqrt64(double a, double b)
+{
+    // principal square root: the result has a non-negative real part, and the
+    // sign of its imaginary part follows the sign of b (including -0)
+    const double r = hypot(a, b);
+    if (r == 0.0) return make_double2(0.0, b);
+    if (a >= 0.0) {
+        const double t = sqrt(0.5 * (r + a));
+        return make_double2(t, b / (2.0 * t));
+    }
+    const double t = sqrt(0.5 * (r - a));
+    return make_double2(fabs(b) / (2.0 * t), copysign(t, b));
+}
+
+__global__ void constants_kernel(int n, const double *__restrict__ diag, int cplx, void *cst,
+                                 int *bad)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (!cplx) {
+        const double c = diag[p];
+        if (!(c != 0.0) || !isfinite(c)) { atomicMin(bad, p); return; }
+        const double r = sqrt(fabs(c));
+        CstR k;
+        k.alpha = (float)(1.0 / r);
+        k.beta = (float)((c > 0.0 ? 1.0 : -1.0) / r);
+        k.inv_d = (float)(1.0 / c);
+        k.pad = 0.f;
+        ((CstR *)cst)[p] = k;
+    } else {
+        const double a = diag[2 * p], b = diag[2 * p + 1];
+        if (!isfinite(a) || !isfinite(b) || (a == 0.0 && b == 0.0)) { atomicMin(bad, p); return; }
+        const double2 s = csqrt64(a, b);
+        const double2 al = crecip64(s.x, s.y);
+        const double2 be = crecip64(s.x, -s.y);
+        const double2 d = crecip64(a, b);
+        CstC k;
+        k.alpha = make_float2((float)al.x, (float)al.y);
+        k.beta = make_float2((float)be.x, (float)be.y);
+        k.inv_d = make_float2((float)d.x, (float)d.y);
+        k.pad = make_float2(0.f, 0.f);
+        ((CstC *)cst)[p] = k;
+    }
+}
+
+cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int *bad,
+                             cudaStream_t s)
+{
+    constants_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, diag, cplx, cst, bad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Scalar helpers for the two sweep precisions.
+// ---------------------------------------------------------------------------
+template <bool CPLX> struct Prec;
+template <> struct Prec<false> {
+    using T = float;
+    using Ent = EntR;
+    using Cst = CstR;
+    static __device__ __forceinline__ T zero() { return 0.f; }
+    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x) { acc = fmaf(e.val, x, acc); }
+    // Eq. 4 / Eq. 5 right-hand sides
+    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s) { return phi * k.alpha - k.inv_d * s; }
+    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s) { return phi * k.beta - k.inv_d * s; }
+    static __device__ __forceinline__ T mulconj(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ bool finite_bounded(T v) { return fabsf(v) <= 1e30f; }
+};
+template <> struct Prec<true> {
+    using T = float2;
+    using Ent = EntC;
+    using Cst = CstC;
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x)
+    {
+        acc.x = fmaf(e.re, x.x, fmaf(-e.im, x.y, acc.x));
+        acc.y = fmaf(e.re, x.y, fmaf(e.im, x.x, acc.y));
+    }
+    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s)
+    {   // phi alpha - inv_d s
+        return make_float2(phi * k.alpha.x - (k.inv_d.x * s.x - k.inv_d.y * s.y),
+                           phi * k.alpha.y - (k.inv_d.x * s.y + k.inv_d.y * s.x));
+    }
+    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s)
+    {   // phi beta - conj(inv_d) s
+        return make_float2(phi * k.beta.x - (k.inv_d.x * s.x + k.inv_d.y * s.y),
+                           phi * k.beta.y - (k.inv_d.x * s.y - k.inv_d.y * s.x));
+    }
+    static __device__ __forceinline__ T mulconj(T a, T b)
+    {   // a conj(b)
+        return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ T shfl_xor(T v, int o)
+    {
+        return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    }
+    static __device__ __forceinline__ bool finite_bounded(T v) { return fabsf(v.x) <= 1e30f && fabsf(v.y) <= 1e30f; }
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float x)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// ---------------------------------------------------------------------------
+// The coupled sweep.  CTA = one slice of W chains (W lanes per row), for all
+// rows and `ncyc` cycles; chains are independent, so CTAs never communicate.
+// Within a cycle the CTA walks the dependency levels; rows of a level are
+// spread over the warps (32/W rows per warp instruction) and a block barrier
+// separates levels.  State is double-buffered: a row reads z_j (j < i) from
+// the buffer being written this cycle and z_j (j > i) from last cycle's
+// buffer, which is exactly the in-place semantics of Eq. 4 (and Eq. 5 for w).
+// ---------------------------------------------------------------------------
+template <bool CPLX, int W>
+__global__ void __launch_bounds__(1024) cc_sweep_kernel(const SweepArgs a)
+{
+    using P = Prec<CPLX>;
+    using T = typename P::T;
+    using Ent = typename P::Ent;
+    using Cst = typename P::Cst;
+    constexpr int RPW = 32 / W;  // rows per warp instruction
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int sub = lane / W;
+    const int cl = lane % W;
+    const int slice = blockIdx.x;
+    const int c = slice * W + cl;
+    const bool chain_ok = c < a.K;
+    const size_t K = (size_t)a.K;
+    const int stride = nwarps * RPW;
+    const Ent *zent = (const Ent *)a.zent;
+    const Ent *went = (const Ent *)a.went;
+    const Cst *cst = (const Cst *)a.cst;
+    const uint32_t cbit = (uint32_t)(c & 31);
+    T *diag = (T *)a.diag_part + (size_t)slice * a.n;
+    int cur = a.cur;
+    bool diverged = false;
+
+    for (int cyc = 0; cyc < a.ncyc; ++cyc) {
+        const T *zo = (const T *)a.z[cur];
+        T *zn = (T *)a.z[cur ^ 1];
+        const T *wo = (const T *)a.w[cur];
+        T *wn = (T *)a.w[cur ^ 1];
+        const uint32_t *noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c >> 5)) * (size_t)a.n;
+        const int shcol = a.cyc0_in_batch + cyc;
+        for (int lev = 0; lev < a.nlev; ++lev) {
+            const int pb = a.lev_ptr[lev], pe = a.lev_ptr[lev + 1];
+            for (int base = pb + warp * RPW; base < pe; base += stride) {
+                const int p = base + sub;
+                const bool ok = chain_ok && p < pe;
+                T prod = P::zero();
+                int i = 0;
+                if (ok) {
+                    i = a.perm[p];
+                    T sz = P::zero(), sw = P::zero();
+                    const int ze = a.zptr[p + 1];
+                    for (int e = a.zptr[p]; e < ze; ++e) {
+                        const Ent en = zent[e];
+                        const T *src = en.col < i ? zn : zo;
+                        P::fma(sz, en, src[(size_t)en.col * K + c]);
+                    }
+                    const int we = a.wptr[p + 1];
+                    for (int e = a.wptr[p]; e < we; ++e) {
+                        const Ent en = went[e];
+                        const T *src = en.col < i ? wn : wo;
+                        P::fma(sw, en, src[(size_t)en.col * K + c]);
+                    }
+                    const float phi = ((noise[i] >> cbit) & 1u) ? -1.f : 1.f;
+                    const Cst k = cst[p];
+                    const T zv = P::zrow(k, phi, sz);
+                    const T wv = P::wrow(k, phi, sw);
+                    zn[(size_t)i * K + c] = zv;
+                    wn[(size_t)i * K + c] = wv;
+                    diverged |= !(P::finite_bounded(zv) && P::finite_bounded(wv));
+                    prod = P::mulconj(zv, wv);
+                    if (a.rpos) {
+                        // shadow column of (cycle, chain): cycle block of kp elements, then
+                        // the chain (x2 for re,im); blocks are padded to 64 and the pad
+                        // stays zero
+                        const int r = a.rpos[i];
+                        const int s = a.spos[i];
+                        const size_t o = (size_t)shcol * a.kp + (size_t)c * (CPLX ? 2 : 1);
+                        if constexpr (!CPLX) {
+                            if (r >= 0) a.zsh[(size_t)r * a.ldsh + o] = bf16_bits(zv);
+                            if (s >= 0) a.wsh[(size_t)s * a.ldsh + o] = bf16_bits(wv);
+                        } else {
+                            if (r >= 0) {
+                                a.zsh[(size_t)r * a.ldsh + o] = bf16_bits(zv.x);
+                                a.zsh[(size_t)r * a.ldsh + o + 1] = bf16_bits(zv.y);
+                            }
+                            if (s >= 0) {
+                                // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
+                                // [-wi, wr] to Im(z conj w), so the product comes out
+                                // interleaved re,im
+                                uint16_t *w0 = a.wsh + (size_t)(2 * s) * a.ldsh + o;
+                                uint16_t *w1 = w0 + a.ldsh;
+                                w0[0] = bf16_bits(wv.x);
+                                w0[1] = bf16_bits(wv.y);
+                                w1[0] = bf16_bits(-wv.y);
+                                w1[1] = bf16_bits(wv.x);
+                            }
+                        }
+                    }
+                }
+                if (a.diag_part) {
+#pragma unroll
+                    for (int o = W / 2; o > 0; o >>= 1) prod = P::add(prod, P::shfl_xor(prod, o));
+                    if (ok && cl == 0) diag[i] = P::add(diag[i], prod);
+                }
+            }
+            __syncthreads();
+        }
+        cur ^= 1;
+    }
+    if (diverged) atomicOr(a.status, 1);
+}
+
+template <bool CPLX>
+static cudaError_t launch_sweep_w(const SweepArgs &a, int W, int slices, int threads, cudaStream_t s)
+{
+    switch (W) {
+    case 1: cc_sweep_kernel<CPLX, 1><<<slices, threads, 0, s>>>(a); break;
+    case 2: cc_sweep_kernel<CPLX, 2><<<slices, threads, 0, s>>>(a); break;
+    case 4: cc_sweep_kernel<CPLX, 4><<<slices, threads, 0, s>>>(a); break;
+    case 8: cc_sweep_kernel<CPLX, 8><<<slices, threads, 0, s>>>(a); break;
+    case 16: cc_sweep_kernel<CPLX, 16><<<slices, threads, 0, s>>>(a); break;
+    case 32: cc_sweep_kernel<CPLX, 32><<<slices, threads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SweepArgs &a, int cplx, int W, int slices, int threads,
+                         cudaStream_t s)
+{
+    return cplx ? launch_sweep_w<true>(a, W, slices, threads, s)
+                : launch_sweep_w<false>(a, W, slices, threads, s);
+}
+
+}  // namespace mcinv

@@ -1,0 +1,23 @@
+// tc_gemm.h -- tensor-core (tcgen05, TMA, TMEM) block contraction
+//   D[M][N] = A[M][inner] . B[N][inner]^T,  A, B bf16 K-major, D fp32 row-major.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace mcinv {
+
+struct TcGemmPlan;
+
+// A: a_rows x ld bf16 (rows padded to the tile height, pad rows zero),
+// B: b_rows x ld bf16, D: M x N fp32.  Returns NULL (and why) when the
+// device or the shapes are unsupported.
+TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t *B, size_t b_rows,
+                                long long ld, float *D, long long M, long long N, std::string *why);
+// Contract the first `inner` columns (a multiple of 64, <= ld).
+cudaError_t tc_gemm_run(TcGemmPlan *plan, long long inner, cudaStream_t s);
+void tc_gemm_plan_destroy(TcGemmPlan *plan);
+
+}  // namespace mcinv

@@ -1,0 +1,273 @@
+"""Python binding of libmcinv (include/mcinv.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the CUDA library through
+ctypes; all computation happens in the library's kernels.  There is no CPU
+fallback: if ``_build/libmcinv.so`` is missing, :func:`lib` raises.
+
+PyTorch supplies the CUDA stream (``torch.cuda.current_stream()``) when it
+is importable and a GPU is present; otherwise the legacy default stream is used.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmcinv.so")
+
+MCINV_OK = 0
+STATUS_NAMES = {0: "MCINV_OK", 1: "MCINV_E_ARG", 2: "MCINV_E_SINGULAR_DIAG", 3: "MCINV_E_DIVERGED",
+                4: "MCINV_E_NOMEM", 5: "MCINV_E_CUDA", 6: "MCINV_E_TIMEOUT", 7: "MCINV_E_STATE",
+                8: "MCINV_E_UNSUPPORTED"}
+MCINV_REAL64, MCINV_COMPLEX128 = 0, 1
+MCINV_ACC_FP32_SIMT, MCINV_ACC_BF16_TC = 0, 1
+MCINV_EST_BLOCK, MCINV_EST_DIAG, MCINV_EST_TRACE = 0, 1, 2
+MCINV_F_NO_DIAG = 1
+
+# every symbol include/mcinv.h declares
+EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sample",
+           "mcinv_estimate", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
+           "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
+           "mcinv_destroy", "mcinv_last_error")
+MCINV_KERNEL_NOISE, MCINV_KERNEL_SWEEP, MCINV_KERNEL_BLOCK, MCINV_KERNEL_FOLD, MCINV_KERNEL_ESTIMATE = range(5)
+KERNEL_NAMES = ("noise", "sweep", "block", "fold", "estimate")
+
+
+class McinvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mcinv_options(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("seed", ctypes.c_uint64), ("chain_base", ctypes.c_int64),
+                ("matrix_id", ctypes.c_uint32), ("groups", ctypes.c_int32),
+                ("batch_cycles", ctypes.c_int32), ("acc", ctypes.c_int32),
+                ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("block_rows", ctypes.POINTER(ctypes.c_int64)), ("n_block_rows", ctypes.c_int64),
+                ("block_cols", ctypes.POINTER(ctypes.c_int64)), ("n_block_cols", ctypes.c_int64)]
+
+
+class mcinv_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("is_complex", ctypes.c_int32), ("chains_per_cta", ctypes.c_int32),
+                ("threads_per_cta", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("groups", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("batch_cycles", ctypes.c_int32), ("acc", ctypes.c_int32),
+                ("cycle", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("block_batches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libmcinv.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.mcinv_default_options.argtypes = [ctypes.POINTER(mcinv_options)]
+        L.mcinv_default_options.restype = None
+        L.mcinv_create.argtypes = [ctypes.POINTER(vp), i64, vp, vp, vp, ctypes.c_int,
+                                   ctypes.POINTER(mcinv_options)]
+        for name in ("mcinv_burnin", "mcinv_sample"):
+            getattr(L, name).argtypes = [vp, i64]
+        L.mcinv_estimate.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.mcinv_sync.argtypes = [vp]
+        L.mcinv_get_state.argtypes = [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]
+        L.mcinv_set_state.argtypes = [vp, vp, vp, i64]
+        L.mcinv_reset_estimates.argtypes = [vp]
+        L.mcinv_info.argtypes = [vp, ctypes.POINTER(mcinv_info_t)]
+        L.mcinv_profile.argtypes = [vp, ctypes.c_int]
+        L.mcinv_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64),
+                                         ctypes.POINTER(ctypes.c_double)]
+        L.mcinv_destroy.argtypes = [vp]
+        L.mcinv_destroy.restype = None
+        L.mcinv_last_error.argtypes = [vp]
+        L.mcinv_last_error.restype = ctypes.c_char_p
+        for name in ("mcinv_create", "mcinv_burnin", "mcinv_sample", "mcinv_estimate", "mcinv_sync",
+                     "mcinv_get_state", "mcinv_set_state", "mcinv_reset_estimates", "mcinv_info",
+                     "mcinv_profile", "mcinv_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != MCINV_OK:
+        msg = lib().mcinv_last_error(handle).decode(errors="replace")
+        raise McinvError(status, msg)
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def mcinv_default_options(**overrides) -> mcinv_options:
+    opt = mcinv_options()
+    lib().mcinv_default_options(ctypes.byref(opt))
+    for k, v in overrides.items():
+        setattr(opt, k, v)
+    return opt
+
+
+class Handle:
+    """An mcinv_t plus the host arrays its options point to."""
+
+    def __init__(self, ptr, n, K, is_complex, nR, nS, keep):
+        self.ptr, self.n, self.K, self.is_complex = ptr, n, K, is_complex
+        self.nR, self.nS = nR, nS
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().mcinv_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_id=0, groups=0,
+                 batch_cycles=0, acc=MCINV_ACC_BF16_TC, chains_per_cta=0, threads_per_cta=0,
+                 flags=0, stream="current", block_rows=None, block_cols=None) -> Handle:
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    is_complex = np.iscomplexobj(val)
+    if is_complex:
+        v = np.ascontiguousarray(val, dtype=np.complex128).view(np.float64)
+        dt = MCINV_COMPLEX128
+    else:
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        dt = MCINV_REAL64
+    opt = mcinv_default_options(K=K, seed=seed, chain_base=chain_base, matrix_id=matrix_id,
+                                groups=groups, batch_cycles=batch_cycles, acc=acc,
+                                chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta,
+                                flags=flags)
+    opt.stream = current_stream() if stream == "current" else stream
+    keep = []
+    nR = nS = 0
+    if block_rows is not None:
+        R = np.ascontiguousarray(block_rows, dtype=np.int64)
+        S = np.ascontiguousarray(block_cols, dtype=np.int64)
+        keep += [R, S]
+        opt.block_rows = R.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        opt.block_cols = S.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        opt.n_block_rows, opt.n_block_cols = nR, nS = len(R), len(S)
+    h = ctypes.c_void_p()
+    _check(lib().mcinv_create(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(v), dt,
+                              ctypes.byref(opt)))
+    return Handle(h, int(n), int(K), is_complex, nR, nS, keep)
+
+
+def mcinv_burnin(h: Handle, cycles: int):
+    _check(lib().mcinv_burnin(h.ptr, int(cycles)), h.ptr)
+
+
+def mcinv_sample(h: Handle, cycles: int):
+    _check(lib().mcinv_sample(h.ptr, int(cycles)), h.ptr)
+
+
+def mcinv_sync(h: Handle):
+    _check(lib().mcinv_sync(h.ptr), h.ptr)
+
+
+def mcinv_estimate(h: Handle, kind: int, q_diag=None, out=None, se_out=None):
+    """Returns (estimate, standard_error) as float64 / complex128 arrays."""
+    if kind == MCINV_EST_DIAG:
+        shape = (h.n,)
+    elif kind == MCINV_EST_TRACE:
+        shape = ()
+    else:
+        shape = (h.nR, h.nS)
+    nv = 2 if h.is_complex else 1
+    count = int(np.prod(shape)) * nv
+    if out is None:
+        out = np.empty(count, dtype=np.float64)
+    if se_out is None:
+        se_out = np.empty(count, dtype=np.float64)
+    q = None if q_diag is None else np.ascontiguousarray(q_diag, dtype=np.float64)
+    _check(lib().mcinv_estimate(h.ptr, int(kind), _ptr(q), _ptr(out), _ptr(se_out)), h.ptr)
+    if h.is_complex:
+        return out.view(np.complex128).reshape(shape), se_out.view(np.complex128).reshape(shape)
+    return out.reshape(shape), se_out.reshape(shape)
+
+
+def mcinv_get_state(h: Handle, chain0: int = 0, nchains: int | None = None):
+    """Returns (z, w, cycle); z, w are [n][nchains] float64 or complex128."""
+    nchains = h.K - chain0 if nchains is None else nchains
+    nv = 2 if h.is_complex else 1
+    z = np.empty(h.n * nchains * nv, dtype=np.float64)
+    w = np.empty_like(z)
+    cyc = ctypes.c_int64()
+    st = lib().mcinv_get_state(h.ptr, int(chain0), int(nchains), _ptr(z), _ptr(w), ctypes.byref(cyc))
+    if st not in (MCINV_OK, 3):
+        _check(st, h.ptr)
+    if h.is_complex:
+        z, w = z.view(np.complex128), w.view(np.complex128)
+    return z.reshape(h.n, nchains), w.reshape(h.n, nchains), int(cyc.value)
+
+
+def mcinv_set_state(h: Handle, z, w, cycle: int):
+    dt = np.complex128 if h.is_complex else np.float64
+    z = np.ascontiguousarray(z, dtype=dt).reshape(h.n, h.K)
+    w = np.ascontiguousarray(w, dtype=dt).reshape(h.n, h.K)
+    _check(lib().mcinv_set_state(h.ptr, _ptr(z.view(np.float64)), _ptr(w.view(np.float64)), int(cycle)), h.ptr)
+
+
+def mcinv_reset_estimates(h: Handle):
+    _check(lib().mcinv_reset_estimates(h.ptr), h.ptr)
+
+
+def mcinv_info(h: Handle) -> dict:
+    info = mcinv_info_t()
+    _check(lib().mcinv_info(h.ptr, ctypes.byref(info)), h.ptr)
+    return info.as_dict()
+
+
+def mcinv_profile(h: Handle, enable: bool):
+    _check(lib().mcinv_profile(h.ptr, int(bool(enable))), h.ptr)
+
+
+def mcinv_profile_read(h: Handle, kernel: int):
+    """Returns (launches, milliseconds) recorded for one kernel class."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().mcinv_profile_read(h.ptr, int(kernel), ctypes.byref(n), ctypes.byref(ms)), h.ptr)
+    return int(n.value), float(ms.value)
+
+
+def mcinv_destroy(h: Handle):
+    if h.ptr:
+        lib().mcinv_destroy(h.ptr)
+        h.ptr = None
+
+
+def mcinv_last_error(h: Handle | None = None) -> str:
+    return lib().mcinv_last_error(None if h is None else h.ptr).decode(errors="replace")
+
+
+def create_from_csr(csr, **kw) -> Handle:
+    """mcinv_create from a workloads.CSR."""
+    return mcinv_create(csr.n, csr.row_ptr, csr.col, csr.val, **kw)

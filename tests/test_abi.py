@@ -1,0 +1,80 @@
+"""Host-only checks of the C-ABI library: it builds, loads, exports every
+symbol include/mcinv.h declares, and rejects malformed input on the host
+before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_cs_0412107_gb300 import build as libbuild
+from paper_cs_0412107_gb300 import mcinv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return mcinv.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mcinv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcinv_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(mcinv.EXPORTS)
+
+
+def test_options_layout_matches_header(L):
+    opt = mcinv.mcinv_default_options()
+    assert opt.K == 1024 and opt.acc == mcinv.MCINV_ACC_BF16_TC
+    # C layout: 3 x 8-byte fields, 7 x 4-byte fields, 4 bytes of padding, 5 x 8-byte fields
+    assert ctypes.sizeof(mcinv.mcinv_options) == 96
+    assert mcinv.mcinv_options.stream.offset == 56
+    assert ctypes.sizeof(mcinv.mcinv_info_t) == 96
+
+
+def _create(n, rp, col, val, **kw):
+    return mcinv.mcinv_create(n, rp, col, val, stream=None, **kw)
+
+
+def test_rejects_missing_diagonal(L):
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(2, [0, 1, 2], [1, 1], [1.0, 2.0])
+    assert e.value.status == 2 and "row 0" in str(e.value)
+
+
+def test_rejects_zero_diagonal(L):
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(2, [0, 1, 2], [0, 1], [1.0, 0.0])
+    assert e.value.status == 2 and "row 1" in str(e.value)
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(1, [0, 1], [0], np.array([0j]))
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("rp,col,val,msg", [
+    ([0, 2, 3], [1, 0, 1], [1.0, 1.0, 1.0], "strictly increasing"),
+    ([0, 1, 2], [0, 2], [1.0, 1.0], "out of range"),
+    ([1, 1, 2], [0, 1], [1.0, 1.0], "row_ptr"),
+    ([0, 1, 2], [0, 1], [1.0, np.nan], "non-finite"),
+])
+def test_rejects_malformed_csr(L, rp, col, val, msg):
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(2, rp, col, val)
+    assert e.value.status == 1 and msg in str(e.value)
+
+
+def test_rejects_bad_options(L):
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(1, [0, 1], [0], [1.0], K=0)
+    assert e.value.status == 1
