@@ -193,11 +193,12 @@ def run_mine(args, world, rank, local):
 
     hbm, bf16, bf16_sus, peak_kind = read_peaks()
     sw_launches, sw_ms = prof["sweep"]
-    units_per_launch = csr.n * K * B  # (row, chain) coupled updates per sweep launch
+    cyc_per_launch = cycles / max(sw_launches, 1)
+    units_per_launch = csr.n * K * cyc_per_launch  # (row, chain) coupled updates per sweep launch
     alg_bytes = 16.0 * units_per_launch  # read + write z and w, FP32
     achieved = alg_bytes / (sw_ms / sw_launches / 1e3) / 1e9 if sw_launches else None
     nnz_off = csr.nnz - csr.n
-    gather_bytes = (4.0 * (2 * nnz_off + 2 * csr.n)) * K * B  # every stored c_ij gathers z_j and w_j
+    gather_bytes = (4.0 * (2 * nnz_off + 2 * csr.n)) * K * cyc_per_launch  # every stored c_ij gathers z_j and w_j
     bl_launches, bl_ms = prof["block"]
     gemm_flops = 2.0 * csr.n * 512 * K * B  # one contraction per batch
     result = {

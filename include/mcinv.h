@@ -76,8 +76,9 @@ typedef struct {
     int32_t groups;         /* SE replicates G for diag/trace (chain groups); 0 = 32 */
     int32_t batch_cycles;   /* cycles per sweep launch / per block contraction; 0 = 8 */
     int32_t acc;            /* mcinv_acc for the block estimate */
-    int32_t chains_per_cta; /* chain-slice width W (1,2,4,8,16,32); 0 = chosen by the library */
-    int32_t threads_per_cta;/* 0 = chosen by the library (multiple of 32, <= 1024) */
+    int32_t chains_per_cta; /* chain-slice width W per CTA: a power of two <= 128 (real) or
+                               64 (complex); 0 = chosen by the library */
+    int32_t threads_per_cta;/* 0 = chosen by the library (multiple of 32, <= 512) */
     int32_t flags;          /* MCINV_F_* bits */
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     const int64_t *block_rows; /* R (row indices of C^-1), may be NULL when n_block_rows = 0 */
@@ -186,6 +187,16 @@ typedef enum {
  */
 mcinv_status mcinv_profile(mcinv_t h, int enable);
 mcinv_status mcinv_profile_read(mcinv_t h, mcinv_kernel kernel, int64_t *launches, double *ms);
+
+/*
+ * Diagnostic: run the tensor-core contraction used by the block estimate,
+ * D = A B^T, on host data.  A: M x inner and B: N x inner, row-major BF16 bit
+ * patterns; D: M x N row-major FP32.  Allocates and frees its own device
+ * memory on the legacy default stream and waits for the result.
+ * MCINV_E_UNSUPPORTED off sm_103a.
+ */
+mcinv_status mcinv_selftest_tc_gemm(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
+                                    const uint16_t *B, float *D);
 
 /* Free everything the handle owns.  NULL is allowed. */
 void mcinv_destroy(mcinv_t h);

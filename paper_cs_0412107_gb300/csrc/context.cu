@@ -20,7 +20,7 @@ struct mcinv_ctx {
     // problem and options
     int64_t n = 0, nnz = 0, K = 0;
     int cplx = 0;
-    int W = 0, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
+    int W = 0, V = 1, LPR = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
     uint64_t seed = 0;
     int64_t chain_base = 0;
     uint32_t matrix_id = 0;
@@ -137,13 +137,15 @@ extern "C" void mcinv_default_options(mcinv_options *opt)
     opt->acc = MCINV_ACC_BF16_TC;
 }
 
-static int choose_W(int64_t K)
+static int choose_W(int64_t K, int cplx)
 {
     // Chain-slice width: wide slices make each gathered row segment long
-    // (W x 4 or 8 bytes), narrow slices make more CTAs.  Aim for at least two
-    // slices per SM of a 152-SM part, with segments of at least 16 bytes.
-    int W = 32;
-    while (W > 4 && (K + W - 1) / W < 304) W /= 2;
+    // (W x 4 or 8 bytes), narrow slices make more CTAs.  Take the widest slice
+    // that still gives at least 256 CTAs (all resident at once on a 152-SM
+    // part), with segments of at least 16 bytes.
+    const int vmax = cplx ? 2 : 4;
+    int W = 32 * vmax;
+    while (W > vmax && (K + W - 1) / W < 256) W /= 2;
     while (W > 1 && W / 2 >= K) W /= 2;
     return W;
 }
@@ -198,15 +200,21 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     h->flags = opt.flags;
     h->acc = opt.acc;
     h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
-    h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : choose_W(opt.K);
-    if (h->W != 1 && h->W != 2 && h->W != 4 && h->W != 8 && h->W != 16 && h->W != 32) {
-        delete h;
-        return fail(nullptr, MCINV_E_ARG, "chains_per_cta must be 1,2,4,8,16 or 32");
+    h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : choose_W(opt.K, cplx);
+    {
+        // V chains per lane (one vector load per gather) when K allows it
+        const int vmax = cplx ? 2 : 4;
+        h->V = (opt.K % vmax == 0 && h->W % vmax == 0) ? vmax : 1;
+        h->LPR = h->W / h->V;
+        if ((h->W & (h->W - 1)) || h->LPR < 1 || h->LPR > 32) {
+            delete h;
+            return fail(nullptr, MCINV_E_ARG, "chains_per_cta must be a power of two <= %d", 32 * vmax);
+        }
     }
     h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 256;
-    if (h->threads % 32 || h->threads > 1024) {
+    if (h->threads % 32 || h->threads > 512) {
         delete h;
-        return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 1024");
+        return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 512");
     }
     h->slices = (int)((opt.K + h->W - 1) / h->W);
     const int Greq = opt.groups > 0 ? opt.groups : 32;
@@ -449,18 +457,18 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
         if (block && h->acc == MCINV_ACC_FP32_SIMT) {
             for (int k = 0; k < b; ++k) {
                 SweepArgs a = sweep_args(h, 1, k, true, 0);
-                LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->W, h->slices, h->threads, h->stream));
+                LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
                 h->cur ^= 1;
                 LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
                                             (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
             }
         } else {
             SweepArgs a = sweep_args(h, b, 0, accumulate, 0);
-            LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->W, h->slices, h->threads, h->stream));
+            LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
             if (b & 1) h->cur ^= 1;
             if (block) {
                 const long long inner = (long long)b * h->kp;
-                LAUNCH_K(h, MCINV_KERNEL_BLOCK, tc_gemm_run(h->gemm, inner, h->stream));
+                LAUNCH_K(h, MCINV_KERNEL_BLOCK, tc_gemm_run(h->gemm, inner, h->d_status, h->stream));
             }
         }
         if (block) {
@@ -500,6 +508,7 @@ extern "C" mcinv_status mcinv_sync(mcinv_t h)
     int status = 0;
     CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (status & 2) return fail(h, MCINV_E_TIMEOUT, "a bounded wait in the tensor-core contraction expired; its block batch was abandoned");
     if (status & 1) return fail(h, MCINV_E_DIVERGED, "a chain diverged (non-finite or |value| > 1e30): the sweep does not converge for this matrix");
     return MCINV_OK;
 }
@@ -672,4 +681,39 @@ extern "C" const char *mcinv_last_error(mcinv_t h)
 {
     if (!h) return g_create_error.c_str();
     return h->err.c_str();
+}
+
+extern "C" mcinv_status mcinv_selftest_tc_gemm(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
+                                               const uint16_t *B, float *D)
+{
+    if (M <= 0 || N <= 0 || inner <= 0 || !A || !B || !D) return fail(nullptr, MCINV_E_ARG, "bad self-test arguments");
+    const size_t ld = (size_t)((inner + 63) / 64 * 64);
+    const size_t ar = (size_t)((M + 127) / 128 * 128), br = (size_t)((N + 255) / 256 * 256);
+    uint16_t *dA = nullptr, *dB = nullptr;
+    float *dD = nullptr;
+    int *dS = nullptr;
+    mcinv_status st = MCINV_OK;
+    std::string why;
+    TcGemmPlan *plan = nullptr;
+    int status = 0;
+    auto chk = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == MCINV_OK) st = fail(nullptr, MCINV_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+        return e == cudaSuccess;
+    };
+    if (chk(cudaMalloc(&dA, ar * ld * 2), "malloc A") && chk(cudaMalloc(&dB, br * ld * 2), "malloc B") &&
+        chk(cudaMalloc(&dD, (size_t)M * N * 4), "malloc D") && chk(cudaMalloc(&dS, sizeof(int)), "malloc status") &&
+        chk(cudaMemset(dA, 0, ar * ld * 2), "memset") && chk(cudaMemset(dB, 0, br * ld * 2), "memset") &&
+        chk(cudaMemset(dS, 0, sizeof(int)), "memset") &&
+        chk(cudaMemcpy2D(dA, ld * 2, A, inner * 2, inner * 2, M, cudaMemcpyHostToDevice), "copy A") &&
+        chk(cudaMemcpy2D(dB, ld * 2, B, inner * 2, inner * 2, N, cudaMemcpyHostToDevice), "copy B")) {
+        plan = tc_gemm_plan_create(dA, ar, dB, br, (long long)ld, dD, M, N, &why);
+        if (!plan) st = fail(nullptr, MCINV_E_UNSUPPORTED, "%s", why.c_str());
+        else if (chk(tc_gemm_run(plan, (long long)ld, dS, nullptr), "launch") && chk(cudaDeviceSynchronize(), "sync") &&
+                 chk(cudaMemcpy(D, dD, (size_t)M * N * 4, cudaMemcpyDeviceToHost), "copy D") &&
+                 chk(cudaMemcpy(&status, dS, sizeof(int), cudaMemcpyDeviceToHost), "copy status") && status)
+            st = fail(nullptr, MCINV_E_TIMEOUT, "tensor-core contraction timed out");
+    }
+    tc_gemm_plan_destroy(plan);
+    cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(dS);
+    return st;
 }

@@ -59,8 +59,10 @@ cudaError_t launch_noise(uint64_t seed, uint32_t matrix, uint64_t chain_base, in
                          uint32_t cycle0, int ncyc, uint32_t *out, cudaStream_t s);
 cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int *bad,
                              cudaStream_t s);
-cudaError_t launch_sweep(const SweepArgs &a, int cplx, int W, int slices, int threads,
-                         cudaStream_t s);
+// slices CTAs of lanes_per_row x chains_per_lane chains each; chains_per_lane
+// is 1 or the vector width (4 real, 2 complex) and then divides K.
+cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int chains_per_lane,
+                         int slices, int threads, cudaStream_t s);
 
 // accumulate.cu
 cudaError_t launch_diag_fold(int cplx, int n, int slices, int G, void *diag_part, double *acc,

@@ -195,38 +195,93 @@ __device__ __forceinline__ uint16_t bf16_bits(float x)
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
+// V chains of one lane as a single vector: V consecutive chains of one row are
+// contiguous in the [n][K] layout, so each gather is one 4-, 8- or 16-byte load.
+template <bool CPLX, int V> struct Vec;
+template <> struct Vec<false, 1> { using T = float; };
+template <> struct Vec<false, 4> { using T = float4; };
+template <> struct Vec<true, 1> { using T = float2; };
+template <> struct Vec<true, 2> { using T = float4; };
+
+template <bool CPLX, int V>
+struct Lane {
+    using P = Prec<CPLX>;
+    using S = typename P::T;                 // one chain's scalar (float or float2)
+    using T = typename Vec<CPLX, V>::T;      // the lane's V chains
+    static constexpr int NF = (CPLX ? 2 : 1) * V;  // floats per lane vector
+    static __device__ __forceinline__ float *f(T &v) { return reinterpret_cast<float *>(&v); }
+    static __device__ __forceinline__ const float *f(const T &v) { return reinterpret_cast<const float *>(&v); }
+    static __device__ __forceinline__ T zero()
+    {
+        T v;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) f(v)[k] = 0.f;
+        return v;
+    }
+    static __device__ __forceinline__ S get(const T &v, int k)
+    {
+        if constexpr (CPLX) return make_float2(f(v)[2 * k], f(v)[2 * k + 1]);
+        else return f(v)[k];
+    }
+    static __device__ __forceinline__ void set(T &v, int k, S x)
+    {
+        if constexpr (CPLX) { f(v)[2 * k] = x.x; f(v)[2 * k + 1] = x.y; }
+        else f(v)[k] = x;
+    }
+    // acc += c * x for each of the V chains
+    static __device__ __forceinline__ void fma(T &acc, const typename P::Ent &e, const T &x)
+    {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            S s = get(acc, k);
+            P::fma(s, e, get(x, k));
+            set(acc, k, s);
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
-// The coupled sweep.  CTA = one slice of W chains (W lanes per row), for all
-// rows and `ncyc` cycles; chains are independent, so CTAs never communicate.
-// Within a cycle the CTA walks the dependency levels; rows of a level are
-// spread over the warps (32/W rows per warp instruction) and a block barrier
-// separates levels.  State is double-buffered: a row reads z_j (j < i) from
-// the buffer being written this cycle and z_j (j > i) from last cycle's
-// buffer, which is exactly the in-place semantics of Eq. 4 (and Eq. 5 for w).
+// The coupled sweep.  CTA = one slice of LPR x V chains (LPR lanes per row, V
+// chains per lane), for all rows and `ncyc` cycles; chains are independent,
+// so CTAs never communicate.  Within a cycle the CTA walks the dependency
+// levels; rows of a level are spread over the warps (32/LPR rows per warp
+// instruction) and a block barrier separates levels.  State is
+// double-buffered: a row reads z_j (j < i) from the buffer being written this
+// cycle and z_j (j > i) from last cycle's buffer, which is exactly the
+// in-place semantics of Eq. 4 (and of Eq. 5 for w).
+//
+// Memory-level parallelism: the off-diagonal entries of the row in C and in
+// C^dagger are fetched U at a time (read-only path), then all 2U gathers of z
+// and w are issued before any FMA consumes them.
 // ---------------------------------------------------------------------------
-template <bool CPLX, int W>
-__global__ void __launch_bounds__(1024) cc_sweep_kernel(const SweepArgs a)
+template <bool CPLX, int LPR, int V, int U>
+__global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
 {
     using P = Prec<CPLX>;
-    using T = typename P::T;
+    using L = Lane<CPLX, V>;
+    using T = typename L::T;
+    using S = typename L::S;
     using Ent = typename P::Ent;
     using Cst = typename P::Cst;
-    constexpr int RPW = 32 / W;  // rows per warp instruction
+    constexpr int RPW = 32 / LPR;  // rows per warp instruction
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int sub = lane / W;
-    const int cl = lane % W;
+    const int sub = lane / LPR;
+    const int cl = lane % LPR;
     const int slice = blockIdx.x;
-    const int c = slice * W + cl;
-    const bool chain_ok = c < a.K;
+    const int c0 = (slice * LPR + cl) * V;  // first chain of this lane (K % V == 0)
+    const bool chain_ok = c0 < a.K;
     const size_t K = (size_t)a.K;
     const int stride = nwarps * RPW;
-    const Ent *zent = (const Ent *)a.zent;
-    const Ent *went = (const Ent *)a.went;
-    const Cst *cst = (const Cst *)a.cst;
-    const uint32_t cbit = (uint32_t)(c & 31);
-    T *diag = (T *)a.diag_part + (size_t)slice * a.n;
+    const Ent *__restrict__ zent = (const Ent *)a.zent;
+    const Ent *__restrict__ went = (const Ent *)a.went;
+    const Cst *__restrict__ cst = (const Cst *)a.cst;
+    const int *__restrict__ perm = a.perm;
+    const int *__restrict__ zptr = a.zptr;
+    const int *__restrict__ wptr = a.wptr;
+    const uint32_t cshift = (uint32_t)(c0 & 31);
+    S *diag = (S *)a.diag_part + (size_t)slice * a.n;
     int cur = a.cur;
     bool diverged = false;
 
@@ -235,70 +290,101 @@ __global__ void __launch_bounds__(1024) cc_sweep_kernel(const SweepArgs a)
         T *zn = (T *)a.z[cur ^ 1];
         const T *wo = (const T *)a.w[cur];
         T *wn = (T *)a.w[cur ^ 1];
-        const uint32_t *noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c >> 5)) * (size_t)a.n;
+        const uint32_t *__restrict__ noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
         const int shcol = a.cyc0_in_batch + cyc;
         for (int lev = 0; lev < a.nlev; ++lev) {
-            const int pb = a.lev_ptr[lev], pe = a.lev_ptr[lev + 1];
+            const int pb = __ldg(&a.lev_ptr[lev]), pe = __ldg(&a.lev_ptr[lev + 1]);
             for (int base = pb + warp * RPW; base < pe; base += stride) {
                 const int p = base + sub;
                 const bool ok = chain_ok && p < pe;
-                T prod = P::zero();
+                S prod = P::zero();
                 int i = 0;
                 if (ok) {
-                    i = a.perm[p];
-                    T sz = P::zero(), sw = P::zero();
-                    const int ze = a.zptr[p + 1];
-                    for (int e = a.zptr[p]; e < ze; ++e) {
-                        const Ent en = zent[e];
-                        const T *src = en.col < i ? zn : zo;
-                        P::fma(sz, en, src[(size_t)en.col * K + c]);
+                    i = __ldg(&perm[p]);
+                    const int zb = __ldg(&zptr[p]), zeN = __ldg(&zptr[p + 1]);
+                    const int wb = __ldg(&wptr[p]), weN = __ldg(&wptr[p + 1]);
+                    T sz = L::zero(), sw = L::zero();
+                    for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
+                        Ent enz[U], enw[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (ez + u < zeN) enz[u] = zent[ez + u];
+                            if (ew + u < weN) enw[u] = went[ew + u];
+                        }
+                        T xz[U], xw[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            xz[u] = L::zero();
+                            xw[u] = L::zero();
+                            if (ez + u < zeN) {
+                                const T *src = enz[u].col < i ? zn : zo;
+                                xz[u] = src[((size_t)enz[u].col * K + c0) / V];
+                            }
+                            if (ew + u < weN) {
+                                const T *src = enw[u].col < i ? wn : wo;
+                                xw[u] = src[((size_t)enw[u].col * K + c0) / V];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
+                            if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                        }
                     }
-                    const int we = a.wptr[p + 1];
-                    for (int e = a.wptr[p]; e < we; ++e) {
-                        const Ent en = went[e];
-                        const T *src = en.col < i ? wn : wo;
-                        P::fma(sw, en, src[(size_t)en.col * K + c]);
-                    }
-                    const float phi = ((noise[i] >> cbit) & 1u) ? -1.f : 1.f;
+                    const uint32_t bits = __ldg(&noise[i]) >> cshift;
                     const Cst k = cst[p];
-                    const T zv = P::zrow(k, phi, sz);
-                    const T wv = P::wrow(k, phi, sw);
-                    zn[(size_t)i * K + c] = zv;
-                    wn[(size_t)i * K + c] = wv;
-                    diverged |= !(P::finite_bounded(zv) && P::finite_bounded(wv));
-                    prod = P::mulconj(zv, wv);
+                    T zv, wv;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
+                        const S zs = P::zrow(k, phi, L::get(sz, v));
+                        const S ws = P::wrow(k, phi, L::get(sw, v));
+                        L::set(zv, v, zs);
+                        L::set(wv, v, ws);
+                        diverged |= !(P::finite_bounded(zs) && P::finite_bounded(ws));
+                        prod = P::add(prod, P::mulconj(zs, ws));
+                    }
+                    zn[((size_t)i * K + c0) / V] = zv;
+                    wn[((size_t)i * K + c0) / V] = wv;
                     if (a.rpos) {
                         // shadow column of (cycle, chain): cycle block of kp elements, then
                         // the chain (x2 for re,im); blocks are padded to 64 and the pad
                         // stays zero
-                        const int r = a.rpos[i];
-                        const int s = a.spos[i];
-                        const size_t o = (size_t)shcol * a.kp + (size_t)c * (CPLX ? 2 : 1);
-                        if constexpr (!CPLX) {
-                            if (r >= 0) a.zsh[(size_t)r * a.ldsh + o] = bf16_bits(zv);
-                            if (s >= 0) a.wsh[(size_t)s * a.ldsh + o] = bf16_bits(wv);
-                        } else {
-                            if (r >= 0) {
-                                a.zsh[(size_t)r * a.ldsh + o] = bf16_bits(zv.x);
-                                a.zsh[(size_t)r * a.ldsh + o + 1] = bf16_bits(zv.y);
-                            }
-                            if (s >= 0) {
+                        const int r = __ldg(&a.rpos[i]);
+                        const int s = __ldg(&a.spos[i]);
+                        const size_t o = (size_t)shcol * a.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                        constexpr int NF = L::NF;
+                        if (r >= 0) {
+                            uint16_t *dst = a.zsh + (size_t)r * a.ldsh + o;
+#pragma unroll
+                            for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
+                        }
+                        if (s >= 0) {
+                            if constexpr (!CPLX) {
+                                uint16_t *dst = a.wsh + (size_t)s * a.ldsh + o;
+#pragma unroll
+                                for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
+                            } else {
                                 // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
                                 // [-wi, wr] to Im(z conj w), so the product comes out
                                 // interleaved re,im
                                 uint16_t *w0 = a.wsh + (size_t)(2 * s) * a.ldsh + o;
                                 uint16_t *w1 = w0 + a.ldsh;
-                                w0[0] = bf16_bits(wv.x);
-                                w0[1] = bf16_bits(wv.y);
-                                w1[0] = bf16_bits(-wv.y);
-                                w1[1] = bf16_bits(wv.x);
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    const S x = L::get(wv, v);
+                                    w0[2 * v] = bf16_bits(x.x);
+                                    w0[2 * v + 1] = bf16_bits(x.y);
+                                    w1[2 * v] = bf16_bits(-x.y);
+                                    w1[2 * v + 1] = bf16_bits(x.x);
+                                }
                             }
                         }
                     }
                 }
                 if (a.diag_part) {
 #pragma unroll
-                    for (int o = W / 2; o > 0; o >>= 1) prod = P::add(prod, P::shfl_xor(prod, o));
+                    for (int o = LPR / 2; o > 0; o >>= 1) prod = P::add(prod, P::shfl_xor(prod, o));
                     if (ok && cl == 0) diag[i] = P::add(diag[i], prod);
                 }
             }
@@ -309,26 +395,32 @@ __global__ void __launch_bounds__(1024) cc_sweep_kernel(const SweepArgs a)
     if (diverged) atomicOr(a.status, 1);
 }
 
-template <bool CPLX>
-static cudaError_t launch_sweep_w(const SweepArgs &a, int W, int slices, int threads, cudaStream_t s)
+template <bool CPLX, int V, int U>
+static cudaError_t launch_sweep_v(const SweepArgs &a, int LPR, int slices, int threads, cudaStream_t s)
 {
-    switch (W) {
-    case 1: cc_sweep_kernel<CPLX, 1><<<slices, threads, 0, s>>>(a); break;
-    case 2: cc_sweep_kernel<CPLX, 2><<<slices, threads, 0, s>>>(a); break;
-    case 4: cc_sweep_kernel<CPLX, 4><<<slices, threads, 0, s>>>(a); break;
-    case 8: cc_sweep_kernel<CPLX, 8><<<slices, threads, 0, s>>>(a); break;
-    case 16: cc_sweep_kernel<CPLX, 16><<<slices, threads, 0, s>>>(a); break;
-    case 32: cc_sweep_kernel<CPLX, 32><<<slices, threads, 0, s>>>(a); break;
+    switch (LPR) {
+    case 1: cc_sweep_kernel<CPLX, 1, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 2: cc_sweep_kernel<CPLX, 2, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 4: cc_sweep_kernel<CPLX, 4, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 8: cc_sweep_kernel<CPLX, 8, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 16: cc_sweep_kernel<CPLX, 16, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 32: cc_sweep_kernel<CPLX, 32, V, U><<<slices, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const SweepArgs &a, int cplx, int W, int slices, int threads,
-                         cudaStream_t s)
+cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int chains_per_lane,
+                         int slices, int threads, cudaStream_t s)
 {
-    return cplx ? launch_sweep_w<true>(a, W, slices, threads, s)
-                : launch_sweep_w<false>(a, W, slices, threads, s);
+    if (cplx) {
+        if (chains_per_lane == 2) return launch_sweep_v<true, 2, 4>(a, lanes_per_row, slices, threads, s);
+        if (chains_per_lane == 1) return launch_sweep_v<true, 1, 4>(a, lanes_per_row, slices, threads, s);
+    } else {
+        if (chains_per_lane == 4) return launch_sweep_v<false, 4, 8>(a, lanes_per_row, slices, threads, s);
+        if (chains_per_lane == 1) return launch_sweep_v<false, 1, 8>(a, lanes_per_row, slices, threads, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mcinv

@@ -1,15 +1,328 @@
-// tc_gemm.cu -- placeholder until the tcgen05 contraction lands.
+// tc_gemm.cu -- the block estimate's contraction on the 5th-generation tensor
+// cores: D[M][N] = A[M][inner] . B[N][inner]^T with A = BF16 shadows of z rows
+// (chains x cycles along `inner`), B = BF16 shadows of w rows, D in FP32.
+// This is the sum over chains and cycles of z_r conj(w_s) of Eq. 1/C.
+//
+// One CTA per 128 x 256 output tile, 128 threads:
+//   warp 0 lane 0  TMA producer: 64-wide K slices of A and B into a 4-stage
+//                  ring of 128B-swizzled shared-memory tiles (mbarrier tx counts)
+//   warp 1 lane 0  MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
+//                  M=128, N=256, K=16, accumulator in TMEM (256 columns);
+//                  tcgen05.commit frees ring slots and finally signals the epilogue
+//   warps 0-3      epilogue: tcgen05.ld 32 lanes x 32 columns at a time -> D
+// Every wait is bounded (globaltimer); on expiry the CTA records a timeout in
+// `status`, abandons the tile, releases TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "tc_gemm.h"
 
 namespace mcinv {
 
-TcGemmPlan *tc_gemm_plan_create(const uint16_t *, size_t, const uint16_t *, size_t, long long, float *,
-                                long long, long long, std::string *why)
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    if (why) *why = "not available in this build";
-    return nullptr;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-cudaError_t tc_gemm_run(TcGemmPlan *, long long, cudaStream_t) { return cudaErrorNotSupported; }
-void tc_gemm_plan_destroy(TcGemmPlan *) {}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity; false if the CTA gave up
+// (another role aborted, or WAIT_NS elapsed).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with
+// 128-byte swizzling: rows of 128 B, 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)(16u >> 4) << 16;          // leading byte offset (unused with 128B swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                   float *__restrict__ D, int M, int N, int ktiles, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_BYTES;
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accf + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(accf), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kt = 0; kt < ktiles; ++kt) {
+            const int s = kt % STAGES;
+            const uint32_t phase = (uint32_t)(kt / STAGES) & 1u;
+            if (kt >= STAGES && !mbar_wait(smem_u32(&empty[s]), phase ^ 1u, abort_flag)) break;
+            mbar_expect_tx(smem_u32(&full[s]), STAGE_BYTES);
+            tma_load_2d(smem_u32(sA + s * A_BYTES), &ta, smem_u32(&full[s]), kt * BK, m0);
+            tma_load_2d(smem_u32(sB + s * B_BYTES), &tb, smem_u32(&full[s]), kt * BK, n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool ok = true;
+        for (int kt = 0; kt < ktiles; ++kt) {
+            const int s = kt % STAGES;
+            const uint32_t phase = (uint32_t)(kt / STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&full[s]), phase, abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t a = sdesc(smem_u32(sA + s * A_BYTES));
+            const uint64_t b = sdesc(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)  // advance 16 elements = 32 bytes = 2 units of 16 B
+                mma_bf16(tmem, a + 2 * kk, b + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&empty[s]));
+        }
+        if (ok) mma_commit(smem_u32(accf));
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31; tcgen05.ld is
+    // warp-collective, so the decision to read is made warp-uniform
+    const bool have = __all_sync(0xffffffffu, mbar_wait(smem_u32(accf), 0u, abort_flag));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (have) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < M) {
+                float *dst = D + (size_t)row * N + n0 + c0;
+                if (n0 + c0 + 32 <= N && (N & 3) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+                }
+            }
+        }
+    }
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicOr(status, 2);
+        // give TMA copies still in flight time to land before the CTA exits
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool encode(CUtensorMap *map, const uint16_t *base, size_t rows, long long ld, int box_rows, std::string *why)
+{
+    auto fn = encode_fn();
+    if (!fn) {
+        if (why) *why = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (why) *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+struct TcGemmPlan {
+    CUtensorMap ta, tb;
+    float *D;
+    long long M, N, ld;
+};
+
+TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t *B, size_t b_rows,
+                                long long ld, float *D, long long M, long long N, std::string *why)
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+        if (why) *why = "no CUDA device";
+        return nullptr;
+    }
+    if (major != 10 || minor != 3) {
+        if (why) *why = "the tcgen05 contraction is built for sm_103a only";
+        return nullptr;
+    }
+    if (ld % BK || a_rows % BM || b_rows % BN || (long long)a_rows < M || (long long)b_rows < N ||
+        ((uintptr_t)A & 15) || ((uintptr_t)B & 15) || M > (1LL << 31) || N > (1LL << 31)) {
+        if (why) *why = "unsupported shape or alignment";
+        return nullptr;
+    }
+    TcGemmPlan *p = new TcGemmPlan;
+    std::memset(p, 0, sizeof *p);
+    if (!encode(&p->ta, A, a_rows, ld, BM, why) || !encode(&p->tb, B, b_rows, ld, BN, why)) {
+        delete p;
+        return nullptr;
+    }
+    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+        if (why) *why = "cannot reserve shared memory";
+        delete p;
+        return nullptr;
+    }
+    p->D = D;
+    p->M = M;
+    p->N = N;
+    p->ld = ld;
+    return p;
+}
+
+cudaError_t tc_gemm_run(TcGemmPlan *p, long long inner, int *status, cudaStream_t s)
+{
+    if (!p || inner <= 0 || inner % BK || inner > p->ld) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((p->N + BN - 1) / BN), (unsigned)((p->M + BM - 1) / BM));
+    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(p->ta, p->tb, p->D, (int)p->M, (int)p->N, (int)(inner / BK),
+                                                 status);
+    return cudaGetLastError();
+}
+
+void tc_gemm_plan_destroy(TcGemmPlan *p) { delete p; }
 
 }  // namespace mcinv

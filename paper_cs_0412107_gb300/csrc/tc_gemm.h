@@ -16,8 +16,9 @@ struct TcGemmPlan;
 // device or the shapes are unsupported.
 TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t *B, size_t b_rows,
                                 long long ld, float *D, long long M, long long N, std::string *why);
-// Contract the first `inner` columns (a multiple of 64, <= ld).
-cudaError_t tc_gemm_run(TcGemmPlan *plan, long long inner, cudaStream_t s);
+// Contract the first `inner` columns (a multiple of 64, <= ld).  A bounded
+// device-side wait that expires sets bit 1 (value 2) of *status.
+cudaError_t tc_gemm_run(TcGemmPlan *plan, long long inner, int *status, cudaStream_t s);
 void tc_gemm_plan_destroy(TcGemmPlan *plan);
 
 }  // namespace mcinv

@@ -30,7 +30,7 @@ MCINV_F_NO_DIAG = 1
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sample",
            "mcinv_estimate", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
-           "mcinv_destroy", "mcinv_last_error")
+           "mcinv_selftest_tc_gemm", "mcinv_destroy", "mcinv_last_error")
 MCINV_KERNEL_NOISE, MCINV_KERNEL_SWEEP, MCINV_KERNEL_BLOCK, MCINV_KERNEL_FOLD, MCINV_KERNEL_ESTIMATE = range(5)
 KERNEL_NAMES = ("noise", "sweep", "block", "fold", "estimate")
 
@@ -92,6 +92,8 @@ def lib():
         L.mcinv_profile.argtypes = [vp, ctypes.c_int]
         L.mcinv_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64),
                                          ctypes.POINTER(ctypes.c_double)]
+        L.mcinv_selftest_tc_gemm.argtypes = [i64, i64, i64, vp, vp, vp]
+        L.mcinv_selftest_tc_gemm.restype = ctypes.c_int
         L.mcinv_destroy.argtypes = [vp]
         L.mcinv_destroy.restype = None
         L.mcinv_last_error.argtypes = [vp]
@@ -256,6 +258,16 @@ def mcinv_profile_read(h: Handle, kernel: int):
     ms = ctypes.c_double()
     _check(lib().mcinv_profile_read(h.ptr, int(kernel), ctypes.byref(n), ctypes.byref(ms)), h.ptr)
     return int(n.value), float(ms.value)
+
+
+def mcinv_selftest_tc_gemm(A_bits, B_bits):
+    """D = A B^T on the tensor cores; A_bits, B_bits: uint16 BF16 bit patterns [rows][inner]."""
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    assert A.shape[1] == B.shape[1]
+    D = np.empty((A.shape[0], B.shape[0]), dtype=np.float32)
+    _check(lib().mcinv_selftest_tc_gemm(A.shape[0], B.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(D)))
+    return D
 
 
 def mcinv_destroy(h: Handle):

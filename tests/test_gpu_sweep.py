@@ -75,12 +75,24 @@ def test_trajectory_lattice4d_complex():
     _assert_close(errs)
 
 
-@pytest.mark.parametrize("W", [1, 2, 4, 8, 16, 32])
-@pytest.mark.parametrize("threads", [32, 256, 1024])
-def test_trajectory_every_slice_shape(W, threads):
-    """Every chain-slice width and block size gives the same sweep (ragged K = 45)."""
+@pytest.mark.parametrize("W", [1, 2, 4, 8, 16, 32, 64, 128])
+@pytest.mark.parametrize("threads", [32, 256, 512])
+@pytest.mark.parametrize("K", [45, 200])
+def test_trajectory_every_slice_shape(W, threads, K):
+    """Every chain-slice width and block size gives the same sweep: K = 45 runs one
+    chain per lane with a ragged last slice, K = 200 the vector path (4 chains per
+    lane) with a ragged last slice."""
     csr = wl.random_dominant(300, 5, 1.3, 7)
-    _, _, errs = run_pair(csr, 45, [3], chains_per_cta=W, threads_per_cta=threads)
+    _, _, errs = run_pair(csr, K, [3], chains_per_cta=W, threads_per_cta=threads)
+    _assert_close(errs)
+
+
+@pytest.mark.parametrize("W", [1, 2, 8, 64])
+@pytest.mark.parametrize("K", [33, 66])
+def test_trajectory_complex_slice_shapes(W, K):
+    """Complex sweep: one chain per lane (K = 33) and two per lane (K = 66)."""
+    csr = wl.u1_lattice((7, 9), 0.12, 0.08, seed=8)
+    _, _, errs = run_pair(csr, K, [4], chains_per_cta=W, threads_per_cta=128)
     _assert_close(errs)
 
 
