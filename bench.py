@@ -221,7 +221,7 @@ def run_mine(args, world, rank, local):
                      "gather_inclusive_bytes_per_launch": gather_bytes,
                      "gather_inclusive_gbs": gather_bytes / (sw_ms / sw_launches / 1e3) / 1e9 if sw_launches else None},
         "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
-        "block_tflops": (gemm_flops * bl_launches / (bl_ms / 1e3) / 1e12 / max(bl_launches, 1) * 1) if bl_launches and acc else None,
+        "block_tflops": (gemm_flops * bl_launches / (bl_ms / 1e3) / 1e12) if bl_launches and acc else None,
         "gpu_launches": launches,
         "clocks": clocks.summary(),
     }

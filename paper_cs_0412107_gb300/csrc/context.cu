@@ -143,7 +143,7 @@ static int choose_W(int64_t K, int cplx)
     // (W x 4 or 8 bytes), narrow slices make more CTAs.  Take the widest slice
     // that still gives at least 256 CTAs (all resident at once on a 152-SM
     // part), with segments of at least 16 bytes.
-    const int vmax = cplx ? 2 : 4;
+    const int vmax = (K % (cplx ? 2 : 4) == 0) ? (cplx ? 2 : 4) : 1;
     int W = 32 * vmax;
     while (W > vmax && (K + W - 1) / W < 256) W /= 2;
     while (W > 1 && W / 2 >= K) W /= 2;
@@ -208,7 +208,8 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         h->LPR = h->W / h->V;
         if ((h->W & (h->W - 1)) || h->LPR < 1 || h->LPR > 32) {
             delete h;
-            return fail(nullptr, MCINV_E_ARG, "chains_per_cta must be a power of two <= %d", 32 * vmax);
+            return fail(nullptr, MCINV_E_ARG, "chains_per_cta must be a power of two <= %d for K = %lld",
+                        32 * h->V, (long long)opt.K);
         }
     }
     h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 256;
