@@ -85,6 +85,10 @@ typedef struct {
     int64_t n_block_rows;
     const int64_t *block_cols; /* S (column indices of C^-1) */
     int64_t n_block_cols;
+    int32_t ctas_per_slice; /* Q: CTAs of one thread-block cluster sharing a chain slice and
+                               splitting each dependency level's rows (1..16); 0 = chosen by
+                               the library */
+    int32_t reserved;
 } mcinv_options;
 
 #define MCINV_F_NO_DIAG 1 /* do not accumulate the diagonal (and trace) */
@@ -154,7 +158,9 @@ typedef struct {
     int32_t is_complex;
     int32_t chains_per_cta;  /* W */
     int32_t threads_per_cta;
-    int32_t slices;          /* CTAs per sweep = ceil(K / W) */
+    int32_t slices;          /* chain slices = ceil(K / W) */
+    int32_t ctas_per_slice;  /* Q: the sweep launches slices x Q CTAs */
+    int32_t chains_per_lane; /* vector width of one lane's chains (1, 2 or 4) */
     int32_t groups;          /* G actually used (divides slices) */
     int32_t levels;          /* Gauss-Seidel dependency levels of C and C^dagger */
     int32_t batch_cycles;

@@ -20,7 +20,7 @@ struct mcinv_ctx {
     // problem and options
     int64_t n = 0, nnz = 0, K = 0;
     int cplx = 0;
-    int W = 0, V = 1, LPR = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
+    int W = 0, V = 1, LPR = 1, Q = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
     uint64_t seed = 0;
     int64_t chain_base = 0;
     uint32_t matrix_id = 0;
@@ -137,17 +137,33 @@ extern "C" void mcinv_default_options(mcinv_options *opt)
     opt->acc = MCINV_ACC_BF16_TC;
 }
 
-static int choose_W(int64_t K, int cplx)
+static int sm_count()
 {
-    // Chain-slice width: wide slices make each gathered row segment long
-    // (W x 4 or 8 bytes), narrow slices make more CTAs.  Take the widest slice
-    // that still gives at least 256 CTAs (all resident at once on a 152-SM
-    // part), with segments of at least 16 bytes.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 152;
+    return sms;
+}
+
+// Default slice shape: wide chain slices (8 to 32 lanes on one row, so a
+// gathered row segment is 128 to 512 contiguous bytes) spread over a cluster
+// of Q CTAs when there are fewer slices than SMs; among those, the one that
+// keeps the most SMs busy.
+static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q)
+{
     const int vmax = (K % (cplx ? 2 : 4) == 0) ? (cplx ? 2 : 4) : 1;
-    int W = 32 * vmax;
-    while (W > vmax && (K + W - 1) / W < 256) W /= 2;
-    while (W > 1 && W / 2 >= K) W /= 2;
-    return W;
+    int bestW = vmax, bestQ = 1;
+    int64_t best = -1;
+    for (int lpr = 32; lpr >= 8; lpr /= 2) {
+        const int w = lpr * vmax;
+        const int64_t slices = (K + w - 1) / w;
+        int q = (int)std::max<int64_t>(1, std::min<int64_t>(16, sms / std::max<int64_t>(slices, 1)));
+        const int64_t ctas = std::min<int64_t>(slices * q, sms);
+        if (ctas > best) { best = ctas; bestW = w; bestQ = q; }
+    }
+    while (bestW > 1 && bestW / 2 >= K) bestW /= 2;
+    *W = bestW;
+    *Q = bestQ;
 }
 
 extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr,
@@ -200,7 +216,16 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     h->flags = opt.flags;
     h->acc = opt.acc;
     h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
-    h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : choose_W(opt.K, cplx);
+    {
+        int w = 0, q = 1;
+        choose_shape(opt.K, cplx, sm_count(), &w, &q);
+        h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : w;
+        h->Q = opt.ctas_per_slice > 0 ? opt.ctas_per_slice : (opt.chains_per_cta > 0 ? 1 : q);
+        if (h->Q > 16) {
+            delete h;
+            return fail(nullptr, MCINV_E_ARG, "ctas_per_slice must be <= 16");
+        }
+    }
     {
         // V chains per lane (one vector load per gather) when K allows it
         const int vmax = cplx ? 2 : 4;
@@ -212,12 +237,22 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
                         32 * h->V, (long long)opt.K);
         }
     }
-    h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 256;
+    h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 512;
     if (h->threads % 32 || h->threads > 512) {
         delete h;
         return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 512");
     }
     h->slices = (int)((opt.K + h->W - 1) / h->W);
+    if (h->Q > 1) {
+        // fall back to smaller clusters if this one cannot be resident
+        int q = h->Q;
+        while (q > 1 && max_active_clusters(cplx, h->LPR, h->V, h->threads, q) < 1) --q;
+        if (q != h->Q && opt.ctas_per_slice > 0) {
+            delete h;
+            return fail(nullptr, MCINV_E_UNSUPPORTED, "a cluster of %d CTAs of %d threads cannot be resident", opt.ctas_per_slice, opt.threads_per_cta);
+        }
+        h->Q = q;
+    }
     const int Greq = opt.groups > 0 ? opt.groups : 32;
     h->G = 1;
     for (int g = std::min(Greq, h->slices); g >= 1; --g)
@@ -273,6 +308,14 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     {
         std::vector<int32_t> fill(lev_ptr.begin(), lev_ptr.end() - 1);
         for (int64_t i = 0; i < n; ++i) perm[fill[level[i]]++] = (int32_t)i;
+        // rows of one level are independent: order them by decreasing work so
+        // the rows a warp takes together cost about the same
+        for (int l = 0; l < nlev; ++l)
+            std::stable_sort(perm.begin() + lev_ptr[l], perm.begin() + lev_ptr[l + 1], [&](int32_t x, int32_t y) {
+                const int64_t dx = (row_ptr[x + 1] - row_ptr[x]) + (wcount[x + 1] - wcount[x]);
+                const int64_t dy = (row_ptr[y + 1] - row_ptr[y]) + (wcount[y + 1] - wcount[y]);
+                return dx > dy;
+            });
     }
 
     // ---- pack rows by position
@@ -445,6 +488,7 @@ static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumula
         a.cyc0_in_batch = cyc0_in_batch;
     }
     a.status = h->d_status;
+    a.ctas_per_slice = h->Q;
     return a;
 }
 
@@ -624,6 +668,7 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     if (!h || !info) return fail(h, MCINV_E_ARG, "NULL argument");
     info->n = h->n; info->nnz = h->nnz; info->K = h->K;
     info->is_complex = h->cplx; info->chains_per_cta = h->W; info->threads_per_cta = h->threads;
+    info->ctas_per_slice = h->Q; info->chains_per_lane = h->V;
     info->slices = h->slices; info->groups = h->G; info->levels = h->nlev;
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;

@@ -51,6 +51,7 @@ struct SweepArgs {
     long long ldsh;            // elements per shadow row (batch_cycles * kp)
     long long kp;              // elements per cycle block: K (x2 complex) rounded up to 64
     int cyc0_in_batch;         // shadow column block of this launch's first cycle
+    int ctas_per_slice;        // Q: CTAs (one thread-block cluster) per chain slice
     int *status;               // bit 0: a chain diverged
 };
 
@@ -63,6 +64,9 @@ cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int
 // is 1 or the vector width (4 real, 2 complex) and then divides K.
 cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int chains_per_lane,
                          int slices, int threads, cudaStream_t s);
+
+// Clusters of q CTAs of the sweep that can be resident at once (0: not launchable).
+int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q);
 
 // accumulate.cu
 cudaError_t launch_diag_fold(int cplx, int n, int slices, int G, void *diag_part, double *acc,

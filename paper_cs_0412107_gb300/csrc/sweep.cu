@@ -254,7 +254,29 @@ struct Lane {
 // C^dagger are fetched U at a time (read-only path), then all 2U gathers of z
 // and w are issued before any FMA consumes them.
 // ---------------------------------------------------------------------------
-template <bool CPLX, int LPR, int V, int U>
+// State reads of the cluster variant go to L2 (ld.global.cg): rows written by
+// another CTA of the cluster are seen after the cluster barrier, never a stale
+// L1 line.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_state(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
 __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
 {
     using P = Prec<CPLX>;
@@ -269,11 +291,16 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
     const int nwarps = blockDim.x >> 5;
     const int sub = lane / LPR;
     const int cl = lane % LPR;
-    const int slice = blockIdx.x;
+    // Q CTAs (a thread-block cluster) share one chain slice and split each
+    // level's rows; Q = 1 without clusters
+    const int Q = CLUSTER ? a.ctas_per_slice : 1;
+    const int rank = CLUSTER ? (int)cluster_rank() : 0;
+    const int slice = blockIdx.x / Q;
     const int c0 = (slice * LPR + cl) * V;  // first chain of this lane (K % V == 0)
     const bool chain_ok = c0 < a.K;
     const size_t K = (size_t)a.K;
-    const int stride = nwarps * RPW;
+    const int stride = Q * nwarps * RPW;
+    const int first = (rank * nwarps + warp) * RPW;
     const Ent *__restrict__ zent = (const Ent *)a.zent;
     const Ent *__restrict__ went = (const Ent *)a.went;
     const Cst *__restrict__ cst = (const Cst *)a.cst;
@@ -294,7 +321,7 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
         const int shcol = a.cyc0_in_batch + cyc;
         for (int lev = 0; lev < a.nlev; ++lev) {
             const int pb = __ldg(&a.lev_ptr[lev]), pe = __ldg(&a.lev_ptr[lev + 1]);
-            for (int base = pb + warp * RPW; base < pe; base += stride) {
+            for (int base = pb + first; base < pe; base += stride) {
                 const int p = base + sub;
                 const bool ok = chain_ok && p < pe;
                 S prod = P::zero();
@@ -318,11 +345,11 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                             xw[u] = L::zero();
                             if (ez + u < zeN) {
                                 const T *src = enz[u].col < i ? zn : zo;
-                                xz[u] = src[((size_t)enz[u].col * K + c0) / V];
+                                xz[u] = ld_state<CLUSTER>(&src[((size_t)enz[u].col * K + c0) / V]);
                             }
                             if (ew + u < weN) {
                                 const T *src = enw[u].col < i ? wn : wo;
-                                xw[u] = src[((size_t)enw[u].col * K + c0) / V];
+                                xw[u] = ld_state<CLUSTER>(&src[((size_t)enw[u].col * K + c0) / V]);
                             }
                         }
 #pragma unroll
@@ -388,26 +415,52 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                     if (ok && cl == 0) diag[i] = P::add(diag[i], prod);
                 }
             }
-            __syncthreads();
+            if constexpr (CLUSTER) cluster_barrier();
+            else __syncthreads();
         }
         cur ^= 1;
     }
     if (diverged) atomicOr(a.status, 1);
 }
 
+template <bool CPLX, int LPR, int V, int U>
+static cudaError_t launch_one(const SweepArgs &a, int slices, int threads, cudaStream_t s)
+{
+    if (a.ctas_per_slice <= 1) {
+        cc_sweep_kernel<CPLX, LPR, V, U, false><<<slices, threads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    auto kern = cc_sweep_kernel<CPLX, LPR, V, U, true>;
+    if (a.ctas_per_slice > 8) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(slices * a.ctas_per_slice));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.ctas_per_slice;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <bool CPLX, int V, int U>
 static cudaError_t launch_sweep_v(const SweepArgs &a, int LPR, int slices, int threads, cudaStream_t s)
 {
     switch (LPR) {
-    case 1: cc_sweep_kernel<CPLX, 1, V, U><<<slices, threads, 0, s>>>(a); break;
-    case 2: cc_sweep_kernel<CPLX, 2, V, U><<<slices, threads, 0, s>>>(a); break;
-    case 4: cc_sweep_kernel<CPLX, 4, V, U><<<slices, threads, 0, s>>>(a); break;
-    case 8: cc_sweep_kernel<CPLX, 8, V, U><<<slices, threads, 0, s>>>(a); break;
-    case 16: cc_sweep_kernel<CPLX, 16, V, U><<<slices, threads, 0, s>>>(a); break;
-    case 32: cc_sweep_kernel<CPLX, 32, V, U><<<slices, threads, 0, s>>>(a); break;
+    case 1: return launch_one<CPLX, 1, V, U>(a, slices, threads, s);
+    case 2: return launch_one<CPLX, 2, V, U>(a, slices, threads, s);
+    case 4: return launch_one<CPLX, 4, V, U>(a, slices, threads, s);
+    case 8: return launch_one<CPLX, 8, V, U>(a, slices, threads, s);
+    case 16: return launch_one<CPLX, 16, V, U>(a, slices, threads, s);
+    case 32: return launch_one<CPLX, 32, V, U>(a, slices, threads, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int chains_per_lane,
@@ -421,6 +474,40 @@ cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int ch
         if (chains_per_lane == 1) return launch_sweep_v<false, 1, 8>(a, lanes_per_row, slices, threads, s);
     }
     return cudaErrorInvalidValue;
+}
+
+int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q)
+{
+    // how many clusters of q CTAs can be resident at once (0 if none)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)q);
+    cfg.blockDim = dim3((unsigned)threads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)q;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const void *k = nullptr;
+#define MCINV_PICK(C, L, V, U)                                                                       \
+    if (cplx == C && lanes_per_row == L && chains_per_lane == V) k = (const void *)cc_sweep_kernel<C, L, V, U, true>;
+#define MCINV_PICK_L(C, V, U) MCINV_PICK(C, 1, V, U) MCINV_PICK(C, 2, V, U) MCINV_PICK(C, 4, V, U) \
+    MCINV_PICK(C, 8, V, U) MCINV_PICK(C, 16, V, U) MCINV_PICK(C, 32, V, U)
+    MCINV_PICK_L(true, 2, 4)
+    MCINV_PICK_L(true, 1, 4)
+    MCINV_PICK_L(false, 4, 8)
+    MCINV_PICK_L(false, 1, 8)
+#undef MCINV_PICK_L
+#undef MCINV_PICK
+    if (!k) return 0;
+    if (q > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace mcinv

@@ -48,13 +48,15 @@ class mcinv_options(ctypes.Structure):
                 ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("block_rows", ctypes.POINTER(ctypes.c_int64)), ("n_block_rows", ctypes.c_int64),
-                ("block_cols", ctypes.POINTER(ctypes.c_int64)), ("n_block_cols", ctypes.c_int64)]
+                ("block_cols", ctypes.POINTER(ctypes.c_int64)), ("n_block_cols", ctypes.c_int64),
+                ("ctas_per_slice", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mcinv_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("K", ctypes.c_int64),
                 ("is_complex", ctypes.c_int32), ("chains_per_cta", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("ctas_per_slice", ctypes.c_int32), ("chains_per_lane", ctypes.c_int32),
                 ("groups", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("batch_cycles", ctypes.c_int32), ("acc", ctypes.c_int32),
                 ("cycle", ctypes.c_int64), ("samples", ctypes.c_int64),
@@ -153,7 +155,8 @@ class Handle:
 
 def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_id=0, groups=0,
                  batch_cycles=0, acc=MCINV_ACC_BF16_TC, chains_per_cta=0, threads_per_cta=0,
-                 flags=0, stream="current", block_rows=None, block_cols=None) -> Handle:
+                 ctas_per_slice=0, flags=0, stream="current", block_rows=None,
+                 block_cols=None) -> Handle:
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     is_complex = np.iscomplexobj(val)
@@ -166,7 +169,7 @@ def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_i
     opt = mcinv_default_options(K=K, seed=seed, chain_base=chain_base, matrix_id=matrix_id,
                                 groups=groups, batch_cycles=batch_cycles, acc=acc,
                                 chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta,
-                                flags=flags)
+                                ctas_per_slice=ctas_per_slice, flags=flags)
     opt.stream = current_stream() if stream == "current" else stream
     keep = []
     nR = nS = 0

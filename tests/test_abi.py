@@ -37,10 +37,11 @@ def test_exports_every_declared_symbol(L):
 def test_options_layout_matches_header(L):
     opt = mcinv.mcinv_default_options()
     assert opt.K == 1024 and opt.acc == mcinv.MCINV_ACC_BF16_TC
-    # C layout: 3 x 8-byte fields, 7 x 4-byte fields, 4 bytes of padding, 5 x 8-byte fields
-    assert ctypes.sizeof(mcinv.mcinv_options) == 96
+    # C layout: 3 x 8-byte fields, 7 x 4-byte fields, 4 bytes of padding, 5 x 8-byte
+    # fields, 2 x 4-byte fields
+    assert ctypes.sizeof(mcinv.mcinv_options) == 104
     assert mcinv.mcinv_options.stream.offset == 56
-    assert ctypes.sizeof(mcinv.mcinv_info_t) == 96
+    assert ctypes.sizeof(mcinv.mcinv_info_t) == 104
 
 
 def _create(n, rp, col, val, **kw):

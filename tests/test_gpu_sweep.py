@@ -103,6 +103,30 @@ def test_trajectory_complex_slice_shapes(W, K):
     _assert_close(errs)
 
 
+@pytest.mark.parametrize("Q", [2, 3, 8, 16])
+@pytest.mark.parametrize("W,threads", [(64, 512), (32, 128), (128, 256)])
+def test_trajectory_cluster_slices(Q, W, threads):
+    """A thread-block cluster of Q CTAs per chain slice (rows of each level split
+    across the cluster, cluster barrier between levels) gives the same sweep."""
+    csr = wl.pedigree(3000, 1.2, 3)
+    _, _, errs = run_pair(csr, 256, [2, 12], chains_per_cta=W, threads_per_cta=threads, ctas_per_slice=Q)
+    _assert_close(errs)
+
+
+def test_trajectory_cluster_complex():
+    csr = wl.u1_lattice((6, 5, 4, 3), 0.06, 0.04, seed=9)
+    _, _, errs = run_pair(csr, 128, [3], chains_per_cta=64, threads_per_cta=256, ctas_per_slice=4)
+    _assert_close(errs)
+
+
+def test_default_shape_uses_clusters_for_few_slices():
+    csr = wl.pedigree(2000, 1.2, 4)
+    h = mcinv.create_from_csr(csr, K=1024, acc=mcinv.MCINV_ACC_FP32_SIMT)
+    info = mcinv.mcinv_info(h)
+    assert info["slices"] * info["ctas_per_slice"] >= 128
+    assert info["chains_per_lane"] == 4
+
+
 def test_trajectory_chain_base_and_matrix_id():
     csr = wl.random_dominant(100, 3, 1.5, 2)
     _, _, errs = run_pair(csr, 20, [5], seed=2 ** 40 + 17, matrix_id=9, chain_base=1000)
