@@ -7,19 +7,21 @@
 
 namespace mcinv {
 
-// acc[g][i] += sum over the group's slices of part[s][i]; part is cleared.
-// Slices are grouped contiguously: group g owns slices [g*spg, (g+1)*spg).
+// acc[g][perm[p]] += sum over the group's units of part[u][p]; part is
+// cleared.  Units are grouped contiguously: group g owns units
+// [g*upg, (g+1)*upg); part is indexed by position p, acc by row.
 template <typename T, int NV>
-__global__ void diag_fold_kernel(int n, int slices, int G, T *__restrict__ part,
-                                 double *__restrict__ acc)
+__global__ void diag_fold_kernel(int n, int units, int G, const int *__restrict__ perm,
+                                 T *__restrict__ part, double *__restrict__ acc)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = blockIdx.y;
-    if (i >= n) return;
-    const int spg = slices / G;
+    if (p >= n) return;
+    const int upg = units / G;
+    const int i = perm[p];
     double s[NV] = {};
-    for (int k = 0; k < spg; ++k) {
-        T *src = part + (size_t)(g * spg + k) * n + i;
+    for (int k = 0; k < upg; ++k) {
+        T *src = part + (size_t)(g * upg + k) * n + p;
         const float *f = (const float *)src;
 #pragma unroll
         for (int v = 0; v < NV; ++v) s[v] += (double)f[v];
@@ -29,12 +31,12 @@ __global__ void diag_fold_kernel(int n, int slices, int G, T *__restrict__ part,
     for (int v = 0; v < NV; ++v) acc[((size_t)g * n + i) * NV + v] += s[v];
 }
 
-cudaError_t launch_diag_fold(int cplx, int n, int slices, int G, void *diag_part, double *acc,
-                             cudaStream_t s)
+cudaError_t launch_diag_fold(int cplx, int n, int units, int G, const int *perm, void *diag_part,
+                             double *acc, cudaStream_t s)
 {
     dim3 grid((n + 255) / 256, G);
-    if (cplx) diag_fold_kernel<float2, 2><<<grid, 256, 0, s>>>(n, slices, G, (float2 *)diag_part, acc);
-    else diag_fold_kernel<float, 1><<<grid, 256, 0, s>>>(n, slices, G, (float *)diag_part, acc);
+    if (cplx) diag_fold_kernel<float2, 2><<<grid, 256, 0, s>>>(n, units, G, perm, (float2 *)diag_part, acc);
+    else diag_fold_kernel<float, 1><<<grid, 256, 0, s>>>(n, units, G, perm, (float *)diag_part, acc);
     return cudaGetLastError();
 }
 

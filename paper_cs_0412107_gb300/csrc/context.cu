@@ -27,8 +27,10 @@ struct mcinv_ctx {
     cudaStream_t stream = nullptr;
     int nlev = 0, nw = 0;
     // device arrays
-    int *d_lev_ptr = nullptr, *d_perm = nullptr, *d_zptr = nullptr, *d_wptr = nullptr;
-    void *d_zent = nullptr, *d_went = nullptr, *d_cst = nullptr;
+    int *d_perm = nullptr, *d_pos = nullptr;
+    uint8_t *d_stream = nullptr;
+    ChunkDesc *d_chunks = nullptr;
+    int nchunks = 0, blob_max = 0, seg = 1, units = 0;
     uint32_t *d_noise = nullptr;
     void *d_z[2] = {nullptr, nullptr}, *d_w[2] = {nullptr, nullptr};
     int cur = 0;
@@ -243,23 +245,6 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 512");
     }
     h->slices = (int)((opt.K + h->W - 1) / h->W);
-    if (h->Q > 1) {
-        // fall back to smaller clusters if this one cannot be resident
-        int q = h->Q;
-        while (q > 1 && max_active_clusters(cplx, h->LPR, h->V, h->threads, q) < 1) --q;
-        if (q != h->Q && opt.ctas_per_slice > 0) {
-            delete h;
-            return fail(nullptr, MCINV_E_UNSUPPORTED, "a cluster of %d CTAs of %d threads cannot be resident", opt.ctas_per_slice, opt.threads_per_cta);
-        }
-        h->Q = q;
-    }
-    const int Greq = opt.groups > 0 ? opt.groups : 32;
-    h->G = 1;
-    for (int g = std::min(Greq, h->slices); g >= 1; --g)
-        if (h->slices % g == 0) { h->G = g; break; }
-    h->counts.assign(h->G, 0.0);
-    for (int s = 0; s < h->slices; ++s)
-        h->counts[s / (h->slices / h->G)] += (double)std::min<int64_t>(h->W, opt.K - (int64_t)s * h->W);
     h->nw = (int)((opt.K + 31) / 32);
     mcinv_t H = h;
     auto bail = [&](mcinv_status st) {
@@ -318,52 +303,109 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
             });
     }
 
-    // ---- pack rows by position
-    std::vector<int32_t> zptr(n + 1, 0), wptr(n + 1, 0);
-    for (int64_t p = 0; p < n; ++p) {
-        const int64_t i = perm[p];
-        zptr[p + 1] = zptr[p] + (int32_t)(row_ptr[i + 1] - row_ptr[i] - 1);
-        wptr[p + 1] = wptr[p] + (int32_t)(wcount[i + 1] - wcount[i]);
+    // ---- the chunk stream (see internal.h): per chunk of a level, the row
+    //      records, constants (filled on the GPU below) and entries of C and C^H
+    const size_t ent_sz = cplx ? sizeof(EntC) : sizeof(EntR);
+    const size_t cst_sz = cplx ? sizeof(CstC) : sizeof(CstR);
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    auto blob_bytes = [&](size_t rows, size_t nz, size_t nwv) {
+        return a16(16 * (rows + 1)) + a16(cst_sz * rows) + a16(ent_sz * nz) + a16(ent_sz * nwv);
+    };
+    auto zdeg = [&](int64_t i) { return (size_t)(row_ptr[i + 1] - row_ptr[i] - 1); };
+    auto wdeg = [&](int64_t i) { return (size_t)(wcount[i + 1] - wcount[i]); };
+    size_t blob_max = 64 * 1024;
+    for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, zdeg(i), wdeg(i)));
+    blob_max = (blob_max + 127) & ~(size_t)127;
+    if (blob_max > 100 * 1024) {
+        fail(h, MCINV_E_UNSUPPORTED, "a row has too many off-diagonal entries in C and C^dagger for one shared-memory chunk (limit about %zu)",
+             (size_t)(100 * 1024 - 64) / ent_sz);
+        return bail(MCINV_E_UNSUPPORTED);
     }
+    h->blob_max = (int)blob_max;
+    std::vector<ChunkDesc> chunks;
+    std::vector<long long> cst_at(n);
+    size_t stream_bytes = 0;
+    for (int l = 0; l < nlev; ++l) {
+        int64_t p = lev_ptr[l];
+        while (p < lev_ptr[l + 1]) {
+            const int64_t pb = p;
+            size_t nz = 0, nwv = 0;
+            while (p < lev_ptr[l + 1] && blob_bytes(p - pb + 1, nz + zdeg(perm[p]), nwv + wdeg(perm[p])) <= blob_max) {
+                nz += zdeg(perm[p]);
+                nwv += wdeg(perm[p]);
+                ++p;
+            }
+            ChunkDesc d{};
+            d.rows = (int)(p - pb);
+            d.pb = (int)pb;
+            d.cst_off = (int)a16(16 * (d.rows + 1));
+            d.zent_off = d.cst_off + (int)a16(cst_sz * d.rows);
+            d.went_off = d.zent_off + (int)a16(ent_sz * nz);
+            d.bytes = d.went_off + (int)a16(ent_sz * nwv);
+            d.off = (long long)stream_bytes;
+            d.flags = p == lev_ptr[l + 1] ? CHUNK_LEVEL_END : 0;
+            stream_bytes += ((size_t)d.bytes + 127) & ~(size_t)127;
+            chunks.push_back(d);
+        }
+    }
+    h->nchunks = (int)chunks.size();
+    std::vector<uint8_t> stream(stream_bytes, 0);
+    for (const ChunkDesc &d : chunks) {
+        uint8_t *blob = stream.data() + d.off;
+        RowMeta *meta = (RowMeta *)blob;
+        int zo = 0, wo = 0;
+        for (int r = 0; r < d.rows; ++r) {
+            const int64_t i = perm[d.pb + r];
+            meta[r] = RowMeta{(int)i, zo, wo, 0};
+            cst_at[d.pb + r] = d.off + d.cst_off + (long long)(r * cst_sz);
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                if (col[e] == i) continue;
+                if (!cplx) ((EntR *)(blob + d.zent_off))[zo++] = EntR{col[e], (float)val[e]};
+                else ((EntC *)(blob + d.zent_off))[zo++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
+            }
+            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) {
+                if (!cplx) ((EntR *)(blob + d.went_off))[wo++] = EntR{wcol[e], (float)wval[e]};
+                else ((EntC *)(blob + d.went_off))[wo++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
+            }
+        }
+        meta[d.rows] = RowMeta{-1, zo, wo, 0};
+    }
+    std::vector<int32_t> pos(n);
+    for (int64_t p = 0; p < n; ++p) pos[perm[p]] = (int32_t)p;
     std::vector<double> diag_pos((size_t)n * NV);
     for (int64_t p = 0; p < n; ++p)
         for (int v = 0; v < NV; ++v) diag_pos[(size_t)p * NV + v] = diag[(size_t)perm[p] * NV + v];
-    cudaError_t ce = cudaSuccess;
-    if (!cplx) {
-        std::vector<EntR> ze(zptr[n]), we(wptr[n]);
-        for (int64_t p = 0; p < n; ++p) {
-            const int64_t i = perm[p];
-            int64_t q = zptr[p];
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                if (col[e] != i) ze[q++] = EntR{col[e], (float)val[e]};
-            q = wptr[p];
-            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) we[q++] = EntR{wcol[e], (float)wval[e]};
+
+    // ---- clusters: fall back to smaller ones if this one cannot be resident
+    if (h->Q > 1) {
+        int q = h->Q;
+        while (q > 1 && max_active_clusters(cplx, h->LPR, h->V, h->threads, q, h->blob_max) < 1) --q;
+        if (q != h->Q && opt.ctas_per_slice > 0) {
+            fail(h, MCINV_E_UNSUPPORTED, "a cluster of %d CTAs of %d threads cannot be resident", opt.ctas_per_slice, h->threads);
+            return bail(MCINV_E_UNSUPPORTED);
         }
-        if ((ce = upload(h, (EntR **)&h->d_zent, ze)) != cudaSuccess || (ce = upload(h, (EntR **)&h->d_went, we)) != cudaSuccess) {
-            fail(h, MCINV_E_NOMEM, "upload: %s", cudaGetErrorString(ce));
-            return bail(MCINV_E_NOMEM);
-        }
-        ce = cudaStreamSynchronize(h->stream);
-    } else {
-        std::vector<EntC> ze(zptr[n]), we(wptr[n]);
-        for (int64_t p = 0; p < n; ++p) {
-            const int64_t i = perm[p];
-            int64_t q = zptr[p];
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                if (col[e] != i) ze[q++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
-            q = wptr[p];
-            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e)
-                we[q++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
-        }
-        if ((ce = upload(h, (EntC **)&h->d_zent, ze)) != cudaSuccess || (ce = upload(h, (EntC **)&h->d_went, we)) != cudaSuccess) {
-            fail(h, MCINV_E_NOMEM, "upload: %s", cudaGetErrorString(ce));
-            return bail(MCINV_E_NOMEM);
-        }
-        ce = cudaStreamSynchronize(h->stream);  // host vectors die at scope exit
+        h->Q = q;
     }
-    if (ce != cudaSuccess) { fail(h, MCINV_E_CUDA, "upload: %s", cudaGetErrorString(ce)); return bail(MCINV_E_CUDA); }
+
+    // ---- SE groups: the diagonal partials are kept per unit of seg lanes (seg x V
+    //      chains, a power of two dividing the slice); G groups of whole units
+    {
+        const int Greq = opt.groups > 0 ? opt.groups : 32;
+        int seg = 1;
+        while (seg * 2 <= h->LPR && (int64_t)seg * 2 * h->V * Greq <= opt.K) seg *= 2;
+        h->seg = seg;
+        const int64_t u = (int64_t)seg * h->V;
+        h->units = (int)((opt.K + u - 1) / u);
+        h->G = 1;
+        for (int g = std::min(Greq, h->units); g >= 1; --g)
+            if (h->units % g == 0) { h->G = g; break; }
+        h->counts.assign(h->G, 0.0);
+        for (int k = 0; k < h->units; ++k)
+            h->counts[k / (h->units / h->G)] += (double)std::min<int64_t>(u, opt.K - (int64_t)k * u);
+    }
 
     double *d_diag = nullptr;
+    long long *d_cst_at = nullptr;
     std::vector<int32_t> bad_init(1, 0x7fffffff);
     int *d_bad = nullptr;
 #define SETUP(call)                                                                               \
@@ -375,14 +417,14 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
             return bail(st_);                                                                     \
         }                                                                                         \
     } while (0)
-    SETUP(upload(h, &h->d_lev_ptr, lev_ptr));
+    SETUP(upload(h, &h->d_stream, stream));
+    SETUP(upload(h, &h->d_chunks, chunks));
     SETUP(upload(h, &h->d_perm, perm));
-    SETUP(upload(h, &h->d_zptr, zptr));
-    SETUP(upload(h, &h->d_wptr, wptr));
+    SETUP(upload(h, &h->d_pos, pos));
     SETUP(upload(h, &d_diag, diag_pos));
+    SETUP(upload(h, &d_cst_at, cst_at));
     SETUP(upload(h, &d_bad, bad_init));
-    SETUP(dalloc(h, (char **)&h->d_cst, (size_t)n * (cplx ? sizeof(CstC) : sizeof(CstR))));
-    SETUP(launch_constants((int)n, d_diag, cplx, h->d_cst, d_bad, h->stream));
+    SETUP(launch_constants((int)n, d_diag, cplx, h->d_stream, d_cst_at, d_bad, h->stream));
     h->launches++;
     int bad = 0x7fffffff;
     SETUP(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -405,8 +447,8 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     SETUP(dalloc(h, &h->d_status, 1));
     SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     if (!(h->flags & MCINV_F_NO_DIAG)) {
-        SETUP(dalloc(h, (char **)&h->d_diag_part, (size_t)h->slices * n * esz));
-        SETUP(cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->slices * n * esz, h->stream));
+        SETUP(dalloc(h, (char **)&h->d_diag_part, (size_t)h->units * n * esz));
+        SETUP(cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->units * n * esz, h->stream));
         SETUP(dalloc(h, &h->d_diag_acc, (size_t)h->G * n * NV));
         SETUP(cudaMemsetAsync(h->d_diag_acc, 0, (size_t)h->G * n * NV * sizeof(double), h->stream));
         SETUP(upload(h, &h->d_counts, h->counts));
@@ -442,8 +484,10 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         SETUP(cudaMemsetAsync(h->d_bsum, 0, elems * NV * sizeof(double), h->stream));
         SETUP(cudaMemsetAsync(h->d_bsq, 0, elems * NV * sizeof(double), h->stream));
         if (h->acc == MCINV_ACC_BF16_TC) {
-            SETUP(upload(h, &h->d_rpos, rpos));
-            SETUP(upload(h, &h->d_spos, spos));
+            std::vector<int32_t> rpos_p(n), spos_p(n);
+            for (int64_t p = 0; p < n; ++p) { rpos_p[p] = rpos[perm[p]]; spos_p[p] = spos[perm[p]]; }
+            SETUP(upload(h, &h->d_rpos, rpos_p));
+            SETUP(upload(h, &h->d_spos, spos_p));
             // shadow rows hold B cycle blocks of K chains (x2 for re,im), each block
             // padded to 64 elements with zeros
             h->kp = (opt.K * NV + 63) / 64 * 64;
@@ -474,14 +518,14 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
 static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumulate, int cyc0_in_batch)
 {
     SweepArgs a{};
-    a.n = (int)h->n; a.K = (int)h->K; a.nlev = h->nlev; a.nw = h->nw;
-    a.lev_ptr = h->d_lev_ptr; a.perm = h->d_perm;
-    a.zptr = h->d_zptr; a.zent = h->d_zent; a.wptr = h->d_wptr; a.went = h->d_went;
-    a.cst = h->d_cst;
+    a.n = (int)h->n; a.K = (int)h->K; a.nw = h->nw;
+    a.nchunks = h->nchunks; a.blob_max = h->blob_max;
+    a.stream = h->d_stream; a.chunks = h->d_chunks;
     a.noise = h->d_noise + (size_t)noise_cyc * h->nw * (size_t)h->n;
     a.z[0] = h->d_z[0]; a.z[1] = h->d_z[1]; a.w[0] = h->d_w[0]; a.w[1] = h->d_w[1];
     a.cur = h->cur; a.ncyc = ncyc;
     a.diag_part = accumulate ? h->d_diag_part : nullptr;
+    a.seg = h->seg;
     if (accumulate && h->gemm) {
         a.rpos = h->d_rpos; a.spos = h->d_spos;
         a.zsh = h->d_zsh; a.wsh = h->d_wsh; a.ldsh = h->ldsh; a.kp = h->kp;
@@ -498,7 +542,7 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
     while (cycles > 0) {
         const int b = (int)std::min<int64_t>(h->B, cycles);
         LAUNCH_K(h, MCINV_KERNEL_NOISE, launch_noise(h->seed, h->matrix_id, (uint64_t)h->chain_base, (int)h->K, (int)h->n,
-                               (uint32_t)h->cycle, b, h->d_noise, h->stream));
+                               (uint32_t)h->cycle, b, h->d_pos, h->d_noise, h->stream));
         if (block && h->acc == MCINV_ACC_FP32_SIMT) {
             for (int k = 0; k < b; ++k) {
                 SweepArgs a = sweep_args(h, 1, k, true, 0);
@@ -524,7 +568,7 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
             h->block_cycles += b;
         }
         if (accumulate && h->d_diag_part) {
-            LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_diag_fold(h->cplx, (int)h->n, h->slices, h->G, h->d_diag_part, h->d_diag_acc, h->stream));
+            LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_diag_fold(h->cplx, (int)h->n, h->units, h->G, h->d_perm, h->d_diag_part, h->d_diag_acc, h->stream));
         }
         h->cycle += b;
         if (accumulate) h->samples += b;
@@ -554,6 +598,7 @@ extern "C" mcinv_status mcinv_sync(mcinv_t h)
     CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (status & 2) return fail(h, MCINV_E_TIMEOUT, "a bounded wait in the tensor-core contraction expired; its block batch was abandoned");
+    if (status & 4) return fail(h, MCINV_E_TIMEOUT, "a bounded wait for matrix data in the sweep expired; the sweep was abandoned");
     if (status & 1) return fail(h, MCINV_E_DIVERGED, "a chain diverged (non-finite or |value| > 1e30): the sweep does not converge for this matrix");
     return MCINV_OK;
 }
@@ -627,7 +672,7 @@ extern "C" mcinv_status mcinv_reset_estimates(mcinv_t h)
     const int NV = h->cplx ? 2 : 1;
     const size_t esz = NV * sizeof(float);
     if (h->d_diag_part) {
-        CUDA_TRY(h, cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->slices * h->n * esz, h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->units * h->n * esz, h->stream));
         CUDA_TRY(h, cudaMemsetAsync(h->d_diag_acc, 0, (size_t)h->G * h->n * NV * sizeof(double), h->stream));
     }
     if (h->nR) {

@@ -26,51 +26,76 @@ struct __align__(16) CstC {
     float2 alpha, beta, inv_d, pad;
 };
 
-// Arguments of the coupled sweep.  Rows are visited in "positions": the rows
-// of Gauss-Seidel dependency level 0, then level 1, ...; within a level rows
-// are independent (no row depends on another row of its level through C or
-// C^dagger), so a CTA may update them concurrently and get exactly the
-// in-place ascending-row result of Eqs. 4/5.
+// The sweep reads the matrix as a stream of chunks, in "position" order: the
+// rows of Gauss-Seidel dependency level 0, then level 1, ... (rows of one
+// level do not read each other through C or C^dagger, so a CTA may update
+// them concurrently and get exactly the in-place ascending-row result of
+// Eqs. 4/5).  A chunk is a run of positions inside one level whose data fit
+// one shared-memory buffer; its blob is
+//   RowMeta[rows + 1] | Cst[rows] | C entries | C^dagger entries
+// (each part 16-byte aligned) and is copied to shared memory in one bulk copy.
+struct RowMeta {
+    int row;   // row index i of C
+    int zoff;  // first entry of row i of C within the chunk's C entries (row rows: end)
+    int woff;  // same for C^dagger
+    int pad;
+};
+
+struct ChunkDesc {
+    long long off;  // byte offset of the blob in the stream (16-byte aligned)
+    int bytes;      // blob size (multiple of 16)
+    int rows;       // positions pb .. pb + rows - 1
+    int pb;
+    int cst_off, zent_off, went_off;  // byte offsets of the parts within the blob
+    int flags;      // CHUNK_LEVEL_END: the next chunk starts a new level
+    int pad;
+};
+constexpr int CHUNK_LEVEL_END = 1;
+
+// Arguments of the coupled sweep.
 struct SweepArgs {
-    int n, K, nlev, nw;        // nw = ceil(K/32) noise words per row
-    const int *lev_ptr;        // [nlev+1] positions
-    const int *perm;           // [n] row at position p
-    const int *zptr;           // [n+1] by position: off-diagonal entries of row perm[p] of C
-    const void *zent;          // EntR / EntC
-    const int *wptr;           // [n+1] by position: off-diagonal entries of row perm[p] of C^dagger
-    const void *went;
-    const void *cst;           // [n] by position: CstR / CstC
-    const uint32_t *noise;     // [ncyc][nw][n] Z2 sign bits (bit c%32 of word c/32), 1 -> phi = -1
-    void *z[2], *w[2];         // double-buffered chain state [n][K] (float / float2)
+    int n, K, nw;              // nw = ceil(K/32) noise words per position
+    int nchunks, blob_max;     // chunks per cycle; bytes of one shared-memory buffer
+    const uint8_t *stream;     // chunk blobs
+    const ChunkDesc *chunks;
+    const uint32_t *noise;     // [ncyc][nw][n] by position: Z2 sign bits (bit c%32 of word c/32), 1 -> phi = -1
+    void *z[2], *w[2];         // double-buffered chain state [n][K] by row (float / float2)
     int cur;                   // buffer holding the state before the first cycle of this launch
     int ncyc;                  // cycles this launch runs
-    void *diag_part;           // [slices][n] running sum of z_i conj(w_i) over the slice's chains, or null
+    // running sums of z_i conj(w_i) over "units" of seg lanes (seg * V chains):
+    // [units][n] by position, read-modify-write by the one lane that owns it; null: off
+    void *diag_part;
+    int seg;
     // BF16 shadows of rows in R (z) and S (w) for the tensor-core block contraction
-    const int *rpos, *spos;    // [n] -> index in R / S, or -1; null disables shadows
+    const int *rpos, *spos;    // [n] by position -> index in R / S, or -1; null disables shadows
     uint16_t *zsh, *wsh;
     long long ldsh;            // elements per shadow row (batch_cycles * kp)
     long long kp;              // elements per cycle block: K (x2 complex) rounded up to 64
     int cyc0_in_batch;         // shadow column block of this launch's first cycle
     int ctas_per_slice;        // Q: CTAs (one thread-block cluster) per chain slice
-    int *status;               // bit 0: a chain diverged
+    int *status;               // bit 0: a chain diverged; bit 2: a staging wait expired
 };
 
 // Launchers (sweep.cu)
+// noise plane by position: pos[row] gives the position of each row
 cudaError_t launch_noise(uint64_t seed, uint32_t matrix, uint64_t chain_base, int K, int n,
-                         uint32_t cycle0, int ncyc, uint32_t *out, cudaStream_t s);
-cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int *bad,
-                             cudaStream_t s);
+                         uint32_t cycle0, int ncyc, const int *pos, uint32_t *out, cudaStream_t s);
+// per-row constants written into the chunk stream at stream + cst_at[p] (by position)
+cudaError_t launch_constants(int n, const double *diag, int cplx, uint8_t *stream,
+                             const long long *cst_at, int *bad, cudaStream_t s);
 // slices CTAs of lanes_per_row x chains_per_lane chains each; chains_per_lane
 // is 1 or the vector width (4 real, 2 complex) and then divides K.
 cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int chains_per_lane,
                          int slices, int threads, cudaStream_t s);
 
 // Clusters of q CTAs of the sweep that can be resident at once (0: not launchable).
-int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q);
+int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q,
+                        int blob_max);
 
 // accumulate.cu
-cudaError_t launch_diag_fold(int cplx, int n, int slices, int G, void *diag_part, double *acc,
-                             cudaStream_t s);
+// acc[g][perm[p]] += sum of the group's units' part[u][p]; part is cleared
+cudaError_t launch_diag_fold(int cplx, int n, int units, int G, const int *perm, void *diag_part,
+                             double *acc, cudaStream_t s);
 cudaError_t launch_block_simt(int cplx, int K, const void *z, const void *w, const int *R, int nR,
                               const int *S, int nS, float *blk, cudaStream_t s);
 cudaError_t launch_block_fold(int cplx, long long elems, double scale_sq, float *blk,

@@ -31,14 +31,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k)
     return x;
 }
 
-// Noise plane for cycles cycle0 .. cycle0+ncyc-1: out[cyc][cw][row] holds the
-// sign bits of chains 32cw .. 32cw+31 at `row`.  One Philox call yields the
-// 128 bits of rows 128rb .. 128rb+127 of one chain (row r -> bit r%32 of word
-// (r/32)%4); a warp of 32 chains transposes them with ballots so every word
-// is written once, coalesced along rows.
+// Noise plane for cycles cycle0 .. cycle0+ncyc-1: out[cyc][cw][pos[row]] holds
+// the sign bits of chains 32cw .. 32cw+31 at `row`.  One Philox call yields
+// the 128 bits of rows 128rb .. 128rb+127 of one chain (row r -> bit r%32 of
+// word (r/32)%4); a warp of 32 chains transposes them with ballots so every
+// word is written once.  The plane is stored by position so the sweep reads
+// it coalesced.
 __global__ void __launch_bounds__(128) noise_kernel(uint64_t seed, uint32_t matrix,
                                                     uint64_t chain_base, int K, int n, int nw,
-                                                    uint32_t cycle0, uint32_t *__restrict__ out)
+                                                    uint32_t cycle0, const int *__restrict__ pos,
+                                                    uint32_t *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     const int cw = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -60,16 +62,16 @@ __global__ void __launch_bounds__(128) noise_kernel(uint64_t seed, uint32_t matr
             if (lane == b) mine = bal;
         }
         const int row = rb * 128 + q * 32 + lane;
-        if (row < n) dst[row] = mine;
+        if (row < n) dst[pos[row]] = mine;
     }
 }
 
 cudaError_t launch_noise(uint64_t seed, uint32_t matrix, uint64_t chain_base, int K, int n,
-                         uint32_t cycle0, int ncyc, uint32_t *out, cudaStream_t s)
+                         uint32_t cycle0, int ncyc, const int *pos, uint32_t *out, cudaStream_t s)
 {
     const int nw = (K + 31) / 32;
     dim3 grid((n + 127) / 128, (nw + 3) / 4, ncyc);
-    noise_kernel<<<grid, 128, 0, s>>>(seed, matrix, chain_base, K, n, nw, cycle0, out);
+    noise_kernel<<<grid, 128, 0, s>>>(seed, matrix, chain_base, K, n, nw, cycle0, pos, out);
     return cudaGetLastError();
 }
 
@@ -102,8 +104,8 @@ __device__ inline double2 csqrt64(double a, double b)
     return make_double2(fabs(b) / (2.0 * t), copysign(t, b));
 }
 
-__global__ void constants_kernel(int n, const double *__restrict__ diag, int cplx, void *cst,
-                                 int *bad)
+__global__ void constants_kernel(int n, const double *__restrict__ diag, int cplx, uint8_t *stream,
+                                 const long long *__restrict__ cst_at, int *bad)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -116,7 +118,7 @@ __global__ void constants_kernel(int n, const double *__restrict__ diag, int cpl
         k.beta = (float)((c > 0.0 ? 1.0 : -1.0) / r);
         k.inv_d = (float)(1.0 / c);
         k.pad = 0.f;
-        ((CstR *)cst)[p] = k;
+        *(CstR *)(stream + cst_at[p]) = k;
     } else {
         const double a = diag[2 * p], b = diag[2 * p + 1];
         if (!isfinite(a) || !isfinite(b) || (a == 0.0 && b == 0.0)) { atomicMin(bad, p); return; }
@@ -129,14 +131,14 @@ __global__ void constants_kernel(int n, const double *__restrict__ diag, int cpl
         k.beta = make_float2((float)be.x, (float)be.y);
         k.inv_d = make_float2((float)d.x, (float)d.y);
         k.pad = make_float2(0.f, 0.f);
-        ((CstC *)cst)[p] = k;
+        *(CstC *)(stream + cst_at[p]) = k;
     }
 }
 
-cudaError_t launch_constants(int n, const double *diag, int cplx, void *cst, int *bad,
-                             cudaStream_t s)
+cudaError_t launch_constants(int n, const double *diag, int cplx, uint8_t *stream,
+                             const long long *cst_at, int *bad, cudaStream_t s)
 {
-    constants_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, diag, cplx, cst, bad);
+    constants_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, diag, cplx, stream, cst_at, bad);
     return cudaGetLastError();
 }
 
@@ -240,20 +242,6 @@ struct Lane {
     }
 };
 
-// ---------------------------------------------------------------------------
-// The coupled sweep.  CTA = one slice of LPR x V chains (LPR lanes per row, V
-// chains per lane), for all rows and `ncyc` cycles; chains are independent,
-// so CTAs never communicate.  Within a cycle the CTA walks the dependency
-// levels; rows of a level are spread over the warps (32/LPR rows per warp
-// instruction) and a block barrier separates levels.  State is
-// double-buffered: a row reads z_j (j < i) from the buffer being written this
-// cycle and z_j (j > i) from last cycle's buffer, which is exactly the
-// in-place semantics of Eq. 4 (and of Eq. 5 for w).
-//
-// Memory-level parallelism: the off-diagonal entries of the row in C and in
-// C^dagger are fetched U at a time (read-only path), then all 2U gathers of z
-// and w are issued before any FMA consumes them.
-// ---------------------------------------------------------------------------
 // State reads of the cluster variant go to L2 (ld.global.cg): rows written by
 // another CTA of the cluster are seen after the cluster barrier, never a stale
 // L1 line.
@@ -276,6 +264,60 @@ __device__ __forceinline__ uint32_t cluster_rank()
     return r;
 }
 
+// ---------------------------------------------------------------------------
+// Staging of the chunk stream: one elected thread moves each chunk's blob into
+// one of two shared-memory buffers with a bulk async copy that completes on
+// the buffer's mbarrier; every wait is bounded (2 s of globaltimer).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void stage_chunk(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (gtimer() - t0 > 2000000000ull) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The coupled sweep.  A chain slice = LPR lanes x V chains per lane; Q CTAs
+// (one thread-block cluster, Q = 1 without) share a slice and split each
+// chunk's rows.  Chains are independent, so slices never communicate.  Per
+// cycle the CTA walks the chunk stream; a block barrier ends every chunk (its
+// buffer is recycled) and a cluster barrier ends every level.  State is
+// double-buffered: a row reads z_j (j < i) from the buffer being written this
+// cycle and z_j (j > i) from last cycle's buffer, exactly the in-place
+// semantics of Eq. 4 (and of Eq. 5 for w).
+//
+// Per row: the row record, constants and entries come from shared memory;
+// the noise word and the diagonal partial are loaded first (they depend only
+// on the position); then all 2U gathers of z and w are issued before any FMA
+// consumes them.  The gathers are the only round trip to memory on the path.
+// ---------------------------------------------------------------------------
 template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
 __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
 {
@@ -286,13 +328,15 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
     using Ent = typename P::Ent;
     using Cst = typename P::Cst;
     constexpr int RPW = 32 / LPR;  // rows per warp instruction
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *bars = (uint64_t *)(smem + 2 * (size_t)a.blob_max);
+    volatile int *abort_flag = (volatile int *)(bars + 2);
+
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int sub = lane / LPR;
     const int cl = lane % LPR;
-    // Q CTAs (a thread-block cluster) share one chain slice and split each
-    // level's rows; Q = 1 without clusters
     const int Q = CLUSTER ? a.ctas_per_slice : 1;
     const int rank = CLUSTER ? (int)cluster_rank() : 0;
     const int slice = blockIdx.x / Q;
@@ -301,53 +345,78 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
     const size_t K = (size_t)a.K;
     const int stride = Q * nwarps * RPW;
     const int first = (rank * nwarps + warp) * RPW;
-    const Ent *__restrict__ zent = (const Ent *)a.zent;
-    const Ent *__restrict__ went = (const Ent *)a.went;
-    const Cst *__restrict__ cst = (const Cst *)a.cst;
-    const int *__restrict__ perm = a.perm;
-    const int *__restrict__ zptr = a.zptr;
-    const int *__restrict__ wptr = a.wptr;
     const uint32_t cshift = (uint32_t)(c0 & 31);
-    S *diag = (S *)a.diag_part + (size_t)slice * a.n;
-    int cur = a.cur;
-    bool diverged = false;
+    const int seg = a.seg;
+    S *dpart = (S *)a.diag_part + (size_t)(c0 / (seg * V)) * a.n;
+    const bool dlead = (cl % seg) == 0;
+    const int total = a.ncyc * a.nchunks;
 
-    for (int cyc = 0; cyc < a.ncyc; ++cyc) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])));
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int t = 0; t < 2 && t < total; ++t) {
+            const ChunkDesc d = a.chunks[t % a.nchunks];
+            stage_chunk(smem_addr(smem + (size_t)t * a.blob_max), a.stream + d.off, (uint32_t)d.bytes,
+                        smem_addr(&bars[t]));
+        }
+    }
+    __syncthreads();
+
+    bool diverged = false;
+    for (int t = 0; t < total; ++t) {
+        const int cyc = t / a.nchunks;
+        const int b = t & 1;
+        const ChunkDesc d = a.chunks[t - cyc * a.nchunks];
+        const int cur = a.cur ^ (cyc & 1);
         const T *zo = (const T *)a.z[cur];
         T *zn = (T *)a.z[cur ^ 1];
         const T *wo = (const T *)a.w[cur];
         T *wn = (T *)a.w[cur ^ 1];
-        const uint32_t *__restrict__ noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
-        const int shcol = a.cyc0_in_batch + cyc;
-        for (int lev = 0; lev < a.nlev; ++lev) {
-            const int pb = __ldg(&a.lev_ptr[lev]), pe = __ldg(&a.lev_ptr[lev + 1]);
-            for (int base = pb + first; base < pe; base += stride) {
-                const int p = base + sub;
-                const bool ok = chain_ok && p < pe;
+        const uint8_t *buf = smem + (size_t)b * a.blob_max;
+        // one thread observes the blob's arrival; the barrier publishes it (and a
+        // give-up decision) to the whole CTA
+        if (threadIdx.x == 0 && !*abort_flag && !wait_chunk(smem_addr(&bars[b]), (uint32_t)(t >> 1) & 1u))
+            *abort_flag = 1;
+        __syncthreads();
+        if (!*abort_flag) {
+            const RowMeta *meta = (const RowMeta *)buf;
+            const Cst *cstv = (const Cst *)(buf + d.cst_off);
+            const Ent *zs = (const Ent *)(buf + d.zent_off);
+            const Ent *ws = (const Ent *)(buf + d.went_off);
+            const uint32_t *__restrict__ noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
+            const int shcol = a.cyc0_in_batch + cyc;
+            for (int base = first; base < d.rows; base += stride) {
+                const int r = base + sub;
+                const bool ok = chain_ok && r < d.rows;
                 S prod = P::zero();
-                int i = 0;
+                S dold = P::zero();
+                const int p = d.pb + r;
                 if (ok) {
-                    i = __ldg(&perm[p]);
-                    const int zb = __ldg(&zptr[p]), zeN = __ldg(&zptr[p + 1]);
-                    const int wb = __ldg(&wptr[p]), weN = __ldg(&wptr[p + 1]);
+                    const uint32_t bits = __ldg(&noise[p]) >> cshift;
+                    if (a.diag_part && dlead) dold = dpart[p];
+                    int rp = -1, sp = -1;
+                    if (a.rpos) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
+                    const RowMeta m = meta[r];
+                    const int i = m.row;
+                    const int zb = m.zoff, zeN = meta[r + 1].zoff;
+                    const int wb = m.woff, weN = meta[r + 1].woff;
                     T sz = L::zero(), sw = L::zero();
                     for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
                         Ent enz[U], enw[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if (ez + u < zeN) enz[u] = zent[ez + u];
-                            if (ew + u < weN) enw[u] = went[ew + u];
-                        }
                         T xz[U], xw[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             xz[u] = L::zero();
                             xw[u] = L::zero();
                             if (ez + u < zeN) {
+                                enz[u] = zs[ez + u];
                                 const T *src = enz[u].col < i ? zn : zo;
                                 xz[u] = ld_state<CLUSTER>(&src[((size_t)enz[u].col * K + c0) / V]);
                             }
                             if (ew + u < weN) {
+                                enw[u] = ws[ew + u];
                                 const T *src = enw[u].col < i ? wn : wo;
                                 xw[u] = ld_state<CLUSTER>(&src[((size_t)enw[u].col * K + c0) / V]);
                             }
@@ -358,44 +427,41 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                             if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
                         }
                     }
-                    const uint32_t bits = __ldg(&noise[i]) >> cshift;
-                    const Cst k = cst[p];
+                    const Cst k = cstv[r];
                     T zv, wv;
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
                         const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
-                        const S zs = P::zrow(k, phi, L::get(sz, v));
-                        const S ws = P::wrow(k, phi, L::get(sw, v));
-                        L::set(zv, v, zs);
-                        L::set(wv, v, ws);
-                        diverged |= !(P::finite_bounded(zs) && P::finite_bounded(ws));
-                        prod = P::add(prod, P::mulconj(zs, ws));
+                        const S zsc = P::zrow(k, phi, L::get(sz, v));
+                        const S wsc = P::wrow(k, phi, L::get(sw, v));
+                        L::set(zv, v, zsc);
+                        L::set(wv, v, wsc);
+                        diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
+                        prod = P::add(prod, P::mulconj(zsc, wsc));
                     }
                     zn[((size_t)i * K + c0) / V] = zv;
                     wn[((size_t)i * K + c0) / V] = wv;
-                    if (a.rpos) {
+                    if (rp >= 0 || sp >= 0) {
                         // shadow column of (cycle, chain): cycle block of kp elements, then
                         // the chain (x2 for re,im); blocks are padded to 64 and the pad
                         // stays zero
-                        const int r = __ldg(&a.rpos[i]);
-                        const int s = __ldg(&a.spos[i]);
                         const size_t o = (size_t)shcol * a.kp + (size_t)c0 * (CPLX ? 2 : 1);
                         constexpr int NF = L::NF;
-                        if (r >= 0) {
-                            uint16_t *dst = a.zsh + (size_t)r * a.ldsh + o;
+                        if (rp >= 0) {
+                            uint16_t *dst = a.zsh + (size_t)rp * a.ldsh + o;
 #pragma unroll
                             for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
                         }
-                        if (s >= 0) {
+                        if (sp >= 0) {
                             if constexpr (!CPLX) {
-                                uint16_t *dst = a.wsh + (size_t)s * a.ldsh + o;
+                                uint16_t *dst = a.wsh + (size_t)sp * a.ldsh + o;
 #pragma unroll
                                 for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
                             } else {
                                 // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
                                 // [-wi, wr] to Im(z conj w), so the product comes out
                                 // interleaved re,im
-                                uint16_t *w0 = a.wsh + (size_t)(2 * s) * a.ldsh + o;
+                                uint16_t *w0 = a.wsh + (size_t)(2 * sp) * a.ldsh + o;
                                 uint16_t *w1 = w0 + a.ldsh;
 #pragma unroll
                                 for (int v = 0; v < V; ++v) {
@@ -410,34 +476,64 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                     }
                 }
                 if (a.diag_part) {
+                    // sum over the seg lanes of a unit (all lanes shuffle); the leader
+                    // adds the running partial it loaded at the start of the row
 #pragma unroll
-                    for (int o = LPR / 2; o > 0; o >>= 1) prod = P::add(prod, P::shfl_xor(prod, o));
-                    if (ok && cl == 0) diag[i] = P::add(diag[i], prod);
+                    for (int o = 1; o < LPR; o <<= 1)
+                        if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
+                    if (ok && dlead) dpart[p] = P::add(dold, prod);
                 }
             }
-            if constexpr (CLUSTER) cluster_barrier();
-            else __syncthreads();
         }
-        cur ^= 1;
+        __syncthreads();
+        if constexpr (CLUSTER) {
+            if (d.flags & CHUNK_LEVEL_END) cluster_barrier();
+        }
+        if (threadIdx.x == 0 && t + 2 < total && !*abort_flag) {
+            // the buffer's readers are done (barrier above); order their generic-proxy
+            // reads before the async-proxy write of the next blob
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const ChunkDesc dn = a.chunks[(t + 2) % a.nchunks];
+            stage_chunk(smem_addr(smem + (size_t)b * a.blob_max), a.stream + dn.off, (uint32_t)dn.bytes,
+                        smem_addr(&bars[b]));
+        }
     }
     if (diverged) atomicOr(a.status, 1);
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicOr(a.status, 4);
+        const uint64_t t0 = gtimer();  // let copies still in flight land before exit
+        while (gtimer() - t0 < 10000000ull) {
+        }
+    }
+}
+
+static size_t sweep_smem(int blob_max) { return 2 * (size_t)blob_max + 64; }
+
+template <bool CPLX, int LPR, int V, int U, bool CL>
+static cudaError_t prepare(int blob_max, int q)
+{
+    auto kern = cc_sweep_kernel<CPLX, LPR, V, U, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem(blob_max));
+    if (e == cudaSuccess && CL && q > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
 template <bool CPLX, int LPR, int V, int U>
 static cudaError_t launch_one(const SweepArgs &a, int slices, int threads, cudaStream_t s)
 {
+    const size_t smem = sweep_smem(a.blob_max);
     if (a.ctas_per_slice <= 1) {
-        cc_sweep_kernel<CPLX, LPR, V, U, false><<<slices, threads, 0, s>>>(a);
+        cudaError_t e = prepare<CPLX, LPR, V, U, false>(a.blob_max, 1);
+        if (e != cudaSuccess) return e;
+        cc_sweep_kernel<CPLX, LPR, V, U, false><<<slices, threads, smem, s>>>(a);
         return cudaGetLastError();
     }
-    auto kern = cc_sweep_kernel<CPLX, LPR, V, U, true>;
-    if (a.ctas_per_slice > 8) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = prepare<CPLX, LPR, V, U, true>(a.blob_max, a.ctas_per_slice);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(slices * a.ctas_per_slice));
     cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -446,7 +542,7 @@ static cudaError_t launch_one(const SweepArgs &a, int slices, int threads, cudaS
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
+    return cudaLaunchKernelEx(&cfg, cc_sweep_kernel<CPLX, LPR, V, U, true>, a);
 }
 
 template <bool CPLX, int V, int U>
@@ -476,12 +572,13 @@ cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int ch
     return cudaErrorInvalidValue;
 }
 
-int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q)
+int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int threads, int q, int blob_max)
 {
     // how many clusters of q CTAs can be resident at once (0 if none)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)q);
     cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = sweep_smem(blob_max);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)q;
@@ -491,8 +588,12 @@ int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int th
     cfg.numAttrs = 1;
     int n = 0;
     const void *k = nullptr;
-#define MCINV_PICK(C, L, V, U)                                                                       \
-    if (cplx == C && lanes_per_row == L && chains_per_lane == V) k = (const void *)cc_sweep_kernel<C, L, V, U, true>;
+    cudaError_t e = cudaErrorInvalidValue;
+#define MCINV_PICK(C, L, V, U)                                                     \
+    if (cplx == C && lanes_per_row == L && chains_per_lane == V) {                   \
+        k = (const void *)cc_sweep_kernel<C, L, V, U, true>;                         \
+        e = prepare<C, L, V, U, true>(blob_max, q);                                  \
+    }
 #define MCINV_PICK_L(C, V, U) MCINV_PICK(C, 1, V, U) MCINV_PICK(C, 2, V, U) MCINV_PICK(C, 4, V, U) \
     MCINV_PICK(C, 8, V, U) MCINV_PICK(C, 16, V, U) MCINV_PICK(C, 32, V, U)
     MCINV_PICK_L(true, 2, 4)
@@ -501,8 +602,10 @@ int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int th
     MCINV_PICK_L(false, 1, 8)
 #undef MCINV_PICK_L
 #undef MCINV_PICK
-    if (!k) return 0;
-    if (q > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    if (!k || e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
