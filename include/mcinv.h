@@ -204,6 +204,37 @@ mcinv_status mcinv_profile_read(mcinv_t h, mcinv_kernel kernel, int64_t *launche
 mcinv_status mcinv_selftest_tc_gemm(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
                                     const uint16_t *B, float *D);
 
+/*
+ * One batch of the block accumulation that allocates nothing.  The paper has
+ * no counterpart: this exists for callers that cannot allocate device memory,
+ * such as a serving process that reserves all device memory up front in its
+ * own arena, or code that cannot take the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply in the middle of its work.
+ *
+ * On caller memory it computes D = A B^T on the tensor cores (BF16 operands,
+ * FP32 accumulation) and folds it into FP64 accumulators:
+ *     sum[e] += D[e],  sq[e] += D[e]^2 * scale_sq,   e < M*N (row-major M x N).
+ *   A: M rows of `inner` BF16 bit patterns, row stride lda elements; B: N rows,
+ *   stride ldb.  Device pointers owned by the caller; A and B start on 16-byte
+ *   boundaries, lda and ldb are multiples of 8 and >= inner.  sum, sq: FP64,
+ *   M*N each.  stream: cudaStream_t (NULL = legacy default stream).
+ * The FP32 product D lives in a fixed 8 MiB array inside the library, so
+ * M*N <= 2^21 (larger sizes return MCINV_E_ARG); every GPU that loads the
+ * library holds that array until the process exits.  All calls share it and
+ * it keeps the last call's product (the product is overwritten whole, so
+ * nothing needs clearing): calls whose work overlaps on the GPU -- different
+ * streams or host threads -- race; calls on one stream do not.  The first call
+ * on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  The call waits for its
+ * stream before returning.  No cudaMalloc, cudaFree or other allocation.
+ * On failure *error (when error is not NULL) points to a static message.
+ * MCINV_E_UNSUPPORTED off sm_103a; MCINV_E_TIMEOUT if a bounded wait expired.
+ */
+mcinv_status mcinv_block_accumulate_noalloc(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
+                                            int64_t lda, const uint16_t *B, int64_t ldb,
+                                            double scale_sq, double *sum, double *sq, void *stream,
+                                            const char **error);
+
 /* Free everything the handle owns.  NULL is allowed. */
 void mcinv_destroy(mcinv_t h);
 

@@ -325,4 +325,40 @@ cudaError_t tc_gemm_run(TcGemmPlan *p, long long inner, int *status, cudaStream_
 
 void tc_gemm_plan_destroy(TcGemmPlan *p) { delete p; }
 
+cudaError_t tc_gemm_run_direct(const uint16_t *A, long long lda, const uint16_t *B, long long ldb, long long M,
+                               long long N, long long inner, float *D, int *status, cudaStream_t s,
+                               const char **why)
+{
+    // the tensor maps live on this stack frame and are passed by value to the
+    // kernel; their extents are the true M, N and inner, so TMA fills the
+    // ragged edges of the last tiles with zeros
+    auto fn = encode_fn();
+    if (!fn) {
+        if (why) *why = "cuTensorMapEncodeTiled unavailable";
+        return cudaErrorNotSupported;
+    }
+    CUtensorMap ta, tb;
+    const uint16_t *bases[2] = {A, B};
+    const long long lds[2] = {lda, ldb}, rows[2] = {M, N};
+    const int boxr[2] = {BM, BN};
+    CUtensorMap *maps[2] = {&ta, &tb};
+    for (int k = 0; k < 2; ++k) {
+        cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows[k]};
+        cuuint64_t strides[1] = {(cuuint64_t)lds[k] * 2};
+        cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)boxr[k]};
+        cuuint32_t estr[2] = {1, 1};
+        if (fn(maps[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)bases[k], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            if (why) *why = "cuTensorMapEncodeTiled rejected an operand (base must be 16-byte aligned, ld a multiple of 8)";
+            return cudaErrorInvalidValue;
+        }
+    }
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ta, tb, D, (int)M, (int)N, (int)((inner + BK - 1) / BK), status);
+    return cudaGetLastError();
+}
+
 }  // namespace mcinv

@@ -21,4 +21,12 @@ TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t
 cudaError_t tc_gemm_run(TcGemmPlan *plan, long long inner, int *status, cudaStream_t s);
 void tc_gemm_plan_destroy(TcGemmPlan *plan);
 
+// One contraction without a plan object: tensor maps are built on the
+// caller's stack with the true extents (M, N, inner), so operands need no
+// padding; A's and B's bases must be 16-byte aligned and lda, ldb multiples of
+// 8 elements.  No allocation of any kind.  On failure *why names the cause.
+cudaError_t tc_gemm_run_direct(const uint16_t *A, long long lda, const uint16_t *B, long long ldb, long long M,
+                               long long N, long long inner, float *D, int *status, cudaStream_t s,
+                               const char **why);
+
 }  // namespace mcinv

@@ -30,7 +30,8 @@ MCINV_F_NO_DIAG = 1
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sample",
            "mcinv_estimate", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
-           "mcinv_selftest_tc_gemm", "mcinv_destroy", "mcinv_last_error")
+           "mcinv_selftest_tc_gemm", "mcinv_block_accumulate_noalloc", "mcinv_destroy",
+           "mcinv_last_error")
 MCINV_KERNEL_NOISE, MCINV_KERNEL_SWEEP, MCINV_KERNEL_BLOCK, MCINV_KERNEL_FOLD, MCINV_KERNEL_ESTIMATE = range(5)
 KERNEL_NAMES = ("noise", "sweep", "block", "fold", "estimate")
 
@@ -96,6 +97,9 @@ def lib():
                                          ctypes.POINTER(ctypes.c_double)]
         L.mcinv_selftest_tc_gemm.argtypes = [i64, i64, i64, vp, vp, vp]
         L.mcinv_selftest_tc_gemm.restype = ctypes.c_int
+        L.mcinv_block_accumulate_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, ctypes.c_double,
+                                                     vp, vp, vp, ctypes.POINTER(ctypes.c_char_p)]
+        L.mcinv_block_accumulate_noalloc.restype = ctypes.c_int
         L.mcinv_destroy.argtypes = [vp]
         L.mcinv_destroy.restype = None
         L.mcinv_last_error.argtypes = [vp]
@@ -271,6 +275,19 @@ def mcinv_selftest_tc_gemm(A_bits, B_bits):
     D = np.empty((A.shape[0], B.shape[0]), dtype=np.float32)
     _check(lib().mcinv_selftest_tc_gemm(A.shape[0], B.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(D)))
     return D
+
+
+def mcinv_block_accumulate_noalloc(M, N, inner, A_ptr, lda, B_ptr, ldb, scale_sq, sum_ptr, sq_ptr,
+                                   stream=None):
+    """One block-accumulation batch on caller device memory (integer addresses);
+    the library allocates nothing.  Raises McinvError with the library's message."""
+    err = ctypes.c_char_p()
+    st = lib().mcinv_block_accumulate_noalloc(int(M), int(N), int(inner), ctypes.c_void_p(A_ptr), int(lda),
+                                              ctypes.c_void_p(B_ptr), int(ldb), float(scale_sq),
+                                              ctypes.c_void_p(sum_ptr), ctypes.c_void_p(sq_ptr),
+                                              stream, ctypes.byref(err))
+    if st != MCINV_OK:
+        raise McinvError(st, (err.value or b"").decode(errors="replace"))
 
 
 def mcinv_destroy(h: Handle):
