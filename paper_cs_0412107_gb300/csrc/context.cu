@@ -313,7 +313,7 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     };
     auto zdeg = [&](int64_t i) { return (size_t)(row_ptr[i + 1] - row_ptr[i] - 1); };
     auto wdeg = [&](int64_t i) { return (size_t)(wcount[i + 1] - wcount[i]); };
-    size_t blob_max = 64 * 1024;
+    size_t blob_max = 48 * 1024;  // two CTAs of the real path share an SM
     for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, zdeg(i), wdeg(i)));
     blob_max = (blob_max + 127) & ~(size_t)127;
     if (blob_max > 100 * 1024) {

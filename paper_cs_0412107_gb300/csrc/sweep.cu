@@ -356,15 +356,15 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[1])));
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int t = 0; t < 2 && t < total; ++t) {
-            const ChunkDesc d = a.chunks[t % a.nchunks];
-            stage_chunk(smem_addr(smem + (size_t)t * a.blob_max), a.stream + d.off, (uint32_t)d.bytes,
-                        smem_addr(&bars[t]));
+        if (total > 0) {
+            const ChunkDesc d = a.chunks[0];
+            stage_chunk(smem_addr(smem), a.stream + d.off, (uint32_t)d.bytes, smem_addr(&bars[0]));
         }
     }
     __syncthreads();
 
     bool diverged = false;
+    bool level_end = false;  // did the previous chunk end a dependency level?
     for (int t = 0; t < total; ++t) {
         const int cyc = t / a.nchunks;
         const int b = t & 1;
@@ -375,11 +375,27 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
         const T *wo = (const T *)a.w[cur];
         T *wn = (T *)a.w[cur ^ 1];
         const uint8_t *buf = smem + (size_t)b * a.blob_max;
-        // one thread observes the blob's arrival; the barrier publishes it (and a
-        // give-up decision) to the whole CTA
+        // One thread observes chunk t's arrival; one barrier then publishes it
+        // to the CTA, ends chunk t-1 (its buffer is free again) and, after a
+        // level, is the cluster barrier that makes the level's rows visible to
+        // every CTA of the slice.
         if (threadIdx.x == 0 && !*abort_flag && !wait_chunk(smem_addr(&bars[b]), (uint32_t)(t >> 1) & 1u))
             *abort_flag = 1;
-        __syncthreads();
+        if constexpr (CLUSTER) {
+            if (level_end) cluster_barrier();
+            else __syncthreads();
+        } else {
+            __syncthreads();
+        }
+        level_end = (d.flags & CHUNK_LEVEL_END) != 0;
+        if (threadIdx.x == 0 && t + 1 < total && !*abort_flag) {
+            // order the CTA's generic-proxy reads of that buffer before the
+            // async-proxy write of the next blob
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const ChunkDesc dn = a.chunks[(t + 1) % a.nchunks];
+            stage_chunk(smem_addr(smem + (size_t)(b ^ 1) * a.blob_max), a.stream + dn.off, (uint32_t)dn.bytes,
+                        smem_addr(&bars[b ^ 1]));
+        }
         if (!*abort_flag) {
             const RowMeta *meta = (const RowMeta *)buf;
             const Cst *cstv = (const Cst *)(buf + d.cst_off);
@@ -404,27 +420,29 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                     const int wb = m.woff, weN = meta[r + 1].woff;
                     T sz = L::zero(), sw = L::zero();
                     for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
-                        Ent enz[U], enw[U];
+                        // issue every gather first (only the column is read from shared
+                        // memory here); the FMA pass re-reads each entry's value, so no
+                        // entry stays live in registers across the memory round trip
                         T xz[U], xw[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             xz[u] = L::zero();
                             xw[u] = L::zero();
                             if (ez + u < zeN) {
-                                enz[u] = zs[ez + u];
-                                const T *src = enz[u].col < i ? zn : zo;
-                                xz[u] = ld_state<CLUSTER>(&src[((size_t)enz[u].col * K + c0) / V]);
+                                const int j = zs[ez + u].col;
+                                const T *src = j < i ? zn : zo;
+                                xz[u] = ld_state<CLUSTER>(&src[((size_t)j * K + c0) / V]);
                             }
                             if (ew + u < weN) {
-                                enw[u] = ws[ew + u];
-                                const T *src = enw[u].col < i ? wn : wo;
-                                xw[u] = ld_state<CLUSTER>(&src[((size_t)enw[u].col * K + c0) / V]);
+                                const int j = ws[ew + u].col;
+                                const T *src = j < i ? wn : wo;
+                                xw[u] = ld_state<CLUSTER>(&src[((size_t)j * K + c0) / V]);
                             }
                         }
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
-                            if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                            if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
+                            if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
                         }
                     }
                     const Cst k = cstv[r];
@@ -485,19 +503,10 @@ __global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
                 }
             }
         }
-        __syncthreads();
-        if constexpr (CLUSTER) {
-            if (d.flags & CHUNK_LEVEL_END) cluster_barrier();
-        }
-        if (threadIdx.x == 0 && t + 2 < total && !*abort_flag) {
-            // the buffer's readers are done (barrier above); order their generic-proxy
-            // reads before the async-proxy write of the next blob
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const ChunkDesc dn = a.chunks[(t + 2) % a.nchunks];
-            stage_chunk(smem_addr(smem + (size_t)b * a.blob_max), a.stream + dn.off, (uint32_t)dn.bytes,
-                        smem_addr(&bars[b]));
-        }
     }
+    // the last chunk's rows are done before anyone leaves (the cluster's CTAs
+    // may still read them through the cluster-wide view until then)
+    if constexpr (CLUSTER) cluster_barrier();
     if (diverged) atomicOr(a.status, 1);
     if (threadIdx.x == 0 && *abort_flag) {
         atomicOr(a.status, 4);
@@ -563,8 +572,8 @@ cudaError_t launch_sweep(const SweepArgs &a, int cplx, int lanes_per_row, int ch
                          int slices, int threads, cudaStream_t s)
 {
     if (cplx) {
-        if (chains_per_lane == 2) return launch_sweep_v<true, 2, 4>(a, lanes_per_row, slices, threads, s);
-        if (chains_per_lane == 1) return launch_sweep_v<true, 1, 4>(a, lanes_per_row, slices, threads, s);
+        if (chains_per_lane == 2) return launch_sweep_v<true, 2, 8>(a, lanes_per_row, slices, threads, s);
+        if (chains_per_lane == 1) return launch_sweep_v<true, 1, 8>(a, lanes_per_row, slices, threads, s);
     } else {
         if (chains_per_lane == 4) return launch_sweep_v<false, 4, 8>(a, lanes_per_row, slices, threads, s);
         if (chains_per_lane == 1) return launch_sweep_v<false, 1, 8>(a, lanes_per_row, slices, threads, s);
@@ -596,8 +605,8 @@ int max_active_clusters(int cplx, int lanes_per_row, int chains_per_lane, int th
     }
 #define MCINV_PICK_L(C, V, U) MCINV_PICK(C, 1, V, U) MCINV_PICK(C, 2, V, U) MCINV_PICK(C, 4, V, U) \
     MCINV_PICK(C, 8, V, U) MCINV_PICK(C, 16, V, U) MCINV_PICK(C, 32, V, U)
-    MCINV_PICK_L(true, 2, 4)
-    MCINV_PICK_L(true, 1, 4)
+    MCINV_PICK_L(true, 2, 8)
+    MCINV_PICK_L(true, 1, 8)
     MCINV_PICK_L(false, 4, 8)
     MCINV_PICK_L(false, 1, 8)
 #undef MCINV_PICK_L
