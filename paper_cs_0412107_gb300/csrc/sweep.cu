@@ -319,7 +319,7 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
 // consumes them.  The gathers are the only round trip to memory on the path.
 // ---------------------------------------------------------------------------
 template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
-__global__ void __launch_bounds__(512) cc_sweep_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
 {
     using P = Prec<CPLX>;
     using L = Lane<CPLX, V>;
