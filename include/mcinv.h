@@ -91,7 +91,10 @@ typedef struct {
     int32_t reserved;
 } mcinv_options;
 
-#define MCINV_F_NO_DIAG 1 /* do not accumulate the diagonal (and trace) */
+#define MCINV_F_NO_DIAG 1  /* do not accumulate the diagonal (and trace) */
+#define MCINV_F_AUTOTUNE 2 /* when chains_per_cta, ctas_per_slice and threads_per_cta are all 0,
+                              time the candidate slice shapes on this matrix for two cycles at
+                              create time and keep the fastest (cached per n, nnz, K, type) */
 
 /* Fill *opt with defaults (K = 1024, seed = 0, everything else automatic). */
 void mcinv_default_options(mcinv_options *opt);

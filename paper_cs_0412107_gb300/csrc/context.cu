@@ -6,7 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -147,25 +150,112 @@ static int sm_count()
     return sms;
 }
 
-// Default slice shape: wide chain slices (8 to 32 lanes on one row, so a
-// gathered row segment is 128 to 512 contiguous bytes) spread over a cluster
-// of Q CTAs when there are fewer slices than SMs; among those, the one that
-// keeps the most SMs busy.
-static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q)
+// Default slice shape, from measurements on the workloads of this library:
+// real sweeps run best with 32-chain slices (8 lanes x 4 chains, one 128-byte
+// line per gathered row) spread over a cluster when there are few slices,
+// about 128 CTAs of 512 threads; complex sweeps with about 256 CTAs of 256
+// threads (two per SM) and 16- to 64-chain slices.  The autotuner
+// (MCINV_F_AUTOTUNE) times the alternatives on the actual matrix instead.
+static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q, int *T)
 {
     const int vmax = (K % (cplx ? 2 : 4) == 0) ? (cplx ? 2 : 4) : 1;
-    int bestW = vmax, bestQ = 1;
-    int64_t best = -1;
-    for (int lpr = 32; lpr >= 8; lpr /= 2) {
-        const int w = lpr * vmax;
+    int w, q, t;
+    if (!cplx) {
+        w = 8 * vmax;
+        t = 512;
         const int64_t slices = (K + w - 1) / w;
-        int q = (int)std::max<int64_t>(1, std::min<int64_t>(16, sms / std::max<int64_t>(slices, 1)));
-        const int64_t ctas = std::min<int64_t>(slices * q, sms);
-        if (ctas > best) { best = ctas; bestW = w; bestQ = q; }
+        q = (int)std::max<int64_t>(1, std::min<int64_t>(16, (sms * 5 / 6) / std::max<int64_t>(slices, 1)));
+    } else {
+        w = 8 * vmax;
+        t = 256;
+        while (w < 32 * vmax && (K + w - 1) / w > 2 * sms) w *= 2;
+        const int64_t slices = (K + w - 1) / w;
+        q = (int)std::max<int64_t>(1, std::min<int64_t>(16, (2 * sms) / std::max<int64_t>(slices, 1)));
     }
-    while (bestW > 1 && bestW / 2 >= K) bestW /= 2;
-    *W = bestW;
-    *Q = bestQ;
+    while (w > 1 && w / 2 >= K) w /= 2;
+    *W = w;
+    *Q = q;
+    *T = t;
+}
+
+static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumulate, int cyc0_in_batch);
+
+// Autotuner: time every reasonable slice shape (chains per CTA, CTAs per
+// cluster, threads per CTA) for two burn-in cycles on the handle's own matrix
+// from the zero state, keep the fastest, and put the state back to zero.  The
+// choice is cached per (n, nnz, K, real/complex) for the process.
+struct TunedShape {
+    int W, V, LPR, Q, T;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
+
+static mcinv_status autotune(mcinv_ctx *h)
+{
+    const auto key = std::make_tuple(h->n, h->nnz, h->K, h->cplx);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
+            h->Q = it->second.Q; h->threads = it->second.T;
+            h->slices = (int)((h->K + h->W - 1) / h->W);
+            return MCINV_OK;
+        }
+    }
+    const int sms = sm_count();
+    const int vmax = (h->K % (h->cplx ? 2 : 4) == 0) ? (h->cplx ? 2 : 4) : 1;
+    const int ncyc = (int)std::min<int64_t>(2, h->B);
+    LAUNCH_K(h, MCINV_KERNEL_NOISE, launch_noise(h->seed, h->matrix_id, (uint64_t)h->chain_base, (int)h->K, (int)h->n,
+                                                 0, ncyc, h->d_pos, h->d_noise, h->stream));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads};
+    float best_ms = 1e30f;
+    for (int lpr = 1; lpr <= 32; lpr *= 2) {
+        const int W = lpr * vmax;
+        if (W > h->K && lpr > 1) break;
+        const int slices = (int)((h->K + W - 1) / W);
+        for (int Q = 1; Q <= 16; Q *= 2) {
+            if (Q > 1 && (int64_t)slices * Q > 2 * sms) break;
+            if ((int64_t)slices * Q < std::min<int64_t>(64, slices) || (int64_t)slices * Q > 8 * sms) continue;
+            for (int T = 256; T <= 512; T *= 2) {
+                if (Q > 1 && max_active_clusters(h->cplx, lpr, vmax, T, Q, h->blob_max) < 1) continue;
+                const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices;
+                h->W = W; h->V = vmax; h->LPR = lpr; h->Q = Q; h->threads = T; h->slices = slices;
+                SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
+                float ms = 1e30f;
+                cudaError_t e = launch_sweep(a, h->cplx, lpr, vmax, slices, T, h->stream);  // warm-up
+                if (e == cudaSuccess) {
+                    cudaEventRecord(e0, h->stream);
+                    e = launch_sweep(a, h->cplx, lpr, vmax, slices, T, h->stream);
+                    cudaEventRecord(e1, h->stream);
+                    if (e == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (e != cudaSuccess) cudaGetLastError();  // launch refused: skip this shape
+                h->launches += 2;
+                if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, T}; }
+                h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T;
+    h->slices = (int)((h->K + h->W - 1) / h->W);
+    // back to Algorithm 1 step 1: z = w = 0, nothing run yet
+    const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
+    for (int b = 0; b < 2; ++b) {
+        CUDA_TRY(h, cudaMemsetAsync(h->d_z[b], 0, bytes, h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(h->d_w[b], 0, bytes, h->stream));
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    return MCINV_OK;
 }
 
 extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr,
@@ -218,9 +308,10 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     h->flags = opt.flags;
     h->acc = opt.acc;
     h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
+    int default_threads = 256;
     {
         int w = 0, q = 1;
-        choose_shape(opt.K, cplx, sm_count(), &w, &q);
+        choose_shape(opt.K, cplx, sm_count(), &w, &q, &default_threads);
         h->W = opt.chains_per_cta > 0 ? opt.chains_per_cta : w;
         h->Q = opt.ctas_per_slice > 0 ? opt.ctas_per_slice : (opt.chains_per_cta > 0 ? 1 : q);
         if (h->Q > 16) {
@@ -239,7 +330,7 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
                         32 * h->V, (long long)opt.K);
         }
     }
-    h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : 512;
+    h->threads = opt.threads_per_cta > 0 ? opt.threads_per_cta : default_threads;
     if (h->threads % 32 || h->threads > 512) {
         delete h;
         return fail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 512");
@@ -387,23 +478,6 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         h->Q = q;
     }
 
-    // ---- SE groups: the diagonal partials are kept per unit of seg lanes (seg x V
-    //      chains, a power of two dividing the slice); G groups of whole units
-    {
-        const int Greq = opt.groups > 0 ? opt.groups : 32;
-        int seg = 1;
-        while (seg * 2 <= h->LPR && (int64_t)seg * 2 * h->V * Greq <= opt.K) seg *= 2;
-        h->seg = seg;
-        const int64_t u = (int64_t)seg * h->V;
-        h->units = (int)((opt.K + u - 1) / u);
-        h->G = 1;
-        for (int g = std::min(Greq, h->units); g >= 1; --g)
-            if (h->units % g == 0) { h->G = g; break; }
-        h->counts.assign(h->G, 0.0);
-        for (int k = 0; k < h->units; ++k)
-            h->counts[k / (h->units / h->G)] += (double)std::min<int64_t>(u, opt.K - (int64_t)k * u);
-    }
-
     double *d_diag = nullptr;
     long long *d_cst_at = nullptr;
     std::vector<int32_t> bad_init(1, 0x7fffffff);
@@ -446,6 +520,27 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
     SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    if ((h->flags & MCINV_F_AUTOTUNE) && opt.chains_per_cta == 0 && opt.threads_per_cta == 0 && opt.ctas_per_slice == 0) {
+        const mcinv_status st = autotune(h);
+        if (st != MCINV_OK) return bail(st);
+    }
+    // ---- SE groups: the diagonal partials are kept per unit of seg lanes (seg x V
+    //      chains, a power of two dividing the slice); G groups of whole units
+    {
+        const int Greq = opt.groups > 0 ? opt.groups : 32;
+        int seg = 1;
+        while (seg * 2 <= h->LPR && (int64_t)seg * 2 * h->V * Greq <= opt.K) seg *= 2;
+        h->seg = seg;
+        const int64_t u = (int64_t)seg * h->V;
+        h->units = (int)((opt.K + u - 1) / u);
+        h->G = 1;
+        for (int g = std::min(Greq, h->units); g >= 1; --g)
+            if (h->units % g == 0) { h->G = g; break; }
+        h->counts.assign(h->G, 0.0);
+        for (int k = 0; k < h->units; ++k)
+            h->counts[k / (h->units / h->G)] += (double)std::min<int64_t>(u, opt.K - (int64_t)k * u);
+    }
+
     if (!(h->flags & MCINV_F_NO_DIAG)) {
         SETUP(dalloc(h, (char **)&h->d_diag_part, (size_t)h->units * n * esz));
         SETUP(cudaMemsetAsync(h->d_diag_part, 0, (size_t)h->units * n * esz, h->stream));

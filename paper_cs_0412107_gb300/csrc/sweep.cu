@@ -420,29 +420,38 @@ __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
                     const int wb = m.woff, weN = meta[r + 1].woff;
                     T sz = L::zero(), sw = L::zero();
                     for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
-                        // issue every gather first (only the column is read from shared
-                        // memory here); the FMA pass re-reads each entry's value, so no
-                        // entry stays live in registers across the memory round trip
+                        // issue every gather before any FMA consumes one; real entries
+                        // (8 B) stay in registers, complex ones (16 B) are re-read from
+                        // shared memory by the FMA pass to keep the register budget
+                        constexpr bool KEEP = !CPLX;
+                        Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
                         T xz[U], xw[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             xz[u] = L::zero();
                             xw[u] = L::zero();
                             if (ez + u < zeN) {
-                                const int j = zs[ez + u].col;
-                                const T *src = j < i ? zn : zo;
-                                xz[u] = ld_state<CLUSTER>(&src[((size_t)j * K + c0) / V]);
+                                const Ent e = zs[ez + u];
+                                if constexpr (KEEP) enz[u] = e;
+                                const T *src = e.col < i ? zn : zo;
+                                xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
                             }
                             if (ew + u < weN) {
-                                const int j = ws[ew + u].col;
-                                const T *src = j < i ? wn : wo;
-                                xw[u] = ld_state<CLUSTER>(&src[((size_t)j * K + c0) / V]);
+                                const Ent e = ws[ew + u];
+                                if constexpr (KEEP) enw[u] = e;
+                                const T *src = e.col < i ? wn : wo;
+                                xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
                             }
                         }
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
-                            if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
+                            if constexpr (KEEP) {
+                                if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                            } else {
+                                if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
+                            }
                         }
                     }
                     const Cst k = cstv[r];

@@ -25,6 +25,7 @@ MCINV_REAL64, MCINV_COMPLEX128 = 0, 1
 MCINV_ACC_FP32_SIMT, MCINV_ACC_BF16_TC = 0, 1
 MCINV_EST_BLOCK, MCINV_EST_DIAG, MCINV_EST_TRACE = 0, 1, 2
 MCINV_F_NO_DIAG = 1
+MCINV_F_AUTOTUNE = 2
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sample",

@@ -119,6 +119,17 @@ def test_trajectory_cluster_complex():
     _assert_close(errs)
 
 
+@pytest.mark.parametrize("complex_", [False, True])
+def test_autotuned_shape_keeps_the_trajectory(complex_):
+    """MCINV_F_AUTOTUNE times candidate shapes from the zero state, then restores it:
+    the tuned handle starts at cycle 0 and follows the oracle."""
+    csr = wl.u1_lattice((12, 10), 0.12, 0.08, seed=1) if complex_ else wl.pedigree(4000, 1.2, 2)
+    h, st, errs = run_pair(csr, 64, [1, 7], flags=mcinv.MCINV_F_AUTOTUNE)
+    _assert_close(errs)
+    info = mcinv.mcinv_info(h)
+    assert info["kernel_launches"] > 4 and info["cycle"] == 7
+
+
 def test_default_shape_uses_clusters_for_few_slices():
     csr = wl.pedigree(2000, 1.2, 4)
     h = mcinv.create_from_csr(csr, K=1024, acc=mcinv.MCINV_ACC_FP32_SIMT)
