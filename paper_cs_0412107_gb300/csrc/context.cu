@@ -164,7 +164,7 @@ static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q, int *T)
         w = 8 * vmax;
         t = 512;
         const int64_t slices = (K + w - 1) / w;
-        q = (int)std::max<int64_t>(1, std::min<int64_t>(16, (sms * 5 / 6) / std::max<int64_t>(slices, 1)));
+        q = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)std::llround(0.85 * sms / (double)std::max<int64_t>(slices, 1))));
     } else {
         w = 8 * vmax;
         t = 256;
