@@ -15,6 +15,7 @@
 
 #include "../../include/mcinv.h"
 #include "internal.h"
+#include "prepare.h"
 #include "tc_gemm.h"
 
 using namespace mcinv;
@@ -278,28 +279,12 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     const int cplx = dt == MCINV_COMPLEX128;
     const int NV = cplx ? 2 : 1;
 
-    // ---- host validation: sorted unique columns in range, diagonal present and usable
-    std::vector<double> diag((size_t)n * NV);
-    for (int64_t i = 0; i < n; ++i) {
-        if (row_ptr[i + 1] < row_ptr[i]) return fail(nullptr, MCINV_E_ARG, "row_ptr decreases at row %lld", (long long)i);
-        bool has_diag = false;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int64_t j = col[e];
-            if (j < 0 || j >= n) return fail(nullptr, MCINV_E_ARG, "column %lld out of range in row %lld", (long long)j, (long long)i);
-            if (e > row_ptr[i] && col[e - 1] >= j) return fail(nullptr, MCINV_E_ARG, "columns not strictly increasing in row %lld", (long long)i);
-            for (int v = 0; v < NV; ++v)
-                if (!std::isfinite(val[e * NV + v])) return fail(nullptr, MCINV_E_ARG, "non-finite value in row %lld", (long long)i);
-            if (j == i) {
-                has_diag = true;
-                for (int v = 0; v < NV; ++v) diag[(size_t)i * NV + v] = val[e * NV + v];
-            }
-        }
-        bool zero = true;
-        for (int v = 0; v < NV; ++v) zero &= diag[(size_t)i * NV + v] == 0.0;
-        if (!has_diag || zero)
-            return fail(nullptr, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %lld is %s", (long long)i, has_diag ? "zero" : "missing");
+    Prepared P;
+    {
+        std::string why;
+        const mcinv_status st = prepare_matrix(n, row_ptr, col, val, cplx, 48 * 1024, P, &why);
+        if (st != MCINV_OK) return fail(nullptr, st, "%s", why.c_str());
     }
-
     mcinv_ctx *h = new (std::nothrow) mcinv_ctx;
     if (!h) return fail(nullptr, MCINV_E_NOMEM, "host allocation failed");
     h->n = n; h->nnz = nnz; h->K = opt.K; h->cplx = cplx;
@@ -345,128 +330,10 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         return st;
     };
 
-    // ---- C^dagger rows: (C^H)_{j,i} = conj(c_ij), off-diagonal only, columns ascending
-    std::vector<int64_t> wcount(n + 1, 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            if (col[e] != i) wcount[col[e] + 1]++;
-    for (int64_t j = 0; j < n; ++j) wcount[j + 1] += wcount[j];
-    std::vector<int32_t> wcol(wcount[n]);
-    std::vector<double> wval((size_t)wcount[n] * NV);
-    {
-        std::vector<int64_t> fill(wcount.begin(), wcount.end() - 1);
-        for (int64_t i = 0; i < n; ++i)
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                const int64_t j = col[e];
-                if (j == i) continue;
-                const int64_t p = fill[j]++;
-                wcol[p] = (int32_t)i;
-                wval[p * NV] = val[e * NV];
-                if (cplx) wval[p * NV + 1] = -val[e * NV + 1];
-            }
-    }
-
-    // ---- dependency levels: row i waits for every j < i it reads this cycle
-    //      through C (Eq. 4) or C^dagger (Eq. 5)
-    std::vector<int32_t> level(n, 0);
-    int nlev = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        int lv = 0;
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1] && col[e] < i; ++e) lv = std::max(lv, level[col[e]] + 1);
-        for (int64_t e = wcount[i]; e < wcount[i + 1] && wcol[e] < i; ++e) lv = std::max(lv, level[wcol[e]] + 1);
-        level[i] = lv;
-        nlev = std::max(nlev, lv + 1);
-    }
-    h->nlev = nlev;
-    std::vector<int32_t> lev_ptr(nlev + 1, 0), perm(n);
-    for (int64_t i = 0; i < n; ++i) lev_ptr[level[i] + 1]++;
-    for (int l = 0; l < nlev; ++l) lev_ptr[l + 1] += lev_ptr[l];
-    {
-        std::vector<int32_t> fill(lev_ptr.begin(), lev_ptr.end() - 1);
-        for (int64_t i = 0; i < n; ++i) perm[fill[level[i]]++] = (int32_t)i;
-        // rows of one level are independent: order them by decreasing work so
-        // the rows a warp takes together cost about the same
-        for (int l = 0; l < nlev; ++l)
-            std::stable_sort(perm.begin() + lev_ptr[l], perm.begin() + lev_ptr[l + 1], [&](int32_t x, int32_t y) {
-                const int64_t dx = (row_ptr[x + 1] - row_ptr[x]) + (wcount[x + 1] - wcount[x]);
-                const int64_t dy = (row_ptr[y + 1] - row_ptr[y]) + (wcount[y + 1] - wcount[y]);
-                return dx > dy;
-            });
-    }
-
-    // ---- the chunk stream (see internal.h): per chunk of a level, the row
-    //      records, constants (filled on the GPU below) and entries of C and C^H
-    const size_t ent_sz = cplx ? sizeof(EntC) : sizeof(EntR);
-    const size_t cst_sz = cplx ? sizeof(CstC) : sizeof(CstR);
-    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    auto blob_bytes = [&](size_t rows, size_t nz, size_t nwv) {
-        return a16(16 * (rows + 1)) + a16(cst_sz * rows) + a16(ent_sz * nz) + a16(ent_sz * nwv);
-    };
-    auto zdeg = [&](int64_t i) { return (size_t)(row_ptr[i + 1] - row_ptr[i] - 1); };
-    auto wdeg = [&](int64_t i) { return (size_t)(wcount[i + 1] - wcount[i]); };
-    size_t blob_max = 48 * 1024;  // two CTAs of the real path share an SM
-    for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, zdeg(i), wdeg(i)));
-    blob_max = (blob_max + 127) & ~(size_t)127;
-    if (blob_max > 100 * 1024) {
-        fail(h, MCINV_E_UNSUPPORTED, "a row has too many off-diagonal entries in C and C^dagger for one shared-memory chunk (limit about %zu)",
-             (size_t)(100 * 1024 - 64) / ent_sz);
-        return bail(MCINV_E_UNSUPPORTED);
-    }
-    h->blob_max = (int)blob_max;
-    std::vector<ChunkDesc> chunks;
-    std::vector<long long> cst_at(n);
-    size_t stream_bytes = 0;
-    for (int l = 0; l < nlev; ++l) {
-        int64_t p = lev_ptr[l];
-        while (p < lev_ptr[l + 1]) {
-            const int64_t pb = p;
-            size_t nz = 0, nwv = 0;
-            while (p < lev_ptr[l + 1] && blob_bytes(p - pb + 1, nz + zdeg(perm[p]), nwv + wdeg(perm[p])) <= blob_max) {
-                nz += zdeg(perm[p]);
-                nwv += wdeg(perm[p]);
-                ++p;
-            }
-            ChunkDesc d{};
-            d.rows = (int)(p - pb);
-            d.pb = (int)pb;
-            d.cst_off = (int)a16(16 * (d.rows + 1));
-            d.zent_off = d.cst_off + (int)a16(cst_sz * d.rows);
-            d.went_off = d.zent_off + (int)a16(ent_sz * nz);
-            d.bytes = d.went_off + (int)a16(ent_sz * nwv);
-            d.off = (long long)stream_bytes;
-            d.flags = p == lev_ptr[l + 1] ? CHUNK_LEVEL_END : 0;
-            stream_bytes += ((size_t)d.bytes + 127) & ~(size_t)127;
-            chunks.push_back(d);
-        }
-    }
-    h->nchunks = (int)chunks.size();
-    std::vector<uint8_t> stream(stream_bytes, 0);
-    for (const ChunkDesc &d : chunks) {
-        uint8_t *blob = stream.data() + d.off;
-        RowMeta *meta = (RowMeta *)blob;
-        int zo = 0, wo = 0;
-        for (int r = 0; r < d.rows; ++r) {
-            const int64_t i = perm[d.pb + r];
-            meta[r] = RowMeta{(int)i, zo, wo, 0};
-            cst_at[d.pb + r] = d.off + d.cst_off + (long long)(r * cst_sz);
-            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-                if (col[e] == i) continue;
-                if (!cplx) ((EntR *)(blob + d.zent_off))[zo++] = EntR{col[e], (float)val[e]};
-                else ((EntC *)(blob + d.zent_off))[zo++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
-            }
-            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) {
-                if (!cplx) ((EntR *)(blob + d.went_off))[wo++] = EntR{wcol[e], (float)wval[e]};
-                else ((EntC *)(blob + d.went_off))[wo++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
-            }
-        }
-        meta[d.rows] = RowMeta{-1, zo, wo, 0};
-    }
-    std::vector<int32_t> pos(n);
-    for (int64_t p = 0; p < n; ++p) pos[perm[p]] = (int32_t)p;
-    std::vector<double> diag_pos((size_t)n * NV);
-    for (int64_t p = 0; p < n; ++p)
-        for (int v = 0; v < NV; ++v) diag_pos[(size_t)p * NV + v] = diag[(size_t)perm[p] * NV + v];
-
+    h->nlev = P.nlev;
+    h->blob_max = P.blob_max;
+    h->nchunks = (int)P.chunks.size();
+    const std::vector<int32_t> &perm = P.perm;
     // ---- clusters: fall back to smaller ones if this one cannot be resident
     if (h->Q > 1) {
         int q = h->Q;
@@ -491,12 +358,12 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
             return bail(st_);                                                                     \
         }                                                                                         \
     } while (0)
-    SETUP(upload(h, &h->d_stream, stream));
-    SETUP(upload(h, &h->d_chunks, chunks));
-    SETUP(upload(h, &h->d_perm, perm));
-    SETUP(upload(h, &h->d_pos, pos));
-    SETUP(upload(h, &d_diag, diag_pos));
-    SETUP(upload(h, &d_cst_at, cst_at));
+    SETUP(upload(h, &h->d_stream, P.stream));
+    SETUP(upload(h, &h->d_chunks, P.chunks));
+    SETUP(upload(h, &h->d_perm, P.perm));
+    SETUP(upload(h, &h->d_pos, P.pos));
+    SETUP(upload(h, &d_diag, P.diag_pos));
+    SETUP(upload(h, &d_cst_at, P.cst_at));
     SETUP(upload(h, &d_bad, bad_init));
     SETUP(launch_constants((int)n, d_diag, cplx, h->d_stream, d_cst_at, d_bad, h->stream));
     h->launches++;

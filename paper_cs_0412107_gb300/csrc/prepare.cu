@@ -1,0 +1,191 @@
+// prepare.cu -- host-side preparation of a matrix for the sweep (Sec. 2):
+// CSR validation (D must be non-singular, Sec. 2.2), the rows of C^dagger
+// that Eq. 5 runs over, the Gauss-Seidel dependency levels of C and C^dagger,
+// and the chunk stream the sweep stages into shared memory.  Shared by the
+// single-matrix handle and the pool.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "prepare.h"
+
+namespace mcinv {
+
+static mcinv_status prep_fail(std::string *err, mcinv_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (err) *err = buf;
+    return st;
+}
+
+mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
+                            int min_blob, Prepared &P, std::string *err)
+{
+    const int NV = cplx ? 2 : 1;
+    if (n <= 0 || n > (1LL << 30)) return prep_fail(err, MCINV_E_ARG, "n = %lld out of range", (long long)n);
+    if (!row_ptr || !col || !val) return prep_fail(err, MCINV_E_ARG, "NULL CSR array");
+    if (row_ptr[0] != 0) return prep_fail(err, MCINV_E_ARG, "row_ptr[0] != 0");
+    const int64_t nnz = row_ptr[n];
+    if (nnz < n || nnz > (1LL << 31) - 1) return prep_fail(err, MCINV_E_ARG, "nnz = %lld out of range", (long long)nnz);
+    P.n = n;
+    P.nnz = nnz;
+    P.cplx = cplx;
+    // ---- host validation: sorted unique columns in range, diagonal present and usable
+    std::vector<double> diag((size_t)n * NV);
+    for (int64_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return prep_fail(err, MCINV_E_ARG, "row_ptr decreases at row %lld", (long long)i);
+        bool has_diag = false;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int64_t j = col[e];
+            if (j < 0 || j >= n) return prep_fail(err, MCINV_E_ARG, "column %lld out of range in row %lld", (long long)j, (long long)i);
+            if (e > row_ptr[i] && col[e - 1] >= j) return prep_fail(err, MCINV_E_ARG, "columns not strictly increasing in row %lld", (long long)i);
+            for (int v = 0; v < NV; ++v)
+                if (!std::isfinite(val[e * NV + v])) return prep_fail(err, MCINV_E_ARG, "non-finite value in row %lld", (long long)i);
+            if (j == i) {
+                has_diag = true;
+                for (int v = 0; v < NV; ++v) diag[(size_t)i * NV + v] = val[e * NV + v];
+            }
+        }
+        bool zero = true;
+        for (int v = 0; v < NV; ++v) zero &= diag[(size_t)i * NV + v] == 0.0;
+        if (!has_diag || zero)
+            return prep_fail(err, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %lld is %s", (long long)i, has_diag ? "zero" : "missing");
+    }
+
+    // ---- C^dagger rows: (C^H)_{j,i} = conj(c_ij), off-diagonal only, columns ascending
+    std::vector<int64_t> wcount(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] != i) wcount[col[e] + 1]++;
+    for (int64_t j = 0; j < n; ++j) wcount[j + 1] += wcount[j];
+    std::vector<int32_t> wcol(wcount[n]);
+    std::vector<double> wval((size_t)wcount[n] * NV);
+    {
+        std::vector<int64_t> fill(wcount.begin(), wcount.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int64_t j = col[e];
+                if (j == i) continue;
+                const int64_t p = fill[j]++;
+                wcol[p] = (int32_t)i;
+                wval[p * NV] = val[e * NV];
+                if (cplx) wval[p * NV + 1] = -val[e * NV + 1];
+            }
+    }
+
+    // ---- dependency levels: row i waits for every j < i it reads this cycle
+    //      through C (Eq. 4) or C^dagger (Eq. 5)
+    std::vector<int32_t> level(n, 0);
+    int nlev = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int lv = 0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1] && col[e] < i; ++e) lv = std::max(lv, level[col[e]] + 1);
+        for (int64_t e = wcount[i]; e < wcount[i + 1] && wcol[e] < i; ++e) lv = std::max(lv, level[wcol[e]] + 1);
+        level[i] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    P.nlev = nlev;
+    std::vector<int32_t> lev_ptr(nlev + 1, 0), perm(n);
+    for (int64_t i = 0; i < n; ++i) lev_ptr[level[i] + 1]++;
+    for (int l = 0; l < nlev; ++l) lev_ptr[l + 1] += lev_ptr[l];
+    {
+        std::vector<int32_t> fill(lev_ptr.begin(), lev_ptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i) perm[fill[level[i]]++] = (int32_t)i;
+        // rows of one level are independent: order them by decreasing work so
+        // the rows a warp takes together cost about the same
+        for (int l = 0; l < nlev; ++l)
+            std::stable_sort(perm.begin() + lev_ptr[l], perm.begin() + lev_ptr[l + 1], [&](int32_t x, int32_t y) {
+                const int64_t dx = (row_ptr[x + 1] - row_ptr[x]) + (wcount[x + 1] - wcount[x]);
+                const int64_t dy = (row_ptr[y + 1] - row_ptr[y]) + (wcount[y + 1] - wcount[y]);
+                return dx > dy;
+            });
+    }
+
+    // ---- the chunk stream (see internal.h): per chunk of a level, the row
+    //      records, constants (filled on the GPU below) and entries of C and C^H
+    const size_t ent_sz = cplx ? sizeof(EntC) : sizeof(EntR);
+    const size_t cst_sz = cplx ? sizeof(CstC) : sizeof(CstR);
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    auto blob_bytes = [&](size_t rows, size_t nz, size_t nwv) {
+        return a16(16 * (rows + 1)) + a16(cst_sz * rows) + a16(ent_sz * nz) + a16(ent_sz * nwv);
+    };
+    auto zdeg = [&](int64_t i) { return (size_t)(row_ptr[i + 1] - row_ptr[i] - 1); };
+    auto wdeg = [&](int64_t i) { return (size_t)(wcount[i + 1] - wcount[i]); };
+    size_t blob_max = (size_t)min_blob;
+    for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, zdeg(i), wdeg(i)));
+    blob_max = (blob_max + 127) & ~(size_t)127;
+    if (blob_max > 100 * 1024)
+        return prep_fail(err, MCINV_E_UNSUPPORTED,
+                         "a row has too many off-diagonal entries in C and C^dagger for one shared-memory chunk (limit about %zu)",
+                         (size_t)(100 * 1024 - 64) / ent_sz);
+    P.blob_max = (int)blob_max;
+    std::vector<ChunkDesc> chunks;
+    std::vector<long long> cst_at(n);
+    size_t stream_bytes = 0;
+    for (int l = 0; l < nlev; ++l) {
+        int64_t p = lev_ptr[l];
+        while (p < lev_ptr[l + 1]) {
+            const int64_t pb = p;
+            size_t nz = 0, nwv = 0;
+            while (p < lev_ptr[l + 1] && blob_bytes(p - pb + 1, nz + zdeg(perm[p]), nwv + wdeg(perm[p])) <= blob_max) {
+                nz += zdeg(perm[p]);
+                nwv += wdeg(perm[p]);
+                ++p;
+            }
+            ChunkDesc d{};
+            d.rows = (int)(p - pb);
+            d.pb = (int)pb;
+            d.cst_off = (int)a16(16 * (d.rows + 1));
+            d.zent_off = d.cst_off + (int)a16(cst_sz * d.rows);
+            d.went_off = d.zent_off + (int)a16(ent_sz * nz);
+            d.bytes = d.went_off + (int)a16(ent_sz * nwv);
+            d.off = (long long)stream_bytes;
+            d.flags = p == lev_ptr[l + 1] ? CHUNK_LEVEL_END : 0;
+            stream_bytes += ((size_t)d.bytes + 127) & ~(size_t)127;
+            chunks.push_back(d);
+        }
+    }
+    std::vector<uint8_t> stream(stream_bytes, 0);
+    for (const ChunkDesc &d : chunks) {
+        uint8_t *blob = stream.data() + d.off;
+        RowMeta *meta = (RowMeta *)blob;
+        int zo = 0, wo = 0;
+        for (int r = 0; r < d.rows; ++r) {
+            const int64_t i = perm[d.pb + r];
+            meta[r] = RowMeta{(int)i, zo, wo, 0};
+            cst_at[d.pb + r] = d.off + d.cst_off + (long long)(r * cst_sz);
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                if (col[e] == i) continue;
+                if (!cplx) ((EntR *)(blob + d.zent_off))[zo++] = EntR{col[e], (float)val[e]};
+                else ((EntC *)(blob + d.zent_off))[zo++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
+            }
+            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) {
+                if (!cplx) ((EntR *)(blob + d.went_off))[wo++] = EntR{wcol[e], (float)wval[e]};
+                else ((EntC *)(blob + d.went_off))[wo++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
+            }
+        }
+        meta[d.rows] = RowMeta{-1, zo, wo, 0};
+    }
+    std::vector<int32_t> pos(n);
+    for (int64_t p = 0; p < n; ++p) pos[perm[p]] = (int32_t)p;
+    std::vector<double> diag_pos((size_t)n * NV);
+    for (int64_t p = 0; p < n; ++p)
+        for (int v = 0; v < NV; ++v) diag_pos[(size_t)p * NV + v] = diag[(size_t)perm[p] * NV + v];
+
+    P.chunks = std::move(chunks);
+    P.stream = std::move(stream);
+    P.cst_at = std::move(cst_at);
+    P.perm = std::move(perm);
+    P.pos = std::move(pos);
+    P.diag_pos = std::move(diag_pos);
+    return MCINV_OK;
+}
+
+}  // namespace mcinv

@@ -318,6 +318,168 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
 // on the position); then all 2U gathers of z and w are issued before any FMA
 // consumes them.  The gathers are the only round trip to memory on the path.
 // ---------------------------------------------------------------------------
+// The rows of one staged chunk for one lane's chains (shared by the
+// single-matrix sweep and the pool's persistent sweep, so both compute the
+// same arithmetic in the same order).
+struct ChunkWork {
+    const uint8_t *buf;        // the chunk's blob in shared memory
+    ChunkDesc d;
+    const void *zo, *wo;       // last cycle's state [n][K]
+    void *zn, *wn;             // this cycle's state
+    const uint32_t *noise;     // noise words of this cycle and this lane's chain word, by position
+    void *dpart;               // this lane's unit of diagonal partials (by position), or null
+    bool diag, dlead;
+    int seg;
+    const int *rpos, *spos;    // by position, or null
+    uint16_t *zsh, *wsh;
+    long long ldsh, kp;
+    int shcol;
+    size_t K;
+    int c0, first, stride, sub;
+    bool chain_ok;
+    uint32_t cshift;
+};
+
+template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
+__device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w)
+{
+    using P = Prec<CPLX>;
+    using L = Lane<CPLX, V>;
+    using T = typename L::T;
+    using S = typename L::S;
+    using Ent = typename P::Ent;
+    using Cst = typename P::Cst;
+    const uint8_t *buf = w.buf;
+    const ChunkDesc &d = w.d;
+    const T *zo = (const T *)w.zo;
+    T *zn = (T *)w.zn;
+    const T *wo = (const T *)w.wo;
+    T *wn = (T *)w.wn;
+    const size_t K = w.K;
+    const int c0 = w.c0, first = w.first, stride = w.stride, sub = w.sub, seg = w.seg;
+    const bool chain_ok = w.chain_ok, dlead = w.dlead;
+    const uint32_t cshift = w.cshift;
+    S *dpart = (S *)w.dpart;
+    bool diverged = false;
+
+            const RowMeta *meta = (const RowMeta *)buf;
+            const Cst *cstv = (const Cst *)(buf + d.cst_off);
+            const Ent *zs = (const Ent *)(buf + d.zent_off);
+            const Ent *ws = (const Ent *)(buf + d.went_off);
+            const uint32_t *__restrict__ noise = w.noise;
+            const int shcol = w.shcol;
+            for (int base = first; base < d.rows; base += stride) {
+                const int r = base + sub;
+                const bool ok = chain_ok && r < d.rows;
+                S prod = P::zero();
+                S dold = P::zero();
+                const int p = d.pb + r;
+                if (ok) {
+                    const uint32_t bits = __ldg(&noise[p]) >> cshift;
+                    if (w.diag && dlead) dold = dpart[p];
+                    int rp = -1, sp = -1;
+                    if (w.rpos) { rp = __ldg(&w.rpos[p]); sp = __ldg(&w.spos[p]); }
+                    const RowMeta m = meta[r];
+                    const int i = m.row;
+                    const int zb = m.zoff, zeN = meta[r + 1].zoff;
+                    const int wb = m.woff, weN = meta[r + 1].woff;
+                    T sz = L::zero(), sw = L::zero();
+                    for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
+                        // issue every gather before any FMA consumes one; real entries
+                        // (8 B) stay in registers, complex ones (16 B) are re-read from
+                        // shared memory by the FMA pass to keep the register budget
+                        constexpr bool KEEP = !CPLX;
+                        Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
+                        T xz[U], xw[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            xz[u] = L::zero();
+                            xw[u] = L::zero();
+                            if (ez + u < zeN) {
+                                const Ent e = zs[ez + u];
+                                if constexpr (KEEP) enz[u] = e;
+                                const T *src = e.col < i ? zn : zo;
+                                xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
+                            }
+                            if (ew + u < weN) {
+                                const Ent e = ws[ew + u];
+                                if constexpr (KEEP) enw[u] = e;
+                                const T *src = e.col < i ? wn : wo;
+                                xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if constexpr (KEEP) {
+                                if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                            } else {
+                                if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
+                            }
+                        }
+                    }
+                    const Cst k = cstv[r];
+                    T zv, wv;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
+                        const S zsc = P::zrow(k, phi, L::get(sz, v));
+                        const S wsc = P::wrow(k, phi, L::get(sw, v));
+                        L::set(zv, v, zsc);
+                        L::set(wv, v, wsc);
+                        diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
+                        prod = P::add(prod, P::mulconj(zsc, wsc));
+                    }
+                    zn[((size_t)i * K + c0) / V] = zv;
+                    wn[((size_t)i * K + c0) / V] = wv;
+                    if (rp >= 0 || sp >= 0) {
+                        // shadow column of (cycle, chain): cycle block of kp elements, then
+                        // the chain (x2 for re,im); blocks are padded to 64 and the pad
+                        // stays zero
+                        const size_t o = (size_t)shcol * w.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                        constexpr int NF = L::NF;
+                        if (rp >= 0) {
+                            uint16_t *dst = w.zsh + (size_t)rp * w.ldsh + o;
+#pragma unroll
+                            for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
+                        }
+                        if (sp >= 0) {
+                            if constexpr (!CPLX) {
+                                uint16_t *dst = w.wsh + (size_t)sp * w.ldsh + o;
+#pragma unroll
+                                for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
+                            } else {
+                                // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
+                                // [-wi, wr] to Im(z conj w), so the product comes out
+                                // interleaved re,im
+                                uint16_t *w0 = w.wsh + (size_t)(2 * sp) * w.ldsh + o;
+                                uint16_t *w1 = w0 + w.ldsh;
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    const S x = L::get(wv, v);
+                                    w0[2 * v] = bf16_bits(x.x);
+                                    w0[2 * v + 1] = bf16_bits(x.y);
+                                    w1[2 * v] = bf16_bits(-x.y);
+                                    w1[2 * v + 1] = bf16_bits(x.x);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (w.diag) {
+                    // sum over the seg lanes of a unit (all lanes shuffle); the leader
+                    // adds the running partial it loaded at the start of the row
+#pragma unroll
+                    for (int o = 1; o < LPR; o <<= 1)
+                        if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
+                    if (ok && dlead) dpart[p] = P::add(dold, prod);
+                }
+            }
+        
+    return diverged;
+}
+
 template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
 __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
 {
@@ -397,120 +559,16 @@ __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
                         smem_addr(&bars[b ^ 1]));
         }
         if (!*abort_flag) {
-            const RowMeta *meta = (const RowMeta *)buf;
-            const Cst *cstv = (const Cst *)(buf + d.cst_off);
-            const Ent *zs = (const Ent *)(buf + d.zent_off);
-            const Ent *ws = (const Ent *)(buf + d.went_off);
-            const uint32_t *__restrict__ noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
-            const int shcol = a.cyc0_in_batch + cyc;
-            for (int base = first; base < d.rows; base += stride) {
-                const int r = base + sub;
-                const bool ok = chain_ok && r < d.rows;
-                S prod = P::zero();
-                S dold = P::zero();
-                const int p = d.pb + r;
-                if (ok) {
-                    const uint32_t bits = __ldg(&noise[p]) >> cshift;
-                    if (a.diag_part && dlead) dold = dpart[p];
-                    int rp = -1, sp = -1;
-                    if (a.rpos) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
-                    const RowMeta m = meta[r];
-                    const int i = m.row;
-                    const int zb = m.zoff, zeN = meta[r + 1].zoff;
-                    const int wb = m.woff, weN = meta[r + 1].woff;
-                    T sz = L::zero(), sw = L::zero();
-                    for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
-                        // issue every gather before any FMA consumes one; real entries
-                        // (8 B) stay in registers, complex ones (16 B) are re-read from
-                        // shared memory by the FMA pass to keep the register budget
-                        constexpr bool KEEP = !CPLX;
-                        Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
-                        T xz[U], xw[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            xz[u] = L::zero();
-                            xw[u] = L::zero();
-                            if (ez + u < zeN) {
-                                const Ent e = zs[ez + u];
-                                if constexpr (KEEP) enz[u] = e;
-                                const T *src = e.col < i ? zn : zo;
-                                xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
-                            }
-                            if (ew + u < weN) {
-                                const Ent e = ws[ew + u];
-                                if constexpr (KEEP) enw[u] = e;
-                                const T *src = e.col < i ? wn : wo;
-                                xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if constexpr (KEEP) {
-                                if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
-                                if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
-                            } else {
-                                if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
-                                if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
-                            }
-                        }
-                    }
-                    const Cst k = cstv[r];
-                    T zv, wv;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
-                        const S zsc = P::zrow(k, phi, L::get(sz, v));
-                        const S wsc = P::wrow(k, phi, L::get(sw, v));
-                        L::set(zv, v, zsc);
-                        L::set(wv, v, wsc);
-                        diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
-                        prod = P::add(prod, P::mulconj(zsc, wsc));
-                    }
-                    zn[((size_t)i * K + c0) / V] = zv;
-                    wn[((size_t)i * K + c0) / V] = wv;
-                    if (rp >= 0 || sp >= 0) {
-                        // shadow column of (cycle, chain): cycle block of kp elements, then
-                        // the chain (x2 for re,im); blocks are padded to 64 and the pad
-                        // stays zero
-                        const size_t o = (size_t)shcol * a.kp + (size_t)c0 * (CPLX ? 2 : 1);
-                        constexpr int NF = L::NF;
-                        if (rp >= 0) {
-                            uint16_t *dst = a.zsh + (size_t)rp * a.ldsh + o;
-#pragma unroll
-                            for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
-                        }
-                        if (sp >= 0) {
-                            if constexpr (!CPLX) {
-                                uint16_t *dst = a.wsh + (size_t)sp * a.ldsh + o;
-#pragma unroll
-                                for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
-                            } else {
-                                // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
-                                // [-wi, wr] to Im(z conj w), so the product comes out
-                                // interleaved re,im
-                                uint16_t *w0 = a.wsh + (size_t)(2 * sp) * a.ldsh + o;
-                                uint16_t *w1 = w0 + a.ldsh;
-#pragma unroll
-                                for (int v = 0; v < V; ++v) {
-                                    const S x = L::get(wv, v);
-                                    w0[2 * v] = bf16_bits(x.x);
-                                    w0[2 * v + 1] = bf16_bits(x.y);
-                                    w1[2 * v] = bf16_bits(-x.y);
-                                    w1[2 * v + 1] = bf16_bits(x.x);
-                                }
-                            }
-                        }
-                    }
-                }
-                if (a.diag_part) {
-                    // sum over the seg lanes of a unit (all lanes shuffle); the leader
-                    // adds the running partial it loaded at the start of the row
-#pragma unroll
-                    for (int o = 1; o < LPR; o <<= 1)
-                        if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
-                    if (ok && dlead) dpart[p] = P::add(dold, prod);
-                }
-            }
+            ChunkWork w;
+            w.buf = buf; w.d = d;
+            w.zo = zo; w.zn = zn; w.wo = wo; w.wn = wn;
+            w.noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
+            w.dpart = dpart; w.diag = a.diag_part != nullptr; w.dlead = dlead; w.seg = seg;
+            w.rpos = a.rpos; w.spos = a.spos; w.zsh = a.zsh; w.wsh = a.wsh; w.ldsh = a.ldsh; w.kp = a.kp;
+            w.shcol = a.cyc0_in_batch + cyc;
+            w.K = K; w.c0 = c0; w.first = first; w.stride = stride; w.sub = sub;
+            w.chain_ok = chain_ok; w.cshift = cshift;
+            diverged |= sweep_chunk_rows<CPLX, LPR, V, U, CLUSTER>(w);
         }
     }
     // the last chunk's rows are done before anyone leaves (the cluster's CTAs
