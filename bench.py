@@ -132,7 +132,9 @@ def traffic_from_profiles(kernel_file, units_per_launch):
     p = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(p):
         return None
-    src = open(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", "sweep.cu"), "rb").read()
+    src = b"".join(open(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f), "rb").read()
+                   for f in ("sweep.cu", "sweep_core.cuh")
+                   if os.path.exists(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f)))
     digest = hashlib.sha256(src).hexdigest()[:16]
     per_unit, ok = None, False
     for line in open(p):

@@ -207,6 +207,78 @@ mcinv_status mcinv_profile_read(mcinv_t h, mcinv_kernel kernel, int64_t *launche
 mcinv_status mcinv_selftest_tc_gemm(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
                                     const uint16_t *B, float *D);
 
+/* ------------------------------------------------------------------------ */
+/* Pool: many independent real matrices advanced together (the batched form) */
+/* with continuous batching.                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct mcinv_pool_ctx *mcinv_pool_t;
+
+typedef struct {
+    int64_t K;              /* chains per matrix, a multiple of 4 */
+    uint64_t seed;          /* Philox key shared by all matrices (each has its own matrix id) */
+    int64_t chain_base;
+    int64_t mem_budget;     /* bytes of device memory reserved for the pool (one arena) */
+    int32_t max_slots;      /* matrices resident at once */
+    int32_t batch_cycles;   /* B: cycles every matrix advances per step; 0 = 8 */
+    int32_t groups;         /* SE groups of the diagonal; 0 = 32 */
+    int32_t chains_per_cta; /* 0 = the first steps time the candidate shapes */
+    int32_t threads_per_cta;
+    int32_t flags;
+    void *stream;
+} mcinv_pool_options;
+
+typedef struct {
+    int64_t K, steps, kernel_launches, arena_bytes, arena_used;
+    int32_t chains_per_cta, threads_per_cta, groups, batch_cycles, active, tuned;
+} mcinv_pool_info_t;
+
+void mcinv_pool_default_options(mcinv_pool_options *opt);
+
+/* Reserve the pool's device arena (mem_budget bytes, one allocation) and its
+ * tables.  Every later device buffer of a member comes out of the arena. */
+mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_options *opt);
+
+/* Device bytes a real matrix with n rows and nnz entries would take (an upper
+ * estimate before preparing it). */
+mcinv_status mcinv_pool_footprint(mcinv_pool_t p, int64_t n, int64_t nnz, int32_t want_inverse, int64_t *bytes);
+
+/*
+ * Admit a real matrix (CSR as for mcinv_create) that will run `burnin` cycles
+ * and then `samples` sampling cycles (Algorithm 1 with a fixed burn-in),
+ * accumulating its diagonal and, if want_inverse, the full inverse (Eq. 1/C).
+ * matrix_id keys its noise (Philox counter word 3).  Returns a ticket.
+ * MCINV_E_NOMEM when no slot is free or the arena cannot hold it: the caller
+ * keeps the request and submits it again after members are released.
+ */
+mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                               const double *val, uint32_t matrix_id, int64_t burnin, int64_t samples,
+                               int32_t want_inverse, int64_t *ticket);
+
+/* Advance every admitted, unfinished matrix by one step of B cycles (their
+ * own mix of burn-in and sampling).  Enqueues work on the pool's stream; a
+ * step is a replay of one CUDA graph once the slice shape is chosen. */
+mcinv_status mcinv_pool_step(mcinv_pool_t p);
+
+/* *done = 1 once the ticket's matrix has run all its cycles. */
+mcinv_status mcinv_pool_poll(mcinv_pool_t p, int64_t ticket, int32_t *done);
+
+/* Estimates of one member, as mcinv_estimate (real only; BLOCK = the full
+ * n x n inverse when want_inverse was set). */
+mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcinv_kind kind, const double *q_diag,
+                                 double *out, double *se_out);
+
+/* Chain state of one member, as mcinv_get_state (test hook). */
+mcinv_status mcinv_pool_get_state(mcinv_pool_t p, int64_t ticket, int64_t chain0, int64_t nchains, double *z,
+                                  double *w, int64_t *cycle);
+
+/* Free a member's slot and arena memory (waits for queued work first). */
+mcinv_status mcinv_pool_release(mcinv_pool_t p, int64_t ticket);
+
+mcinv_status mcinv_pool_info(mcinv_pool_t p, mcinv_pool_info_t *info);
+mcinv_status mcinv_pool_sync(mcinv_pool_t p);
+void mcinv_pool_destroy(mcinv_pool_t p);
+const char *mcinv_pool_last_error(mcinv_pool_t p);
+
 /*
  * One batch of the block accumulation that allocates nothing.  The paper has
  * no counterpart: this exists for callers that cannot allocate device memory,

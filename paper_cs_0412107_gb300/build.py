@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcinv.so")
-SOURCES = ["sweep.cu", "accumulate.cu", "context.cu", "prepare.cu", "tc_gemm.cu", "noalloc.cu"]
-HEADERS = ["internal.h", "tc_gemm.h", "prepare.h"]
+SOURCES = ["sweep.cu", "accumulate.cu", "context.cu", "prepare.cu", "tc_gemm.cu", "noalloc.cu", "pool.cu"]
+HEADERS = ["internal.h", "tc_gemm.h", "prepare.h", "sweep_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -1,0 +1,351 @@
+// sweep_core.cuh -- the row arithmetic of the coupled sweep (Eqs. 4 and 5)
+// and the staging of the chunk stream, shared by the single-matrix sweep
+// (sweep.cu) and the pool's persistent sweep (pool.cu), so both compute the
+// same values in the same order.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace mcinv {
+
+// ---------------------------------------------------------------------------
+// Scalar helpers for the two sweep precisions.
+// ---------------------------------------------------------------------------
+template <bool CPLX> struct Prec;
+template <> struct Prec<false> {
+    using T = float;
+    using Ent = EntR;
+    using Cst = CstR;
+    static __device__ __forceinline__ T zero() { return 0.f; }
+    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x) { acc = fmaf(e.val, x, acc); }
+    // Eq. 4 / Eq. 5 right-hand sides
+    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s) { return phi * k.alpha - k.inv_d * s; }
+    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s) { return phi * k.beta - k.inv_d * s; }
+    static __device__ __forceinline__ T mulconj(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+    static __device__ __forceinline__ bool finite_bounded(T v) { return fabsf(v) <= 1e30f; }
+};
+template <> struct Prec<true> {
+    using T = float2;
+    using Ent = EntC;
+    using Cst = CstC;
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x)
+    {
+        acc.x = fmaf(e.re, x.x, fmaf(-e.im, x.y, acc.x));
+        acc.y = fmaf(e.re, x.y, fmaf(e.im, x.x, acc.y));
+    }
+    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s)
+    {   // phi alpha - inv_d s
+        return make_float2(phi * k.alpha.x - (k.inv_d.x * s.x - k.inv_d.y * s.y),
+                           phi * k.alpha.y - (k.inv_d.x * s.y + k.inv_d.y * s.x));
+    }
+    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s)
+    {   // phi beta - conj(inv_d) s
+        return make_float2(phi * k.beta.x - (k.inv_d.x * s.x + k.inv_d.y * s.y),
+                           phi * k.beta.y - (k.inv_d.x * s.y - k.inv_d.y * s.x));
+    }
+    static __device__ __forceinline__ T mulconj(T a, T b)
+    {   // a conj(b)
+        return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    }
+    static __device__ __forceinline__ T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ T shfl_xor(T v, int o)
+    {
+        return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    }
+    static __device__ __forceinline__ bool finite_bounded(T v) { return fabsf(v.x) <= 1e30f && fabsf(v.y) <= 1e30f; }
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float x)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// V chains of one lane as a single vector: V consecutive chains of one row are
+// contiguous in the [n][K] layout, so each gather is one 4-, 8- or 16-byte load.
+template <bool CPLX, int V> struct Vec;
+template <> struct Vec<false, 1> { using T = float; };
+template <> struct Vec<false, 4> { using T = float4; };
+template <> struct Vec<true, 1> { using T = float2; };
+template <> struct Vec<true, 2> { using T = float4; };
+
+template <bool CPLX, int V>
+struct Lane {
+    using P = Prec<CPLX>;
+    using S = typename P::T;                 // one chain's scalar (float or float2)
+    using T = typename Vec<CPLX, V>::T;      // the lane's V chains
+    static constexpr int NF = (CPLX ? 2 : 1) * V;  // floats per lane vector
+    static __device__ __forceinline__ float *f(T &v) { return reinterpret_cast<float *>(&v); }
+    static __device__ __forceinline__ const float *f(const T &v) { return reinterpret_cast<const float *>(&v); }
+    static __device__ __forceinline__ T zero()
+    {
+        T v;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) f(v)[k] = 0.f;
+        return v;
+    }
+    static __device__ __forceinline__ S get(const T &v, int k)
+    {
+        if constexpr (CPLX) return make_float2(f(v)[2 * k], f(v)[2 * k + 1]);
+        else return f(v)[k];
+    }
+    static __device__ __forceinline__ void set(T &v, int k, S x)
+    {
+        if constexpr (CPLX) { f(v)[2 * k] = x.x; f(v)[2 * k + 1] = x.y; }
+        else f(v)[k] = x;
+    }
+    // acc += c * x for each of the V chains
+    static __device__ __forceinline__ void fma(T &acc, const typename P::Ent &e, const T &x)
+    {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            S s = get(acc, k);
+            P::fma(s, e, get(x, k));
+            set(acc, k, s);
+        }
+    }
+};
+
+// State reads of the cluster variant go to L2 (ld.global.cg): rows written by
+// another CTA of the cluster are seen after the cluster barrier, never a stale
+// L1 line.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_state(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Staging of the chunk stream: one elected thread moves each chunk's blob into
+// one of two shared-memory buffers with a bulk async copy that completes on
+// the buffer's mbarrier; every wait is bounded (2 s of globaltimer).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void stage_chunk(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (gtimer() - t0 > 2000000000ull) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The coupled sweep.  A chain slice = LPR lanes x V chains per lane; Q CTAs
+// (one thread-block cluster, Q = 1 without) share a slice and split each
+// chunk's rows.  Chains are independent, so slices never communicate.  Per
+// cycle the CTA walks the chunk stream; a block barrier ends every chunk (its
+// buffer is recycled) and a cluster barrier ends every level.  State is
+// double-buffered: a row reads z_j (j < i) from the buffer being written this
+// cycle and z_j (j > i) from last cycle's buffer, exactly the in-place
+// semantics of Eq. 4 (and of Eq. 5 for w).
+//
+// Per row: the row record, constants and entries come from shared memory;
+// the noise word and the diagonal partial are loaded first (they depend only
+// on the position); then all 2U gathers of z and w are issued before any FMA
+// consumes them.  The gathers are the only round trip to memory on the path.
+// ---------------------------------------------------------------------------
+// The rows of one staged chunk for one lane's chains (shared by the
+// single-matrix sweep and the pool's persistent sweep, so both compute the
+// same arithmetic in the same order).
+struct ChunkWork {
+    const uint8_t *buf;        // the chunk's blob in shared memory
+    ChunkDesc d;
+    const void *zo, *wo;       // last cycle's state [n][K]
+    void *zn, *wn;             // this cycle's state
+    const uint32_t *noise;     // noise words of this cycle and this lane's chain word, by position
+    void *dpart;               // this lane's unit of diagonal partials (by position), or null
+    bool diag, dlead;
+    int seg;
+    const int *rpos, *spos;    // by position, or null
+    uint16_t *zsh, *wsh;
+    long long ldsh, kp;
+    int shcol;
+    size_t K;
+    int c0, first, stride, sub;
+    bool chain_ok;
+    uint32_t cshift;
+};
+
+template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
+__device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w)
+{
+    using P = Prec<CPLX>;
+    using L = Lane<CPLX, V>;
+    using T = typename L::T;
+    using S = typename L::S;
+    using Ent = typename P::Ent;
+    using Cst = typename P::Cst;
+    const uint8_t *buf = w.buf;
+    const ChunkDesc &d = w.d;
+    const T *zo = (const T *)w.zo;
+    T *zn = (T *)w.zn;
+    const T *wo = (const T *)w.wo;
+    T *wn = (T *)w.wn;
+    const size_t K = w.K;
+    const int c0 = w.c0, first = w.first, stride = w.stride, sub = w.sub, seg = w.seg;
+    const bool chain_ok = w.chain_ok, dlead = w.dlead;
+    const uint32_t cshift = w.cshift;
+    S *dpart = (S *)w.dpart;
+    bool diverged = false;
+
+            const RowMeta *meta = (const RowMeta *)buf;
+            const Cst *cstv = (const Cst *)(buf + d.cst_off);
+            const Ent *zs = (const Ent *)(buf + d.zent_off);
+            const Ent *ws = (const Ent *)(buf + d.went_off);
+            const uint32_t *__restrict__ noise = w.noise;
+            const int shcol = w.shcol;
+            for (int base = first; base < d.rows; base += stride) {
+                const int r = base + sub;
+                const bool ok = chain_ok && r < d.rows;
+                S prod = P::zero();
+                S dold = P::zero();
+                const int p = d.pb + r;
+                if (ok) {
+                    const uint32_t bits = __ldg(&noise[p]) >> cshift;
+                    if (w.diag && dlead) dold = dpart[p];
+                    int rp = -1, sp = -1;
+                    if (w.rpos) { rp = __ldg(&w.rpos[p]); sp = __ldg(&w.spos[p]); }
+                    const RowMeta m = meta[r];
+                    const int i = m.row;
+                    const int zb = m.zoff, zeN = meta[r + 1].zoff;
+                    const int wb = m.woff, weN = meta[r + 1].woff;
+                    T sz = L::zero(), sw = L::zero();
+                    for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
+                        // issue every gather before any FMA consumes one; real entries
+                        // (8 B) stay in registers, complex ones (16 B) are re-read from
+                        // shared memory by the FMA pass to keep the register budget
+                        constexpr bool KEEP = !CPLX;
+                        Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
+                        T xz[U], xw[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            xz[u] = L::zero();
+                            xw[u] = L::zero();
+                            if (ez + u < zeN) {
+                                const Ent e = zs[ez + u];
+                                if constexpr (KEEP) enz[u] = e;
+                                const T *src = e.col < i ? zn : zo;
+                                xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
+                            }
+                            if (ew + u < weN) {
+                                const Ent e = ws[ew + u];
+                                if constexpr (KEEP) enw[u] = e;
+                                const T *src = e.col < i ? wn : wo;
+                                xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if constexpr (KEEP) {
+                                if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                            } else {
+                                if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
+                                if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
+                            }
+                        }
+                    }
+                    const Cst k = cstv[r];
+                    T zv, wv;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
+                        const S zsc = P::zrow(k, phi, L::get(sz, v));
+                        const S wsc = P::wrow(k, phi, L::get(sw, v));
+                        L::set(zv, v, zsc);
+                        L::set(wv, v, wsc);
+                        diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
+                        prod = P::add(prod, P::mulconj(zsc, wsc));
+                    }
+                    zn[((size_t)i * K + c0) / V] = zv;
+                    wn[((size_t)i * K + c0) / V] = wv;
+                    if (rp >= 0 || sp >= 0) {
+                        // shadow column of (cycle, chain): cycle block of kp elements, then
+                        // the chain (x2 for re,im); blocks are padded to 64 and the pad
+                        // stays zero
+                        const size_t o = (size_t)shcol * w.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                        constexpr int NF = L::NF;
+                        if (rp >= 0) {
+                            uint16_t *dst = w.zsh + (size_t)rp * w.ldsh + o;
+#pragma unroll
+                            for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
+                        }
+                        if (sp >= 0) {
+                            if constexpr (!CPLX) {
+                                uint16_t *dst = w.wsh + (size_t)sp * w.ldsh + o;
+#pragma unroll
+                                for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
+                            } else {
+                                // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
+                                // [-wi, wr] to Im(z conj w), so the product comes out
+                                // interleaved re,im
+                                uint16_t *w0 = w.wsh + (size_t)(2 * sp) * w.ldsh + o;
+                                uint16_t *w1 = w0 + w.ldsh;
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    const S x = L::get(wv, v);
+                                    w0[2 * v] = bf16_bits(x.x);
+                                    w0[2 * v + 1] = bf16_bits(x.y);
+                                    w1[2 * v] = bf16_bits(-x.y);
+                                    w1[2 * v + 1] = bf16_bits(x.x);
+                                }
+                            }
+                        }
+                    }
+                }
+                if (w.diag) {
+                    // sum over the seg lanes of a unit (all lanes shuffle); the leader
+                    // adds the running partial it loaded at the start of the row
+#pragma unroll
+                    for (int o = 1; o < LPR; o <<= 1)
+                        if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
+                    if (ok && dlead) dpart[p] = P::add(dold, prod);
+                }
+            }
+        
+    return diverged;
+}
+
+}  // namespace mcinv

@@ -270,6 +270,173 @@ bool encode(CUtensorMap *map, const uint16_t *base, size_t rows, long long ld, i
     return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Grouped, persistent variant for a pool of matrices: CTAs walk a device tile
+// table (matrix, m0, n0); each matrix has its own pair of tensor maps in
+// global memory and its own output.  Warps: 0 = TMA producer, 1 = MMA issuer,
+// 2..5 = epilogue (warp w reads TMEM lanes 32*(w%4) .. +31).  The smem ring's
+// stage/phase counters run on across tiles; tmem_full / tmem_empty hand the
+// single 256-column accumulator between the MMA issuer and the epilogue.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_grouped_kernel(const GroupTile *__restrict__ tiles, const int *__restrict__ ntiles_p,
+                           const CUtensorMap *__restrict__ maps, const GroupOut *__restrict__ outs, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_BYTES;
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 1;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = *ntiles_p;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(tfull), 1);
+        mbar_init(smem_u32(tempty), 4);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int kg = 0;  // k-slices issued so far (ring position)
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const GroupTile tile = tiles[t];
+                const CUtensorMap *ma = &maps[2 * tile.slot], *mb = &maps[2 * tile.slot + 1];
+                const int kt_n = outs[tile.slot].ktiles;
+                for (int kt = 0; kt < kt_n; ++kt, ++kg) {
+                    const int s = kg % STAGES;
+                    const uint32_t phase = (uint32_t)(kg / STAGES) & 1u;
+                    if (kg >= STAGES && !mbar_wait(smem_u32(&empty[s]), phase ^ 1u, abort_flag)) break;
+                    mbar_expect_tx(smem_u32(&full[s]), STAGE_BYTES);
+                    tma_load_2d(smem_u32(sA + s * A_BYTES), ma, smem_u32(&full[s]), kt * BK, tile.m0);
+                    tma_load_2d(smem_u32(sB + s * B_BYTES), mb, smem_u32(&full[s]), kt * BK, tile.n0);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int kg = 0, tl = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
+                const int kt_n = outs[tiles[t].slot].ktiles;
+                // the epilogue must have drained the accumulator of the previous tile
+                if (tl > 0 && !mbar_wait(smem_u32(tempty), (uint32_t)(tl - 1) & 1u, abort_flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool ok = true;
+                for (int kt = 0; kt < kt_n; ++kt, ++kg) {
+                    const int s = kg % STAGES;
+                    const uint32_t phase = (uint32_t)(kg / STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&full[s]), phase, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t a = sdesc(smem_u32(sA + s * A_BYTES));
+                    const uint64_t b = sdesc(smem_u32(sB + s * B_BYTES));
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(tmem, a + 2 * kk, b + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(tfull));
+            }
+        }
+    } else {
+        // epilogue warps 2..5
+        const int q = warp & 3;
+        int tl = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const GroupTile tile = tiles[t];
+            const GroupOut o = outs[tile.slot];
+            const bool have = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull), (uint32_t)tl & 1u, abort_flag));
+            if (!have) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = tile.m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                if (row < o.M) {
+                    float *dst = o.D + (size_t)row * o.N + tile.n0 + c0;
+                    if (tile.n0 + c0 + 32 <= o.N && (o.N & 3) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (tile.n0 + c0 + j < o.N) dst[j] = __uint_as_float(r[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+        }
+    }
+    __syncwarp();
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicOr(status, 2);
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+}  // namespace
+
+bool tc_encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, long long ld, long long inner,
+                       bool is_b, const char **why)
+{
+    auto fn = encode_fn();
+    if (!fn) {
+        if (why) *why = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(is_b ? BN : BM)};
+    cuuint32_t estr[2] = {1, 1};
+    if (fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        if (why) *why = "cuTensorMapEncodeTiled rejected an operand";
+        return false;
+    }
+    return true;
+}
+
+cudaError_t tc_gemm_grouped_run(const GroupTile *tiles, const int *ntiles, const CUtensorMap *maps, const GroupOut *outs,
+                                int grid, int *status, cudaStream_t s)
+{
+    const int smem = STAGES * STAGE_BYTES + 1024 + 256;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    tc_gemm_grouped_kernel<<<grid, 192, smem, s>>>(tiles, ntiles, maps, outs, status);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 struct TcGemmPlan {

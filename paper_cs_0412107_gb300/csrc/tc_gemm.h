@@ -5,9 +5,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include <string>
 
 namespace mcinv {
+
+// Grouped contraction for a pool of matrices: tile t computes the 128 x 256
+// block (m0, n0) of matrix `slot`; maps[2*slot] / maps[2*slot+1] are that
+// matrix's A and B tensor maps (in device memory), outs[slot] its output.
+struct GroupTile {
+    int slot, m0, n0, pad;
+};
+struct GroupOut {
+    float *D;   // M x N row-major FP32
+    int M, N;
+    int ktiles; // 64-wide slices of the contraction dimension this step
+    int pad;
+};
+bool tc_encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, long long ld, long long inner,
+                       bool is_b, const char **why);
+cudaError_t tc_gemm_grouped_run(const GroupTile *tiles, const int *ntiles, const CUtensorMap *maps, const GroupOut *outs,
+                                int grid, int *status, cudaStream_t s);
 
 struct TcGemmPlan;
 

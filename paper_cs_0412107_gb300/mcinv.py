@@ -32,7 +32,11 @@ EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sampl
            "mcinv_estimate", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
            "mcinv_selftest_tc_gemm", "mcinv_block_accumulate_noalloc", "mcinv_destroy",
-           "mcinv_last_error")
+           "mcinv_last_error",
+           "mcinv_pool_default_options", "mcinv_pool_create", "mcinv_pool_footprint", "mcinv_pool_submit",
+           "mcinv_pool_step", "mcinv_pool_poll", "mcinv_pool_estimate", "mcinv_pool_get_state",
+           "mcinv_pool_release", "mcinv_pool_info", "mcinv_pool_sync", "mcinv_pool_destroy",
+           "mcinv_pool_last_error")
 MCINV_KERNEL_NOISE, MCINV_KERNEL_SWEEP, MCINV_KERNEL_BLOCK, MCINV_KERNEL_FOLD, MCINV_KERNEL_ESTIMATE = range(5)
 KERNEL_NAMES = ("noise", "sweep", "block", "fold", "estimate")
 
@@ -64,6 +68,25 @@ class mcinv_info_t(ctypes.Structure):
                 ("cycle", ctypes.c_int64), ("samples", ctypes.c_int64),
                 ("block_batches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class mcinv_pool_options(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("seed", ctypes.c_uint64), ("chain_base", ctypes.c_int64),
+                ("mem_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("batch_cycles", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class mcinv_pool_info_t(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("steps", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
+                ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("groups", ctypes.c_int32), ("batch_cycles", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("tuned", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -103,6 +126,26 @@ def lib():
         L.mcinv_block_accumulate_noalloc.restype = ctypes.c_int
         L.mcinv_destroy.argtypes = [vp]
         L.mcinv_destroy.restype = None
+        L.mcinv_pool_default_options.argtypes = [ctypes.POINTER(mcinv_pool_options)]
+        L.mcinv_pool_default_options.restype = None
+        L.mcinv_pool_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mcinv_pool_options)]
+        L.mcinv_pool_footprint.argtypes = [vp, i64, i64, i32, ctypes.POINTER(i64)]
+        L.mcinv_pool_submit.argtypes = [vp, i64, vp, vp, vp, ctypes.c_uint32, i64, i64, i32, ctypes.POINTER(i64)]
+        L.mcinv_pool_step.argtypes = [vp]
+        L.mcinv_pool_poll.argtypes = [vp, i64, ctypes.POINTER(i32)]
+        L.mcinv_pool_estimate.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp]
+        L.mcinv_pool_get_state.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.POINTER(i64)]
+        L.mcinv_pool_release.argtypes = [vp, i64]
+        L.mcinv_pool_info.argtypes = [vp, ctypes.POINTER(mcinv_pool_info_t)]
+        L.mcinv_pool_sync.argtypes = [vp]
+        L.mcinv_pool_destroy.argtypes = [vp]
+        L.mcinv_pool_destroy.restype = None
+        L.mcinv_pool_last_error.argtypes = [vp]
+        L.mcinv_pool_last_error.restype = ctypes.c_char_p
+        for name in ("mcinv_pool_create", "mcinv_pool_footprint", "mcinv_pool_submit", "mcinv_pool_step",
+                     "mcinv_pool_poll", "mcinv_pool_estimate", "mcinv_pool_get_state", "mcinv_pool_release",
+                     "mcinv_pool_info", "mcinv_pool_sync"):
+            getattr(L, name).restype = ctypes.c_int
         L.mcinv_last_error.argtypes = [vp]
         L.mcinv_last_error.restype = ctypes.c_char_p
         for name in ("mcinv_create", "mcinv_burnin", "mcinv_sample", "mcinv_estimate", "mcinv_sync",
@@ -304,3 +347,115 @@ def mcinv_last_error(h: Handle | None = None) -> str:
 def create_from_csr(csr, **kw) -> Handle:
     """mcinv_create from a workloads.CSR."""
     return mcinv_create(csr.n, csr.row_ptr, csr.col, csr.val, **kw)
+
+
+# -- pool: many matrices advanced together, continuous batching -------------------------
+
+def _pcheck(status, pool=None):
+    if status != MCINV_OK:
+        msg = lib().mcinv_pool_last_error(pool).decode(errors="replace")
+        raise McinvError(status, msg)
+
+
+class Pool:
+    def __init__(self, ptr, K):
+        self.ptr, self.K = ptr, K
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().mcinv_pool_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def mcinv_pool_default_options(**overrides) -> mcinv_pool_options:
+    o = mcinv_pool_options()
+    lib().mcinv_pool_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def mcinv_pool_create(*, K=256, seed=0, chain_base=0, mem_budget=1 << 32, max_slots=512, batch_cycles=8,
+                      groups=32, chains_per_cta=0, threads_per_cta=0, stream="current") -> Pool:
+    o = mcinv_pool_default_options(K=K, seed=seed, chain_base=chain_base, mem_budget=mem_budget,
+                                   max_slots=max_slots, batch_cycles=batch_cycles, groups=groups,
+                                   chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta)
+    o.stream = current_stream() if stream == "current" else stream
+    p = ctypes.c_void_p()
+    _pcheck(lib().mcinv_pool_create(ctypes.byref(p), ctypes.byref(o)))
+    return Pool(p, K)
+
+
+def mcinv_pool_footprint(pool: Pool, n, nnz, want_inverse=True) -> int:
+    b = ctypes.c_int64()
+    _pcheck(lib().mcinv_pool_footprint(pool.ptr, int(n), int(nnz), int(bool(want_inverse)), ctypes.byref(b)), pool.ptr)
+    return int(b.value)
+
+
+def mcinv_pool_submit(pool: Pool, csr, matrix_id, burnin, samples, want_inverse=True) -> int:
+    """Admit a real matrix; raises McinvError with status MCINV_E_NOMEM (4) if it does not fit now."""
+    rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(csr.col, dtype=np.int32)
+    val = np.ascontiguousarray(csr.val, dtype=np.float64)
+    t = ctypes.c_int64()
+    _pcheck(lib().mcinv_pool_submit(pool.ptr, csr.n, _ptr(rp), _ptr(col), _ptr(val), int(matrix_id),
+                                    int(burnin), int(samples), int(bool(want_inverse)), ctypes.byref(t)),
+            pool.ptr)
+    return int(t.value)
+
+
+def mcinv_pool_step(pool: Pool):
+    _pcheck(lib().mcinv_pool_step(pool.ptr), pool.ptr)
+
+
+def mcinv_pool_poll(pool: Pool, ticket) -> bool:
+    d = ctypes.c_int32()
+    _pcheck(lib().mcinv_pool_poll(pool.ptr, int(ticket), ctypes.byref(d)), pool.ptr)
+    return bool(d.value)
+
+
+def mcinv_pool_estimate(pool: Pool, ticket, kind, n, q_diag=None):
+    shape = {MCINV_EST_DIAG: (n,), MCINV_EST_TRACE: (), MCINV_EST_BLOCK: (n, n)}[kind]
+    count = int(np.prod(shape))
+    out = np.empty(count)
+    se = np.empty(count)
+    q = None if q_diag is None else np.ascontiguousarray(q_diag, dtype=np.float64)
+    _pcheck(lib().mcinv_pool_estimate(pool.ptr, int(ticket), int(kind), _ptr(q), _ptr(out), _ptr(se)), pool.ptr)
+    return out.reshape(shape), se.reshape(shape)
+
+
+def mcinv_pool_get_state(pool: Pool, ticket, n, chain0=0, nchains=None):
+    nchains = pool.K - chain0 if nchains is None else nchains
+    z = np.empty(n * nchains)
+    w = np.empty(n * nchains)
+    cyc = ctypes.c_int64()
+    _pcheck(lib().mcinv_pool_get_state(pool.ptr, int(ticket), int(chain0), int(nchains), _ptr(z), _ptr(w),
+                                       ctypes.byref(cyc)), pool.ptr)
+    return z.reshape(n, nchains), w.reshape(n, nchains), int(cyc.value)
+
+
+def mcinv_pool_release(pool: Pool, ticket):
+    _pcheck(lib().mcinv_pool_release(pool.ptr, int(ticket)), pool.ptr)
+
+
+def mcinv_pool_info(pool: Pool) -> dict:
+    i = mcinv_pool_info_t()
+    _pcheck(lib().mcinv_pool_info(pool.ptr, ctypes.byref(i)), pool.ptr)
+    return i.as_dict()
+
+
+def mcinv_pool_sync(pool: Pool):
+    _pcheck(lib().mcinv_pool_sync(pool.ptr), pool.ptr)
+
+
+def mcinv_pool_destroy(pool: Pool):
+    if pool.ptr:
+        lib().mcinv_pool_destroy(pool.ptr)
+        pool.ptr = None
+
+
+def mcinv_pool_last_error(pool: Pool | None = None) -> str:
+    return lib().mcinv_pool_last_error(None if pool is None else pool.ptr).decode(errors="replace")

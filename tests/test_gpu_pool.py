@@ -1,0 +1,131 @@
+"""The pool: many real matrices advanced together by persistent kernels that
+read device tables (the batched form), with members joining and leaving
+between steps (continuous batching).
+
+Checks: every member's chains follow the FP64 oracle (same draws: the matrix
+id keys the noise); a member's results are bit-identical whether it runs
+alone or alongside others that join later; its full inverse equals the
+single-matrix handle's; admission refuses what does not fit in the arena
+and accepts it after a release; the batch estimates cover the dense inverse.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_cs_0412107_gb300 import build as libbuild
+from paper_cs_0412107_gb300 import mcinv
+from paper_cs_0412107_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    libbuild.build()
+    mcinv.lib()
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+def run_until_done(pool, tickets, max_steps=10_000):
+    for _ in range(max_steps):
+        if all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
+            return
+        mcinv.mcinv_pool_step(pool)
+    raise AssertionError("pool did not finish")
+
+
+def test_pool_members_follow_the_oracle():
+    K, B, burn, samp = 64, 4, 6, 7
+    mats = [wl.random_dominant(n, 4, 1.5, seed) for n, seed in ((64, 1), (200, 2), (517, 3))]
+    pool = mcinv.mcinv_pool_create(K=K, seed=11, mem_budget=1 << 28, max_slots=8, batch_cycles=B)
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=100 + k, burnin=burn, samples=samp, want_inverse=True)
+               for k, c in enumerate(mats)]
+    run_until_done(pool, tickets)
+    for k, (c, t) in enumerate(zip(mats, tickets)):
+        z, w, cyc = mcinv.mcinv_pool_get_state(pool, t, c.n)
+        assert cyc == burn + samp
+        st, dacc, _ = oracle.run(c, K, seed=11, matrix=100 + k, ncycles=burn + samp, acc_from=burn)
+        assert rel_err(z, st.z.real) < TOL and rel_err(w, st.w.real) < TOL
+        dm, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, c.n)
+        assert rel_err(dm, dacc.sum(0).real / (K * samp)) < TOL
+    info = mcinv.mcinv_pool_info(pool)
+    assert info["active"] == 3 and info["kernel_launches"] >= 4
+
+
+def test_pool_result_is_the_same_alone_and_in_the_mix():
+    K, B = 64, 4
+    a = wl.random_dominant(300, 4, 1.5, 7)
+    others = [wl.random_dominant(n, 4, 1.5, 20 + n) for n in (90, 640, 150)]
+
+    alone = mcinv.mcinv_pool_create(K=K, seed=3, mem_budget=1 << 28, max_slots=8, batch_cycles=B)
+    ta = mcinv.mcinv_pool_submit(alone, a, matrix_id=5, burnin=9, samples=23)
+    run_until_done(alone, [ta])
+    ref = {k: mcinv.mcinv_pool_estimate(alone, ta, k, a.n) for k in (mcinv.MCINV_EST_DIAG, mcinv.MCINV_EST_BLOCK)}
+
+    mix = mcinv.mcinv_pool_create(K=K, seed=3, mem_budget=1 << 28, max_slots=8, batch_cycles=B)
+    t0 = mcinv.mcinv_pool_submit(mix, others[0], matrix_id=1, burnin=3, samples=5)
+    mcinv.mcinv_pool_step(mix)
+    tm = mcinv.mcinv_pool_submit(mix, a, matrix_id=5, burnin=9, samples=23)  # joins while others run
+    mcinv.mcinv_pool_step(mix)
+    t1 = mcinv.mcinv_pool_submit(mix, others[1], matrix_id=2, burnin=11, samples=40)
+    mcinv.mcinv_pool_step(mix)
+    run_until_done(mix, [t0])
+    mcinv.mcinv_pool_release(mix, t0)  # leaves; its memory is reused by the next member
+    t2 = mcinv.mcinv_pool_submit(mix, others[2], matrix_id=3, burnin=2, samples=30)
+    run_until_done(mix, [tm, t1, t2])
+    for k, (m, se) in ref.items():
+        m2, se2 = mcinv.mcinv_pool_estimate(mix, tm, k, a.n)
+        assert np.array_equal(m, m2) and np.array_equal(se, se2), k
+
+
+def test_pool_full_inverse_equals_single_handle():
+    K, B, burn, samp = 128, 4, 8, 16
+    c = wl.random_dominant(256, 4, 1.5, 0)
+    pool = mcinv.mcinv_pool_create(K=K, seed=9, mem_budget=1 << 28, max_slots=4, batch_cycles=B)
+    t = mcinv.mcinv_pool_submit(pool, c, matrix_id=4, burnin=burn, samples=samp)
+    run_until_done(pool, [t])
+    pm, pse = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
+    R = np.arange(c.n)
+    h = mcinv.create_from_csr(c, K=K, seed=9, matrix_id=4, batch_cycles=B, acc=mcinv.MCINV_ACC_BF16_TC,
+                              block_rows=R, block_cols=R)
+    mcinv.mcinv_burnin(h, burn)
+    mcinv.mcinv_sample(h, samp)
+    hm, hse = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+    assert np.abs(pm - hm).max() <= 1e-12 * np.abs(hm).max()
+    assert np.abs(pse - hse).max() <= 1e-9 * np.abs(hse).max()
+
+
+def test_pool_admission_by_device_memory():
+    c = wl.random_dominant(1024, 4, 1.5, 5)
+    probe = mcinv.mcinv_pool_create(K=64, mem_budget=1 << 24, max_slots=4)
+    need = mcinv.mcinv_pool_footprint(probe, c.n, c.nnz, True)
+    pool = mcinv.mcinv_pool_create(K=64, mem_budget=int(need * 1.5), max_slots=4)
+    t0 = mcinv.mcinv_pool_submit(pool, c, matrix_id=0, burnin=2, samples=4)
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_pool_submit(pool, c, matrix_id=1, burnin=2, samples=4)
+    assert e.value.status == 4
+    run_until_done(pool, [t0])
+    mcinv.mcinv_pool_release(pool, t0)
+    t1 = mcinv.mcinv_pool_submit(pool, c, matrix_id=1, burnin=2, samples=4)
+    run_until_done(pool, [t1])
+    assert mcinv.mcinv_pool_info(pool)["arena_used"] > 0
+
+
+def test_pool_batch_estimates_cover_the_dense_inverse():
+    sizes = wl.batch_sizes(6, 64, 160, seed=1)
+    mats = [wl.random_dominant(int(n), 4, 1.5, 1000 + k) for k, n in enumerate(sizes)]
+    pool = mcinv.mcinv_pool_create(K=256, seed=0, mem_budget=1 << 30, max_slots=16, batch_cycles=8)
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=80, samples=800) for k, c in enumerate(mats)]
+    run_until_done(pool, tickets)
+    zs = []
+    for c, t in zip(mats, tickets):
+        m, se = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
+        truth = np.linalg.inv(c.to_dense())
+        zs.append(((m - truth) / se).ravel())
+    zs = np.concatenate(zs)
+    assert np.mean(np.abs(zs) > 3) < 0.01
+    assert 0.8 < np.sqrt(np.mean(zs ** 2)) < 1.25
