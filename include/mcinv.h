@@ -279,6 +279,44 @@ mcinv_status mcinv_pool_sync(mcinv_pool_t p);
 void mcinv_pool_destroy(mcinv_pool_t p);
 const char *mcinv_pool_last_error(mcinv_pool_t p);
 
+/* ------------------------------------------------------------------------ */
+/* Server: estimate requests on a pool, admitted by device memory, run with  */
+/* continuous batching by one engine thread.                                */
+/* ------------------------------------------------------------------------ */
+typedef struct mcinv_server_ctx *mcinv_server_t;
+
+typedef struct {
+    int64_t completed, queued, running, steps;
+    double p50_ms, p99_ms, max_ms; /* submission-to-result latency of completed requests */
+    double elapsed_s, busy_s;      /* since creation / last reset; time spent stepping */
+} mcinv_server_stats_t;
+
+/* Create a pool with these options and start its engine thread. */
+mcinv_status mcinv_server_create(mcinv_server_t *out, const mcinv_pool_options *opt);
+
+/*
+ * Queue an estimate request (thread-safe; returns at once).  The CSR (real) is
+ * copied.  kind: DIAG (out[n]), TRACE (out[1], q_diag[n] copied) or BLOCK (the
+ * full n x n inverse).  The engine admits requests in arrival order while a
+ * slot and arena memory are free, runs `burnin` + `samples` cycles of the
+ * matrix alongside every other admitted request, then reads the estimate back
+ * and releases the slot.
+ */
+mcinv_status mcinv_server_submit(mcinv_server_t s, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                 const double *val, uint32_t matrix_id, int64_t burnin, int64_t samples,
+                                 mcinv_kind kind, const double *q_diag, int64_t *request);
+
+/* Block until the request is done (MCINV_E_TIMEOUT after timeout_s seconds),
+ * copy its estimate and SE (sized by its kind) and its latency in ms. */
+mcinv_status mcinv_server_wait(mcinv_server_t s, int64_t request, double timeout_s, double *out, double *se_out,
+                               double *latency_ms);
+
+mcinv_status mcinv_server_stats(mcinv_server_t s, mcinv_server_stats_t *stats);
+mcinv_status mcinv_server_reset_stats(mcinv_server_t s);
+const char *mcinv_server_last_error(mcinv_server_t s);
+/* Stop the engine (requests still queued or running are abandoned) and free everything. */
+void mcinv_server_destroy(mcinv_server_t s);
+
 /*
  * One batch of the block accumulation that allocates nothing.  The paper has
  * no counterpart: this exists for callers that cannot allocate device memory,

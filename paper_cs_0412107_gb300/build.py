@@ -15,10 +15,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcinv.so")
-SOURCES = ["sweep.cu", "accumulate.cu", "context.cu", "prepare.cu", "tc_gemm.cu", "noalloc.cu", "pool.cu"]
+SOURCES = ["sweep.cu", "accumulate.cu", "context.cu", "prepare.cu", "tc_gemm.cu", "noalloc.cu", "pool.cu", "server.cpp"]
 HEADERS = ["internal.h", "tc_gemm.h", "prepare.h", "sweep_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
+              "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
@@ -42,7 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(OUT, src.rsplit(".", 1)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             jobs.append([nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o])

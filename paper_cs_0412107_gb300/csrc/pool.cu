@@ -776,6 +776,16 @@ static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256
 extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
 {
     if (!p) return pfail(nullptr, MCINV_E_ARG, "NULL pool");
+    // the step's slice shape is fixed before the work items are split by it
+    const int nc = (int)(sizeof kTuneL / sizeof kTuneL[0]);
+    const bool timed = !p->tuned && !p->fixed_shape;
+    int k_tune = -1;
+    if (timed) {
+        if (p->tune_score.empty()) p->tune_score.assign(nc, 1e300);
+        k_tune = p->tune_next;
+        p->LPR = kTuneL[k_tune][0];
+        p->threads = kTuneL[k_tune][1];
+    }
     StepTables T;
     build_tables(p, T);
     if (T.items.empty()) return MCINV_OK;
@@ -825,15 +835,11 @@ extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
     PCUDA(p, cudaMemcpyAsync(p->d_cnt, put(&c, sizeof c), sizeof c, cudaMemcpyHostToDevice, s));
     PCUDA(p, cudaEventRecord(p->staged, s));
 
-    bool timed = false;
-    if (!p->tuned && !p->fixed_shape) {
+    if (timed) {
         // autotune on live steps: each candidate shape runs one real step (every
         // shape computes the same values), the fastest per unit of work is kept
-        const int nc = (int)(sizeof kTuneL / sizeof kTuneL[0]);
-        if (p->tune_score.empty()) p->tune_score.assign(nc, 1e300);
-        const int k = p->tune_next++;
-        p->LPR = kTuneL[k][0];
-        p->threads = kTuneL[k][1];
+        const int k = k_tune;
+        p->tune_next++;
         cudaEvent_t ea, eb;
         PCUDA(p, cudaEventCreate(&ea));
         PCUDA(p, cudaEventCreate(&eb));
@@ -858,7 +864,6 @@ extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
             p->threads = kTuneL[best][1];
             p->tuned = true;
         }
-        timed = true;
     }
     if (!timed) {
         if (!p->graph || p->graph_LPR != p->LPR || p->graph_threads != p->threads) {

@@ -19,12 +19,14 @@ template <> struct Prec<false> {
     using Ent = EntR;
     using Cst = CstR;
     static __device__ __forceinline__ T zero() { return 0.f; }
-    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x) { acc = fmaf(e.val, x, acc); }
+    static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x) { acc = __fmaf_rn(e.val, x, acc); }
     // Eq. 4 / Eq. 5 right-hand sides
-    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s) { return phi * k.alpha - k.inv_d * s; }
-    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s) { return phi * k.beta - k.inv_d * s; }
-    static __device__ __forceinline__ T mulconj(T a, T b) { return a * b; }
-    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    // every operation is an explicit fmaf / mul / add with round-to-nearest, so
+    // all template instantiations (any slice shape) give the same bits
+    static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s) { return __fmaf_rn(-k.inv_d, s, phi * k.alpha); }
+    static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s) { return __fmaf_rn(-k.inv_d, s, phi * k.beta); }
+    static __device__ __forceinline__ T mulconj(T a, T b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ T add(T a, T b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     static __device__ __forceinline__ bool finite_bounded(T v) { return fabsf(v) <= 1e30f; }
 };
@@ -35,24 +37,26 @@ template <> struct Prec<true> {
     static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
     static __device__ __forceinline__ void fma(T &acc, const Ent &e, T x)
     {
-        acc.x = fmaf(e.re, x.x, fmaf(-e.im, x.y, acc.x));
-        acc.y = fmaf(e.re, x.y, fmaf(e.im, x.x, acc.y));
+        acc.x = __fmaf_rn(e.re, x.x, __fmaf_rn(-e.im, x.y, acc.x));
+        acc.y = __fmaf_rn(e.re, x.y, __fmaf_rn(e.im, x.x, acc.y));
     }
     static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s)
-    {   // phi alpha - inv_d s
-        return make_float2(phi * k.alpha.x - (k.inv_d.x * s.x - k.inv_d.y * s.y),
-                           phi * k.alpha.y - (k.inv_d.x * s.y + k.inv_d.y * s.x));
+    {   // phi alpha - inv_d s   (phi = +-1, so phi*alpha is exact)
+        const float re = __fmaf_rn(-k.inv_d.y, s.y, __fmul_rn(k.inv_d.x, s.x));
+        const float im = __fmaf_rn(k.inv_d.y, s.x, __fmul_rn(k.inv_d.x, s.y));
+        return make_float2(__fsub_rn(phi * k.alpha.x, re), __fsub_rn(phi * k.alpha.y, im));
     }
     static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s)
     {   // phi beta - conj(inv_d) s
-        return make_float2(phi * k.beta.x - (k.inv_d.x * s.x + k.inv_d.y * s.y),
-                           phi * k.beta.y - (k.inv_d.x * s.y - k.inv_d.y * s.x));
+        const float re = __fmaf_rn(k.inv_d.y, s.y, __fmul_rn(k.inv_d.x, s.x));
+        const float im = __fmaf_rn(-k.inv_d.y, s.x, __fmul_rn(k.inv_d.x, s.y));
+        return make_float2(__fsub_rn(phi * k.beta.x, re), __fsub_rn(phi * k.beta.y, im));
     }
     static __device__ __forceinline__ T mulconj(T a, T b)
     {   // a conj(b)
-        return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+        return make_float2(__fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)), __fmaf_rn(-a.x, b.y, __fmul_rn(a.y, b.x)));
     }
-    static __device__ __forceinline__ T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ T add(T a, T b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
     static __device__ __forceinline__ T shfl_xor(T v, int o)
     {
         return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));

@@ -36,7 +36,9 @@ EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sampl
            "mcinv_pool_default_options", "mcinv_pool_create", "mcinv_pool_footprint", "mcinv_pool_submit",
            "mcinv_pool_step", "mcinv_pool_poll", "mcinv_pool_estimate", "mcinv_pool_get_state",
            "mcinv_pool_release", "mcinv_pool_info", "mcinv_pool_sync", "mcinv_pool_destroy",
-           "mcinv_pool_last_error")
+           "mcinv_pool_last_error",
+           "mcinv_server_create", "mcinv_server_submit", "mcinv_server_wait", "mcinv_server_stats",
+           "mcinv_server_reset_stats", "mcinv_server_last_error", "mcinv_server_destroy")
 MCINV_KERNEL_NOISE, MCINV_KERNEL_SWEEP, MCINV_KERNEL_BLOCK, MCINV_KERNEL_FOLD, MCINV_KERNEL_ESTIMATE = range(5)
 KERNEL_NAMES = ("noise", "sweep", "block", "fold", "estimate")
 
@@ -92,6 +94,15 @@ class mcinv_pool_info_t(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class mcinv_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("elapsed_s", ctypes.c_double), ("busy_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -142,6 +153,19 @@ def lib():
         L.mcinv_pool_destroy.restype = None
         L.mcinv_pool_last_error.argtypes = [vp]
         L.mcinv_pool_last_error.restype = ctypes.c_char_p
+        L.mcinv_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(mcinv_pool_options)]
+        L.mcinv_server_submit.argtypes = [vp, i64, vp, vp, vp, ctypes.c_uint32, i64, i64, ctypes.c_int, vp,
+                                          ctypes.POINTER(i64)]
+        L.mcinv_server_wait.argtypes = [vp, i64, ctypes.c_double, vp, vp, ctypes.POINTER(ctypes.c_double)]
+        L.mcinv_server_stats.argtypes = [vp, ctypes.POINTER(mcinv_server_stats_t)]
+        L.mcinv_server_reset_stats.argtypes = [vp]
+        L.mcinv_server_last_error.argtypes = [vp]
+        L.mcinv_server_last_error.restype = ctypes.c_char_p
+        L.mcinv_server_destroy.argtypes = [vp]
+        L.mcinv_server_destroy.restype = None
+        for name in ("mcinv_server_create", "mcinv_server_submit", "mcinv_server_wait", "mcinv_server_stats",
+                     "mcinv_server_reset_stats"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("mcinv_pool_create", "mcinv_pool_footprint", "mcinv_pool_submit", "mcinv_pool_step",
                      "mcinv_pool_poll", "mcinv_pool_estimate", "mcinv_pool_get_state", "mcinv_pool_release",
                      "mcinv_pool_info", "mcinv_pool_sync"):
@@ -459,3 +483,74 @@ def mcinv_pool_destroy(pool: Pool):
 
 def mcinv_pool_last_error(pool: Pool | None = None) -> str:
     return lib().mcinv_pool_last_error(None if pool is None else pool.ptr).decode(errors="replace")
+
+
+# -- server: requests on a pool, continuous batching ------------------------------------
+
+class Server:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().mcinv_server_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def mcinv_server_create(*, stream=None, **pool_options) -> Server:
+    o = mcinv_pool_default_options(**pool_options)
+    o.stream = stream
+    p = ctypes.c_void_p()
+    st = lib().mcinv_server_create(ctypes.byref(p), ctypes.byref(o))
+    if st != MCINV_OK:
+        raise McinvError(st, lib().mcinv_pool_last_error(None).decode(errors="replace"))
+    return Server(p)
+
+
+def mcinv_server_submit(server: Server, csr, matrix_id, burnin, samples, kind, q_diag=None) -> int:
+    rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(csr.col, dtype=np.int32)
+    val = np.ascontiguousarray(csr.val, dtype=np.float64)
+    q = None if q_diag is None else np.ascontiguousarray(q_diag, dtype=np.float64)
+    rid = ctypes.c_int64()
+    st = lib().mcinv_server_submit(server.ptr, csr.n, _ptr(rp), _ptr(col), _ptr(val), int(matrix_id), int(burnin),
+                                   int(samples), int(kind), _ptr(q), ctypes.byref(rid))
+    if st != MCINV_OK:
+        raise McinvError(st, "submit rejected")
+    return int(rid.value)
+
+
+def mcinv_server_wait(server: Server, request, n, kind, timeout_s=600.0):
+    """Returns (estimate, se, latency_ms)."""
+    count = {MCINV_EST_DIAG: n, MCINV_EST_TRACE: 1, MCINV_EST_BLOCK: n * n}[kind]
+    out = np.empty(count)
+    se = np.empty(count)
+    lat = ctypes.c_double()
+    st = lib().mcinv_server_wait(server.ptr, int(request), float(timeout_s), _ptr(out), _ptr(se), ctypes.byref(lat))
+    if st != MCINV_OK:
+        raise McinvError(st, lib().mcinv_server_last_error(server.ptr).decode(errors="replace"))
+    shape = {MCINV_EST_DIAG: (n,), MCINV_EST_TRACE: (), MCINV_EST_BLOCK: (n, n)}[kind]
+    return out.reshape(shape), se.reshape(shape), float(lat.value)
+
+
+def mcinv_server_stats(server: Server) -> dict:
+    s = mcinv_server_stats_t()
+    lib().mcinv_server_stats(server.ptr, ctypes.byref(s))
+    return s.as_dict()
+
+
+def mcinv_server_reset_stats(server: Server):
+    lib().mcinv_server_reset_stats(server.ptr)
+
+
+def mcinv_server_last_error(server: Server) -> str:
+    return lib().mcinv_server_last_error(server.ptr).decode(errors="replace")
+
+
+def mcinv_server_destroy(server: Server):
+    if server.ptr:
+        lib().mcinv_server_destroy(server.ptr)
+        server.ptr = None
