@@ -298,6 +298,93 @@ def run_e2e(args, csr, K, acc, rank):
             "seconds_per_job": dt}
 
 
+def batch_workload(count, seed=0):
+    """The batched workload: `count` random-dominant matrices (4 off-diagonals per
+    row, diagonal 1.5 x row sum) with n log-uniform in [64, 4096], seeds 0.."""
+    from paper_cs_0412107_gb300 import workloads as wl
+    sizes = wl.batch_sizes(count, 64, 4096, seed=seed)
+    return [wl.random_dominant(int(n), 4, 1.5, k) for k, n in enumerate(sizes)]
+
+
+def run_batch(args, world, rank, local):
+    """512 matrices in one pool (one persistent launch per kernel per step,
+    graph-replayed), full inverse each: throughput of the whole batch, then the
+    same matrices as a Poisson request stream through the server at 50% and 90%
+    of that throughput, with p50/p99 latency."""
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    torch.cuda.set_device(local)
+    mats = batch_workload(args.batch_count)
+    burn, samp, K, B = args.batch_burnin, args.batch_samples, 256, 8
+    budget = int(args.batch_mem_gb * (1 << 30))
+    nnz_total = sum(c.nnz for c in mats)
+    pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
+                                   max_slots=len(mats), batch_cycles=B)
+    # warm-up pool: tuning steps and graph capture on a few members
+    for k in range(min(8, len(mats))):
+        mcinv.mcinv_pool_submit(pool, mats[k], matrix_id=10_000 + k, burnin=2 * B, samples=6 * B)
+    for _ in range(8):
+        mcinv.mcinv_pool_step(pool)
+    mcinv.mcinv_pool_destroy(pool)
+    pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
+                                   max_slots=len(mats), batch_cycles=B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
+    t_admit = time.perf_counter() - t0
+    steps = 0
+    while not all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
+        mcinv.mcinv_pool_step(pool)
+        steps += 1
+    mcinv.mcinv_pool_sync(pool)
+    dt = time.perf_counter() - t0
+    info = mcinv.mcinv_pool_info(pool)
+    # accuracy on a few members against the dense inverse
+    errs = []
+    for k in range(0, len(mats), max(1, len(mats) // 8)):
+        m, se = mcinv.mcinv_pool_estimate(pool, tickets[k], mcinv.MCINV_EST_BLOCK, mats[k].n)
+        truth = np.linalg.inv(mats[k].to_dense())
+        errs.append(float(np.sqrt(np.mean((m - truth) ** 2))))
+    mcinv.mcinv_pool_destroy(pool)
+    updates = float(nnz_total) * K * (burn + samp)
+    value = updates / dt
+    flops = sum(2.0 * c.n * c.n for c in mats) * K * samp
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "impl": "mine",
+           "dtype": "f32 sweep, bf16 tensor-core accumulation",
+           "config": {"workload": "batch512", "matrices": len(mats), "K": K, "burnin": burn, "samples": samp,
+                      "sum_n": int(sum(c.n for c in mats)), "sum_nnz": int(nnz_total),
+                      "estimate": "full inverse of every matrix", "batch_cycles": B,
+                      "chains_per_cta": info["chains_per_cta"], "threads_per_cta": info["threads_per_cta"]},
+           "seconds": dt, "admission_seconds": t_admit, "steps": steps,
+           "block_tflops_effective": flops / dt / 1e12,
+           "rms_error_vs_dense_inverse": {"median": float(np.median(errs)), "max": float(np.max(errs))},
+           "kernel_launches": info["kernel_launches"]}
+    # serving: Poisson arrivals at 50% and 90% of the batch throughput (matrices/s)
+    rate_max = len(mats) / dt
+    serving = {}
+    for frac in (0.5, 0.9):
+        srv = mcinv.mcinv_server_create(K=K, seed=args.seed, mem_budget=budget, max_slots=len(mats), batch_cycles=B)
+        rng = np.random.default_rng(1)
+        n_req = min(len(mats), args.serve_requests)
+        gaps = rng.exponential(1.0 / (frac * rate_max), size=n_req)
+        ids = []
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            ids.append(mcinv.mcinv_server_submit(srv, mats[k], k, burn, samp, mcinv.MCINV_EST_DIAG))
+            time.sleep(gaps[k])
+        lat = [mcinv.mcinv_server_wait(srv, ids[k], mats[k].n, mcinv.MCINV_EST_DIAG, 3600)[2] for k in range(n_req)]
+        el = time.perf_counter() - t0
+        st = mcinv.mcinv_server_stats(srv)
+        mcinv.mcinv_server_destroy(srv)
+        serving[f"{int(frac * 100)}pct"] = {"offered_matrices_per_s": frac * rate_max, "requests": n_req,
+                                           "p50_ms": float(np.percentile(lat, 50)),
+                                           "p99_ms": float(np.percentile(lat, 99)),
+                                           "completed_per_s": n_req / el, "engine_steps": st["steps"]}
+    res["serving"] = serving
+    return res
+
+
 def cpu_baseline(csr, K, seconds):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     `chains` chains (one OpenMP thread per chain group) for `cycles` cycles."""
@@ -364,12 +451,20 @@ def main():
     ap.add_argument("--e2e-burnin", type=int, default=500)
     ap.add_argument("--e2e-samples", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-burnin", type=int, default=200)
+    ap.add_argument("--batch-samples", type=int, default=2000)
+    ap.add_argument("--batch-mem-gb", type=float, default=64.0)
+    ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload == "batch512":
+        res = run_batch(args, world, rank, local)
     else:
         res = run_mine(args, world, rank, local)
     if rank == 0 and res is not None:
