@@ -118,6 +118,19 @@ mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr, const
  * (burn-in, Algorithm 1 steps 1-5 with a fixed count).  cycles >= 0. */
 mcinv_status mcinv_burnin(mcinv_t h, int64_t cycles);
 
+/*
+ * Burn-in with the coupling test of Algorithm 1 (steps 1-5): the run length p
+ * is the first cycle after which two paths started at z = w = 0 and at
+ * z*_i = w*_i = i (1-based), sharing their noise, agree to max_i |z_i - z*_i| < tol
+ * and max_i |w_i - w*_i| < tol (the paper's "z'z* < tol" read as this
+ * sup-norm).  By Eq. 12 the difference follows noise-free Gauss-Seidel on C
+ * (and on C^dagger), the same for every chain, so it is swept once as a
+ * single chain; then every chain runs p burn-in cycles (as mcinv_burnin).
+ * *cycles_out = p.  MCINV_E_DIVERGED if the paths still differ after
+ * max_cycles cycles (sp(T) or sp(S) >= 1, or too tight a tol for FP32).
+ */
+mcinv_status mcinv_burnin_coupled(mcinv_t h, double tol, int64_t max_cycles, int64_t *cycles_out);
+
 /* Advance every chain `cycles` cycles and accumulate each cycle's z w^dagger
  * into the diagonal / block estimates (Eq. 1/C; Algorithm 1 steps 6-9). */
 mcinv_status mcinv_sample(mcinv_t h, int64_t cycles);
@@ -136,6 +149,25 @@ mcinv_status mcinv_sample(mcinv_t h, int64_t cycles);
  */
 mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double *q_diag, double *out,
                             double *se_out);
+
+/*
+ * Monte Carlo error of the trace by Geyer's effective length (Sec. 2.3, as the
+ * paper's tables report it).  mcinv_set_trace_weights(h, q) (q[n], before any
+ * sampling) makes every sampling cycle also record the realised value
+ *     t_k = (1/K) sum_chains sum_i q_i Re(z_i conj(w_i))
+ * (one FP64 value per cycle, reduced in a fixed order on the GPU).
+ * mcinv_trace_mc_error returns its mean, variance gamma(0), Geyer's
+ * initial-positive-sequence effective length and SE = sqrt(gamma(0) / ess).
+ * mcinv_trace_series copies the series (up to capacity values).
+ * mcinv_sample_until samples check_every cycles at a time until
+ * SE < rel_tol * |mean| (the paper's stop rule, checked every 100 cycles there)
+ * or max_cycles would be exceeded; *cycles_out = cycles sampled.
+ */
+mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q_diag);
+mcinv_status mcinv_trace_mc_error(mcinv_t h, double *mean, double *var, double *ess, double *se);
+mcinv_status mcinv_trace_series(mcinv_t h, double *out, int64_t capacity, int64_t *length);
+mcinv_status mcinv_sample_until(mcinv_t h, double rel_tol, int64_t check_every, int64_t max_cycles,
+                                int64_t *cycles_out);
 
 /* Wait for queued work; report MCINV_E_DIVERGED / CUDA errors raised since the last check. */
 mcinv_status mcinv_sync(mcinv_t h);

@@ -65,7 +65,7 @@ def lib():
                                      ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      vp, vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp,
-                                     ctypes.c_int64, vp, ctypes.c_int]
+                                     ctypes.c_int64, vp, vp, vp, ctypes.c_int]
             L.orc_cc_run.restype = ctypes.c_int64
             L.orc_coupling_burnin.argtypes = [ctypes.c_int64, vp, vp, vp, ctypes.c_int,
                                               ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -132,11 +132,14 @@ class State:
 
 
 def run(csr, K, seed=0, matrix=0, chain0=0, cycle0=0, ncycles=1, acc_from=None,
-        state=None, cpg=None, R=None, S=None, diag=True, threads=1):
+        state=None, cpg=None, R=None, S=None, diag=True, threads=1, q=None, series_out=None):
     """Advance K chains ``ncycles`` cycles from ``state`` (zeros if None).
 
     Cycles with global index >= ``acc_from`` are accumulated (default: none).
     Returns (state, diag_acc [G][n] or None, blk_acc [G][|R|][|S|] or None).
+    With ``q`` and a list ``series_out``, the realised per-cycle trace values
+    (1/K) sum_chains sum_i q_i Re(z_i conj(w_i)) of the accumulated cycles are
+    appended to ``series_out``.
     """
     n = csr.n
     if state is None:
@@ -155,14 +158,19 @@ def run(csr, K, seed=0, matrix=0, chain0=0, cycle0=0, ncycles=1, acc_from=None,
         bacc = None
     zv = state.z.view(np.float64)
     wv = state.w.view(np.float64)
+    nacc = max(0, cycle0 + ncycles - max(acc_from, cycle0))
+    qv = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+    tser = np.zeros((G, max(nacc, 1))) if qv is not None else None
     assert state.z.flags.c_contiguous and state.w.flags.c_contiguous
     rc = lib().orc_cc_run(n, _ptr(rp), _ptr(col), _ptr(val), cx, K, chain0, seed, matrix,
                           cycle0, ncycles, acc_from, _ptr(zv), _ptr(wv), cpg,
                           _ptr(None if dacc is None else dacc.view(np.float64)),
                           _ptr(R), 0 if R is None else len(R), _ptr(S), 0 if S is None else len(S),
-                          _ptr(None if bacc is None else bacc.view(np.float64)), threads)
+                          _ptr(None if bacc is None else bacc.view(np.float64)), _ptr(qv), _ptr(tser), threads)
     if rc:
         raise ValueError(f"singular diagonal at row {-rc - 1}")
+    if tser is not None and series_out is not None:
+        series_out.extend((tser.sum(axis=0)[:nacc] / K).tolist())
     return state, dacc, bacc
 
 
@@ -200,6 +208,34 @@ def group_estimate(acc, counts, samples):
     if np.iscomplexobj(acc):
         return m, se(mg.real, m.real) + 1j * se(mg.imag, m.imag)
     return m, se(mg, m)
+
+
+def geyer_ips(x):
+    """Geyer's (1992) initial positive sequence estimator for a stationary series.
+
+    gamma(k): lag-k autocovariance (divided by M); Gamma_j = gamma(2j) + gamma(2j+1),
+    summed while positive and made non-increasing; asymptotic variance
+    sigma^2 = -gamma(0) + 2 sum Gamma_j; effective length M gamma(0) / sigma^2;
+    standard error of the mean sqrt(sigma^2 / M) = sqrt(gamma(0) / ess).
+    Returns dict(mean, var, ess, se).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    M = len(x)
+    d = x - x.mean()
+    # autocovariances through an FFT of the zero-padded series
+    f = np.fft.rfft(d, 2 * M)
+    acov = np.fft.irfft(f * np.conj(f))[:M] / M
+    total, prev = 0.0, np.inf
+    for j in range(M // 2):
+        G = acov[2 * j] + acov[2 * j + 1]
+        if G <= 0:
+            break
+        G = min(G, prev)
+        prev = G
+        total += G
+    sigma2 = -acov[0] + 2 * total
+    ess = M * acov[0] / sigma2
+    return {"mean": float(x.mean()), "var": float(acov[0]), "ess": float(ess), "se": float(np.sqrt(sigma2 / M))}
 
 
 # -- dense statements used as pins (small n) -------------------------------------------

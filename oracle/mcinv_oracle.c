@@ -213,6 +213,9 @@ static void orc_cycle_one_chain(const orc_matrix *m, const orc_columns *cols,
  * diag_acc  : [G][n] interleaved, += sum over the group's chains of z_i conj(w_i);
  *             may be NULL.
  * blk_acc   : [G][nR][nS] interleaved, += z_{R[a]} conj(w_{S[b]}); may be NULL.
+ * q, tser   : if both set, tser[g][k] += sum_i q_i Re(z_i conj(w_i)) over the group's
+ *             chains for every accumulated cycle k (k counted from acc_from): the
+ *             realised trace values whose Monte Carlo error Sec. 2.3 estimates.
  * threads   : OpenMP threads over groups (1 = serial); groups are independent.
  *
  * Returns 0, or a negative row index - 1 if D is singular.
@@ -222,7 +225,7 @@ int64_t orc_cc_run(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
                    int64_t cycle0, int64_t ncycles, int64_t acc_from,
                    double *z, double *w, int64_t cpg,
                    double *diag_acc, const int64_t *R, int64_t nR, const int64_t *S, int64_t nS,
-                   double *blk_acc, int threads)
+                   double *blk_acc, const double *q, double *tser, int threads)
 {
     orc_matrix m = {n, row_ptr, col, val, is_complex};
     double *abuf = malloc(sizeof(double) * 6 * (size_t)(n ? n : 1));
@@ -257,6 +260,13 @@ int64_t orc_cc_run(int64_t n, const int64_t *row_ptr, const int32_t *col, const 
                 orc_cycle_one_chain(&m, &cols, alpha, beta, inv_d, seed, matrix,
                                     (uint32_t)(chain0 + c), (uint32_t)cyc, Z + c, Wv + c, K);
                 if (cyc < acc_from) continue;
+                if (q && tser) {
+                    /* cycles of this call that are accumulated: first .. cycle0+ncycles-1 */
+                    const int64_t first = acc_from > cycle0 ? acc_from : cycle0;
+                    double t = 0.0;
+                    for (int64_t i = 0; i < n; ++i) t += q[i] * creal(Z[i * K + c] * conj(Wv[i * K + c]));
+                    tser[g * (cycle0 + ncycles - first) + (cyc - first)] += t;
+                }
                 if (DA)
                     for (int64_t i = 0; i < n; ++i)
                         DA[g * n + i] += Z[i * K + c] * conj(Wv[i * K + c]);

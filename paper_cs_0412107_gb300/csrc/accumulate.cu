@@ -3,6 +3,8 @@
 //   * the FP32 CUDA-core block contraction  blk += Z_R W_S^dagger  (one cycle),
 //   * folding block batches into FP64 sums and batch-mean second moments,
 //   * means and Monte Carlo standard errors in FP64.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace mcinv {
@@ -258,6 +260,74 @@ cudaError_t launch_block_estimate(int cplx, long long elems, double K, double T,
     if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (blocks < 1) blocks = 1;
     block_estimate_kernel<<<(unsigned)blocks, 256, 0, s>>>(total, K, T, nb, sum, sq, mean, se);
+    return cudaGetLastError();
+}
+
+__global__ void series_fold_kernel(int ncyc, int ctas, int warps, const float *__restrict__ tpart, double K,
+                                   double *__restrict__ series, long long first)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncyc) return;
+    double s = 0.0;
+    for (int k = 0; k < ctas * warps; ++k) s += (double)tpart[(size_t)c * ctas * warps + k];
+    series[first + c] = s / K;
+}
+
+cudaError_t launch_series_fold(int ncyc, int ctas, int warps, const float *tpart, double K, double *series,
+                               long long first, cudaStream_t s)
+{
+    series_fold_kernel<<<(ncyc + 127) / 128, 128, 0, s>>>(ncyc, ctas, warps, tpart, K, series, first);
+    return cudaGetLastError();
+}
+
+// max_i |d_i| of two length-n vectors (float or float2), as float bits in out[0], out[1]
+// (non-negative floats order like their integer bit patterns)
+template <int NV>
+__global__ void maxabs2_kernel(int n, const float *__restrict__ a, const float *__restrict__ b, unsigned *out)
+{
+    float ma = 0.f, mb = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (NV == 1) {
+            ma = fmaxf(ma, fabsf(a[i]));
+            mb = fmaxf(mb, fabsf(b[i]));
+        } else {
+            ma = fmaxf(ma, hypotf(a[2 * i], a[2 * i + 1]));
+            mb = fmaxf(mb, hypotf(b[2 * i], b[2 * i + 1]));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // NaN (a diverged difference) has the largest bit pattern, so it never passes the test
+        atomicMax(&out[0], __float_as_uint(ma));
+        atomicMax(&out[1], __float_as_uint(mb));
+    }
+}
+
+cudaError_t launch_maxabs2(int cplx, int n, const void *a, const void *b, unsigned *out, cudaStream_t s)
+{
+    const int blocks = std::min((n + 255) / 256, 152 * 4);
+    if (cplx) maxabs2_kernel<2><<<blocks, 256, 0, s>>>(n, (const float *)a, (const float *)b, out);
+    else maxabs2_kernel<1><<<blocks, 256, 0, s>>>(n, (const float *)a, (const float *)b, out);
+    return cudaGetLastError();
+}
+
+// d = (1, 2, ..., n): the difference z* - z of the coupled starts of Algorithm 1, step 1
+template <int NV>
+__global__ void iota1_kernel(int n, float *d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d[NV * i] = (float)(i + 1);
+    if (NV == 2) d[2 * i + 1] = 0.f;
+}
+
+cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s)
+{
+    if (cplx) iota1_kernel<2><<<(n + 255) / 256, 256, 0, s>>>(n, (float *)d);
+    else iota1_kernel<1><<<(n + 255) / 256, 256, 0, s>>>(n, (float *)d);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,10 @@ struct mcinv_ctx {
     TcGemmPlan *gemm = nullptr;
     // estimate scratch
     double *d_mean = nullptr, *d_se = nullptr, *d_q = nullptr;
+    // per-cycle trace series (Geyer's Monte Carlo error, Sec. 2.3)
+    float *d_tq = nullptr, *d_tpart = nullptr;
+    double *d_series = nullptr;
+    int64_t nseries = 0, cap_series = 0;
     int *d_status = nullptr;
     // counters
     int64_t cycle = 0, samples = 0, block_batches = 0, block_cycles = 0, launches = 0;
@@ -495,7 +499,29 @@ static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumula
     }
     a.status = h->d_status;
     a.ctas_per_slice = h->Q;
+    if (accumulate && h->d_tq) {
+        a.tq = h->d_tq;
+        a.tpart = h->d_tpart;
+    }
     return a;
+}
+
+// Append the last sweep launch's `ncyc` trace-series values (device FP64).
+static mcinv_status series_append(mcinv_ctx *h, int ncyc)
+{
+    if (h->nseries + ncyc > h->cap_series) {
+        const int64_t cap = std::max<int64_t>(2 * h->cap_series, std::max<int64_t>(h->nseries + ncyc, 4096));
+        double *nb = nullptr;
+        CUDA_TRY(h, cudaMallocAsync((void **)&nb, (size_t)cap * sizeof(double), h->stream));
+        if (h->nseries) CUDA_TRY(h, cudaMemcpyAsync(nb, h->d_series, (size_t)h->nseries * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        if (h->d_series) CUDA_TRY(h, cudaFreeAsync(h->d_series, h->stream));
+        h->d_series = nb;
+        h->cap_series = cap;
+    }
+    LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_series_fold(ncyc, h->slices * h->Q, h->threads / 32, h->d_tpart, (double)h->K,
+                                                      h->d_series, h->nseries, h->stream));
+    h->nseries += ncyc;
+    return MCINV_OK;
 }
 
 static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
@@ -509,6 +535,10 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
             for (int k = 0; k < b; ++k) {
                 SweepArgs a = sweep_args(h, 1, k, true, 0);
                 LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
+                if (h->d_tq) {
+                    mcinv_status st = series_append(h, 1);
+                    if (st != MCINV_OK) return st;
+                }
                 h->cur ^= 1;
                 LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
                                             (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
@@ -516,6 +546,10 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
         } else {
             SweepArgs a = sweep_args(h, b, 0, accumulate, 0);
             LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
+            if (accumulate && h->d_tq) {
+                mcinv_status st = series_append(h, b);
+                if (st != MCINV_OK) return st;
+            }
             if (b & 1) h->cur ^= 1;
             if (block) {
                 const long long inner = (long long)b * h->kp;
@@ -537,6 +571,60 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
         cycles -= b;
     }
     return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_burnin_coupled(mcinv_t h, double tol, int64_t max_cycles, int64_t *cycles_out)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (!(tol > 0.0) || max_cycles < 0) return fail(h, MCINV_E_ARG, "need tol > 0 and max_cycles >= 0");
+    // Algorithm 1, steps 1-5, by Eq. 12: the difference of the coupled paths
+    // (z* - z, started at (1..n) - 0 and sharing the noise) evolves by
+    // noise-free Gauss-Seidel on C (and on C^dagger for w), identically for
+    // every chain; it is swept once, one cycle at a time, until
+    // max_i |d_i| < tol for both, and every chain then runs that many cycles.
+    const size_t esz = h->cplx ? 8 : 4;
+    const size_t n = (size_t)h->n;
+    char *buf = nullptr;
+    CUDA_TRY(h, cudaMallocAsync((void **)&buf, 4 * n * esz + 256, h->stream));
+    void *dz[2] = {buf, buf + n * esz}, *dw[2] = {buf + 2 * n * esz, buf + 3 * n * esz};
+    unsigned *d_max = (unsigned *)(buf + 4 * n * esz);
+    mcinv_status st = MCINV_OK;
+    int64_t p = -1;
+    auto run = [&]() -> mcinv_status {
+        LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_iota1(h->cplx, (int)n, dz[0], h->stream));
+        LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_iota1(h->cplx, (int)n, dw[0], h->stream));
+        SweepArgs a = sweep_args(h, 1, 0, false, 0);
+        a.K = 1;
+        a.nw = 1;
+        a.noise = nullptr;
+        a.ctas_per_slice = 1;
+        int cur = 0;
+        for (int64_t k = 1; k <= max_cycles; ++k) {
+            a.z[0] = dz[0]; a.z[1] = dz[1]; a.w[0] = dw[0]; a.w[1] = dw[1];
+            a.cur = cur;
+            LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, 1, 1, 1, 256, h->stream));
+            cur ^= 1;
+            CUDA_TRY(h, cudaMemsetAsync(d_max, 0, 2 * sizeof(unsigned), h->stream));
+            LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_maxabs2(h->cplx, (int)n, dz[cur], dw[cur], d_max, h->stream));
+            unsigned m[2];
+            CUDA_TRY(h, cudaMemcpyAsync(m, d_max, sizeof m, cudaMemcpyDeviceToHost, h->stream));
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            float fz, fw;
+            std::memcpy(&fz, &m[0], 4);
+            std::memcpy(&fw, &m[1], 4);
+            if (fz < tol && fw < tol) {
+                p = k;
+                return MCINV_OK;
+            }
+        }
+        return MCINV_OK;
+    };
+    st = run();
+    cudaFreeAsync(buf, h->stream);
+    if (st != MCINV_OK) return st;
+    if (p < 0) return fail(h, MCINV_E_DIVERGED, "coupled paths still differ by more than %g after %lld cycles", tol, (long long)max_cycles);
+    if (cycles_out) *cycles_out = p;
+    return mcinv_burnin(h, p);
 }
 
 extern "C" mcinv_status mcinv_burnin(mcinv_t h, int64_t cycles)
@@ -606,6 +694,105 @@ extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double 
     return MCINV_OK;
 }
 
+extern "C" mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q)
+{
+    if (!h || !q) return fail(h, MCINV_E_ARG, "NULL argument");
+    if (h->samples > 0) return fail(h, MCINV_E_STATE, "trace weights must be set before sampling");
+    std::vector<float> qp((size_t)h->n);
+    std::vector<int32_t> perm((size_t)h->n);
+    CUDA_TRY(h, cudaMemcpy(perm.data(), h->d_perm, (size_t)h->n * 4, cudaMemcpyDeviceToHost));
+    for (int64_t p = 0; p < h->n; ++p) qp[p] = (float)q[perm[p]];
+    if (!h->d_tq) {
+        CUDA_TRY(h, dalloc(h, &h->d_tq, (size_t)h->n));
+        CUDA_TRY(h, dalloc(h, &h->d_tpart, (size_t)h->B * h->slices * h->Q * (h->threads / 32)));
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_tq, qp.data(), (size_t)h->n * 4, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->nseries = 0;
+    return MCINV_OK;
+}
+
+// Geyer (1992) initial positive sequence estimate on the per-cycle series:
+// gamma(k) the lag-k autocovariance, Gamma_j = gamma(2j) + gamma(2j+1) summed
+// while positive (and made monotone), asymptotic variance
+// sigma^2 = -gamma(0) + 2 sum_j Gamma_j, effective length M gamma(0) / sigma^2,
+// Monte Carlo SE = sqrt(gamma(0) / effective length) (Sec. 2.3, Sec. 3.1).
+static void geyer(const std::vector<double> &x, double *mean, double *var, double *ess, double *se)
+{
+    const size_t M = x.size();
+    double m = 0.0;
+    for (double v : x) m += v;
+    m /= (double)M;
+    auto gamma = [&](size_t k) {
+        double g = 0.0;
+        for (size_t t = 0; t + k < M; ++t) g += (x[t] - m) * (x[t + k] - m);
+        return g / (double)M;
+    };
+    const double g0 = gamma(0);
+    double sum = 0.0, prev = 1e300;
+    for (size_t j = 0; 2 * j + 1 < M; ++j) {
+        double G = gamma(2 * j) + gamma(2 * j + 1);
+        if (!(G > 0.0)) break;
+        G = std::min(G, prev);
+        prev = G;
+        sum += G;
+    }
+    const double sigma2 = std::max(-g0 + 2.0 * sum, 1e-300);
+    *mean = m;
+    *var = g0;
+    *ess = (double)M * g0 / sigma2;
+    *se = std::sqrt(sigma2 / (double)M);
+}
+
+extern "C" mcinv_status mcinv_trace_mc_error(mcinv_t h, double *mean, double *var, double *ess, double *se)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (!h->d_tq) return fail(h, MCINV_E_STATE, "no trace weights were set (mcinv_set_trace_weights)");
+    if (h->nseries < 4) return fail(h, MCINV_E_STATE, "need at least 4 sampled cycles");
+    mcinv_status st = mcinv_sync(h);
+    if (st != MCINV_OK) return st;
+    std::vector<double> x((size_t)h->nseries);
+    CUDA_TRY(h, cudaMemcpy(x.data(), h->d_series, x.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    double m, v, e, s2;
+    geyer(x, &m, &v, &e, &s2);
+    if (mean) *mean = m;
+    if (var) *var = v;
+    if (ess) *ess = e;
+    if (se) *se = s2;
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_trace_series(mcinv_t h, double *out, int64_t capacity, int64_t *length)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    mcinv_status st = mcinv_sync(h);
+    if (st != MCINV_OK) return st;
+    if (length) *length = h->nseries;
+    if (out && capacity > 0 && h->nseries > 0)
+        CUDA_TRY(h, cudaMemcpy(out, h->d_series, (size_t)std::min(capacity, h->nseries) * sizeof(double), cudaMemcpyDeviceToHost));
+    return MCINV_OK;
+}
+
+extern "C" mcinv_status mcinv_sample_until(mcinv_t h, double rel_tol, int64_t check_every, int64_t max_cycles,
+                                           int64_t *cycles_out)
+{
+    if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (!(rel_tol > 0.0) || check_every < 4 || max_cycles < check_every) return fail(h, MCINV_E_ARG, "bad stop-rule arguments");
+    if (!h->d_tq) return fail(h, MCINV_E_STATE, "the stop rule needs trace weights (mcinv_set_trace_weights)");
+    int64_t done = 0;
+    for (;;) {
+        mcinv_status st = mcinv_sample(h, check_every);
+        if (st != MCINV_OK) return st;
+        done += check_every;
+        double m, v, e, se;
+        st = mcinv_trace_mc_error(h, &m, &v, &e, &se);
+        if (st != MCINV_OK) return st;
+        if (se < rel_tol * std::fabs(m) || done + check_every > max_cycles) break;
+    }
+    if (cycles_out) *cycles_out = done;
+    return MCINV_OK;
+}
+
 extern "C" mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchains, double *z, double *w, int64_t *cycle)
 {
     if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
@@ -646,6 +833,7 @@ extern "C" mcinv_status mcinv_reset_estimates(mcinv_t h)
     h->samples = 0;
     h->block_batches = 0;
     h->block_cycles = 0;
+    h->nseries = 0;
     return MCINV_OK;
 }
 
@@ -725,6 +913,7 @@ extern "C" void mcinv_destroy(mcinv_t h)
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     for (auto &e : h->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    if (h->d_series) cudaFree(h->d_series);
     if (h->gemm) tc_gemm_plan_destroy(h->gemm);
     for (void *p : h->allocs) cudaFree(p);
     delete h;

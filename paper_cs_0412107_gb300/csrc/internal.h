@@ -58,7 +58,8 @@ struct SweepArgs {
     int nchunks, blob_max;     // chunks per cycle; bytes of one shared-memory buffer
     const uint8_t *stream;     // chunk blobs
     const ChunkDesc *chunks;
-    const uint32_t *noise;     // [ncyc][nw][n] by position: Z2 sign bits (bit c%32 of word c/32), 1 -> phi = -1
+    const uint32_t *noise;     // [ncyc][nw][n] by position: Z2 sign bits (bit c%32 of word c/32), 1 -> phi = -1;
+                               // null: phi = 0 (noise-free Gauss-Seidel, Eq. 12)
     void *z[2], *w[2];         // double-buffered chain state [n][K] by row (float / float2)
     int cur;                   // buffer holding the state before the first cycle of this launch
     int ncyc;                  // cycles this launch runs
@@ -73,6 +74,10 @@ struct SweepArgs {
     long long kp;              // elements per cycle block: K (x2 complex) rounded up to 64
     int cyc0_in_batch;         // shadow column block of this launch's first cycle
     int ctas_per_slice;        // Q: CTAs (one thread-block cluster) per chain slice
+    // per-cycle trace series (Geyer's Monte Carlo error): q_i by position, and
+    // per-(cycle, CTA, warp) partial sums of q_i Re(z_i conj(w_i)); null: off
+    const float *tq;
+    float *tpart;
     int *status;               // bit 0: a chain diverged; bit 2: a staging wait expired
 };
 
@@ -107,5 +112,13 @@ cudaError_t launch_trace_estimate(int cplx, int n, int G, const double *counts, 
 cudaError_t launch_block_estimate(int cplx, long long elems, double K, double T, double nb,
                                   const double *sum, const double *sq, double *mean, double *se,
                                   cudaStream_t s);
+
+// series[first + c] = (sum over CTAs and warps of tpart[c][cta][warp]) / K, FP64, fixed order
+cudaError_t launch_series_fold(int ncyc, int ctas, int warps, const float *tpart, double K, double *series,
+                               long long first, cudaStream_t s);
+
+// coupling burn-in helpers (accumulate.cu)
+cudaError_t launch_maxabs2(int cplx, int n, const void *a, const void *b, unsigned *out, cudaStream_t s);
+cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s);
 
 }  // namespace mcinv

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
 
     bool diverged = false;
     bool level_end = false;  // did the previous chunk end a dependency level?
+    float tsum = 0.f;        // this lane's share of the cycle's trace series value
     for (int t = 0; t < total; ++t) {
         const int cyc = t / a.nchunks;
         const int b = t & 1;
@@ -225,13 +226,30 @@ __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
             ChunkWork w;
             w.buf = buf; w.d = d;
             w.zo = zo; w.zn = zn; w.wo = wo; w.wn = wn;
-            w.noise = a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n;
+            w.noise = a.noise ? a.noise + ((size_t)cyc * a.nw + (size_t)(c0 >> 5)) * (size_t)a.n : nullptr;
             w.dpart = dpart; w.diag = a.diag_part != nullptr; w.dlead = dlead; w.seg = seg;
             w.rpos = a.rpos; w.spos = a.spos; w.zsh = a.zsh; w.wsh = a.wsh; w.ldsh = a.ldsh; w.kp = a.kp;
             w.shcol = a.cyc0_in_batch + cyc;
             w.K = K; w.c0 = c0; w.first = first; w.stride = stride; w.sub = sub;
             w.chain_ok = chain_ok; w.cshift = cshift;
-            diverged |= sweep_chunk_rows<CPLX, LPR, V, U, CLUSTER>(w);
+            w.tq = a.tq;
+            diverged |= sweep_chunk_rows<CPLX, LPR, V, U, CLUSTER>(w, &tsum);
+            if (a.tpart && (t + 1) % a.nchunks == 0) {
+                // end of a cycle: this warp's partial of the trace series, reduced in a
+                // fixed order, one slot per (cycle, CTA, warp)
+                float v = tsum;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+                if (lane == 0) a.tpart[((size_t)cyc * gridDim.x + blockIdx.x) * nwarps + warp] = v;
+                tsum = 0.f;
+            }
+            // warm L2 with the next chunk's reads of last cycle's state
+            if (t + 1 < total && chunk_ready(smem_addr(&bars[b ^ 1]), (uint32_t)((t + 1) >> 1) & 1u, 64)) {
+                const int cn = (t + 1) / a.nchunks;
+                const int curn = a.cur ^ (cn & 1);
+                prefetch_upper<CPLX, LPR, V>(smem + (size_t)(b ^ 1) * a.blob_max, a.chunks[(t + 1) - cn * a.nchunks],
+                                             a.z[curn], a.w[curn], K, c0, first, stride, sub, cl, chain_ok);
+            }
         }
     }
     // the last chunk's rows are done before anyone leaves (the cluster's CTAs

@@ -190,6 +190,58 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
 // on the position); then all 2U gathers of z and w are issued before any FMA
 // consumes them.  The gathers are the only round trip to memory on the path.
 // ---------------------------------------------------------------------------
+// L2 prefetch of the next chunk's upper-neighbour gathers: z_j and w_j with
+// j > i come from last cycle's state, which nothing writes this cycle, so
+// they can be requested while the current chunk is still being swept; the
+// next chunk's rows then wait on L2 rather than DRAM.  One prefetch per
+// 128-byte line of the lane group's row segment.
+template <bool CPLX, int LPR, int V>
+__device__ __forceinline__ void prefetch_upper(const uint8_t *buf, const ChunkDesc &d, const void *zo, const void *wo,
+                                               size_t K, int c0, int first, int stride, int sub, int cl,
+                                               bool chain_ok)
+{
+    using P = Prec<CPLX>;
+    using Ent = typename P::Ent;
+    constexpr int BYTES_PER_LANE = V * (CPLX ? 8 : 4);
+    constexpr int LANES_PER_LINE = 128 / BYTES_PER_LANE > 0 ? 128 / BYTES_PER_LANE : 1;
+    if (!chain_ok || (cl % LANES_PER_LINE) != 0) return;
+    const RowMeta *meta = (const RowMeta *)buf;
+    const Ent *zs = (const Ent *)(buf + d.zent_off);
+    const Ent *ws = (const Ent *)(buf + d.went_off);
+    const char *zb = (const char *)zo, *wb = (const char *)wo;
+    const size_t esz = CPLX ? 8 : 4;
+    for (int base = first; base < d.rows; base += stride) {
+        const int r = base + sub;
+        if (r >= d.rows) break;
+        const int i = meta[r].row;
+        for (int e = meta[r].zoff; e < meta[r + 1].zoff; ++e) {
+            const int j = zs[e].col;
+            if (j > i) asm volatile("prefetch.global.L2 [%0];" ::"l"(zb + ((size_t)j * K + c0) * esz));
+        }
+        for (int e = meta[r].woff; e < meta[r + 1].woff; ++e) {
+            const int j = ws[e].col;
+            if (j > i) asm volatile("prefetch.global.L2 [%0];" ::"l"(wb + ((size_t)j * K + c0) * esz));
+        }
+    }
+}
+
+// Non-blocking look at whether a staged chunk has landed (bounded spin).
+__device__ __forceinline__ bool chunk_ready(uint32_t bar, uint32_t parity, int spins)
+{
+    for (int k = 0; k < spins; ++k) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // The rows of one staged chunk for one lane's chains (shared by the
 // single-matrix sweep and the pool's persistent sweep, so both compute the
 // same arithmetic in the same order).
@@ -198,7 +250,8 @@ struct ChunkWork {
     ChunkDesc d;
     const void *zo, *wo;       // last cycle's state [n][K]
     void *zn, *wn;             // this cycle's state
-    const uint32_t *noise;     // noise words of this cycle and this lane's chain word, by position
+    const uint32_t *noise;     // noise words of this cycle and this lane's chain word, by position;
+                               // null: no noise (phi = 0), the difference of two coupled paths (Eq. 12)
     void *dpart;               // this lane's unit of diagonal partials (by position), or null
     bool diag, dlead;
     int seg;
@@ -210,10 +263,13 @@ struct ChunkWork {
     int c0, first, stride, sub;
     bool chain_ok;
     uint32_t cshift;
+    const float *tq;           // trace weights q_i by position, or null
 };
 
+// Returns whether a chain left the finite bound; adds q_i Re(sum over this
+// lane's chains of z_i conj(w_i)) of its rows to *tsum when w.tq is set.
 template <bool CPLX, int LPR, int V, int U, bool CLUSTER>
-__device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w)
+__device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w, float *tsum)
 {
     using P = Prec<CPLX>;
     using L = Lane<CPLX, V>;
@@ -247,7 +303,8 @@ __device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w)
                 S dold = P::zero();
                 const int p = d.pb + r;
                 if (ok) {
-                    const uint32_t bits = __ldg(&noise[p]) >> cshift;
+                    const uint32_t bits = noise ? __ldg(&noise[p]) >> cshift : 0u;
+                    const float phi_scale = noise ? 1.f : 0.f;
                     if (w.diag && dlead) dold = dpart[p];
                     int rp = -1, sp = -1;
                     if (w.rpos) { rp = __ldg(&w.rpos[p]); sp = __ldg(&w.spos[p]); }
@@ -295,13 +352,19 @@ __device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w)
                     T zv, wv;
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        const float phi = ((bits >> v) & 1u) ? -1.f : 1.f;
+                        const float phi = phi_scale * (((bits >> v) & 1u) ? -1.f : 1.f);
                         const S zsc = P::zrow(k, phi, L::get(sz, v));
                         const S wsc = P::wrow(k, phi, L::get(sw, v));
                         L::set(zv, v, zsc);
                         L::set(wv, v, wsc);
                         diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
                         prod = P::add(prod, P::mulconj(zsc, wsc));
+                    }
+                    if (w.tq) {
+                        float re;
+                        if constexpr (CPLX) re = prod.x;
+                        else re = prod;
+                        *tsum = __fmaf_rn(__ldg(&w.tq[p]), re, *tsum);
                     }
                     zn[((size_t)i * K + c0) / V] = zv;
                     wn[((size_t)i * K + c0) / V] = wv;

@@ -28,8 +28,9 @@ MCINV_F_NO_DIAG = 1
 MCINV_F_AUTOTUNE = 2
 
 # every symbol include/mcinv.h declares
-EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_sample",
-           "mcinv_estimate", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
+EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
+           "mcinv_estimate", "mcinv_set_trace_weights", "mcinv_trace_mc_error", "mcinv_trace_series",
+           "mcinv_sample_until", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
            "mcinv_selftest_tc_gemm", "mcinv_block_accumulate_noalloc", "mcinv_destroy",
            "mcinv_last_error",
@@ -121,6 +122,15 @@ def lib():
                                    ctypes.POINTER(mcinv_options)]
         for name in ("mcinv_burnin", "mcinv_sample"):
             getattr(L, name).argtypes = [vp, i64]
+        L.mcinv_burnin_coupled.argtypes = [vp, ctypes.c_double, i64, ctypes.POINTER(i64)]
+        L.mcinv_burnin_coupled.restype = ctypes.c_int
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.mcinv_set_trace_weights.argtypes = [vp, vp]
+        L.mcinv_trace_mc_error.argtypes = [vp, dp, dp, dp, dp]
+        L.mcinv_trace_series.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+        L.mcinv_sample_until.argtypes = [vp, ctypes.c_double, i64, i64, ctypes.POINTER(i64)]
+        for name in ("mcinv_set_trace_weights", "mcinv_trace_mc_error", "mcinv_trace_series", "mcinv_sample_until"):
+            getattr(L, name).restype = ctypes.c_int
         L.mcinv_estimate.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         L.mcinv_sync.argtypes = [vp]
         L.mcinv_get_state.argtypes = [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]
@@ -260,6 +270,39 @@ def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_i
 
 def mcinv_burnin(h: Handle, cycles: int):
     _check(lib().mcinv_burnin(h.ptr, int(cycles)), h.ptr)
+
+
+def mcinv_burnin_coupled(h: Handle, tol: float, max_cycles: int = 100_000) -> int:
+    """Algorithm 1 steps 1-5: burn in until the coupled paths agree within tol; returns p."""
+    p = ctypes.c_int64()
+    _check(lib().mcinv_burnin_coupled(h.ptr, float(tol), int(max_cycles), ctypes.byref(p)), h.ptr)
+    return int(p.value)
+
+
+def mcinv_set_trace_weights(h: Handle, q_diag):
+    q = np.ascontiguousarray(q_diag, dtype=np.float64)
+    _check(lib().mcinv_set_trace_weights(h.ptr, _ptr(q)), h.ptr)
+
+
+def mcinv_trace_mc_error(h: Handle) -> dict:
+    """Geyer's Monte Carlo error of the trace: mean, var, ess, se."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(lib().mcinv_trace_mc_error(h.ptr, *[ctypes.byref(x) for x in v]), h.ptr)
+    return dict(zip(("mean", "var", "ess", "se"), (x.value for x in v)))
+
+
+def mcinv_trace_series(h: Handle) -> np.ndarray:
+    n = ctypes.c_int64()
+    _check(lib().mcinv_trace_series(h.ptr, None, 0, ctypes.byref(n)), h.ptr)
+    out = np.empty(n.value)
+    _check(lib().mcinv_trace_series(h.ptr, _ptr(out), n.value, ctypes.byref(n)), h.ptr)
+    return out
+
+
+def mcinv_sample_until(h: Handle, rel_tol: float, check_every: int = 100, max_cycles: int = 1_000_000) -> int:
+    c = ctypes.c_int64()
+    _check(lib().mcinv_sample_until(h.ptr, float(rel_tol), int(check_every), int(max_cycles), ctypes.byref(c)), h.ptr)
+    return int(c.value)
 
 
 def mcinv_sample(h: Handle, cycles: int):

@@ -282,3 +282,45 @@ def test_pure_gauge_lattice_closed_form():
     inv = np.linalg.inv(csr.to_dense())
     assert np.allclose(np.diag(inv), wl.free_lattice_diag(dims, 0.2, 0.1), atol=1e-13)
     assert not np.allclose(csr.to_dense(), csr.to_dense().conj().T)  # non-Hermitian
+
+
+# -- Monte Carlo error: Geyer's effective length (Sec. 2.3) ---------------------------------
+
+def test_paper_tables_se_is_sqrt_var_over_effective_length():
+    """The printed MC standard errors equal sqrt(Var / eff. length) (Tables 2, 4, 5)."""
+    with open(os.path.join(GOLDEN, "paper_tables.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 4
+    for r in rows:
+        var, eff, se = float(r[1]), float(r[2]), float(r[3])
+        assert abs(np.sqrt(var / eff) - se) <= 0.0006 * se + 5e-4
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9])
+def test_geyer_effective_length_of_ar1(rho):
+    """AR(1) with coefficient rho: effective length M (1 - rho)/(1 + rho)."""
+    rng = np.random.default_rng(2)
+    M = 200_000
+    e = rng.normal(size=M)
+    x = np.empty(M)
+    x[0] = e[0]
+    for t in range(1, M):
+        x[t] = rho * x[t - 1] + e[t]
+    g = oracle.geyer_ips(x)
+    want = M * (1 - rho) / (1 + rho)
+    assert abs(g["ess"] / want - 1) < 0.08
+    assert abs(g["se"] - np.sqrt(g["var"] / g["ess"])) < 1e-12
+    assert abs(g["var"] - 1 / (1 - rho ** 2)) < 0.05 / (1 - rho ** 2)
+
+
+def test_trace_series_mean_is_the_diagonal_trace():
+    """The realised per-cycle trace values average to sum_i q_i diag_i (Eq. tr)."""
+    csr = _small_random(18, 9, complex_=True)
+    q = np.random.default_rng(0).uniform(0, 1, 18)
+    series = []
+    st, dacc, _ = oracle.run(csr, 16, seed=3, ncycles=40, acc_from=10, q=q, series_out=series)
+    st, dacc2, _ = oracle.run(csr, 16, seed=3, cycle0=40, ncycles=15, acc_from=10, state=st, q=q,
+                              series_out=series)
+    assert len(series) == 45
+    tr = ((dacc.sum(0) + dacc2.sum(0)) * q).sum().real / (16 * 45)
+    assert abs(np.mean(series) - tr) < 1e-12 * abs(tr)
