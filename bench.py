@@ -215,7 +215,7 @@ def run_mine(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
                    "cycles_per_step": B, "estimates": "diagonal + C^-1[:, 0:512]",
                    "block_accumulation": "bf16 tensor cores" if acc else "fp32 simt",
-                   "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"],
+                   "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"], "ctas_per_slice": info0["ctas_per_slice"],
                    "levels": info0["levels"],
                    "l2": "inputs larger than L2 (z, w double-buffered: %.0f MB)" % (4 * 4 * csr.n * K / 1e6),
                    "parallelism": f"replicas x{world} (disjoint chains)"},
@@ -385,7 +385,7 @@ def run_batch(args, world, rank, local):
     return res
 
 
-def cpu_baseline(csr, K, seconds):
+def cpu_baseline(csr, K, seconds, workload=WORKLOAD):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     `chains` chains (one OpenMP thread per chain group) for `cycles` cycles."""
     import oracle
@@ -399,8 +399,94 @@ def cpu_baseline(csr, K, seconds):
     oracle.run(csr, chains, seed=0, ncycles=cycles, cpg=1, diag=False, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": float(csr.nnz) * chains * cycles / dt, "unit": UNIT, "cores": threads,
-            "kind": "oracle", "sample": f"{chains} chains x {cycles} cycles of {WORKLOAD} (of K={K})",
+            "kind": "oracle", "sample": f"{chains} chains x {cycles} cycles of {workload} (of K={K})",
             "seconds": dt}
+
+
+DIRAC_PAPER = {"exact": 413007.84, "cc_cycles": 10832 + 18, "cc_se": 4.128, "cpu_seconds": 10859.0}
+
+
+def run_dirac(args, world, rank, local):
+    """Algorithm 1 in full on the paper's Example 2, case 1 (Table 3): the free Wilson-Dirac
+    matrix on an 18^4 lattice (n = 419,904, 14 nonzeros per row, K = 0.1).
+
+    Coupling burn-in at tol 1e-5 (Eq. 12), then sampling until the trace's MC error
+    (Geyer's effective length) is below 1e-5 of the estimate, checked every 100 cycles,
+    the rule behind Tables 4 and 5.  The whole run is timed on the device; the estimate
+    is compared with the exact trace from the momentum-space closed form."""
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    from paper_cs_0412107_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dims = (18, 18, 18, 18)
+    csr = wl.wilson_dirac(dims, 0.1)
+    exact = wl.wilson_dirac_inverse_trace(dims, 0.1).real
+    K = args.chains
+    stream = torch.cuda.current_stream()
+    h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
+                              batch_cycles=10, chains_per_cta=args.W, threads_per_cta=args.threads,
+                              flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+    info0 = mcinv.mcinv_info(h)
+    mcinv.mcinv_set_trace_weights(h, np.ones(csr.n))
+    mcinv.mcinv_sync(h)
+    launches0 = info0["kernel_launches"]
+    mcinv.mcinv_profile(h, True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        p = mcinv.mcinv_burnin_coupled(h, 1e-5, 1000)
+        used = mcinv.mcinv_sample_until(h, 1e-5, 100, 100_000)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    prof = {mcinv.KERNEL_NAMES[k]: mcinv.mcinv_profile_read(h, k) for k in range(5)}
+    mcinv.mcinv_profile(h, False)
+    g = mcinv.mcinv_trace_mc_error(h)
+    launches = mcinv.mcinv_info(h)["kernel_launches"] - launches0
+    mcinv.mcinv_destroy(h)
+    ms_max = max_over_ranks(ms, world)
+    cycles = p + used
+    value = float(csr.nnz) * K * cycles * world / (ms_max / 1e3)
+    hbm, _, _, peak_kind = read_peaks()
+    sw_launches, sw_ms = prof["sweep"]
+    # the coupled-difference sweeps (one chain, no noise) are launched as well; count the
+    # units of every launch: K chains per chain cycle, one per difference cycle
+    units = float(csr.n) * (K * cycles + p)
+    compulsory = 32.0 * units  # read + write z and w once, complex64
+    gather = 8.0 * (2 * (csr.nnz - csr.n) + 2 * csr.n) / csr.n * units
+    achieved = compulsory / (sw_ms / 1e3) / 1e9 if sw_ms else None
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 (f32)", "data": "synthetic: the paper's own matrix (free Wilson-Dirac, 18^4, K=0.1)",
+        "config": {"workload": "dirac18", "n": csr.n, "nnz": csr.nnz, "K": K, "step": "one Algorithm 1 run",
+                   "burnin": "coupled, tol 1e-5", "stop": "MC error < 1e-5 of tr, checked every 100 cycles",
+                   "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"],
+                   "ctas_per_slice": info0["ctas_per_slice"], "levels": info0["levels"],
+                   "l2": "inputs larger than L2 (z, w double-buffered: %.1f GB)" % (4 * 8 * csr.n * K / 1e9)},
+        "result": {"burnin_cycles": p, "sampling_cycles": used, "trace": g["mean"], "mc_error": g["se"],
+                   "effective_length": g["ess"], "exact": exact, "z": (g["mean"] - exact) / g["se"],
+                   "seconds": ms_max / 1e3},
+        "paper_table4": DIRAC_PAPER,
+        "roofline": {"kernel": "cc_sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_unit": 32.0,
+                     "bytes": "compulsory (stencil neighbours are reuse)",
+                     "gather_inclusive_gbs": gather / (sw_ms / 1e3) / 1e9 if sw_ms else None,
+                     "sweep_ms_per_chain_cycle": sw_ms / cycles},
+        "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(csr, K, args.cpu_seconds, "dirac18")
+    return result
 
 
 def run_reference(args, world, rank):
@@ -451,7 +537,7 @@ def main():
     ap.add_argument("--e2e-burnin", type=int, default=500)
     ap.add_argument("--e2e-samples", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-burnin", type=int, default=200)
     ap.add_argument("--batch-samples", type=int, default=2000)
@@ -465,6 +551,8 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload == "batch512":
         res = run_batch(args, world, rank, local)
+    elif args.workload == "dirac18":
+        res = run_dirac(args, world, rank, local)
     else:
         res = run_mine(args, world, rank, local)
     if rank == 0 and res is not None:

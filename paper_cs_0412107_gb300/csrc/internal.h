@@ -32,13 +32,22 @@ struct __align__(16) CstC {
 // them concurrently and get exactly the in-place ascending-row result of
 // Eqs. 4/5).  A chunk is a run of positions inside one level whose data fit
 // one shared-memory buffer; its blob is
-//   RowMeta[rows + 1] | Cst[rows] | C entries | C^dagger entries
+//   RowMeta[items + 1] | Cst[rows] | C entries | C^dagger entries
 // (each part 16-byte aligned) and is copied to shared memory in one bulk copy.
+//
+// A chunk's rows are cut into work items.  A row with more than SPLIT_ENTRIES
+// off-diagonal entries in C or in C^dagger becomes P = 2 or 4 items, each a
+// contiguous slice of both entry lists (at most P = 4; a slice may be empty);
+// the slices' partial sums are added in piece order, ((p0 + p1) + p2) + p3,
+// whichever lanes compute them, so every launch shape gives the same bits.
+// Items of one row are consecutive and start at a multiple of P inside the
+// chunk (rows are ordered by decreasing P within a level).
+constexpr int SPLIT_ENTRIES = 8;
 struct RowMeta {
     int row;   // row index i of C
-    int zoff;  // first entry of row i of C within the chunk's C entries (row rows: end)
+    int zoff;  // first C entry of the item within the chunk's C entries (item `items`: end)
     int woff;  // same for C^dagger
-    int pad;
+    int info;  // bits 0-1: the item's piece k; bits 2-3: log2 P; bits 4-31: the row's index in the chunk
 };
 
 struct ChunkDesc {
@@ -47,10 +56,11 @@ struct ChunkDesc {
     int rows;       // positions pb .. pb + rows - 1
     int pb;
     int cst_off, zent_off, went_off;  // byte offsets of the parts within the blob
-    int flags;      // CHUNK_LEVEL_END: the next chunk starts a new level
-    int pad;
+    int flags;      // CHUNK_LEVEL_END: the next chunk starts a new level; CHUNK_SPLIT
+    int items;      // work items (rows + the extra pieces of split rows)
 };
 constexpr int CHUNK_LEVEL_END = 1;
+constexpr int CHUNK_SPLIT = 2;  // the chunk holds split rows (some item with P > 1)
 
 // Arguments of the coupled sweep.
 struct SweepArgs {

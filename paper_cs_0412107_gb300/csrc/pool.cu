@@ -208,13 +208,6 @@ __global__ void __launch_bounds__(512, 1) pool_sweep_kernel(const PoolSlotDev *_
             w.tq = nullptr;
             float tdummy = 0.f;
             diverged |= sweep_chunk_rows<false, LPR, V, U, false>(w, &tdummy);
-            if (t + 1 < total && chunk_ready(smem_addr(&bars[b ^ 1]), (uint32_t)((g + 1) >> 1) & 1u, 64)) {
-                const int cn = (t + 1) / S.nchunks;
-                const int curn = S.cur ^ (cn & 1);
-                prefetch_upper<false, LPR, V>(smem + (size_t)(b ^ 1) * blob_max, S.chunks[(t + 1) - cn * S.nchunks],
-                                              S.z[curn], S.w[curn], (size_t)K, c0, warp * RPW, nwarps * RPW, sub, cl,
-                                              chain_ok);
-            }
         }
         __syncthreads();  // the item's last chunk is done before its buffers are reused
     }

@@ -92,16 +92,25 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
         nlev = std::max(nlev, lv + 1);
     }
     P.nlev = nlev;
+    // pieces of a row: 1 up to SPLIT_ENTRIES entries on either side, 2 up to twice that, else 4
+    auto pieces_of = [&](int64_t i) {
+        const int64_t dz = row_ptr[i + 1] - row_ptr[i] - 1, dw = wcount[i + 1] - wcount[i];
+        const int64_t dm = std::max(dz, dw);
+        return dm <= SPLIT_ENTRIES ? 1 : dm <= 2 * SPLIT_ENTRIES ? 2 : 4;
+    };
     std::vector<int32_t> lev_ptr(nlev + 1, 0), perm(n);
     for (int64_t i = 0; i < n; ++i) lev_ptr[level[i] + 1]++;
     for (int l = 0; l < nlev; ++l) lev_ptr[l + 1] += lev_ptr[l];
     {
         std::vector<int32_t> fill(lev_ptr.begin(), lev_ptr.end() - 1);
         for (int64_t i = 0; i < n; ++i) perm[fill[level[i]]++] = (int32_t)i;
-        // rows of one level are independent: order them by decreasing work so
-        // the rows a warp takes together cost about the same
+        // rows of one level are independent: order them by decreasing number of
+        // pieces (so every split row's items start at a multiple of its P), then
+        // by decreasing work, so the rows a warp takes together cost about the same
         for (int l = 0; l < nlev; ++l)
             std::stable_sort(perm.begin() + lev_ptr[l], perm.begin() + lev_ptr[l + 1], [&](int32_t x, int32_t y) {
+                const int px = pieces_of(x), py = pieces_of(y);
+                if (px != py) return px > py;
                 const int64_t dx = (row_ptr[x + 1] - row_ptr[x]) + (wcount[x + 1] - wcount[x]);
                 const int64_t dy = (row_ptr[y + 1] - row_ptr[y]) + (wcount[y + 1] - wcount[y]);
                 return dx > dy;
@@ -113,13 +122,13 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
     const size_t ent_sz = cplx ? sizeof(EntC) : sizeof(EntR);
     const size_t cst_sz = cplx ? sizeof(CstC) : sizeof(CstR);
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    auto blob_bytes = [&](size_t rows, size_t nz, size_t nwv) {
-        return a16(16 * (rows + 1)) + a16(cst_sz * rows) + a16(ent_sz * nz) + a16(ent_sz * nwv);
+    auto blob_bytes = [&](size_t rows, size_t items, size_t nz, size_t nwv) {
+        return a16(16 * (items + 1)) + a16(cst_sz * rows) + a16(ent_sz * nz) + a16(ent_sz * nwv);
     };
     auto zdeg = [&](int64_t i) { return (size_t)(row_ptr[i + 1] - row_ptr[i] - 1); };
     auto wdeg = [&](int64_t i) { return (size_t)(wcount[i + 1] - wcount[i]); };
     size_t blob_max = (size_t)min_blob;
-    for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, zdeg(i), wdeg(i)));
+    for (int64_t i = 0; i < n; ++i) blob_max = std::max(blob_max, blob_bytes(1, pieces_of(i), zdeg(i), wdeg(i)));
     blob_max = (blob_max + 127) & ~(size_t)127;
     if (blob_max > 100 * 1024)
         return prep_fail(err, MCINV_E_UNSUPPORTED,
@@ -133,21 +142,24 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
         int64_t p = lev_ptr[l];
         while (p < lev_ptr[l + 1]) {
             const int64_t pb = p;
-            size_t nz = 0, nwv = 0;
-            while (p < lev_ptr[l + 1] && blob_bytes(p - pb + 1, nz + zdeg(perm[p]), nwv + wdeg(perm[p])) <= blob_max) {
+            size_t nz = 0, nwv = 0, items = 0;
+            while (p < lev_ptr[l + 1] &&
+                   blob_bytes(p - pb + 1, items + pieces_of(perm[p]), nz + zdeg(perm[p]), nwv + wdeg(perm[p])) <= blob_max) {
                 nz += zdeg(perm[p]);
                 nwv += wdeg(perm[p]);
+                items += pieces_of(perm[p]);
                 ++p;
             }
             ChunkDesc d{};
             d.rows = (int)(p - pb);
+            d.items = (int)items;
             d.pb = (int)pb;
-            d.cst_off = (int)a16(16 * (d.rows + 1));
+            d.cst_off = (int)a16(16 * (items + 1));
             d.zent_off = d.cst_off + (int)a16(cst_sz * d.rows);
             d.went_off = d.zent_off + (int)a16(ent_sz * nz);
             d.bytes = d.went_off + (int)a16(ent_sz * nwv);
             d.off = (long long)stream_bytes;
-            d.flags = p == lev_ptr[l + 1] ? CHUNK_LEVEL_END : 0;
+            d.flags = (p == lev_ptr[l + 1] ? CHUNK_LEVEL_END : 0) | (items > (size_t)d.rows ? CHUNK_SPLIT : 0);
             stream_bytes += ((size_t)d.bytes + 127) & ~(size_t)127;
             chunks.push_back(d);
         }
@@ -156,11 +168,17 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
     for (const ChunkDesc &d : chunks) {
         uint8_t *blob = stream.data() + d.off;
         RowMeta *meta = (RowMeta *)blob;
-        int zo = 0, wo = 0;
+        int zo = 0, wo = 0, it = 0;
         for (int r = 0; r < d.rows; ++r) {
             const int64_t i = perm[d.pb + r];
-            meta[r] = RowMeta{(int)i, zo, wo, 0};
             cst_at[d.pb + r] = d.off + d.cst_off + (long long)(r * cst_sz);
+            const int np = pieces_of(i);
+            const int lg = np == 1 ? 0 : np == 2 ? 1 : 2;
+            const int dz = (int)zdeg(i), dw = (int)wdeg(i);
+            const int cz = (dz + np - 1) / np, cw = (dw + np - 1) / np;  // entries per piece
+            for (int k = 0; k < np; ++k)
+                meta[it + k] = RowMeta{(int)i, zo + std::min(dz, k * cz), wo + std::min(dw, k * cw), k | (lg << 2) | (r << 4)};
+            it += np;
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                 if (col[e] == i) continue;
                 if (!cplx) ((EntR *)(blob + d.zent_off))[zo++] = EntR{col[e], (float)val[e]};
@@ -171,7 +189,7 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
                 else ((EntC *)(blob + d.went_off))[wo++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
             }
         }
-        meta[d.rows] = RowMeta{-1, zo, wo, 0};
+        meta[d.items] = RowMeta{-1, zo, wo, 0};
     }
     std::vector<int32_t> pos(n);
     for (int64_t p = 0; p < n; ++p) pos[perm[p]] = (int32_t)p;

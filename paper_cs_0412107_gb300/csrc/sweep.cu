@@ -243,13 +243,6 @@ __global__ void __launch_bounds__(512, 1) cc_sweep_kernel(const SweepArgs a)
                 if (lane == 0) a.tpart[((size_t)cyc * gridDim.x + blockIdx.x) * nwarps + warp] = v;
                 tsum = 0.f;
             }
-            // warm L2 with the next chunk's reads of last cycle's state
-            if (t + 1 < total && chunk_ready(smem_addr(&bars[b ^ 1]), (uint32_t)((t + 1) >> 1) & 1u, 64)) {
-                const int cn = (t + 1) / a.nchunks;
-                const int curn = a.cur ^ (cn & 1);
-                prefetch_upper<CPLX, LPR, V>(smem + (size_t)(b ^ 1) * a.blob_max, a.chunks[(t + 1) - cn * a.nchunks],
-                                             a.z[curn], a.w[curn], K, c0, first, stride, sub, cl, chain_ok);
-            }
         }
     }
     // the last chunk's rows are done before anyone leaves (the cluster's CTAs

@@ -112,6 +112,21 @@ struct Lane {
             set(acc, k, s);
         }
     }
+    // a + b, component by component (joins the partial sums of a split row)
+    static __device__ __forceinline__ T add(const T &a, const T &b)
+    {
+        T v;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) f(v)[k] = __fadd_rn(f(a)[k], f(b)[k]);
+        return v;
+    }
+    static __device__ __forceinline__ T shfl_down(const T &a, int o)
+    {
+        T v;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) f(v)[k] = __shfl_down_sync(0xffffffffu, f(a)[k], o);
+        return v;
+    }
 };
 
 // State reads of the cluster variant go to L2 (ld.global.cg): rows written by
@@ -185,63 +200,16 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar, uint32_t parity)
 // cycle and z_j (j > i) from last cycle's buffer, exactly the in-place
 // semantics of Eq. 4 (and of Eq. 5 for w).
 //
-// Per row: the row record, constants and entries come from shared memory;
-// the noise word and the diagonal partial are loaded first (they depend only
+// Per work item (a row, or one of the 2 or 4 pieces of a long row): the item
+// record, constants and entries come from shared memory; the row's first
+// piece loads the noise word and the diagonal partial first (they depend only
 // on the position); then all 2U gathers of z and w are issued before any FMA
 // consumes them.  The gathers are the only round trip to memory on the path.
+// Splitting a long row over sibling lane groups keeps the chunk's slowest
+// item, which everyone waits for at the chunk barrier, to about one round
+// trip: rows are sorted by decreasing length, so without it the first warp
+// of every chunk walks the level's longest rows U entries at a time.
 // ---------------------------------------------------------------------------
-// L2 prefetch of the next chunk's upper-neighbour gathers: z_j and w_j with
-// j > i come from last cycle's state, which nothing writes this cycle, so
-// they can be requested while the current chunk is still being swept; the
-// next chunk's rows then wait on L2 rather than DRAM.  One prefetch per
-// 128-byte line of the lane group's row segment.
-template <bool CPLX, int LPR, int V>
-__device__ __forceinline__ void prefetch_upper(const uint8_t *buf, const ChunkDesc &d, const void *zo, const void *wo,
-                                               size_t K, int c0, int first, int stride, int sub, int cl,
-                                               bool chain_ok)
-{
-    using P = Prec<CPLX>;
-    using Ent = typename P::Ent;
-    constexpr int BYTES_PER_LANE = V * (CPLX ? 8 : 4);
-    constexpr int LANES_PER_LINE = 128 / BYTES_PER_LANE > 0 ? 128 / BYTES_PER_LANE : 1;
-    if (!chain_ok || (cl % LANES_PER_LINE) != 0) return;
-    const RowMeta *meta = (const RowMeta *)buf;
-    const Ent *zs = (const Ent *)(buf + d.zent_off);
-    const Ent *ws = (const Ent *)(buf + d.went_off);
-    const char *zb = (const char *)zo, *wb = (const char *)wo;
-    const size_t esz = CPLX ? 8 : 4;
-    for (int base = first; base < d.rows; base += stride) {
-        const int r = base + sub;
-        if (r >= d.rows) break;
-        const int i = meta[r].row;
-        for (int e = meta[r].zoff; e < meta[r + 1].zoff; ++e) {
-            const int j = zs[e].col;
-            if (j > i) asm volatile("prefetch.global.L2 [%0];" ::"l"(zb + ((size_t)j * K + c0) * esz));
-        }
-        for (int e = meta[r].woff; e < meta[r + 1].woff; ++e) {
-            const int j = ws[e].col;
-            if (j > i) asm volatile("prefetch.global.L2 [%0];" ::"l"(wb + ((size_t)j * K + c0) * esz));
-        }
-    }
-}
-
-// Non-blocking look at whether a staged chunk has landed (bounded spin).
-__device__ __forceinline__ bool chunk_ready(uint32_t bar, uint32_t parity, int spins)
-{
-    for (int k = 0; k < spins; ++k) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 // The rows of one staged chunk for one lane's chains (shared by the
 // single-matrix sweep and the pool's persistent sweep, so both compute the
 // same arithmetic in the same order).
@@ -290,128 +258,165 @@ __device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w, float *tsum
     S *dpart = (S *)w.dpart;
     bool diverged = false;
 
-            const RowMeta *meta = (const RowMeta *)buf;
-            const Cst *cstv = (const Cst *)(buf + d.cst_off);
-            const Ent *zs = (const Ent *)(buf + d.zent_off);
-            const Ent *ws = (const Ent *)(buf + d.went_off);
-            const uint32_t *__restrict__ noise = w.noise;
-            const int shcol = w.shcol;
-            for (int base = first; base < d.rows; base += stride) {
-                const int r = base + sub;
-                const bool ok = chain_ok && r < d.rows;
-                S prod = P::zero();
-                S dold = P::zero();
-                const int p = d.pb + r;
-                if (ok) {
-                    const uint32_t bits = noise ? __ldg(&noise[p]) >> cshift : 0u;
-                    const float phi_scale = noise ? 1.f : 0.f;
-                    if (w.diag && dlead) dold = dpart[p];
-                    int rp = -1, sp = -1;
-                    if (w.rpos) { rp = __ldg(&w.rpos[p]); sp = __ldg(&w.spos[p]); }
-                    const RowMeta m = meta[r];
-                    const int i = m.row;
-                    const int zb = m.zoff, zeN = meta[r + 1].zoff;
-                    const int wb = m.woff, weN = meta[r + 1].woff;
-                    T sz = L::zero(), sw = L::zero();
-                    for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
-                        // issue every gather before any FMA consumes one; real entries
-                        // (8 B) stay in registers, complex ones (16 B) are re-read from
-                        // shared memory by the FMA pass to keep the register budget
-                        constexpr bool KEEP = !CPLX;
-                        Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
-                        T xz[U], xw[U];
+    constexpr int RPW = 32 / LPR;  // lane groups (items) per warp
+    const bool split = (d.flags & CHUNK_SPLIT) != 0;
+    const RowMeta *meta = (const RowMeta *)buf;
+    const Cst *cstv = (const Cst *)(buf + d.cst_off);
+    const Ent *zs = (const Ent *)(buf + d.zent_off);
+    const Ent *ws = (const Ent *)(buf + d.went_off);
+    const uint32_t *__restrict__ noise = w.noise;
+    const int shcol = w.shcol;
+    // this lane's partial sums over item q's slices of the C and C^dagger entries of row i
+    auto piece = [&](int q, int i, T &sz, T &sw) {
+        const int zb = meta[q].zoff, zeN = meta[q + 1].zoff;
+        const int wb = meta[q].woff, weN = meta[q + 1].woff;
+        for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += U, ew += U) {
+            // issue every gather before any FMA consumes one; real entries
+            // (8 B) stay in registers, complex ones (16 B) are re-read from
+            // shared memory by the FMA pass to keep the register budget
+            constexpr bool KEEP = !CPLX;
+            Ent enz[KEEP ? U : 1], enw[KEEP ? U : 1];
+            T xz[U], xw[U];
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            xz[u] = L::zero();
-                            xw[u] = L::zero();
-                            if (ez + u < zeN) {
-                                const Ent e = zs[ez + u];
-                                if constexpr (KEEP) enz[u] = e;
-                                const T *src = e.col < i ? zn : zo;
-                                xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
-                            }
-                            if (ew + u < weN) {
-                                const Ent e = ws[ew + u];
-                                if constexpr (KEEP) enw[u] = e;
-                                const T *src = e.col < i ? wn : wo;
-                                xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            if constexpr (KEEP) {
-                                if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
-                                if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
-                            } else {
-                                if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
-                                if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
-                            }
-                        }
-                    }
-                    const Cst k = cstv[r];
-                    T zv, wv;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const float phi = phi_scale * (((bits >> v) & 1u) ? -1.f : 1.f);
-                        const S zsc = P::zrow(k, phi, L::get(sz, v));
-                        const S wsc = P::wrow(k, phi, L::get(sw, v));
-                        L::set(zv, v, zsc);
-                        L::set(wv, v, wsc);
-                        diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
-                        prod = P::add(prod, P::mulconj(zsc, wsc));
-                    }
-                    if (w.tq) {
-                        float re;
-                        if constexpr (CPLX) re = prod.x;
-                        else re = prod;
-                        *tsum = __fmaf_rn(__ldg(&w.tq[p]), re, *tsum);
-                    }
-                    zn[((size_t)i * K + c0) / V] = zv;
-                    wn[((size_t)i * K + c0) / V] = wv;
-                    if (rp >= 0 || sp >= 0) {
-                        // shadow column of (cycle, chain): cycle block of kp elements, then
-                        // the chain (x2 for re,im); blocks are padded to 64 and the pad
-                        // stays zero
-                        const size_t o = (size_t)shcol * w.kp + (size_t)c0 * (CPLX ? 2 : 1);
-                        constexpr int NF = L::NF;
-                        if (rp >= 0) {
-                            uint16_t *dst = w.zsh + (size_t)rp * w.ldsh + o;
-#pragma unroll
-                            for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
-                        }
-                        if (sp >= 0) {
-                            if constexpr (!CPLX) {
-                                uint16_t *dst = w.wsh + (size_t)sp * w.ldsh + o;
-#pragma unroll
-                                for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
-                            } else {
-                                // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
-                                // [-wi, wr] to Im(z conj w), so the product comes out
-                                // interleaved re,im
-                                uint16_t *w0 = w.wsh + (size_t)(2 * sp) * w.ldsh + o;
-                                uint16_t *w1 = w0 + w.ldsh;
-#pragma unroll
-                                for (int v = 0; v < V; ++v) {
-                                    const S x = L::get(wv, v);
-                                    w0[2 * v] = bf16_bits(x.x);
-                                    w0[2 * v + 1] = bf16_bits(x.y);
-                                    w1[2 * v] = bf16_bits(-x.y);
-                                    w1[2 * v + 1] = bf16_bits(x.x);
-                                }
-                            }
-                        }
-                    }
+            for (int u = 0; u < U; ++u) {
+                xz[u] = L::zero();
+                xw[u] = L::zero();
+                if (ez + u < zeN) {
+                    const Ent e = zs[ez + u];
+                    if constexpr (KEEP) enz[u] = e;
+                    const T *src = e.col < i ? zn : zo;
+                    xz[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
                 }
-                if (w.diag) {
-                    // sum over the seg lanes of a unit (all lanes shuffle); the leader
-                    // adds the running partial it loaded at the start of the row
-#pragma unroll
-                    for (int o = 1; o < LPR; o <<= 1)
-                        if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
-                    if (ok && dlead) dpart[p] = P::add(dold, prod);
+                if (ew + u < weN) {
+                    const Ent e = ws[ew + u];
+                    if constexpr (KEEP) enw[u] = e;
+                    const T *src = e.col < i ? wn : wo;
+                    xw[u] = ld_state<CLUSTER>(&src[((size_t)e.col * K + c0) / V]);
                 }
             }
-        
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if constexpr (KEEP) {
+                    if (ez + u < zeN) L::fma(sz, enz[u], xz[u]);
+                    if (ew + u < weN) L::fma(sw, enw[u], xw[u]);
+                } else {
+                    if (ez + u < zeN) L::fma(sz, zs[ez + u], xz[u]);
+                    if (ew + u < weN) L::fma(sw, ws[ew + u], xw[u]);
+                }
+            }
+        }
+    };
+    for (int base = first; base < d.items; base += stride) {
+        const int it = base + sub;
+        const bool live = chain_ok && it < d.items;
+        const RowMeta m = it < d.items ? meta[it] : RowMeta{0, 0, 0, 0};
+        const int i = m.row;
+        const int pk = m.info & 3;              // this item's piece
+        const int np = 1 << ((m.info >> 2) & 3);  // pieces of its row
+        const int r = m.info >> 4;              // the row within the chunk
+        // the pieces of a row run on sibling lane groups of this warp when they fit
+        // in it (they start at a multiple of np, so they do); otherwise the first
+        // piece's lanes run them one after another.  Either way the partial sums
+        // are added in piece order, ((p0 + p1) + p2) + p3.
+        const bool par = np <= RPW;
+        const bool ok = live && pk == 0;  // the row's update is made by its first piece
+        S prod = P::zero();
+        S dold = P::zero();
+        const int p = d.pb + r;
+        uint32_t bits = 0u;
+        int rp = -1, sp = -1;
+        if (ok) {
+            bits = noise ? __ldg(&noise[p]) >> cshift : 0u;
+            if (w.diag && dlead) dold = dpart[p];
+            if (w.rpos) { rp = __ldg(&w.rpos[p]); sp = __ldg(&w.spos[p]); }
+        }
+        T sz = L::zero(), sw = L::zero();
+        if constexpr (RPW >= 4) {
+            if (live) piece(it, i, sz, sw);  // np <= 4 <= RPW: always on sibling lane groups
+        } else if (!split) {
+            if (live) piece(it, i, sz, sw);  // every item is a whole row
+        } else if (live && (par || ok)) {
+            const int nq = par ? 1 : np;
+#pragma unroll 1
+            for (int q = 0; q < nq; ++q) {
+                T pz = L::zero(), pw = L::zero();
+                piece(it + q, i, pz, pw);
+                if (q == 0) { sz = pz; sw = pw; }
+                else { sz = L::add(sz, pz); sw = L::add(sw, pw); }
+            }
+        }
+        // the first piece's lanes fold in the others' partial sums; only they add,
+        // so every shuffle reads a piece's own partial sum
+#pragma unroll
+        for (int q = 1; q < 4 && q < RPW && split; ++q) {
+            const T oz = L::shfl_down(sz, q * LPR), ow = L::shfl_down(sw, q * LPR);
+            if (par && pk == 0 && q < np) { sz = L::add(sz, oz); sw = L::add(sw, ow); }
+        }
+        if (ok) {
+            const float phi_scale = noise ? 1.f : 0.f;
+            const Cst k = cstv[r];
+            T zv, wv;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float phi = phi_scale * (((bits >> v) & 1u) ? -1.f : 1.f);
+                const S zsc = P::zrow(k, phi, L::get(sz, v));
+                const S wsc = P::wrow(k, phi, L::get(sw, v));
+                L::set(zv, v, zsc);
+                L::set(wv, v, wsc);
+                diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
+                prod = P::add(prod, P::mulconj(zsc, wsc));
+            }
+            if (w.tq) {
+                float re;
+                if constexpr (CPLX) re = prod.x;
+                else re = prod;
+                *tsum = __fmaf_rn(__ldg(&w.tq[p]), re, *tsum);
+            }
+            zn[((size_t)i * K + c0) / V] = zv;
+            wn[((size_t)i * K + c0) / V] = wv;
+            if (rp >= 0 || sp >= 0) {
+                // shadow column of (cycle, chain): cycle block of kp elements, then
+                // the chain (x2 for re,im); blocks are padded to 64 and the pad
+                // stays zero
+                const size_t o = (size_t)shcol * w.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                constexpr int NF = L::NF;
+                if (rp >= 0) {
+                    uint16_t *dst = w.zsh + (size_t)rp * w.ldsh + o;
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
+                }
+                if (sp >= 0) {
+                    if constexpr (!CPLX) {
+                        uint16_t *dst = w.wsh + (size_t)sp * w.ldsh + o;
+#pragma unroll
+                        for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
+                    } else {
+                        // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
+                        // [-wi, wr] to Im(z conj w), so the product comes out
+                        // interleaved re,im
+                        uint16_t *w0 = w.wsh + (size_t)(2 * sp) * w.ldsh + o;
+                        uint16_t *w1 = w0 + w.ldsh;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const S x = L::get(wv, v);
+                            w0[2 * v] = bf16_bits(x.x);
+                            w0[2 * v + 1] = bf16_bits(x.y);
+                            w1[2 * v] = bf16_bits(-x.y);
+                            w1[2 * v + 1] = bf16_bits(x.x);
+                        }
+                    }
+                }
+            }
+        }
+        if (w.diag) {
+            // sum over the seg lanes of a unit (all lanes shuffle); the leader
+            // adds the running partial it loaded at the start of the row
+#pragma unroll
+            for (int o = 1; o < LPR; o <<= 1)
+                if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
+            if (ok && dlead) dpart[p] = P::add(dold, prod);
+        }
+    }
     return diverged;
 }
 

@@ -22,6 +22,11 @@ Workloads
   d_{x-mu} with U(1) link phases.  Site index i = x0 + L0*(x1 + L1*(...)),
   x0 fastest.  ``pure_gauge=True`` makes the links a gauge transform of the
   free field, so diag(C^-1) has a closed form (used as a truth value).
+* ``wilson_dirac``     -- the paper's own Example 2 matrix (Sec. 3.2, Eqs.
+  disDirac and explicit): the free 4-spinor Wilson-Dirac operator on a periodic
+  N1 x N2 x N3 x N0 lattice, 14 nonzeros per row (Table 3).
+  ``wilson_dirac_propagator`` / ``wilson_dirac_inverse_trace`` give its exact
+  inverse from the momentum-space closed form (truth values, not the sampler).
 * ``batch_sizes``      -- n log-uniform in [lo, hi] for the batched form.
 
 All CSR outputs: ``row_ptr`` int64[n+1], ``col`` int32[nnz] strictly
@@ -186,6 +191,72 @@ def free_lattice_diag(dims, kappa_f, kappa_b) -> complex:
     for p in grids:
         lam -= kappa_f * np.exp(1j * p) + kappa_b * np.exp(-1j * p)
     return complex(np.mean(1.0 / lam))
+
+
+# Euclidean gamma matrices in the Dirac representation: gamma^k = [[0, -i s_k], [i s_k, 0]]
+# (k = 1, 2, 3, Pauli s_k) and gamma^4 = diag(1, 1, -1, -1).  Hermitian, square to 1 and
+# anticommute.  The paper prints gamma^k without the -i / i factors and with s_2 = [[0,-i],[-i,0]];
+# only this Hermitian set reproduces its exact traces (Tables 4, 5), and only the Dirac form of
+# gamma^4 gives its 14 nonzeros per row (Table 3).
+_PAULI = (np.array([[0, 1], [1, 0]], dtype=np.complex128),
+          np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+          np.array([[1, 0], [0, -1]], dtype=np.complex128))
+_Z2 = np.zeros((2, 2), dtype=np.complex128)
+DIRAC_GAMMA = tuple([np.block([[_Z2, -1j * s], [1j * s, _Z2]]) for s in _PAULI]
+                    + [np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)])
+
+
+def wilson_dirac(dims=(18, 18, 18, 18), kappa: float = 0.1) -> CSR:
+    """The free Wilson-Dirac matrix of Sec. 3.2 (Eqs. disDirac and explicit).
+
+    L = I + kappa sum_mu [(1 + gamma^mu) d_{y, x+mu} + (1 - gamma^mu) d_{y, x-mu}] on a
+    periodic lattice ``dims = (N1, N2, N3, N0)``; direction mu = 1, 2, 3, 4 moves
+    coordinate N1, N2, N3, N0 (time last).  Row index, 0-based, follows the paper's
+    mapping with the spinor index slowest: i = a + N1 (b + N2 (c + N3 (d + N0 s))).
+    Zero entries of (1 +- gamma^4) are not stored: 14 nonzeros per row.
+    """
+    dims = tuple(int(L) for L in dims)
+    V = int(np.prod(dims))
+    coords = np.indices(dims[::-1]).reshape(4, -1)[::-1]  # coords[mu][site], N1 fastest
+    strides = np.cumprod((1,) + dims[:-1])
+    x = (coords * strides[:, None]).sum(axis=0)
+    rows, cols, vals = [np.arange(4 * V)], [np.arange(4 * V)], [np.ones(4 * V, dtype=np.complex128)]
+    eye = np.eye(4, dtype=np.complex128)
+    for mu in range(4):
+        for sign in (1, -1):
+            nb = coords.copy()
+            nb[mu] = (nb[mu] + sign) % dims[mu]
+            y = (nb * strides[:, None]).sum(axis=0)
+            blk = kappa * (eye + sign * DIRAC_GAMMA[mu])
+            for s in range(4):
+                for t in range(4):
+                    if blk[s, t] != 0:
+                        rows.append(x + V * s)
+                        cols.append(y + V * t)
+                        vals.append(np.full(V, blk[s, t]))
+    return csr_from_coo(4 * V, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def wilson_dirac_propagator(dims, kappa: float, r=(0, 0, 0, 0)) -> np.ndarray:
+    """The 4x4 spinor block L^-1(x, x + r) of ``wilson_dirac``, exactly (any site x).
+
+    L is block-circulant on the periodic lattice: a plane wave e^{ip.y} u is mapped to
+    e^{ip.x} M(p) u with M(p) = I + kappa sum_mu [2 cos p_mu + 2i sin p_mu gamma^mu], so
+    L^-1(x, x + r) = (1/V) sum_p e^{-ip.r} M(p)^-1, p_mu = 2 pi k / N_mu.
+    """
+    grids = np.meshgrid(*[2 * math.pi * np.arange(L) / L for L in dims], indexing="ij")
+    P = np.stack([g.ravel() for g in grids], axis=-1)
+    M = np.broadcast_to(np.eye(4, dtype=np.complex128), (len(P), 4, 4)).copy()
+    for mu in range(4):
+        M += kappa * (2 * np.cos(P[:, mu])[:, None, None] * np.eye(4)
+                      + 2j * np.sin(P[:, mu])[:, None, None] * DIRAC_GAMMA[mu])
+    phase = np.exp(-1j * (P @ np.asarray(r, dtype=np.float64)))
+    return np.einsum("p,pij->ij", phase, np.linalg.inv(M)) / len(P)
+
+
+def wilson_dirac_inverse_trace(dims, kappa: float) -> complex:
+    """tr(L^-1) of ``wilson_dirac``: the lattice volume times the trace of the r = 0 block."""
+    return complex(np.prod(dims) * np.trace(wilson_dirac_propagator(dims, kappa)))
 
 
 # -- the five workloads the library is measured on ---------------------------------
