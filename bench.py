@@ -127,13 +127,14 @@ def max_over_ranks(x, world):
 
 def traffic_from_profiles(kernel_file, units_per_launch):
     """DRAM bytes per launch of the sweep from the committed ncu summary, if the
-    summary was taken on the current source of the kernel (matching hash)."""
+    summary was taken on the current source of the kernel and its chunk layout
+    (matching hash of sweep.cu, sweep_core.cuh and internal.h)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(p):
         return None
     src = b"".join(open(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f), "rb").read()
-                   for f in ("sweep.cu", "sweep_core.cuh")
+                   for f in ("sweep.cu", "sweep_core.cuh", "internal.h")
                    if os.path.exists(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f)))
     digest = hashlib.sha256(src).hexdigest()[:16]
     per_unit, ok = None, False
@@ -360,6 +361,11 @@ def run_batch(args, world, rank, local):
            "block_tflops_effective": flops / dt / 1e12,
            "rms_error_vs_dense_inverse": {"median": float(np.median(errs)), "max": float(np.max(errs))},
            "kernel_launches": info["kernel_launches"]}
+    # time to 1e-2 RMS error of every inverse: the same schedule through the batched
+    # BF16 pool and through the plain path (one FP32 handle per matrix, SIMT
+    # accumulation, launches issued one by one), RMS checked on every 64th matrix
+    if args.rms_samples > 0:
+        res["time_to_rms"] = time_to_rms(args, mats, burn, K, B, budget, rank)
     # serving: Poisson arrivals at 50% and 90% of the batch throughput (matrices/s)
     rate_max = len(mats) / dt
     serving = {}
@@ -383,6 +389,47 @@ def run_batch(args, world, rank, local):
                                            "completed_per_s": n_req / el, "engine_steps": st["steps"]}
     res["serving"] = serving
     return res
+
+
+def time_to_rms(args, mats, burn, K, B, budget, rank):
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    samp = args.rms_samples
+    check = list(range(0, len(mats), 64))
+    truth = {k: np.linalg.inv(mats[k].to_dense()) for k in check}
+    out = {"target_rms": 1e-2, "burnin": burn, "samples": samp, "checked_matrices": len(check)}
+    # batched form
+    pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
+                                   max_slots=len(mats), batch_cycles=B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
+    while not all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
+        mcinv.mcinv_pool_step(pool)
+    est = {k: mcinv.mcinv_pool_estimate(pool, tickets[k], mcinv.MCINV_EST_BLOCK, mats[k].n)[0] for k in check}
+    t_pool = time.perf_counter() - t0
+    mcinv.mcinv_pool_destroy(pool)
+    rms_pool = [float(np.sqrt(np.mean((est[k] - truth[k]) ** 2))) for k in check]
+    # plain path: every matrix on its own handle, FP32 CUDA-core accumulation of the full inverse
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rms_plain = []
+    for k, c in enumerate(mats):
+        h = mcinv.create_from_csr(c, K=K, seed=args.seed, chain_base=rank * K, matrix_id=k,
+                                  acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=B,
+                                  block_rows=np.arange(c.n), block_cols=np.arange(c.n))
+        mcinv.mcinv_burnin(h, burn)
+        mcinv.mcinv_sample(h, samp)
+        m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+        mcinv.mcinv_destroy(h)
+        if k in truth:
+            rms_plain.append(float(np.sqrt(np.mean((m - truth[k]) ** 2))))
+    t_plain = time.perf_counter() - t0
+    out["batched_bf16"] = {"seconds": t_pool, "rms_max": max(rms_pool), "rms_median": float(np.median(rms_pool))}
+    out["plain_fp32"] = {"seconds": t_plain, "rms_max": max(rms_plain), "rms_median": float(np.median(rms_plain))}
+    out["speedup"] = t_plain / t_pool
+    return out
 
 
 def cpu_baseline(csr, K, seconds, workload=WORKLOAD):
@@ -543,6 +590,7 @@ def main():
     ap.add_argument("--batch-samples", type=int, default=2000)
     ap.add_argument("--batch-mem-gb", type=float, default=64.0)
     ap.add_argument("--serve-requests", type=int, default=128)
+    ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"

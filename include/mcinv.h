@@ -95,6 +95,25 @@ typedef struct {
 #define MCINV_F_AUTOTUNE 2 /* when chains_per_cta, ctas_per_slice and threads_per_cta are all 0,
                               time the candidate slice shapes on this matrix for two cycles at
                               create time and keep the fastest (cached per n, nnz, K, type) */
+#define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
+                              handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
+                              of C), whose Gauss-Seidel sweep has one dependency level per colour.
+                              E[z w^dagger] is then P C^-1 P^T; every row-indexed argument and
+                              result (block rows and columns, q, the diagonal, the chain state)
+                              stays in the rows of C as given.  The noise of C' row k is drawn
+                              for row k, so the draws differ from the given order's. */
+
+/*
+ * The colour sweep order (Sec. 4: the paper's suggestion to reorder the rows and
+ * columns of C).  Rows, in ascending index order, each take the smallest colour
+ * not used by an already-coloured neighbour in the graph of C + C^T (off-diagonal
+ * entries); order[k], k < n, lists colour 0's rows ascending, then colour 1's, and
+ * so on, and *ncolors (may be NULL) receives the number of colours.  Host only: no
+ * GPU is touched.  order is caller-owned, n entries.  Returns MCINV_E_ARG for a
+ * malformed CSR or NULL order and MCINV_E_SINGULAR_DIAG for a missing diagonal.
+ */
+mcinv_status mcinv_color_order(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t *order,
+                               int32_t *ncolors);
 
 /* Fill *opt with defaults (K = 1024, seed = 0, everything else automatic). */
 void mcinv_default_options(mcinv_options *opt);

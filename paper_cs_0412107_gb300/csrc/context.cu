@@ -56,6 +56,9 @@ struct mcinv_ctx {
     double *d_series = nullptr;
     int64_t nseries = 0, cap_series = 0;
     int *d_status = nullptr;
+    // MCINV_F_COLOR_ORDER: the handle samples C' = P C P^T; ord[k] is the row of C
+    // that is row k of C' (empty: the rows of C in their given order)
+    std::vector<int32_t> ord;
     // counters
     int64_t cycle = 0, samples = 0, block_batches = 0, block_cycles = 0, launches = 0;
     int64_t bytes = 0;
@@ -197,7 +200,7 @@ static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_c
 
 static mcinv_status autotune(mcinv_ctx *h)
 {
-    const auto key = std::make_tuple(h->n, h->nnz, h->K, h->cplx);
+    const auto key = std::make_tuple(h->n, h->nnz, h->K, h->cplx | (h->ord.empty() ? 0 : 2));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -283,6 +286,24 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     const int cplx = dt == MCINV_COMPLEX128;
     const int NV = cplx ? 2 : 1;
 
+    // the colour order (Sec. 4): sample C' = P C P^T, whose Gauss-Seidel sweep has
+    // one dependency level per colour; row-indexed inputs and outputs are mapped
+    std::vector<int32_t> ord, inv;
+    std::vector<int64_t> rp2;
+    std::vector<int32_t> col2;
+    std::vector<double> val2;
+    if (opt.flags & MCINV_F_COLOR_ORDER) {
+        std::string why;
+        int nc = 0;
+        const mcinv_status st = color_order(n, row_ptr, col, val, cplx, ord, &nc, &why);
+        if (st != MCINV_OK) return fail(nullptr, st, "%s", why.c_str());
+        permute_csr(n, row_ptr, col, val, cplx, ord, rp2, col2, val2);
+        inv.resize(n);
+        for (int64_t k = 0; k < n; ++k) inv[ord[k]] = (int32_t)k;
+        row_ptr = rp2.data();
+        col = col2.data();
+        val = val2.data();
+    }
     Prepared P;
     {
         std::string why;
@@ -295,6 +316,7 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     h->seed = opt.seed; h->chain_base = opt.chain_base; h->matrix_id = opt.matrix_id;
     h->stream = (cudaStream_t)opt.stream;
     h->flags = opt.flags;
+    h->ord = std::move(ord);
     h->acc = opt.acc;
     h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
     int default_threads = 256;
@@ -375,7 +397,7 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     SETUP(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     SETUP(cudaStreamSynchronize(h->stream));
     if (bad != 0x7fffffff) {
-        fail(h, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %d is not usable", perm[bad]);
+        fail(h, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %d is not usable", h->ord.empty() ? perm[bad] : h->ord[perm[bad]]);
         return bail(MCINV_E_SINGULAR_DIAG);
     }
 
@@ -429,14 +451,14 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
         std::vector<int32_t> R(h->nR), S(h->nS), rpos(n, -1), spos(n, -1);
         for (int64_t a = 0; a < h->nR; ++a) {
             if (opt.block_rows[a] < 0 || opt.block_rows[a] >= n) { fail(h, MCINV_E_ARG, "block row out of range"); return bail(MCINV_E_ARG); }
-            R[a] = (int32_t)opt.block_rows[a];
-            if (rpos[R[a]] >= 0) { fail(h, MCINV_E_ARG, "repeated block row %d", R[a]); return bail(MCINV_E_ARG); }
+            R[a] = inv.empty() ? (int32_t)opt.block_rows[a] : inv[opt.block_rows[a]];
+            if (rpos[R[a]] >= 0) { fail(h, MCINV_E_ARG, "repeated block row %lld", (long long)opt.block_rows[a]); return bail(MCINV_E_ARG); }
             rpos[R[a]] = (int32_t)a;
         }
         for (int64_t b = 0; b < h->nS; ++b) {
             if (opt.block_cols[b] < 0 || opt.block_cols[b] >= n) { fail(h, MCINV_E_ARG, "block column out of range"); return bail(MCINV_E_ARG); }
-            S[b] = (int32_t)opt.block_cols[b];
-            if (spos[S[b]] >= 0) { fail(h, MCINV_E_ARG, "repeated block column %d", S[b]); return bail(MCINV_E_ARG); }
+            S[b] = inv.empty() ? (int32_t)opt.block_cols[b] : inv[opt.block_cols[b]];
+            if (spos[S[b]] >= 0) { fail(h, MCINV_E_ARG, "repeated block column %lld", (long long)opt.block_cols[b]); return bail(MCINV_E_ARG); }
             spos[S[b]] = (int32_t)b;
         }
         const size_t elems = (size_t)h->nR * h->nS;
@@ -653,6 +675,14 @@ extern "C" mcinv_status mcinv_sync(mcinv_t h)
     return MCINV_OK;
 }
 
+// rows of C' (the colour order) back to rows of C: x[ord[k]] = x'[k], `width` values per row
+static void unpermute_rows(mcinv_ctx *h, double *x, size_t width)
+{
+    std::vector<double> t(x, x + (size_t)h->n * width);
+    for (int64_t k = 0; k < h->n; ++k)
+        for (size_t v = 0; v < width; ++v) x[(size_t)h->ord[k] * width + v] = t[(size_t)k * width + v];
+}
+
 extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double *q, double *out, double *se_out)
 {
     if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
@@ -670,9 +700,21 @@ extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double 
             count = (size_t)h->n * NV;
             CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_se, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            if (!h->ord.empty()) {
+                CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+                unpermute_rows(h, out, NV);
+                if (se_out) unpermute_rows(h, se_out, NV);
+            }
         } else {
             if (!q) return fail(h, MCINV_E_ARG, "q_diag is NULL");
+            std::vector<double> qk;
+            if (!h->ord.empty()) {
+                qk.resize((size_t)h->n);
+                for (int64_t k = 0; k < h->n; ++k) qk[k] = q[h->ord[k]];
+                q = qk.data();
+            }
             CUDA_TRY(h, cudaMemcpyAsync(h->d_q, q, (size_t)h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
             LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_trace_estimate(h->cplx, (int)h->n, h->G, h->d_counts, (double)h->samples,
                                             h->d_diag_acc, h->d_q, h->d_mean, h->stream));
             CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -701,7 +743,7 @@ extern "C" mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q)
     std::vector<float> qp((size_t)h->n);
     std::vector<int32_t> perm((size_t)h->n);
     CUDA_TRY(h, cudaMemcpy(perm.data(), h->d_perm, (size_t)h->n * 4, cudaMemcpyDeviceToHost));
-    for (int64_t p = 0; p < h->n; ++p) qp[p] = (float)q[perm[p]];
+    for (int64_t p = 0; p < h->n; ++p) qp[p] = (float)q[h->ord.empty() ? perm[p] : h->ord[perm[p]]];
     if (!h->d_tq) {
         CUDA_TRY(h, dalloc(h, &h->d_tq, (size_t)h->n));
         CUDA_TRY(h, dalloc(h, &h->d_tpart, (size_t)h->B * h->slices * h->Q * (h->threads / 32)));
@@ -810,6 +852,7 @@ extern "C" mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchai
                                       nchains * esz, h->n, cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         for (size_t k = 0; k < tmp.size(); ++k) dst[v][k] = (double)tmp[k];
+        if (!h->ord.empty()) unpermute_rows(h, dst[v], (size_t)nchains * NV);
     }
     if (cycle) *cycle = h->cycle;
     return st;
@@ -848,8 +891,14 @@ extern "C" mcinv_status mcinv_set_state(mcinv_t h, const double *z, const double
     std::vector<float> tmp(count);
     const double *srcs[2] = {z, w};
     void *dsts[2] = {h->d_z[h->cur], h->d_w[h->cur]};
+    const size_t row = (size_t)h->K * NV;
     for (int v = 0; v < 2; ++v) {
-        for (size_t k = 0; k < count; ++k) tmp[k] = (float)srcs[v][k];
+        if (h->ord.empty()) {
+            for (size_t k = 0; k < count; ++k) tmp[k] = (float)srcs[v][k];
+        } else {
+            for (int64_t r = 0; r < h->n; ++r)
+                for (size_t c = 0; c < row; ++c) tmp[(size_t)r * row + c] = (float)srcs[v][(size_t)h->ord[r] * row + c];
+        }
         CUDA_TRY(h, cudaMemcpyAsync(dsts[v], tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }

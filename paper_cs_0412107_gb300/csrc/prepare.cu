@@ -206,4 +206,106 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
     return MCINV_OK;
 }
 
+mcinv_status color_order(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
+                         std::vector<int32_t> &order, int *ncolors, std::string *err)
+{
+    const int NV = cplx ? 2 : 1;
+    if (n <= 0 || n > (1LL << 30)) return prep_fail(err, MCINV_E_ARG, "n = %lld out of range", (long long)n);
+    if (!row_ptr || !col) return prep_fail(err, MCINV_E_ARG, "NULL CSR array");
+    if (row_ptr[0] != 0) return prep_fail(err, MCINV_E_ARG, "row_ptr[0] != 0");
+    for (int64_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return prep_fail(err, MCINV_E_ARG, "row_ptr decreases at row %lld", (long long)i);
+        bool has_diag = false, zero = true;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int64_t j = col[e];
+            if (j < 0 || j >= n) return prep_fail(err, MCINV_E_ARG, "column %lld out of range in row %lld", (long long)j, (long long)i);
+            if (e > row_ptr[i] && col[e - 1] >= j) return prep_fail(err, MCINV_E_ARG, "columns not strictly increasing in row %lld", (long long)i);
+            if (j == i) {
+                has_diag = true;
+                if (val)
+                    for (int v = 0; v < NV; ++v) zero &= val[e * NV + v] == 0.0;
+                else
+                    zero = false;
+            }
+        }
+        if (!has_diag || zero)
+            return prep_fail(err, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %lld is %s", (long long)i, has_diag ? "zero" : "missing");
+    }
+    // lower neighbours of every row in C + C^T: j < i with c_ij != 0 (row i) or c_ji != 0 (column i)
+    std::vector<int64_t> tptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] > i) tptr[col[e] + 1]++;
+    for (int64_t j = 0; j < n; ++j) tptr[j + 1] += tptr[j];
+    std::vector<int32_t> trow(tptr[n]);
+    {
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (col[e] > i) trow[fill[col[e]]++] = (int32_t)i;  // row i < col[e] reads col[e]'s column
+    }
+    std::vector<int32_t> color(n, 0);
+    std::vector<int64_t> mark;  // mark[c] == i: colour c is taken by a neighbour of row i
+    int nc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        auto take = [&](int64_t j) {
+            const int c = color[j];
+            if ((size_t)c >= mark.size()) mark.resize(c + 1, -1);
+            mark[c] = i;
+        };
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1] && col[e] < i; ++e) take(col[e]);
+        for (int64_t e = tptr[i]; e < tptr[i + 1]; ++e) take(trow[e]);
+        int c = 0;
+        while ((size_t)c < mark.size() && mark[c] == i) ++c;
+        color[i] = c;
+        nc = std::max(nc, c + 1);
+    }
+    std::vector<int64_t> cptr(nc + 1, 0);
+    for (int64_t i = 0; i < n; ++i) cptr[color[i] + 1]++;
+    for (int c = 0; c < nc; ++c) cptr[c + 1] += cptr[c];
+    order.assign(n, 0);
+    for (int64_t i = 0; i < n; ++i) order[cptr[color[i]]++] = (int32_t)i;
+    if (ncolors) *ncolors = nc;
+    return MCINV_OK;
+}
+
+void permute_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
+                 const std::vector<int32_t> &order, std::vector<int64_t> &rp2, std::vector<int32_t> &col2,
+                 std::vector<double> &val2)
+{
+    const int NV = cplx ? 2 : 1;
+    std::vector<int32_t> inv(n);
+    for (int64_t k = 0; k < n; ++k) inv[order[k]] = (int32_t)k;
+    rp2.assign(n + 1, 0);
+    for (int64_t k = 0; k < n; ++k) rp2[k + 1] = rp2[k] + (row_ptr[order[k] + 1] - row_ptr[order[k]]);
+    col2.resize(rp2[n]);
+    val2.resize((size_t)rp2[n] * NV);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t i = order[k];
+        row.clear();
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) row.emplace_back(inv[col[e]], e);
+        std::sort(row.begin(), row.end());
+        int64_t o = rp2[k];
+        for (const auto &pr : row) {
+            col2[o] = pr.first;
+            for (int v = 0; v < NV; ++v) val2[(size_t)o * NV + v] = val[(size_t)pr.second * NV + v];
+            ++o;
+        }
+    }
+}
+
 }  // namespace mcinv
+
+extern "C" mcinv_status mcinv_color_order(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t *order,
+                                          int32_t *ncolors)
+{
+    if (!order) return MCINV_E_ARG;
+    std::vector<int32_t> ord;
+    int nc = 0;
+    const mcinv_status st = mcinv::color_order(n, row_ptr, col, nullptr, 0, ord, &nc, nullptr);
+    if (st != MCINV_OK) return st;
+    std::copy(ord.begin(), ord.end(), order);
+    if (ncolors) *ncolors = nc;
+    return MCINV_OK;
+}

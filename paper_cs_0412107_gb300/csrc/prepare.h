@@ -27,4 +27,20 @@ struct Prepared {
 mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
                             int min_blob, Prepared &P, std::string *err);
 
+// The colour sweep order (Sec. 4: reordering the rows and columns of C):
+// rows in ascending index order each take the smallest colour not used by an
+// already-coloured neighbour in the graph of C + C^T (off-diagonal entries);
+// order[k] lists colour 0's rows ascending, then colour 1's, ...  No two rows
+// of one colour read each other, so the Gauss-Seidel sweep of P C P^T has one
+// dependency level per colour.  Checks the CSR structure and the diagonal
+// (errors name rows of C as given).
+mcinv_status color_order(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
+                         std::vector<int32_t> &order, int *ncolors, std::string *err);
+
+// C' = P C P^T: row k of C' is row order[k] of C, columns renumbered by the
+// inverse order and sorted ascending.
+void permute_csr(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int cplx,
+                 const std::vector<int32_t> &order, std::vector<int64_t> &rp2, std::vector<int32_t> &col2,
+                 std::vector<double> &val2);
+
 }  // namespace mcinv

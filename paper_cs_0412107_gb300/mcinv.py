@@ -21,11 +21,13 @@ MCINV_OK = 0
 STATUS_NAMES = {0: "MCINV_OK", 1: "MCINV_E_ARG", 2: "MCINV_E_SINGULAR_DIAG", 3: "MCINV_E_DIVERGED",
                 4: "MCINV_E_NOMEM", 5: "MCINV_E_CUDA", 6: "MCINV_E_TIMEOUT", 7: "MCINV_E_STATE",
                 8: "MCINV_E_UNSUPPORTED"}
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 MCINV_REAL64, MCINV_COMPLEX128 = 0, 1
 MCINV_ACC_FP32_SIMT, MCINV_ACC_BF16_TC = 0, 1
 MCINV_EST_BLOCK, MCINV_EST_DIAG, MCINV_EST_TRACE = 0, 1, 2
 MCINV_F_NO_DIAG = 1
 MCINV_F_AUTOTUNE = 2
+MCINV_F_COLOR_ORDER = 4
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
@@ -33,7 +35,7 @@ EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_burni
            "mcinv_sample_until", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
            "mcinv_selftest_tc_gemm", "mcinv_block_accumulate_noalloc", "mcinv_destroy",
-           "mcinv_last_error",
+           "mcinv_last_error", "mcinv_color_order",
            "mcinv_pool_default_options", "mcinv_pool_create", "mcinv_pool_footprint", "mcinv_pool_submit",
            "mcinv_pool_step", "mcinv_pool_poll", "mcinv_pool_estimate", "mcinv_pool_get_state",
            "mcinv_pool_release", "mcinv_pool_info", "mcinv_pool_sync", "mcinv_pool_destroy",
@@ -124,6 +126,8 @@ def lib():
             getattr(L, name).argtypes = [vp, i64]
         L.mcinv_burnin_coupled.argtypes = [vp, ctypes.c_double, i64, ctypes.POINTER(i64)]
         L.mcinv_burnin_coupled.restype = ctypes.c_int
+        L.mcinv_color_order.argtypes = [i64, vp, vp, vp, ctypes.POINTER(i32)]
+        L.mcinv_color_order.restype = ctypes.c_int
         dp = ctypes.POINTER(ctypes.c_double)
         L.mcinv_set_trace_weights.argtypes = [vp, vp]
         L.mcinv_trace_mc_error.argtypes = [vp, dp, dp, dp, dp]
@@ -409,6 +413,19 @@ def mcinv_destroy(h: Handle):
 
 def mcinv_last_error(h: Handle | None = None) -> str:
     return lib().mcinv_last_error(None if h is None else h.ptr).decode(errors="replace")
+
+
+def mcinv_color_order(n: int, row_ptr, col):
+    """The colour sweep order of C (host only): returns (order int32[n], ncolors)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    order = np.empty(int(n), dtype=np.int32)
+    nc = ctypes.c_int32()
+    st = lib().mcinv_color_order(int(n), rp.ctypes.data_as(ctypes.c_void_p), cl.ctypes.data_as(ctypes.c_void_p),
+                                 order.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nc))
+    if st != MCINV_OK:
+        raise McinvError(st, "mcinv_color_order failed")
+    return order, int(nc.value)
 
 
 def create_from_csr(csr, **kw) -> Handle:
