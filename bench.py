@@ -148,6 +148,13 @@ def traffic_from_profiles(kernel_file, units_per_launch):
     return None
 
 
+def order_flag(args):
+    """The sweep order: the rows as given (Eqs. 4/5 for i = 1..n), or the colour order
+    (Sec. 4 reordering: the sampler of P C P^T, one dependency level per colour)."""
+    from paper_cs_0412107_gb300 import mcinv
+    return mcinv.MCINV_F_COLOR_ORDER if args.order == "colour" else 0
+
+
 def run_mine(args, world, rank, local):
     import torch
 
@@ -165,7 +172,7 @@ def run_mine(args, world, rank, local):
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=acc,
                               batch_cycles=args.batch, block_rows=R, block_cols=S,
                               chains_per_cta=args.W, threads_per_cta=args.threads,
-                              flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+                              flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
     info0 = mcinv.mcinv_info(h)
     B = info0["batch_cycles"]
     mcinv.mcinv_burnin(h, args.burnin)
@@ -217,7 +224,7 @@ def run_mine(args, world, rank, local):
                    "cycles_per_step": B, "estimates": "diagonal + C^-1[:, 0:512]",
                    "block_accumulation": "bf16 tensor cores" if acc else "fp32 simt",
                    "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"], "ctas_per_slice": info0["ctas_per_slice"],
-                   "levels": info0["levels"],
+                   "levels": info0["levels"], "sweep_order": args.order,
                    "l2": "inputs larger than L2 (z, w double-buffered: %.0f MB)" % (4 * 4 * csr.n * K / 1e6),
                    "parallelism": f"replicas x{world} (disjoint chains)"},
         "roofline": {"kernel": "cc_sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
@@ -267,7 +274,7 @@ def run_e2e(args, csr, K, acc, rank):
     def job():
         opt = mcinv.mcinv_default_options(K=K, seed=args.seed + 1, chain_base=rank * K, acc=acc,
                                           batch_cycles=args.batch,
-                                          flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+                                          flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
         opt.stream = mcinv.current_stream()
         Ra = np.ascontiguousarray(R, dtype=np.int64)
         Sa = np.ascontiguousarray(S, dtype=np.int64)
@@ -474,7 +481,7 @@ def run_dirac(args, world, rank, local):
     stream = torch.cuda.current_stream()
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
                               batch_cycles=10, chains_per_cta=args.W, threads_per_cta=args.threads,
-                              flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+                              flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
     info0 = mcinv.mcinv_info(h)
     mcinv.mcinv_set_trace_weights(h, np.ones(csr.n))
     mcinv.mcinv_sync(h)
@@ -515,7 +522,7 @@ def run_dirac(args, world, rank, local):
         "config": {"workload": "dirac18", "n": csr.n, "nnz": csr.nnz, "K": K, "step": "one Algorithm 1 run",
                    "burnin": "coupled, tol 1e-5", "stop": "MC error < 1e-5 of tr, checked every 100 cycles",
                    "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"],
-                   "ctas_per_slice": info0["ctas_per_slice"], "levels": info0["levels"],
+                   "ctas_per_slice": info0["ctas_per_slice"], "levels": info0["levels"], "sweep_order": args.order,
                    "l2": "inputs larger than L2 (z, w double-buffered: %.1f GB)" % (4 * 8 * csr.n * K / 1e9)},
         "result": {"burnin_cycles": p, "sampling_cycles": used, "trace": g["mean"], "mc_error": g["se"],
                    "effective_length": g["ess"], "exact": exact, "z": (g["mean"] - exact) / g["se"],
@@ -591,6 +598,7 @@ def main():
     ap.add_argument("--batch-mem-gb", type=float, default=64.0)
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
+    ap.add_argument("--order", default="natural", choices=["natural", "colour"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"
