@@ -71,6 +71,9 @@ def lib():
                                               ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                               ctypes.c_double, ctypes.c_int64, vp, vp]
             L.orc_coupling_burnin.restype = ctypes.c_int64
+            L.orc_noise_plane.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.c_uint32, ctypes.c_uint32, vp]
+            L.orc_noise_plane.restype = None
             _lib = L
     return _lib
 
@@ -100,6 +103,14 @@ def philox4x32_10(ctr, key):
 
 def phi(seed, matrix, chain, cycle, row) -> int:
     return int(lib().orc_phi(seed, matrix, chain, cycle, row))
+
+
+def noise_plane(n, K, seed, matrix, chain0, cycle) -> np.ndarray:
+    """phi^(cycle) of every row and of chains chain0 .. chain0+K-1: float64 [n][K]."""
+    out = np.empty((n, K), dtype=np.int8)
+    lib().orc_noise_plane(ctypes.c_int64(n), ctypes.c_int64(K), ctypes.c_uint64(seed), ctypes.c_uint32(matrix),
+                          ctypes.c_uint32(chain0), ctypes.c_uint32(cycle), _ptr(out))
+    return out.astype(np.float64)
 
 
 def noise_matrix(n, seed, matrix, chain, cycle) -> np.ndarray:
@@ -276,3 +287,88 @@ def expected_covariance(a, k):
     for _ in range(k):
         X = Gm + T @ X @ S
     return X
+
+
+# -- the block partition of Sec. 4 ---------------------------------------------------
+#
+# C is cut into contiguous diagonal blocks D_b (block_ptr[b] .. block_ptr[b+1]-1); the
+# sweep visits the blocks in ascending order and updates each block as a whole:
+#   z_b <- A_b phi_b - D_b^-1 sum_{c != b} C_bc z_c       (new z_c for c < b, old for c > b)
+#   w_b <- B_b phi_b - D_b^-H sum_{c != b} (C^H)_bc w_c
+# with A_b B_b^H = D_b^-1, the condition that makes E[z w^H] converge to C^-1 (the block
+# form of the demonstration of Sec. 2.2).  The factors are read from the scalar case
+# (alpha = 1/sqrt(c_ii), beta = 1/conj(sqrt(c_ii))): A_b = S_b^-1 and B_b = (S_b^-1)^H with
+# S_b the principal square root of D_b.  Blocks of one row keep the scalar constants.
+
+def block_factors(csr, block_ptr):
+    """Per block: (rows, D_b^-1, A_b, B_b).  One-row blocks take the scalar constants
+    (row_constants: alpha, beta, 1/c_ii, including the real reading for c_ii < 0)."""
+    import scipy.linalg as sl
+    a = csr.to_dense().astype(np.complex128)
+    out = []
+    for b in range(len(block_ptr) - 1):
+        r = np.arange(block_ptr[b], block_ptr[b + 1])
+        if len(r) == 1:
+            c = a[r[0], r[0]]
+            if c == 0:
+                raise ValueError(f"one-row block {b} has a zero diagonal")
+            if not csr.is_complex and c.real < 0:  # the real reading: alpha = 1/sqrt|c|, beta = -alpha
+                al = 1.0 / np.sqrt(-c.real); be = -al
+            else:
+                sq = np.sqrt(c)
+                al = 1.0 / sq; be = 1.0 / np.conj(sq)
+            out.append((r, np.array([[1.0 / c]]), np.array([[al]]), np.array([[be]])))
+        else:
+            D = a[np.ix_(r, r)]
+            A = np.linalg.inv(sl.sqrtm(D))
+            out.append((r, np.linalg.inv(D), A, A.conj().T))
+    return out
+
+
+def block_cycle(a, fac, st, ph):
+    """One cycle of the block sweep on the dense matrix a with noise ph [n][K], in place."""
+    ah = a.conj().T
+    for r, Dinv, A, B in fac:
+        sz = a[r, :] @ st.z - a[np.ix_(r, r)] @ st.z[r, :]  # sum over the other blocks
+        st.z[r, :] = A @ ph[r, :] - Dinv @ sz
+    for r, Dinv, A, B in fac:
+        sw = ah[r, :] @ st.w - ah[np.ix_(r, r)] @ st.w[r, :]
+        st.w[r, :] = B @ ph[r, :] - Dinv.conj().T @ sw
+    return st
+
+
+def run_block(csr, block_ptr, K, seed=0, matrix=0, chain0=0, cycle0=0, ncycles=1, state=None):
+    """The block-partition sweep above, FP64 complex, dense (small n); returns the state."""
+    a = csr.to_dense().astype(np.complex128)
+    st = state if state is not None else State(csr.n, K)
+    fac = block_factors(csr, block_ptr)
+    for cyc in range(cycle0, cycle0 + ncycles):
+        block_cycle(a, fac, st, noise_plane(csr.n, K, seed, matrix, chain0, cyc))
+    return st
+
+
+def block_expected_covariance(a, block_ptr, k):
+    """E[z^(k) w^(k)H] of the block sweep from zero: the recursion of expected_covariance
+    with D block-diagonal and L, U the blocks below and above it (A_b B_b^H = D_b^-1)."""
+    a = np.asarray(a, dtype=np.complex128)
+    n = a.shape[0]
+    D = np.zeros_like(a)
+    for b in range(len(block_ptr) - 1):
+        r = np.arange(block_ptr[b], block_ptr[b + 1])
+        D[np.ix_(r, r)] = a[np.ix_(r, r)]
+    blk = np.zeros(n, dtype=np.int64)
+    for b in range(len(block_ptr) - 1):
+        blk[block_ptr[b]:block_ptr[b + 1]] = b
+    lower = blk[:, None] > blk[None, :]
+    L = np.where(lower, a, 0)
+    U = np.where(blk[:, None] < blk[None, :], a, 0)
+    DL = np.linalg.inv(D + L)
+    DU = np.linalg.inv(D + U)
+    T = DL @ U
+    S = L @ DU
+    Gm = DL @ D @ DU
+    X = np.zeros_like(a)
+    for _ in range(k):
+        X = Gm + T @ X @ S
+    return X
+

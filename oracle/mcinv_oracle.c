@@ -83,6 +83,16 @@ int orc_phi(uint64_t seed, uint32_t matrix, uint32_t chain, uint32_t cycle, uint
     return bit ? -1 : 1;
 }
 
+/* The noise of every row and of chains chain0 .. chain0+K-1 in one cycle:
+ * out[i*K + c] = phi(seed, matrix, chain0 + c, cycle, i). */
+void orc_noise_plane(int64_t n, int64_t K, uint64_t seed, uint32_t matrix, uint32_t chain0, uint32_t cycle,
+                     int8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t c = 0; c < K; ++c)
+            out[i * K + c] = (int8_t)orc_phi(seed, matrix, chain0 + (uint32_t)c, cycle, (uint32_t)i);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Problem: a CSR matrix C with its diagonal present.                          */
 /* ------------------------------------------------------------------------- */
