@@ -101,7 +101,8 @@ typedef struct {
                               E[z w^dagger] is then P C^-1 P^T; every row-indexed argument and
                               result (block rows and columns, q, the diagonal, the chain state)
                               stays in the rows of C as given.  The noise of C' row k is drawn
-                              for row k, so the draws differ from the given order's. */
+                              for row k, so the draws differ from the given order's.  Also a
+                              pool flag (mcinv_pool_options.flags): every matrix of the pool. */
 
 /*
  * The colour sweep order (Sec. 4: the paper's suggestion to reorder the rows and
@@ -132,6 +133,38 @@ void mcinv_default_options(mcinv_options *opt);
  */
 mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
                           const double *val, mcinv_dtype dt, const mcinv_options *opt);
+
+/* Largest diagonal block of a partition (rows). */
+#define MCINV_MAX_PARTITION_BLOCK 8
+
+/*
+ * Create a sampler that sweeps C block by block (Sec. 4: a partition of C into
+ * small non-singular diagonal blocks, for matrices whose diagonal has zeros or
+ * small entries).  block_ptr[0..nblocks] cuts the rows into contiguous blocks:
+ * block b holds rows block_ptr[b] .. block_ptr[b+1]-1 (1 to
+ * MCINV_MAX_PARTITION_BLOCK rows), block_ptr[0] = 0, block_ptr[nblocks] = n.
+ * A block b of two or more rows is updated as a whole,
+ *   z_b <- S_b^-1 phi_b - D_b^-1 sum_{c != b} C_bc z_c,
+ *   w_b <- S_b^-H phi_b - D_b^-H sum_{c != b} (C^H)_bc w_c,
+ * with S_b the principal square root of its diagonal block D_b, so that
+ * S_b^-1 (S_b^-H)^H = D_b^-1, the block form of alpha_i conj(beta_i) = 1/c_ii in
+ * Eqs. 4/5; a one-row block is a row of Eqs. 4/5.  Rows inside blocks of two or
+ * more rows may lack a diagonal entry.  The block sweep is the row sweep of
+ * C~ = S^-1 C S^-1 (S = blockdiag(S_b), 1 for one-row blocks) with z = S^-1 z~,
+ * w = S^-H w~, which is how it runs on the GPU.  Options, estimates and the chain
+ * state (mcinv_get_state returns the block sweep's z and w) are as for
+ * mcinv_create, except that block_rows and block_cols may only name rows of
+ * one-row blocks, the per-cycle trace series (mcinv_set_trace_weights,
+ * mcinv_trace_series, mcinv_trace_mc_error, mcinv_sample_until) is
+ * MCINV_E_UNSUPPORTED when a block has two or more rows, and
+ * mcinv_burnin_coupled couples the paths of C~.  The arrays are the caller's.
+ * Returns MCINV_E_ARG for a malformed partition and MCINV_E_SINGULAR_DIAG for a
+ * block without a principal square root (singular, or an eigenvalue on the
+ * closed negative real axis).
+ */
+mcinv_status mcinv_create_partitioned(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                      const double *val, mcinv_dtype dt, const mcinv_options *opt,
+                                      int64_t nblocks, const int64_t *block_ptr);
 
 /* Advance every chain `cycles` CC cycles (Eqs. 4, 5) without accumulating
  * (burn-in, Algorithm 1 steps 1-5 with a fixed count).  cycles >= 0. */

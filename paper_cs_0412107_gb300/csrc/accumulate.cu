@@ -331,4 +331,59 @@ cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Block partition (Sec. 4): the products z_r conj(w_s) of the rows of one
+// diagonal block, per chain group, summed in FP64 in chain order (one thread
+// per (entry, group)); the estimate maps them through S_b^-1 on both sides.
+template <int NV>
+__global__ void pblock_acc_kernel(int nent, const int *__restrict__ ent_r, const int *__restrict__ ent_s, int K,
+                                  int G, const int *__restrict__ gch, const float *__restrict__ z,
+                                  const float *__restrict__ w, double *__restrict__ acc)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)nent * G) return;
+    const int e = (int)(t % nent), g = (int)(t / nent);
+    const size_t r = (size_t)ent_r[e], s = (size_t)ent_s[e];
+    double re = 0.0, im = 0.0;
+    for (int c = gch[g]; c < gch[g + 1]; ++c) {
+        if (NV == 1) {
+            re += (double)z[r * K + c] * (double)w[s * K + c];
+        } else {
+            const double zr = z[(r * K + c) * 2], zi = z[(r * K + c) * 2 + 1];
+            const double wr = w[(s * K + c) * 2], wi = w[(s * K + c) * 2 + 1];
+            re += zr * wr + zi * wi;  // z conj(w)
+            im += zi * wr - zr * wi;
+        }
+    }
+    acc[((size_t)g * nent + e) * NV] += re;
+    if (NV == 2) acc[((size_t)g * nent + e) * NV + 1] += im;
+}
+
+cudaError_t launch_pblock_acc(int cplx, int nent, const int *ent_r, const int *ent_s, int K, int G, const int *gch,
+                              const void *z, const void *w, double *acc, cudaStream_t s)
+{
+    const long long threads = (long long)nent * G;
+    if (threads == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (cplx)
+        pblock_acc_kernel<2><<<blocks, 256, 0, s>>>(nent, ent_r, ent_s, K, G, gch, (const float *)z, (const float *)w, acc);
+    else
+        pblock_acc_kernel<1><<<blocks, 256, 0, s>>>(nent, ent_r, ent_s, K, G, gch, (const float *)z, (const float *)w, acc);
+    return cudaGetLastError();
+}
+
+__global__ void scatter_kernel(int count, const long long *__restrict__ idx, const double *__restrict__ val,
+                               double *__restrict__ dst)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) dst[idx[k]] = val[k];
+}
+
+cudaError_t launch_scatter(int count, const long long *idx, const double *val, double *dst, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    scatter_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, idx, val, dst);
+    return cudaGetLastError();
+}
+
 }  // namespace mcinv

@@ -3,6 +3,7 @@
 // the orchestration of the sweep / accumulation / estimate kernels.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 
 #include "../../include/mcinv.h"
 #include "internal.h"
+#include "partition.h"
 #include "prepare.h"
 #include "tc_gemm.h"
 
@@ -58,7 +60,15 @@ struct mcinv_ctx {
     int *d_status = nullptr;
     // MCINV_F_COLOR_ORDER: the handle samples C' = P C P^T; ord[k] is the row of C
     // that is row k of C' (empty: the rows of C in their given order)
-    std::vector<int32_t> ord;
+    std::vector<int32_t> ord, inv;
+    // mcinv_create_partitioned with blocks of two or more rows: the handle samples
+    // C~ = S^-1 C S^-1; per such block the products z~_r conj(w~_s) of its rows are
+    // summed per chain group (entries pent_off[m] .. of block pblk[m], row-major)
+    Partition part;
+    std::vector<int64_t> pblk, pent_off;
+    int nent = 0;
+    int *d_pent_r = nullptr, *d_pent_s = nullptr, *d_gch = nullptr;
+    double *d_pacc = nullptr, *d_acc_est = nullptr;
     // counters
     int64_t cycle = 0, samples = 0, block_batches = 0, block_cycles = 0, launches = 0;
     int64_t bytes = 0;
@@ -266,9 +276,38 @@ static mcinv_status autotune(mcinv_ctx *h)
     return MCINV_OK;
 }
 
+static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                const double *val, mcinv_dtype dt, const mcinv_options *opt_in, const Partition *part);
+
 extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row_ptr,
                                      const int32_t *col, const double *val, mcinv_dtype dt,
                                      const mcinv_options *opt_in)
+{
+    return create_impl(out, n, row_ptr, col, val, dt, opt_in, nullptr);
+}
+
+extern "C" mcinv_status mcinv_create_partitioned(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                                 const double *val, mcinv_dtype dt, const mcinv_options *opt,
+                                                 int64_t nblocks, const int64_t *block_ptr)
+{
+    if (!out) return fail(nullptr, MCINV_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || n > (1LL << 30)) return fail(nullptr, MCINV_E_ARG, "n = %lld out of range", (long long)n);
+    if (dt != MCINV_REAL64 && dt != MCINV_COMPLEX128) return fail(nullptr, MCINV_E_ARG, "bad dtype");
+    // the block sweep of C is the row sweep of C~ = S^-1 C S^-1 (Sec. 4 partition)
+    Partition part;
+    std::vector<int64_t> rp2;
+    std::vector<int32_t> col2;
+    std::vector<double> val2;
+    std::string why;
+    const mcinv_status st = partition_transform(n, row_ptr, col, val, dt == MCINV_COMPLEX128, nblocks, block_ptr, rp2,
+                                                col2, val2, part, &why);
+    if (st != MCINV_OK) return fail(nullptr, st, "%s", why.c_str());
+    return create_impl(out, n, rp2.data(), col2.data(), val2.data(), dt, opt, &part);
+}
+
+static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                                const double *val, mcinv_dtype dt, const mcinv_options *opt_in, const Partition *part)
 {
     if (!out) return fail(nullptr, MCINV_E_ARG, "out is NULL");
     *out = nullptr;
@@ -317,6 +356,7 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     h->stream = (cudaStream_t)opt.stream;
     h->flags = opt.flags;
     h->ord = std::move(ord);
+    h->inv = inv;
     h->acc = opt.acc;
     h->B = opt.batch_cycles > 0 ? opt.batch_cycles : 8;
     int default_threads = 256;
@@ -447,6 +487,23 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     // ---- block estimate
     if (opt.n_block_rows > 0 && opt.n_block_cols > 0) {
         if (!opt.block_rows || !opt.block_cols) { fail(h, MCINV_E_ARG, "block index arrays are NULL"); return bail(MCINV_E_ARG); }
+        if (part && part->multi > 0) {
+            // rows of a block of two or more rows would need S^-1 on both sides of C~^-1
+            std::vector<char> multi(n, 0);
+            for (size_t b = 0; b + 1 < part->block_ptr.size(); ++b)
+                if (part->block_ptr[b + 1] - part->block_ptr[b] > 1)
+                    for (int64_t i = part->block_ptr[b]; i < part->block_ptr[b + 1]; ++i) multi[i] = 1;
+            for (int64_t a = 0; a < opt.n_block_rows; ++a)
+                if (opt.block_rows[a] >= 0 && opt.block_rows[a] < n && multi[opt.block_rows[a]]) {
+                    fail(h, MCINV_E_UNSUPPORTED, "block row %lld lies in a partition block of two or more rows", (long long)opt.block_rows[a]);
+                    return bail(MCINV_E_UNSUPPORTED);
+                }
+            for (int64_t b = 0; b < opt.n_block_cols; ++b)
+                if (opt.block_cols[b] >= 0 && opt.block_cols[b] < n && multi[opt.block_cols[b]]) {
+                    fail(h, MCINV_E_UNSUPPORTED, "block column %lld lies in a partition block of two or more rows", (long long)opt.block_cols[b]);
+                    return bail(MCINV_E_UNSUPPORTED);
+                }
+        }
         h->nR = opt.n_block_rows; h->nS = opt.n_block_cols;
         std::vector<int32_t> R(h->nR), S(h->nS), rpos(n, -1), spos(n, -1);
         for (int64_t a = 0; a < h->nR; ++a) {
@@ -497,6 +554,34 @@ extern "C" mcinv_status mcinv_create(mcinv_t *out, int64_t n, const int64_t *row
     }
     SETUP(dalloc(h, &h->d_mean, est_elems * NV));
     SETUP(dalloc(h, &h->d_se, est_elems * NV));
+
+    // ---- block partition: the row pairs of every block of two or more rows (rows of
+    //      the sampled matrix), the chain range of each SE group, the FP64 sums
+    if (part && part->multi > 0) {
+        h->part = *part;
+        std::vector<int32_t> er, es;
+        for (int64_t b = 0; b + 1 < (int64_t)part->block_ptr.size(); ++b) {
+            const int64_t b0 = part->block_ptr[b], sz = part->block_ptr[b + 1] - b0;
+            if (sz < 2) continue;
+            h->pblk.push_back(b);
+            h->pent_off.push_back((int64_t)er.size());
+            for (int64_t r = 0; r < sz; ++r)
+                for (int64_t c = 0; c < sz; ++c) {
+                    er.push_back(inv.empty() ? (int32_t)(b0 + r) : inv[b0 + r]);
+                    es.push_back(inv.empty() ? (int32_t)(b0 + c) : inv[b0 + c]);
+                }
+        }
+        h->nent = (int)er.size();
+        std::vector<int32_t> gch(h->G + 1);
+        const int64_t u = (int64_t)h->seg * h->V, upg = h->units / h->G;
+        for (int g = 0; g <= h->G; ++g) gch[g] = (int32_t)std::min<int64_t>(opt.K, (int64_t)g * upg * u);
+        SETUP(upload(h, &h->d_pent_r, er));
+        SETUP(upload(h, &h->d_pent_s, es));
+        SETUP(upload(h, &h->d_gch, gch));
+        SETUP(dalloc(h, &h->d_pacc, (size_t)h->G * h->nent * NV));
+        SETUP(cudaMemsetAsync(h->d_pacc, 0, (size_t)h->G * h->nent * NV * sizeof(double), h->stream));
+        if (h->d_diag_acc) SETUP(dalloc(h, &h->d_acc_est, (size_t)h->G * n * NV));
+    }
     SETUP(cudaStreamSynchronize(h->stream));
     *out = h;
     return MCINV_OK;
@@ -553,17 +638,28 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
         const int b = (int)std::min<int64_t>(h->B, cycles);
         LAUNCH_K(h, MCINV_KERNEL_NOISE, launch_noise(h->seed, h->matrix_id, (uint64_t)h->chain_base, (int)h->K, (int)h->n,
                                (uint32_t)h->cycle, b, h->d_pos, h->d_noise, h->stream));
-        if (block && h->acc == MCINV_ACC_FP32_SIMT) {
+        const bool simt_block = block && h->acc == MCINV_ACC_FP32_SIMT;
+        const bool pblock = accumulate && h->nent > 0;
+        if (simt_block || pblock) {
+            // one cycle per launch: the state of every cycle is read before the next overwrites it
             for (int k = 0; k < b; ++k) {
-                SweepArgs a = sweep_args(h, 1, k, true, 0);
+                SweepArgs a = sweep_args(h, 1, k, accumulate, k);
                 LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
-                if (h->d_tq) {
+                if (accumulate && h->d_tq) {
                     mcinv_status st = series_append(h, 1);
                     if (st != MCINV_OK) return st;
                 }
                 h->cur ^= 1;
-                LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
-                                            (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
+                if (simt_block)
+                    LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
+                                                (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
+                if (pblock)
+                    LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_pblock_acc(h->cplx, h->nent, h->d_pent_r, h->d_pent_s, (int)h->K, h->G,
+                                                h->d_gch, h->d_z[h->cur], h->d_w[h->cur], h->d_pacc, h->stream));
+            }
+            if (block && !simt_block) {
+                const long long inner = (long long)b * h->kp;
+                LAUNCH_K(h, MCINV_KERNEL_BLOCK, tc_gemm_run(h->gemm, inner, h->d_status, h->stream));
             }
         } else {
             SweepArgs a = sweep_args(h, b, 0, accumulate, 0);
@@ -675,6 +771,96 @@ extern "C" mcinv_status mcinv_sync(mcinv_t h)
     return MCINV_OK;
 }
 
+// The diagonal accumulators with the rows of partition blocks of two or more rows
+// replaced, group by group, by the diagonal of S_b^-1 M_g S_b^-1 (M_g the group's sums
+// of z~_r conj(w~_s) over the block's rows): linear in the sums, so the group means
+// and SE of the estimate kernels stay exact.  Returns the buffer to estimate from.
+static const double *partition_acc(mcinv_ctx *h, mcinv_status *st)
+{
+    *st = MCINV_OK;
+    if (h->nent == 0) return h->d_diag_acc;
+    const int NV = h->cplx ? 2 : 1;
+    const size_t n = (size_t)h->n, G = (size_t)h->G;
+    std::vector<double> pacc(G * h->nent * NV);
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && *st == MCINV_OK) *st = fail(h, MCINV_E_CUDA, "partition estimate: %s", cudaGetErrorString(e));
+    };
+    chk(cudaMemcpyAsync(h->d_acc_est, h->d_diag_acc, G * n * NV * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    chk(cudaMemcpyAsync(pacc.data(), h->d_pacc, pacc.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    chk(cudaStreamSynchronize(h->stream));
+    if (*st != MCINV_OK) return nullptr;
+    std::vector<long long> idx;
+    std::vector<double> vals;
+    using cd = std::complex<double>;
+    for (size_t m = 0; m < h->pblk.size(); ++m) {
+        const int64_t b = h->pblk[m], b0 = h->part.block_ptr[b], sz = h->part.block_ptr[b + 1] - b0;
+        const cd *Z = h->part.sinv.data() + h->part.sinv_off[b];
+        for (size_t g = 0; g < G; ++g) {
+            const double *M = pacc.data() + (g * h->nent + h->pent_off[m]) * NV;
+            for (int64_t i = 0; i < sz; ++i) {
+                cd x = 0.0;  // (Z M Z)_ii
+                for (int64_t r = 0; r < sz; ++r)
+                    for (int64_t c = 0; c < sz; ++c) {
+                        const cd mrc = NV == 2 ? cd(M[(r * sz + c) * 2], M[(r * sz + c) * 2 + 1]) : cd(M[r * sz + c], 0.0);
+                        x += Z[i * sz + r] * mrc * Z[c * sz + i];
+                    }
+                const int64_t row = h->inv.empty() ? b0 + i : h->inv[b0 + i];
+                idx.push_back((long long)((g * n + (size_t)row) * NV));
+                vals.push_back(x.real());
+                if (NV == 2) {
+                    idx.push_back((long long)((g * n + (size_t)row) * NV + 1));
+                    vals.push_back(x.imag());
+                }
+            }
+        }
+    }
+    long long *d_idx = nullptr;
+    double *d_vals = nullptr;
+    chk(cudaMallocAsync((void **)&d_idx, idx.size() * sizeof(long long), h->stream));
+    chk(cudaMallocAsync((void **)&d_vals, vals.size() * sizeof(double), h->stream));
+    if (*st == MCINV_OK) {
+        chk(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+        chk(cudaMemcpyAsync(d_vals, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        chk(launch_scatter((int)idx.size(), d_idx, d_vals, h->d_acc_est, h->stream));
+        h->launches++;
+    }
+    if (d_idx) chk(cudaFreeAsync(d_idx, h->stream));
+    if (d_vals) chk(cudaFreeAsync(d_vals, h->stream));
+    chk(cudaStreamSynchronize(h->stream));
+    return *st == MCINV_OK ? h->d_acc_est : nullptr;
+}
+
+// Chain state of the sampled matrix C~ to that of the block sweep of C and back:
+// z = S^-1 z~, w = S^-H w~ (to_c), or z~ = S z, w~ = S^H w; x is [n][width] with rows
+// of C, complex values interleaved when the handle is complex.
+static void partition_state(mcinv_ctx *h, double *x, size_t width, bool is_w, bool to_c)
+{
+    using cd = std::complex<double>;
+    const int NV = h->cplx ? 2 : 1;
+    const size_t nc = width / NV;  // chains
+    for (size_t m = 0; m < h->pblk.size(); ++m) {
+        const int64_t b = h->pblk[m], b0 = h->part.block_ptr[b], sz = h->part.block_ptr[b + 1] - b0;
+        const cd *F = (to_c ? h->part.sinv.data() : h->part.s.data()) + h->part.sinv_off[b];
+        std::vector<cd> v(sz), y(sz);
+        for (size_t c = 0; c < nc; ++c) {
+            for (int64_t r = 0; r < sz; ++r) {
+                const double *p = x + (size_t)(b0 + r) * width + c * NV;
+                v[r] = NV == 2 ? cd(p[0], p[1]) : cd(p[0], 0.0);
+            }
+            for (int64_t r = 0; r < sz; ++r) {
+                cd acc = 0.0;
+                for (int64_t k = 0; k < sz; ++k) acc += (is_w ? std::conj(F[k * sz + r]) : F[r * sz + k]) * v[k];
+                y[r] = acc;
+            }
+            for (int64_t r = 0; r < sz; ++r) {
+                double *p = x + (size_t)(b0 + r) * width + c * NV;
+                p[0] = y[r].real();
+                if (NV == 2) p[1] = y[r].imag();
+            }
+        }
+    }
+}
+
 // rows of C' (the colour order) back to rows of C: x[ord[k]] = x'[k], `width` values per row
 static void unpermute_rows(mcinv_ctx *h, double *x, size_t width)
 {
@@ -694,9 +880,12 @@ extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double 
     if (kind == MCINV_EST_DIAG || kind == MCINV_EST_TRACE) {
         if (!h->d_diag_acc) return fail(h, MCINV_E_STATE, "diagonal accumulation was disabled");
         if (h->samples == 0) return fail(h, MCINV_E_STATE, "no cycles sampled yet");
+        mcinv_status pst;
+        const double *acc_in = partition_acc(h, &pst);
+        if (!acc_in) return pst;
         if (kind == MCINV_EST_DIAG) {
             LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_diag_estimate(h->cplx, (int)h->n, h->G, h->d_counts, (double)h->samples,
-                                           h->d_diag_acc, h->d_mean, h->d_se, h->stream));
+                                           acc_in, h->d_mean, h->d_se, h->stream));
             count = (size_t)h->n * NV;
             CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_se, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -716,7 +905,7 @@ extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double 
             CUDA_TRY(h, cudaMemcpyAsync(h->d_q, q, (size_t)h->n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
             CUDA_TRY(h, cudaStreamSynchronize(h->stream));
             LAUNCH_K(h, MCINV_KERNEL_ESTIMATE, launch_trace_estimate(h->cplx, (int)h->n, h->G, h->d_counts, (double)h->samples,
-                                            h->d_diag_acc, h->d_q, h->d_mean, h->stream));
+                                            acc_in, h->d_q, h->d_mean, h->stream));
             CUDA_TRY(h, cudaMemcpyAsync(out, h->d_mean, NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             if (se_out) CUDA_TRY(h, cudaMemcpyAsync(se_out, h->d_mean + NV, NV * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         }
@@ -739,6 +928,7 @@ extern "C" mcinv_status mcinv_estimate(mcinv_t h, mcinv_kind kind, const double 
 extern "C" mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q)
 {
     if (!h || !q) return fail(h, MCINV_E_ARG, "NULL argument");
+    if (h->nent) return fail(h, MCINV_E_UNSUPPORTED, "the trace series is not available with partition blocks of two or more rows");
     if (h->samples > 0) return fail(h, MCINV_E_STATE, "trace weights must be set before sampling");
     std::vector<float> qp((size_t)h->n);
     std::vector<int32_t> perm((size_t)h->n);
@@ -789,6 +979,7 @@ static void geyer(const std::vector<double> &x, double *mean, double *var, doubl
 extern "C" mcinv_status mcinv_trace_mc_error(mcinv_t h, double *mean, double *var, double *ess, double *se)
 {
     if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (h->nent) return fail(h, MCINV_E_UNSUPPORTED, "the trace series is not available with partition blocks of two or more rows");
     if (!h->d_tq) return fail(h, MCINV_E_STATE, "no trace weights were set (mcinv_set_trace_weights)");
     if (h->nseries < 4) return fail(h, MCINV_E_STATE, "need at least 4 sampled cycles");
     mcinv_status st = mcinv_sync(h);
@@ -807,6 +998,7 @@ extern "C" mcinv_status mcinv_trace_mc_error(mcinv_t h, double *mean, double *va
 extern "C" mcinv_status mcinv_trace_series(mcinv_t h, double *out, int64_t capacity, int64_t *length)
 {
     if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (h->nent) return fail(h, MCINV_E_UNSUPPORTED, "the trace series is not available with partition blocks of two or more rows");
     mcinv_status st = mcinv_sync(h);
     if (st != MCINV_OK) return st;
     if (length) *length = h->nseries;
@@ -819,6 +1011,7 @@ extern "C" mcinv_status mcinv_sample_until(mcinv_t h, double rel_tol, int64_t ch
                                            int64_t *cycles_out)
 {
     if (!h) return fail(nullptr, MCINV_E_ARG, "NULL handle");
+    if (h->nent) return fail(h, MCINV_E_UNSUPPORTED, "the trace series is not available with partition blocks of two or more rows");
     if (!(rel_tol > 0.0) || check_every < 4 || max_cycles < check_every) return fail(h, MCINV_E_ARG, "bad stop-rule arguments");
     if (!h->d_tq) return fail(h, MCINV_E_STATE, "the stop rule needs trace weights (mcinv_set_trace_weights)");
     int64_t done = 0;
@@ -853,6 +1046,7 @@ extern "C" mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchai
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         for (size_t k = 0; k < tmp.size(); ++k) dst[v][k] = (double)tmp[k];
         if (!h->ord.empty()) unpermute_rows(h, dst[v], (size_t)nchains * NV);
+        if (h->nent) partition_state(h, dst[v], (size_t)nchains * NV, v == 1, true);
     }
     if (cycle) *cycle = h->cycle;
     return st;
@@ -873,6 +1067,8 @@ extern "C" mcinv_status mcinv_reset_estimates(mcinv_t h)
         CUDA_TRY(h, cudaMemsetAsync(h->d_bsum, 0, elems * sizeof(double), h->stream));
         CUDA_TRY(h, cudaMemsetAsync(h->d_bsq, 0, elems * sizeof(double), h->stream));
     }
+    if (h->d_pacc)
+        CUDA_TRY(h, cudaMemsetAsync(h->d_pacc, 0, (size_t)h->G * h->nent * NV * sizeof(double), h->stream));
     h->samples = 0;
     h->block_batches = 0;
     h->block_cycles = 0;
@@ -892,12 +1088,19 @@ extern "C" mcinv_status mcinv_set_state(mcinv_t h, const double *z, const double
     const double *srcs[2] = {z, w};
     void *dsts[2] = {h->d_z[h->cur], h->d_w[h->cur]};
     const size_t row = (size_t)h->K * NV;
+    std::vector<double> part_in;
     for (int v = 0; v < 2; ++v) {
+        const double *src = srcs[v];
+        if (h->nent) {  // the block sweep's z, w to the sampled matrix's z~ = S z, w~ = S^H w
+            part_in.assign(src, src + count);
+            partition_state(h, part_in.data(), row, v == 1, false);
+            src = part_in.data();
+        }
         if (h->ord.empty()) {
-            for (size_t k = 0; k < count; ++k) tmp[k] = (float)srcs[v][k];
+            for (size_t k = 0; k < count; ++k) tmp[k] = (float)src[k];
         } else {
             for (int64_t r = 0; r < h->n; ++r)
-                for (size_t c = 0; c < row; ++c) tmp[(size_t)r * row + c] = (float)srcs[v][(size_t)h->ord[r] * row + c];
+                for (size_t c = 0; c < row; ++c) tmp[(size_t)r * row + c] = (float)src[(size_t)h->ord[r] * row + c];
         }
         CUDA_TRY(h, cudaMemcpyAsync(dsts[v], tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));

@@ -130,5 +130,12 @@ cudaError_t launch_series_fold(int ncyc, int ctas, int warps, const float *tpart
 // coupling burn-in helpers (accumulate.cu)
 cudaError_t launch_maxabs2(int cplx, int n, const void *a, const void *b, unsigned *out, cudaStream_t s);
 cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s);
+// Block partition (Sec. 4): for every pair (r, s) of rows of one diagonal block
+// (entry e: rows ent_r[e], ent_s[e] of the state) and every chain group g (chains
+// gch[g] .. gch[g+1]-1): acc[g][e] += sum over the group's chains of z_r conj(w_s), FP64.
+cudaError_t launch_pblock_acc(int cplx, int nent, const int *ent_r, const int *ent_s, int K, int G, const int *gch,
+                              const void *z, const void *w, double *acc, cudaStream_t s);
+// dst[idx[k]] = val[k], k < count
+cudaError_t launch_scatter(int count, const long long *idx, const double *val, double *dst, cudaStream_t s);
 
 }  // namespace mcinv

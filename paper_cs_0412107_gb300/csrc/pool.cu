@@ -367,6 +367,7 @@ struct HostSlot {
     int64_t sampled = 0, batches = 0; // samples accumulated, block batches folded
     int inverse = 0;
     int cur = 0;
+    std::vector<int32_t> ord;  // MCINV_F_COLOR_ORDER: row k of the sampled P C P^T is row ord[k] of C
     std::vector<Alloc> allocs;
     PoolSlotDev dev{};
     CUtensorMap maps[2];
@@ -383,7 +384,7 @@ struct mcinv_pool_ctx {
     int LPR = 8, V = 4, threads = 512, grid_sweep = 152;
     int blob_max = 48 * 1024;
     int max_slots = 0;
-    bool tuned = false, fixed_shape = false;
+    bool tuned = false, fixed_shape = false, color = false;
     int tune_next = 0;                 // next candidate shape to time
     std::vector<double> tune_score;    // ms per unit of work, per candidate
     cudaStream_t stream = nullptr;
@@ -470,6 +471,7 @@ extern "C" mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_op
     p->B = o.batch_cycles > 0 ? o.batch_cycles : 8;
     p->max_slots = (int)o.max_slots;
     p->stream = (cudaStream_t)o.stream;
+    p->color = (o.flags & MCINV_F_COLOR_ORDER) != 0;
     p->nw = (int)((o.K + 31) / 32);
     p->V = 4;
     if (o.chains_per_cta > 0) {
@@ -595,6 +597,20 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     if (si < 0) return pfail(p, MCINV_E_NOMEM, "no free slot");
     Prepared P;
     std::string why;
+    // the colour order (Sec. 4 reordering): sample P C P^T, map rows back in the results
+    std::vector<int32_t> ord;
+    std::vector<int64_t> rp2;
+    std::vector<int32_t> col2;
+    std::vector<double> val2;
+    if (p->color) {
+        int nc = 0;
+        mcinv_status st = color_order(n, row_ptr, col, val, 0, ord, &nc, &why);
+        if (st != MCINV_OK) return pfail(p, st, "%s", why.c_str());
+        permute_csr(n, row_ptr, col, val, 0, ord, rp2, col2, val2);
+        row_ptr = rp2.data();
+        col = col2.data();
+        val = val2.data();
+    }
     mcinv_status st = prepare_matrix(n, row_ptr, col, val, 0, p->blob_max, P, &why);
     if (st != MCINV_OK) return pfail(p, st, "%s", why.c_str());
     if (P.blob_max > p->blob_max) return pfail(p, MCINV_E_UNSUPPORTED, "a row has too many entries for the pool's chunks");
@@ -602,6 +618,7 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     slot_parts(p, P, want_inverse, parts);
     HostSlot &s = p->slots[si];
     s = HostSlot{};
+    s.ord = std::move(ord);
     for (size_t b : parts) {
         Alloc a;
         a.bytes = b;
@@ -948,8 +965,15 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
         e = launch_diag_estimate(0, (int)n, p->G, p->d_counts, (double)s.sampled, s.dev.dacc, mean, se, str);
     } else if (kind == MCINV_EST_TRACE) {
         double *dq = se + elems;
+        std::vector<double> qk;
+        if (q && !s.ord.empty()) {
+            qk.resize(n);
+            for (size_t k = 0; k < n; ++k) qk[k] = q[s.ord[k]];
+            q = qk.data();
+        }
         if (!q) st = pfail(p, MCINV_E_ARG, "q_diag is NULL");
-        else if ((e = cudaMemcpyAsync(dq, q, n * 8, cudaMemcpyHostToDevice, str)) == cudaSuccess)
+        else if ((e = cudaMemcpyAsync(dq, q, n * 8, cudaMemcpyHostToDevice, str)) == cudaSuccess &&
+                 (e = cudaStreamSynchronize(str)) == cudaSuccess)
             e = launch_trace_estimate(0, (int)n, p->G, p->d_counts, (double)s.sampled, s.dev.dacc, dq, mean, str);
     } else {
         e = launch_block_estimate(0, (long long)(n * n), (double)p->K, (double)s.sampled, (double)s.batches, s.dev.bsum,
@@ -968,6 +992,19 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
     p->heap.release(a.off, a.bytes);
     if (st != MCINV_OK) return st;
     if (e != cudaSuccess) return pfail(p, MCINV_E_CUDA, "estimate: %s", cudaGetErrorString(e));
+    if (!s.ord.empty() && kind != MCINV_EST_TRACE) {
+        // rows (and, for the inverse, columns) of P C^-1 P^T back to those of C^-1
+        for (double *x : {out, se_out}) {
+            if (!x) continue;
+            std::vector<double> t(x, x + elems);
+            if (kind == MCINV_EST_DIAG) {
+                for (size_t k = 0; k < n; ++k) x[s.ord[k]] = t[k];
+            } else {
+                for (size_t i = 0; i < n; ++i)
+                    for (size_t j = 0; j < n; ++j) x[(size_t)s.ord[i] * n + s.ord[j]] = t[i * n + j];
+            }
+        }
+    }
     return MCINV_OK;
 }
 
@@ -986,7 +1023,12 @@ extern "C" mcinv_status mcinv_pool_get_state(mcinv_pool_t p, int64_t ticket, int
     for (int v = 0; v < 2; ++v) {
         if (!dst[v] || nchains == 0) continue;
         PCUDA(p, cudaMemcpy2D(tmp.data(), nchains * 4, src[v] + chain0, p->K * 4, nchains * 4, s.n, cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < tmp.size(); ++k) dst[v][k] = tmp[k];
+        if (s.ord.empty()) {
+            for (size_t k = 0; k < tmp.size(); ++k) dst[v][k] = tmp[k];
+        } else {
+            for (int64_t r = 0; r < s.n; ++r)
+                for (int64_t c = 0; c < nchains; ++c) dst[v][(size_t)s.ord[r] * nchains + c] = tmp[(size_t)r * nchains + c];
+        }
     }
     if (cycle) *cycle = s.cycle;
     return MCINV_OK;

@@ -30,7 +30,7 @@ MCINV_F_AUTOTUNE = 2
 MCINV_F_COLOR_ORDER = 4
 
 # every symbol include/mcinv.h declares
-EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
+EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
            "mcinv_estimate", "mcinv_set_trace_weights", "mcinv_trace_mc_error", "mcinv_trace_series",
            "mcinv_sample_until", "mcinv_sync", "mcinv_get_state", "mcinv_set_state",
            "mcinv_reset_estimates", "mcinv_info", "mcinv_profile", "mcinv_profile_read",
@@ -126,6 +126,9 @@ def lib():
             getattr(L, name).argtypes = [vp, i64]
         L.mcinv_burnin_coupled.argtypes = [vp, ctypes.c_double, i64, ctypes.POINTER(i64)]
         L.mcinv_burnin_coupled.restype = ctypes.c_int
+        L.mcinv_create_partitioned.argtypes = [ctypes.POINTER(vp), i64, vp, vp, vp, ctypes.c_int,
+                                               ctypes.POINTER(mcinv_options), i64, vp]
+        L.mcinv_create_partitioned.restype = ctypes.c_int
         L.mcinv_color_order.argtypes = [i64, vp, vp, vp, ctypes.POINTER(i32)]
         L.mcinv_color_order.restype = ctypes.c_int
         dp = ctypes.POINTER(ctypes.c_double)
@@ -242,7 +245,9 @@ class Handle:
 def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_id=0, groups=0,
                  batch_cycles=0, acc=MCINV_ACC_BF16_TC, chains_per_cta=0, threads_per_cta=0,
                  ctas_per_slice=0, flags=0, stream="current", block_rows=None,
-                 block_cols=None) -> Handle:
+                 block_cols=None, partition=None) -> Handle:
+    """mcinv_create, or mcinv_create_partitioned when `partition` (block_ptr, int64[nblocks+1])
+    is given."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
     is_complex = np.iscomplexobj(val)
@@ -267,8 +272,13 @@ def mcinv_create(n, row_ptr, col, val, *, K=1024, seed=0, chain_base=0, matrix_i
         opt.block_cols = S.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         opt.n_block_rows, opt.n_block_cols = nR, nS = len(R), len(S)
     h = ctypes.c_void_p()
-    _check(lib().mcinv_create(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(v), dt,
-                              ctypes.byref(opt)))
+    if partition is None:
+        _check(lib().mcinv_create(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(v), dt,
+                                  ctypes.byref(opt)))
+    else:
+        bp = np.ascontiguousarray(partition, dtype=np.int64)
+        _check(lib().mcinv_create_partitioned(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(v), dt,
+                                              ctypes.byref(opt), int(len(bp) - 1), _ptr(bp)))
     return Handle(h, int(n), int(K), is_complex, nR, nS, keep)
 
 
@@ -463,10 +473,10 @@ def mcinv_pool_default_options(**overrides) -> mcinv_pool_options:
 
 
 def mcinv_pool_create(*, K=256, seed=0, chain_base=0, mem_budget=1 << 32, max_slots=512, batch_cycles=8,
-                      groups=32, chains_per_cta=0, threads_per_cta=0, stream="current") -> Pool:
+                      groups=32, chains_per_cta=0, threads_per_cta=0, flags=0, stream="current") -> Pool:
     o = mcinv_pool_default_options(K=K, seed=seed, chain_base=chain_base, mem_budget=mem_budget,
                                    max_slots=max_slots, batch_cycles=batch_cycles, groups=groups,
-                                   chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta)
+                                   chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta, flags=flags)
     o.stream = current_stream() if stream == "current" else stream
     p = ctypes.c_void_p()
     _pcheck(lib().mcinv_pool_create(ctypes.byref(p), ctypes.byref(o)))

@@ -5,24 +5,43 @@ order lists colour 0's rows ascending, then colour 1's, ..."""
 import numpy as np
 
 
-def greedy_order(csr):
+def _lower_neighbours(csr):
     n = csr.n
-    nbr = [set() for _ in range(n)]
-    for i in range(n):
+    rows = np.repeat(np.arange(n), np.diff(csr.row_ptr))
+    col = np.asarray(csr.col, dtype=np.int64)
+    off = col != rows
+    a = np.concatenate([rows[off], col[off]])
+    b = np.concatenate([col[off], rows[off]])
+    keep = b < a  # neighbours coloured before the row
+    a, b = a[keep], b[keep]
+    o = np.argsort(a, kind="stable")
+    return np.searchsorted(a[o], np.arange(n + 1)), b[o]
+
+
+def greedy_order(csr):
+    """Returns (order, colour of each row)."""
+    ptr, nb = _lower_neighbours(csr)
+    color = np.zeros(csr.n, dtype=np.int64)
+    for i in range(csr.n):
+        used = set(color[nb[ptr[i]:ptr[i + 1]]].tolist())
+        k = 0
+        while k in used:
+            k += 1
+        color[i] = k
+    order = np.lexsort((np.arange(csr.n), color))
+    return order.astype(np.int64), color
+
+
+def neighbours(csr):
+    """Neighbour sets of every row in the graph of C + C^T."""
+    nbr = [set() for _ in range(csr.n)]
+    for i in range(csr.n):
         for e in range(csr.row_ptr[i], csr.row_ptr[i + 1]):
             j = int(csr.col[e])
             if j != i:
                 nbr[i].add(j)
                 nbr[j].add(i)
-    color = [0] * n
-    for i in range(n):
-        used = {color[j] for j in nbr[i] if j < i}
-        k = 0
-        while k in used:
-            k += 1
-        color[i] = k
-    order = sorted(range(n), key=lambda i: (color[i], i))
-    return np.array(order, dtype=np.int64), np.array(color), nbr
+    return nbr
 
 
 def permuted(csr, order):

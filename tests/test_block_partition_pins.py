@@ -11,14 +11,16 @@ from paper_cs_0412107_gb300 import workloads as wl
 
 
 def zero_diagonal_pairs(npairs, seed, complex_=False, coupling=0.12):
-    """Rows (2k, 2k+1) form a block [[0, a], [b, 0]] (a zero diagonal, so the scalar sweep
-    cannot run), plus weak random couplings between blocks."""
+    """Rows (2k, 2k+1) form a block [[0, a], [b, 0]] with ab < 0 (a zero diagonal, so the
+    scalar sweep cannot run; eigenvalues +-i sqrt|ab|, so the block has a real principal
+    square root), plus weak random couplings between blocks."""
     rng = np.random.default_rng(seed)
     n = 2 * npairs
     rows, cols, vals = [], [], []
     for k in range(npairs):
         i = 2 * k
-        a, b = rng.uniform(1.0, 2.0, 2) * rng.choice([-1, 1], 2)
+        sgn = rng.choice([-1, 1])
+        a, b = rng.uniform(1.0, 2.0) * sgn, -rng.uniform(1.0, 2.0) * sgn
         rows += [i, i + 1]; cols += [i + 1, i]; vals += [a, b]
     for i in range(n):
         for j in rng.choice(n, 3, replace=False):
@@ -100,3 +102,10 @@ def test_hermitian_blocks_give_w_equal_z():
     hc = wl.csr_from_coo(c.n, *np.nonzero(h), h[np.nonzero(h)])
     st = oracle.run_block(hc, bp, 8, seed=1, ncycles=10)
     assert np.abs(st.z - st.w).max() < 1e-12 * np.abs(st.z).max()
+
+
+def test_block_without_principal_square_root_is_rejected():
+    c = wl.csr_from_coo(2, [0, 1], [1, 0], np.array([1.0, 2.0]))  # eigenvalues +-sqrt(2)
+    with pytest.raises(ValueError):
+        oracle.block_factors(c, np.array([0, 2]))
+

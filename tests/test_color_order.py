@@ -4,7 +4,7 @@ of the graph of C + C^T, and give one dependency level per colour."""
 import numpy as np
 import pytest
 
-from _greedy import greedy_order, permuted
+from _greedy import greedy_order, neighbours, permuted
 from paper_cs_0412107_gb300 import build as libbuild
 from paper_cs_0412107_gb300 import mcinv
 from paper_cs_0412107_gb300 import workloads as wl
@@ -25,7 +25,8 @@ CASES = [lambda: wl.random_dominant(300, 4, 1.5, 3), lambda: wl.pedigree(2000, 1
 def test_library_order_is_the_greedy_colouring(make):
     c = make()
     order, nc = mcinv.mcinv_color_order(c.n, c.row_ptr, c.col)
-    want, color, nbr = greedy_order(c)
+    want, color = greedy_order(c)
+    nbr = neighbours(c)
     assert np.array_equal(order, want) and nc == color.max() + 1
     # a proper colouring: no edge of C + C^T joins two rows of one colour
     for i in range(c.n):

@@ -129,3 +129,34 @@ def test_pool_batch_estimates_cover_the_dense_inverse():
     zs = np.concatenate(zs)
     assert np.mean(np.abs(zs) > 3) < 0.01
     assert 0.8 < np.sqrt(np.mean(zs ** 2)) < 1.25
+
+
+def test_pool_colour_order_follows_the_oracle_on_the_permuted_matrices():
+    """MCINV_F_COLOR_ORDER in a pool: every member samples P C P^T (Sec. 4 reordering),
+    so its chains follow the oracle on that matrix, and its diagonal and inverse, mapped
+    back to the rows of C, match the oracle's accumulation mapped the same way."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from _greedy import greedy_order, permuted
+    K, B, burn, samp = 64, 4, 6, 9
+    mats = [wl.random_dominant(n, 4, 1.5, seed) for n, seed in ((90, 4), (333, 5))]
+    pool = mcinv.mcinv_pool_create(K=K, seed=13, mem_budget=1 << 28, max_slots=4, batch_cycles=B,
+                                   flags=mcinv.MCINV_F_COLOR_ORDER)
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=7 + k, burnin=burn, samples=samp, want_inverse=True)
+               for k, c in enumerate(mats)]
+    run_until_done(pool, tickets)
+    for k, (c, t) in enumerate(zip(mats, tickets)):
+        order, _ = greedy_order(c)
+        cp = permuted(c, order)
+        z, w, cyc = mcinv.mcinv_pool_get_state(pool, t, c.n)
+        st, dacc, _ = oracle.run(cp, K, seed=13, matrix=7 + k, ncycles=burn + samp, acc_from=burn)
+        assert rel_err(z[order], st.z.real) < TOL and rel_err(w[order], st.w.real) < TOL
+        dm, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, c.n)
+        assert rel_err(dm[order], dacc.sum(0).real / (K * samp)) < TOL
+        inv, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
+        q = wl.q_diag(c.n, 2)
+        tr, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_TRACE, c.n, q_diag=q)
+        assert abs(tr - (q * dm).sum()) < 1e-9 * abs(tr)
+        # the inverse's diagonal is the diagonal estimate, in the rows of C (BF16 products)
+        assert np.abs(np.diag(inv) - dm).max() < 2e-2 * np.abs(dm).max()
+    mcinv.mcinv_pool_destroy(pool)
