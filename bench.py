@@ -328,7 +328,7 @@ def run_batch(args, world, rank, local):
     budget = int(args.batch_mem_gb * (1 << 30))
     nnz_total = sum(c.nnz for c in mats)
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
-                                   max_slots=len(mats), batch_cycles=B)
+                                   max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
     # warm-up pool: tuning steps and graph capture on a few members
     for k in range(min(8, len(mats))):
         mcinv.mcinv_pool_submit(pool, mats[k], matrix_id=10_000 + k, burnin=2 * B, samples=6 * B)
@@ -336,7 +336,7 @@ def run_batch(args, world, rank, local):
         mcinv.mcinv_pool_step(pool)
     mcinv.mcinv_pool_destroy(pool)
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
-                                   max_slots=len(mats), batch_cycles=B)
+                                   max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
@@ -363,7 +363,8 @@ def run_batch(args, world, rank, local):
            "config": {"workload": "batch512", "matrices": len(mats), "K": K, "burnin": burn, "samples": samp,
                       "sum_n": int(sum(c.n for c in mats)), "sum_nnz": int(nnz_total),
                       "estimate": "full inverse of every matrix", "batch_cycles": B,
-                      "chains_per_cta": info["chains_per_cta"], "threads_per_cta": info["threads_per_cta"]},
+                      "chains_per_cta": info["chains_per_cta"], "threads_per_cta": info["threads_per_cta"],
+                      "sweep_order": args.order},
            "seconds": dt, "admission_seconds": t_admit, "steps": steps,
            "block_tflops_effective": flops / dt / 1e12,
            "rms_error_vs_dense_inverse": {"median": float(np.median(errs)), "max": float(np.max(errs))},
@@ -377,7 +378,7 @@ def run_batch(args, world, rank, local):
     rate_max = len(mats) / dt
     serving = {}
     for frac in (0.5, 0.9):
-        srv = mcinv.mcinv_server_create(K=K, seed=args.seed, mem_budget=budget, max_slots=len(mats), batch_cycles=B)
+        srv = mcinv.mcinv_server_create(K=K, seed=args.seed, mem_budget=budget, max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
         rng = np.random.default_rng(1)
         n_req = min(len(mats), args.serve_requests)
         gaps = rng.exponential(1.0 / (frac * rate_max), size=n_req)
@@ -408,7 +409,7 @@ def time_to_rms(args, mats, burn, K, B, budget, rank):
     out = {"target_rms": 1e-2, "burnin": burn, "samples": samp, "checked_matrices": len(check)}
     # batched form
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
-                                   max_slots=len(mats), batch_cycles=B)
+                                   max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
@@ -424,7 +425,7 @@ def time_to_rms(args, mats, burn, K, B, budget, rank):
     rms_plain = []
     for k, c in enumerate(mats):
         h = mcinv.create_from_csr(c, K=K, seed=args.seed, chain_base=rank * K, matrix_id=k,
-                                  acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=B,
+                                  acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=B, flags=order_flag(args),
                                   block_rows=np.arange(c.n), block_cols=np.arange(c.n))
         mcinv.mcinv_burnin(h, burn)
         mcinv.mcinv_sample(h, samp)
@@ -438,6 +439,63 @@ def time_to_rms(args, mats, burn, K, B, budget, rank):
     out["speedup"] = t_plain / t_pool
     return out
 
+
+
+def lattice_truth(csr, cols):
+    """Columns of C^-1 by FP64 BiCGSTAB on the host (C is strictly diagonally dominant, so
+    the solves converge quickly): the truth for the RMS error of the block estimate."""
+    import scipy.sparse.linalg as spl
+    A = csr.to_scipy()
+    out = np.empty((csr.n, len(cols)), dtype=np.complex128)
+    for k, j in enumerate(cols):
+        e = np.zeros(csr.n, dtype=np.complex128)
+        e[j] = 1.0
+        x, info = spl.bicgstab(A, e, rtol=1e-12, atol=0.0, maxiter=2000)
+        assert info == 0, info
+        out[:, k] = x
+    return out
+
+
+def run_lattice(args, world, rank, local):
+    """The 4D lattice (16^4, K = 8192, complex64): the 4096 x 4096 block C^-1[0:4096, 0:4096]
+    accumulated with BF16 operands on the tensor cores against FP32 CUDA-core accumulation,
+    after 50 burn-in cycles; RMS error against FP64 solves on 64 of its columns after every
+    batch of 8 sampling cycles, and the time each form takes to reach 1e-2 and 3e-3."""
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    from paper_cs_0412107_gb300 import workloads as wl
+    torch.cuda.set_device(local)
+    csr = wl.WORKLOADS["lattice4d16"].build()
+    K, B, burn, nb = 8192, 8, 50, args.lattice_batches
+    R = np.arange(4096)
+    check = np.arange(0, 4096, 64)
+    truth = lattice_truth(csr, check)[:4096]
+    res = {"metric": "time to RMS inverse error", "unit": "s", "higher_is_better": False, "n_gpus": world,
+           "impl": "mine", "config": {"workload": "lattice4d16", "n": csr.n, "nnz": csr.nnz, "K": K,
+                                      "block": "C^-1[0:4096, 0:4096]", "burnin": burn, "batch_cycles": B,
+                                      "sweep_order": args.order,
+                                      "rms_over": "4096 x 64 columns of the block (FP64 BiCGSTAB truth)"},
+           "forms": {}}
+    for name, acc in (("bf16_tensor_cores", mcinv.MCINV_ACC_BF16_TC), ("fp32_cuda_cores", mcinv.MCINV_ACC_FP32_SIMT)):
+        h = mcinv.create_from_csr(csr, K=K, seed=args.seed, acc=acc, batch_cycles=B, block_rows=R, block_cols=R,
+                                  flags=mcinv.MCINV_F_AUTOTUNE | order_flag(args))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mcinv.mcinv_burnin(h, burn)
+        curve = []
+        for k in range(nb):
+            mcinv.mcinv_sample(h, B)
+            m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)  # synchronises
+            rms = float(np.sqrt(np.mean(np.abs(m[:, check] - truth) ** 2)))
+            curve.append({"cycles": burn + (k + 1) * B, "seconds": time.perf_counter() - t0, "rms": rms})
+        mcinv.mcinv_destroy(h)
+        first = lambda tgt: next((c["seconds"] for c in curve if c["rms"] <= tgt), None)
+        res["forms"][name] = {"curve": curve, "seconds_to_1e-2": first(1e-2), "seconds_to_3e-3": first(3e-3)}
+    a, b = res["forms"]["bf16_tensor_cores"], res["forms"]["fp32_cuda_cores"]
+    res["value"] = a["seconds_to_3e-3"]
+    res["speedup_to_3e-3"] = (b["seconds_to_3e-3"] / a["seconds_to_3e-3"]) if a["seconds_to_3e-3"] and b["seconds_to_3e-3"] else None
+    return res
 
 def cpu_baseline(csr, K, seconds, workload=WORKLOAD):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
@@ -591,7 +649,7 @@ def main():
     ap.add_argument("--e2e-burnin", type=int, default=500)
     ap.add_argument("--e2e-samples", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18", "lattice4d16"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-burnin", type=int, default=200)
     ap.add_argument("--batch-samples", type=int, default=2000)
@@ -599,6 +657,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--order", default="natural", choices=["natural", "colour"])
+    ap.add_argument("--lattice-batches", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"
@@ -609,6 +668,8 @@ def main():
         res = run_batch(args, world, rank, local)
     elif args.workload == "dirac18":
         res = run_dirac(args, world, rank, local)
+    elif args.workload == "lattice4d16":
+        res = run_lattice(args, world, rank, local)
     else:
         res = run_mine(args, world, rank, local)
     if rank == 0 and res is not None:
