@@ -5,7 +5,9 @@ Workload "pedigree50k": pedigree-shaped real non-symmetric C, n = 50,000, about
 C^-1 and the 512-column block C^-1[:, 0:512] (BF16 tensor-core accumulation).
 A step = one sampling batch: B cycles of the coupled sweep (Eqs. 4/5) with
 the fused diagonal partials, one block contraction over the batch, and the FP64
-folds.  value = nnz(C) * K * cycles / seconds.
+folds.  value = nnz(C) * K * cycles / seconds.  The rows are swept in the colour
+order by default (Sec. 4 reordering: the sampler of P C P^T, 7 dependency levels
+instead of 80); the same step in the given row order is reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 
@@ -242,6 +244,32 @@ def run_mine(args, world, rank, local):
         "clocks": clocks.summary(),
     }
     mcinv.mcinv_destroy(h)
+    if args.order == "colour" and not args.no_natural:
+        # the same step with the rows swept in their given order (Eqs. 4/5 for i = 1..n),
+        # for comparison: same kernels, 80 dependency levels instead of 7
+        hn = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=acc,
+                                   batch_cycles=args.batch, block_rows=R, block_cols=S,
+                                   flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+        mcinv.mcinv_burnin(hn, args.burnin)
+        for _ in range(args.warmup):
+            mcinv.mcinv_sample(hn, B)
+        mcinv.mcinv_profile(hn, True)
+        nsteps = max(3, args.steps // 3)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(nsteps):
+            mcinv.mcinv_sample(hn, B)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        msn = max_over_ranks(ev0.elapsed_time(ev1), world)
+        nl, nms = mcinv.mcinv_profile_read(hn, mcinv.MCINV_KERNEL_SWEEP)
+        ni = mcinv.mcinv_info(hn)
+        mcinv.mcinv_destroy(hn)
+        ach_n = alg_bytes / (nms / nl / 1e3) / 1e9 if nl else None
+        result["natural_order"] = {"value": float(csr.nnz) * K * nsteps * B * world / (msn / 1e3),
+                                   "ms_per_step": msn / nsteps, "steps": nsteps, "levels": ni["levels"],
+                                   "sweep_gbs": ach_n, "sweep_frac": ach_n / hbm if ach_n else None}
     if rank == 0 and not args.no_e2e:
         result["e2e"] = run_e2e(args, csr, K, acc, rank)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -656,7 +684,8 @@ def main():
     ap.add_argument("--batch-mem-gb", type=float, default=64.0)
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
-    ap.add_argument("--order", default="natural", choices=["natural", "colour"])
+    ap.add_argument("--order", default="colour", choices=["natural", "colour"])
+    ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--lattice-batches", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

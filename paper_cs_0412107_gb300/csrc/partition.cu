@@ -156,7 +156,8 @@ mcinv_status partition_transform(int64_t n, const int64_t *row_ptr, const int32_
                 if (col[e] >= b0 && col[e] < b0 + sz) D[r * sz + (col[e] - b0)] = value(e);
         if (!sqrt_pair(sz, D, Y, Z))
             return part_fail(err, MCINV_E_SINGULAR_DIAG,
-                             "diagonal block %lld (rows %d..%d) is singular or has an eigenvalue on the negative real axis",
+                             "diagonal block %lld (rows %d..%d) has no principal square root (it is singular or "
+                             "has an eigenvalue on the closed negative real axis)",
                              (long long)b, b0, b0 + sz - 1);
         if (!cplx)
             for (std::vector<cd> *m : {&Y, &Z})

@@ -79,3 +79,51 @@ def test_rejects_bad_options(L):
     with pytest.raises(mcinv.McinvError) as e:
         _create(1, [0, 1], [0], [1.0], K=0)
     assert e.value.status == 1
+
+
+def test_rejects_empty_and_oversized_problems(L):
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(0, [0], [], np.zeros(0))
+    assert e.value.status == 1
+    n = 1 << 20  # n * K beyond the state the library addresses (4e9 elements)
+    rp = np.arange(n + 1, dtype=np.int64)
+    with pytest.raises(mcinv.McinvError) as e:
+        _create(n, rp, np.arange(n, dtype=np.int32), np.ones(n), K=1 << 13)
+    assert e.value.status == 1 and "n*K" in str(e.value)
+
+
+@pytest.mark.parametrize("bp,status", [
+    ([0, 2, 5], 1),         # does not end at n = 4
+    ([0, 3, 2, 4], 1),      # decreasing
+    ([0, 4], 2),            # D_b = [[0,1,..]]: the 4x4 block below is singular
+])
+def test_partition_rejections_before_any_device_work(L, bp, status):
+    # rows 0-1 and 2-3: [[0, 2], [2, 0]] blocks (eigenvalues +-2: no principal root) would be
+    # rejected too; here the 4x4 diagonal block is singular (rows 0 and 1 are equal)
+    rp = [0, 2, 4, 5, 6]
+    col = [0, 1, 0, 1, 2, 3]
+    val = [1.0, 1.0, 1.0, 1.0, 1.0, 1.0]
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_create(4, rp, col, val, stream=None, partition=np.array(bp))
+    assert e.value.status == status
+
+
+def test_partition_block_size_limit_and_square_roots(L):
+    rp, col, val = [0, 1, 2], [1, 0], [2.0, 2.0]  # [[0, 2], [2, 0]]: eigenvalues +-2
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_create(2, rp, col, val, stream=None, partition=np.array([0, 2]))
+    assert e.value.status == 2 and "square root" in str(e.value)
+    with pytest.raises(mcinv.McinvError) as e:  # one-row blocks need their own diagonal
+        mcinv.mcinv_create(2, rp, col, val, stream=None, partition=np.array([0, 1, 2]))
+    assert e.value.status == 2
+    n = 9
+    with pytest.raises(mcinv.McinvError) as e:  # a 9-row block exceeds the limit
+        mcinv.mcinv_create(n, np.arange(n + 1), np.arange(n, dtype=np.int32), np.ones(n), stream=None,
+                           partition=np.array([0, n]))
+    assert e.value.status == 1
+
+
+def test_colour_order_rejects_malformed_input(L):
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_create(2, [0, 1, 2], [0, 3], [1.0, 1.0], stream=None, flags=mcinv.MCINV_F_COLOR_ORDER)
+    assert e.value.status == 1
