@@ -298,7 +298,9 @@ def expected_covariance(a, k):
 # with A_b B_b^H = D_b^-1, the condition that makes E[z w^H] converge to C^-1 (the block
 # form of the demonstration of Sec. 2.2).  The factors are read from the scalar case
 # (alpha = 1/sqrt(c_ii), beta = 1/conj(sqrt(c_ii))): A_b = S_b^-1 and B_b = (S_b^-1)^H with
-# S_b the principal square root of D_b.  Blocks of one row keep the scalar constants.
+# S_b the principal square root of D_b, which exists when no eigenvalue of D_b lies on the
+# closed negative real axis (a block without one is rejected).  Blocks of one row keep the
+# scalar constants.
 
 def block_factors(csr, block_ptr):
     """Per block: (rows, D_b^-1, A_b, B_b).  One-row blocks take the scalar constants
@@ -320,6 +322,9 @@ def block_factors(csr, block_ptr):
             out.append((r, np.array([[1.0 / c]]), np.array([[al]]), np.array([[be]])))
         else:
             D = a[np.ix_(r, r)]
+            ev = np.linalg.eigvals(D)
+            if np.any((np.abs(ev.imag) <= 1e-12 * np.abs(ev)) & (ev.real <= 0)):
+                raise ValueError(f"block {b} has no principal square root (an eigenvalue on the closed negative real axis)")
             A = np.linalg.inv(sl.sqrtm(D))
             out.append((r, np.linalg.inv(D), A, A.conj().T))
     return out
