@@ -206,14 +206,16 @@ DIRAC_GAMMA = tuple([np.block([[_Z2, -1j * s], [1j * s, _Z2]]) for s in _PAULI]
                     + [np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)])
 
 
-def wilson_dirac(dims=(18, 18, 18, 18), kappa: float = 0.1) -> CSR:
+def wilson_dirac(dims=(18, 18, 18, 18), kappa: float = 0.1, spin_fastest: bool = False) -> CSR:
     """The free Wilson-Dirac matrix of Sec. 3.2 (Eqs. disDirac and explicit).
 
     L = I + kappa sum_mu [(1 + gamma^mu) d_{y, x+mu} + (1 - gamma^mu) d_{y, x-mu}] on a
     periodic lattice ``dims = (N1, N2, N3, N0)``; direction mu = 1, 2, 3, 4 moves
     coordinate N1, N2, N3, N0 (time last).  Row index, 0-based, follows the paper's
     mapping with the spinor index slowest: i = a + N1 (b + N2 (c + N3 (d + N0 s))).
-    Zero entries of (1 +- gamma^4) are not stored: 14 nonzeros per row.
+    ``spin_fastest`` numbers the same operator with the spinor index fastest,
+    i = s + 4 (a + N1 (...)): a relabelling (P L P^T) that keeps a site's four spinor
+    rows together.  Zero entries of (1 +- gamma^4) are not stored: 14 nonzeros per row.
     """
     dims = tuple(int(L) for L in dims)
     V = int(np.prod(dims))
@@ -231,8 +233,12 @@ def wilson_dirac(dims=(18, 18, 18, 18), kappa: float = 0.1) -> CSR:
             for s in range(4):
                 for t in range(4):
                     if blk[s, t] != 0:
-                        rows.append(x + V * s)
-                        cols.append(y + V * t)
+                        if spin_fastest:
+                            rows.append(4 * x + s)
+                            cols.append(4 * y + t)
+                        else:
+                            rows.append(x + V * s)
+                            cols.append(y + V * t)
                         vals.append(np.full(V, blk[s, t]))
     return csr_from_coo(4 * V, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 

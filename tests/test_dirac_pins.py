@@ -90,3 +90,14 @@ def test_oracle_trace_estimate_on_a_small_lattice():
     g = oracle.geyer_ips(np.array(series))
     assert abs(g["mean"] - exact) < 4 * g["se"]
     assert g["se"] < 0.01 * exact
+
+
+def test_spin_fastest_numbering_is_a_relabelling():
+    """The spinor-fastest numbering is P L P^T of the paper's spinor-slowest one."""
+    dims = (3, 3, 3, 4)
+    V = int(np.prod(dims))
+    a = wl.wilson_dirac(dims, 0.1).to_dense()
+    b = wl.wilson_dirac(dims, 0.1, spin_fastest=True).to_dense()
+    i = np.arange(4 * V)
+    new = (i % V) * 4 + i // V  # row i = site + V s of the paper's numbering -> 4 site + s
+    assert np.array_equal(b[np.ix_(new, new)], a)
