@@ -95,6 +95,10 @@ typedef struct {
 #define MCINV_F_AUTOTUNE 2 /* when chains_per_cta, ctas_per_slice and threads_per_cta are all 0,
                               time the candidate slice shapes on this matrix for two cycles at
                               create time and keep the fastest (cached per n, nnz, K, type) */
+#define MCINV_F_STAGED 8   /* real matrices: run the sweep whose producer warp stages the gathers in
+                              shared memory (bulk copies on mbarriers) instead of the register
+                              kernel; needs 16- or 32-chain slices and K a multiple of the slice
+                              (MCINV_E_UNSUPPORTED otherwise).  MCINV_F_AUTOTUNE considers both. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.

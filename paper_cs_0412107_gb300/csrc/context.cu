@@ -27,6 +27,7 @@ struct mcinv_ctx {
     int64_t n = 0, nnz = 0, K = 0;
     int cplx = 0;
     int W = 0, V = 1, LPR = 1, Q = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
+    bool staged = false;  // the staged sweep kernel (sweep_staged.cu) instead of the register one
     uint64_t seed = 0;
     int64_t chain_base = 0;
     uint32_t matrix_id = 0;
@@ -198,12 +199,20 @@ static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q, int *T)
 
 static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumulate, int cyc0_in_batch);
 
+// one sweep launch of the handle's kernel and shape
+static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
+{
+    if (h->staged) return launch_sweep_staged(a, h->LPR, h->slices, h->stream);
+    return launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream);
+}
+
 // Autotuner: time every reasonable slice shape (chains per CTA, CTAs per
 // cluster, threads per CTA) for two burn-in cycles on the handle's own matrix
 // from the zero state, keep the fastest, and put the state back to zero.  The
 // choice is cached per (n, nnz, K, real/complex) for the process.
 struct TunedShape {
     int W, V, LPR, Q, T;
+    bool staged;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -216,7 +225,7 @@ static mcinv_status autotune(mcinv_ctx *h)
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
-            h->Q = it->second.Q; h->threads = it->second.T;
+            h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -229,7 +238,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -253,14 +262,39 @@ static mcinv_status autotune(mcinv_ctx *h)
                 }
                 if (e != cudaSuccess) cudaGetLastError();  // launch refused: skip this shape
                 h->launches += 2;
-                if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, T}; }
+                if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, T, false}; }
                 h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS;
             }
         }
     }
+    // the staged kernel: real matrices, 4 chains per lane
+    for (int lpr = 4; lpr <= 8; lpr *= 2) {
+        if (!staged_supported(h->cplx, lpr, vmax, h->K, h->blob_max)) continue;
+        const int W = lpr * vmax;
+        const int slices = (int)((h->K + W - 1) / W);
+        for (int Q = 1; Q <= 16; Q *= 2) {
+            if ((int64_t)slices * Q > 2 * sms) break;
+            if ((int64_t)slices * Q < std::min<int64_t>(64, slices)) continue;
+            const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices;
+            h->W = W; h->V = vmax; h->LPR = lpr; h->Q = Q; h->threads = staged_threads(); h->slices = slices;
+            SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
+            float ms = 1e30f;
+            cudaError_t e = launch_sweep_staged(a, lpr, slices, h->stream);  // warm-up
+            if (e == cudaSuccess) {
+                cudaEventRecord(e0, h->stream);
+                e = launch_sweep_staged(a, lpr, slices, h->stream);
+                cudaEventRecord(e1, h->stream);
+                if (e == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e != cudaSuccess) cudaGetLastError();
+            h->launches += 2;
+            if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, staged_threads(), true}; }
+            h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T;
+    h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T; h->staged = best.staged;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -411,6 +445,15 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         h->Q = q;
     }
 
+    if (h->flags & MCINV_F_STAGED) {
+        if (!staged_supported(cplx, h->LPR, h->V, opt.K, h->blob_max)) {
+            fail(h, MCINV_E_UNSUPPORTED,
+                 "the staged sweep needs a real matrix, 4 or 8 lanes per row of 4 chains (16- or 32-chain slices) and K a multiple of the slice");
+            return bail(MCINV_E_UNSUPPORTED);
+        }
+        h->staged = true;
+        h->threads = staged_threads();
+    }
     double *d_diag = nullptr;
     long long *d_cst_at = nullptr;
     std::vector<int32_t> bad_init(1, 0x7fffffff);
@@ -644,7 +687,7 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
             // one cycle per launch: the state of every cycle is read before the next overwrites it
             for (int k = 0; k < b; ++k) {
                 SweepArgs a = sweep_args(h, 1, k, accumulate, k);
-                LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
+                LAUNCH_K(h, MCINV_KERNEL_SWEEP, sweep_launch(h, a));
                 if (accumulate && h->d_tq) {
                     mcinv_status st = series_append(h, 1);
                     if (st != MCINV_OK) return st;
@@ -663,7 +706,7 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
             }
         } else {
             SweepArgs a = sweep_args(h, b, 0, accumulate, 0);
-            LAUNCH_K(h, MCINV_KERNEL_SWEEP, launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream));
+            LAUNCH_K(h, MCINV_KERNEL_SWEEP, sweep_launch(h, a));
             if (accumulate && h->d_tq) {
                 mcinv_status st = series_append(h, b);
                 if (st != MCINV_OK) return st;

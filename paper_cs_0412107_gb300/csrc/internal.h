@@ -130,6 +130,11 @@ cudaError_t launch_series_fold(int ncyc, int ctas, int warps, const float *tpart
 // coupling burn-in helpers (accumulate.cu)
 cudaError_t launch_maxabs2(int cplx, int n, const void *a, const void *b, unsigned *out, cudaStream_t s);
 cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s);
+// The staged sweep (sweep_staged.cu): real matrices, 4 chains per lane, 4 or 8 lanes
+// per row, K a multiple of the slice; a producer warp stages the gathers in shared memory.
+bool staged_supported(int cplx, int lanes_per_row, int chains_per_lane, int64_t K, int blob_max);
+cudaError_t launch_sweep_staged(const SweepArgs &a, int lanes_per_row, int slices, cudaStream_t s);
+int staged_threads();
 // Block partition (Sec. 4): for every pair (r, s) of rows of one diagonal block
 // (entry e: rows ent_r[e], ent_s[e] of the state) and every chain group g (chains
 // gch[g] .. gch[g+1]-1): acc[g][e] += sum over the group's chains of z_r conj(w_s), FP64.

@@ -69,6 +69,22 @@ __device__ __forceinline__ uint16_t bf16_bits(float x)
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
+// NF BF16 values to dst.  Four of them are 8 bytes at an 8-byte boundary (shadow rows
+// are padded to 64 elements and a lane's chain offset is a multiple of 4 elements)
+// and go out as one 64-bit store.
+template <int NF>
+__device__ __forceinline__ void store_bf16(uint16_t *dst, const float *v)
+{
+    if constexpr (NF == 4) {
+        const uint32_t lo = (uint32_t)bf16_bits(v[0]) | ((uint32_t)bf16_bits(v[1]) << 16);
+        const uint32_t hi = (uint32_t)bf16_bits(v[2]) | ((uint32_t)bf16_bits(v[3]) << 16);
+        *(uint2 *)dst = make_uint2(lo, hi);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(v[q]);
+    }
+}
+
 // V chains of one lane as a single vector: V consecutive chains of one row are
 // contiguous in the [n][K] layout, so each gather is one 4-, 8- or 16-byte load.
 template <bool CPLX, int V> struct Vec;
@@ -380,30 +396,26 @@ __device__ __forceinline__ bool sweep_chunk_rows(const ChunkWork &w, float *tsum
                 // stays zero
                 const size_t o = (size_t)shcol * w.kp + (size_t)c0 * (CPLX ? 2 : 1);
                 constexpr int NF = L::NF;
-                if (rp >= 0) {
-                    uint16_t *dst = w.zsh + (size_t)rp * w.ldsh + o;
-#pragma unroll
-                    for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(zv)[q]);
-                }
+                if (rp >= 0) store_bf16<NF>(w.zsh + (size_t)rp * w.ldsh + o, L::f(zv));
                 if (sp >= 0) {
                     if constexpr (!CPLX) {
-                        uint16_t *dst = w.wsh + (size_t)sp * w.ldsh + o;
-#pragma unroll
-                        for (int q = 0; q < NF; ++q) dst[q] = bf16_bits(L::f(wv)[q]);
+                        store_bf16<NF>(w.wsh + (size_t)sp * w.ldsh + o, L::f(wv));
                     } else {
                         // row 2s = [wr, wi] contracts to Re(z conj w), row 2s+1 =
                         // [-wi, wr] to Im(z conj w), so the product comes out
                         // interleaved re,im
                         uint16_t *w0 = w.wsh + (size_t)(2 * sp) * w.ldsh + o;
-                        uint16_t *w1 = w0 + w.ldsh;
+                        float f0[2 * V], f1[2 * V];
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const S x = L::get(wv, v);
-                            w0[2 * v] = bf16_bits(x.x);
-                            w0[2 * v + 1] = bf16_bits(x.y);
-                            w1[2 * v] = bf16_bits(-x.y);
-                            w1[2 * v + 1] = bf16_bits(x.x);
+                            f0[2 * v] = x.x;
+                            f0[2 * v + 1] = x.y;
+                            f1[2 * v] = -x.y;
+                            f1[2 * v + 1] = x.x;
                         }
+                        store_bf16<2 * V>(w0, f0);
+                        store_bf16<2 * V>(w0 + w.ldsh, f1);
                     }
                 }
             }

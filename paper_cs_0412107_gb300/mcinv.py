@@ -28,6 +28,7 @@ MCINV_EST_BLOCK, MCINV_EST_DIAG, MCINV_EST_TRACE = 0, 1, 2
 MCINV_F_NO_DIAG = 1
 MCINV_F_AUTOTUNE = 2
 MCINV_F_COLOR_ORDER = 4
+MCINV_F_STAGED = 8
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
