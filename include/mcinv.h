@@ -99,6 +99,15 @@ typedef struct {
                               shared memory (bulk copies on mbarriers) instead of the register
                               kernel; needs 16- or 32-chain slices and K a multiple of the slice
                               (MCINV_E_UNSUPPORTED otherwise).  MCINV_F_AUTOTUNE considers both. */
+#define MCINV_F_GRID 16    /* run the sweep as one cooperative launch over every SM: a warp updates
+                              one row for 32 x V chains (V = 4 real, 2 complex; a 512-byte segment
+                              of z or w per gathered row), every CTA takes rows of every dependency
+                              level, and a grid-wide barrier ends each level.  Same values, bit for
+                              bit, as the chain-sliced kernel with 32 x V-chain slices.  Needs K a
+                              multiple of V and one resident CTA per SM; threads_per_cta 384
+                              (default) or 512, chains_per_cta and ctas_per_slice are ignored
+                              (MCINV_E_UNSUPPORTED otherwise).  MCINV_F_AUTOTUNE without this flag
+                              times it beside the chain-sliced shapes. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.
@@ -261,6 +270,8 @@ typedef struct {
     int64_t block_batches;   /* batches folded into the block estimate */
     int64_t kernel_launches; /* kernels this handle has launched */
     int64_t device_bytes;    /* device memory held by the handle */
+    int32_t sweep_kernel;    /* 0: chain-sliced (registers), 1: staged, 2: grid-wide (MCINV_F_GRID) */
+    int32_t grid_ctas;       /* CTAs of the grid-wide sweep (0 for the others) */
 } mcinv_info_t;
 
 mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info);

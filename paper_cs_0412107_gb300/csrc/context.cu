@@ -28,6 +28,8 @@ struct mcinv_ctx {
     int cplx = 0;
     int W = 0, V = 1, LPR = 1, Q = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
     bool staged = false;  // the staged sweep kernel (sweep_staged.cu) instead of the register one
+    bool grid = false;    // the grid-wide sweep kernel (sweep_grid.cu)
+    int gctas = 0;        // its CTAs (all resident at once)
     uint64_t seed = 0;
     int64_t chain_base = 0;
     uint32_t matrix_id = 0;
@@ -37,6 +39,12 @@ struct mcinv_ctx {
     int *d_perm = nullptr, *d_pos = nullptr;
     uint8_t *d_stream = nullptr;
     ChunkDesc *d_chunks = nullptr;
+    // the flat form of the matrix for the grid-wide sweep
+    GridRow *d_grow = nullptr;
+    uint8_t *d_gzent[2] = {nullptr, nullptr}, *d_gwent[2] = {nullptr, nullptr}, *d_gcst = nullptr;
+    uint32_t gnkv = 0;
+    int *d_levptr = nullptr;
+    unsigned *d_gbar = nullptr;
     int nchunks = 0, blob_max = 0, seg = 1, units = 0;
     uint32_t *d_noise = nullptr;
     void *d_z[2] = {nullptr, nullptr}, *d_w[2] = {nullptr, nullptr};
@@ -200,8 +208,29 @@ static void choose_shape(int64_t K, int cplx, int sms, int *W, int *Q, int *T)
 static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumulate, int cyc0_in_batch);
 
 // one sweep launch of the handle's kernel and shape
+static GridArgs grid_args(mcinv_ctx *h)
+{
+    GridArgs g{};
+    g.rows = h->d_grow;
+    g.zent[0] = h->d_gzent[0]; g.zent[1] = h->d_gzent[1];
+    g.went[0] = h->d_gwent[0]; g.went[1] = h->d_gwent[1];
+    g.nkv = h->gnkv;
+    g.cst = h->d_gcst;
+    g.lev_ptr = h->d_levptr;
+    g.nlev = h->nlev;
+    g.nblk = (int)((h->K + 32 * h->V - 1) / (32 * h->V));
+    g.bar = h->d_gbar;
+    return g;
+}
+
+// CTAs and warps per CTA of the sweep launch (the trace-series partials hold one
+// slot per cycle, CTA and warp)
+static int sweep_ctas(const mcinv_ctx *h) { return h->grid ? h->gctas : h->slices * h->Q; }
+static int sweep_warps(const mcinv_ctx *h) { return h->threads / 32; }
+
 static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 {
+    if (h->grid) return launch_sweep_grid(a, grid_args(h), h->cplx, h->gctas, h->threads, h->stream);
     if (h->staged) return launch_sweep_staged(a, h->LPR, h->slices, h->stream);
     return launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream);
 }
@@ -213,6 +242,7 @@ static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 struct TunedShape {
     int W, V, LPR, Q, T;
     bool staged;
+    bool grid = false;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -226,6 +256,8 @@ static mcinv_status autotune(mcinv_ctx *h)
         if (it != g_tune_cache.end()) {
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
+            h->grid = it->second.grid;
+            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -238,7 +270,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -262,7 +294,7 @@ static mcinv_status autotune(mcinv_ctx *h)
                 }
                 if (e != cudaSuccess) cudaGetLastError();  // launch refused: skip this shape
                 h->launches += 2;
-                if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, T, false}; }
+                if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, T, false, false}; }
                 h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS;
             }
         }
@@ -288,13 +320,37 @@ static mcinv_status autotune(mcinv_ctx *h)
             }
             if (e != cudaSuccess) cudaGetLastError();
             h->launches += 2;
-            if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, staged_threads(), true}; }
+            if (ms < best_ms) { best_ms = ms; best = TunedShape{W, vmax, lpr, Q, staged_threads(), true, false}; }
             h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS;
         }
+    }
+    // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
+    for (int T = 384; T <= 512; T += 128) {
+        const int ctas = grid_ctas(h->cplx, T);
+        if (!grid_supported(h->cplx, vmax, h->K, T) || ctas < 1) continue;
+        const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
+        const bool sG = h->grid;
+        h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
+        h->slices = (int)((h->K + h->W - 1) / h->W);
+        SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
+        float ms = 1e30f;
+        cudaError_t e = sweep_launch(h, a);  // warm-up
+        if (e == cudaSuccess) {
+            cudaEventRecord(e0, h->stream);
+            e = sweep_launch(h, a);
+            cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        h->launches += 2;
+        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true}; }
+        h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS; h->gctas = sC; h->grid = sG;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T; h->staged = best.staged;
+    h->grid = best.grid;
+    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads) : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -454,6 +510,21 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         h->staged = true;
         h->threads = staged_threads();
     }
+    if (h->flags & MCINV_F_GRID) {
+        const int vmax = cplx ? 2 : 4;
+        const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
+        const int ctas = grid_supported(cplx, vmax, opt.K, T) ? grid_ctas(cplx, T) : 0;
+        if (h->staged || ctas < 1) {
+            fail(h, MCINV_E_UNSUPPORTED,
+                 "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA, a resident CTA per SM "
+                 "and not MCINV_F_STAGED", vmax);
+            return bail(MCINV_E_UNSUPPORTED);
+        }
+        h->grid = true;
+        h->gctas = ctas;
+        h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T;
+        h->slices = (int)((opt.K + h->W - 1) / h->W);
+    }
     double *d_diag = nullptr;
     long long *d_cst_at = nullptr;
     std::vector<int32_t> bad_init(1, 0x7fffffff);
@@ -476,27 +547,64 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     SETUP(upload(h, &d_bad, bad_init));
     SETUP(launch_constants((int)n, d_diag, cplx, h->d_stream, d_cst_at, d_bad, h->stream));
     h->launches++;
-    int bad = 0x7fffffff;
-    SETUP(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    SETUP(cudaStreamSynchronize(h->stream));
-    if (bad != 0x7fffffff) {
-        fail(h, MCINV_E_SINGULAR_DIAG, "diagonal entry of row %d is not usable", h->ord.empty() ? perm[bad] : h->ord[perm[bad]]);
-        return bail(MCINV_E_SINGULAR_DIAG);
+    if (opt.K % (cplx ? 2 : 4) == 0 && (double)n * (double)opt.K / (cplx ? 2 : 4) < 2147483648.0) {
+        // the flat form for the grid-wide sweep: records (.row = i K / V), entries for
+        // each cycle parity (.col = index of the gathered vector from z[0] / w[0]:
+        // this cycle's buffer for j < i, last cycle's for j > i), constants by position
+        const uint32_t kv = (uint32_t)(opt.K / (cplx ? 2 : 4));
+        h->gnkv = (uint32_t)n * kv;
+        std::vector<GridRow> grow = P.grow;
+        const size_t esz_ent = cplx ? sizeof(EntC) : sizeof(EntR);
+        for (int par = 0; par < 2; ++par) {
+            // par: the buffer that holds last cycle's state; this cycle writes the other
+            const uint32_t off_new = par ? 0u : h->gnkv, off_old = par ? h->gnkv : 0u;
+            std::vector<uint8_t> ez = P.gzent, ew = P.gwent;
+            for (int64_t p = 0; p < n; ++p) {
+                const int i = P.grow[p].row;
+                auto fix = [&](std::vector<uint8_t> &v, int b, int e) {
+                    for (int q = b; q < e; ++q) {
+                        int *c = (int *)(v.data() + (size_t)q * esz_ent);  // .col of EntR / EntC
+                        *c = (int)((*c < i ? off_new : off_old) + (uint32_t)*c * kv);
+                    }
+                };
+                fix(ez, P.grow[p].zb, P.grow[p + 1].zb);
+                fix(ew, P.grow[p].wb, P.grow[p + 1].wb);
+            }
+            SETUP(upload(h, &h->d_gzent[par], ez));
+            SETUP(upload(h, &h->d_gwent[par], ew));
+        }
+        for (int64_t p = 0; p < n; ++p) grow[p].row = (int)((uint32_t)P.grow[p].row * kv);
+        SETUP(upload(h, &h->d_grow, grow));
+        SETUP(upload(h, &h->d_levptr, P.lev_ptr));
+        SETUP(dalloc(h, &h->d_gbar, 1));
+        const size_t csz = cplx ? sizeof(CstC) : sizeof(CstR);
+        std::vector<long long> at((size_t)n);
+        for (int64_t p = 0; p < n; ++p) at[p] = (long long)(p * csz);
+        long long *d_at = nullptr;
+        SETUP(upload(h, &d_at, at));
+        SETUP(dalloc(h, &h->d_gcst, (size_t)n * csz));
+        SETUP(launch_constants((int)n, d_diag, cplx, h->d_gcst, d_at, d_bad, h->stream));
+        h->launches++;
+    } else if (h->grid) {
+        fail(h, MCINV_E_UNSUPPORTED, "the grid-wide sweep needs n K / V < 2^31");
+        return bail(MCINV_E_UNSUPPORTED);
     }
-
     // ---- chain state (Algorithm 1 step 1: z = w = 0), noise plane, accumulators
     const size_t esz = cplx ? 8 : 4;
     const size_t state = (size_t)n * (size_t)opt.K;
-    for (int b = 0; b < 2; ++b) {
-        SETUP(dalloc(h, (char **)&h->d_z[b], state * esz));
-        SETUP(dalloc(h, (char **)&h->d_w[b], state * esz));
-        SETUP(cudaMemsetAsync(h->d_z[b], 0, state * esz, h->stream));
-        SETUP(cudaMemsetAsync(h->d_w[b], 0, state * esz, h->stream));
-    }
+    // the two buffers of z (and of w) are one allocation: the grid-wide sweep
+    // addresses both from z[0]
+    SETUP(dalloc(h, (char **)&h->d_z[0], 2 * state * esz));
+    SETUP(dalloc(h, (char **)&h->d_w[0], 2 * state * esz));
+    h->d_z[1] = (char *)h->d_z[0] + state * esz;
+    h->d_w[1] = (char *)h->d_w[0] + state * esz;
+    SETUP(cudaMemsetAsync(h->d_z[0], 0, 2 * state * esz, h->stream));
+    SETUP(cudaMemsetAsync(h->d_w[0], 0, 2 * state * esz, h->stream));
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
     SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
-    if ((h->flags & MCINV_F_AUTOTUNE) && opt.chains_per_cta == 0 && opt.threads_per_cta == 0 && opt.ctas_per_slice == 0) {
+    if ((h->flags & MCINV_F_AUTOTUNE) && !(h->flags & MCINV_F_GRID) && opt.chains_per_cta == 0 && opt.threads_per_cta == 0 &&
+        opt.ctas_per_slice == 0) {
         const mcinv_status st = autotune(h);
         if (st != MCINV_OK) return bail(st);
     }
@@ -668,7 +776,7 @@ static mcinv_status series_append(mcinv_ctx *h, int ncyc)
         h->d_series = nb;
         h->cap_series = cap;
     }
-    LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_series_fold(ncyc, h->slices * h->Q, h->threads / 32, h->d_tpart, (double)h->K,
+    LAUNCH_K(h, MCINV_KERNEL_FOLD, launch_series_fold(ncyc, sweep_ctas(h), sweep_warps(h), h->d_tpart, (double)h->K,
                                                       h->d_series, h->nseries, h->stream));
     h->nseries += ncyc;
     return MCINV_OK;
@@ -979,7 +1087,7 @@ extern "C" mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q)
     for (int64_t p = 0; p < h->n; ++p) qp[p] = (float)q[h->ord.empty() ? perm[p] : h->ord[perm[p]]];
     if (!h->d_tq) {
         CUDA_TRY(h, dalloc(h, &h->d_tq, (size_t)h->n));
-        CUDA_TRY(h, dalloc(h, &h->d_tpart, (size_t)h->B * h->slices * h->Q * (h->threads / 32)));
+        CUDA_TRY(h, dalloc(h, &h->d_tpart, (size_t)h->B * sweep_ctas(h) * sweep_warps(h)));
     }
     CUDA_TRY(h, cudaMemcpyAsync(h->d_tq, qp.data(), (size_t)h->n * 4, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1163,6 +1271,8 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
     info->kernel_launches = h->launches; info->device_bytes = h->bytes;
+    info->sweep_kernel = h->grid ? 2 : h->staged ? 1 : 0;
+    info->grid_ctas = h->grid ? h->gctas : 0;
     return MCINV_OK;
 }
 

@@ -50,6 +50,16 @@ struct RowMeta {
     int info;  // bits 0-1: the item's piece k; bits 2-3: log2 P; bits 4-31: the row's index in the chunk
 };
 
+// The same rows for the grid-wide sweep (sweep_grid.cu), flat and by position:
+// row p's C entries are zent[zb .. next.zb), its C^dagger entries went[wb ..
+// next.wb) (the same order as in its chunk), and info packs log2 P (bits 0-1,
+// the pieces the chunk stream cuts the row into), the C entry count (bits
+// 2-16) and the C^dagger entry count (bits 17-31).  Record n is a sentinel.
+struct __align__(16) GridRow {
+    int row, zb, wb, info;
+};
+constexpr int GRID_DEG_MAX = (1 << 15) - 1;
+
 struct ChunkDesc {
     long long off;  // byte offset of the blob in the stream (16-byte aligned)
     int bytes;      // blob size (multiple of 16)
@@ -135,6 +145,26 @@ cudaError_t launch_iota1(int cplx, int n, void *d, cudaStream_t s);
 bool staged_supported(int cplx, int lanes_per_row, int chains_per_lane, int64_t K, int blob_max);
 cudaError_t launch_sweep_staged(const SweepArgs &a, int lanes_per_row, int slices, cudaStream_t s);
 int staged_threads();
+// The grid-wide sweep (sweep_grid.cu): one cooperative launch of grid_ctas()
+// CTAs; a warp takes a (row, 32 x V chain) item, all CTAs share every dependency
+// level, a grid barrier ends each level.  Real matrices with 4 chains per lane
+// or complex with 2, K a multiple of that.  The two state buffers of z (and of
+// w) are one allocation: z[1] = z[0] + n K / V vectors.
+struct GridArgs {
+    const GridRow *rows;       // [n + 1] by position; .row holds i * K / V (the row's first vector)
+    const void *zent[2];       // EntR / EntC of C by position, for the cycles that start from state
+    const void *went[2];       // buffer 0 / 1; .col holds the gathered vector's index from z[0] / w[0]
+    const void *cst;           // CstR / CstC by position
+    const int *lev_ptr;        // [nlev + 1]: first position of each level
+    int nlev;
+    int nblk;                  // chain blocks per row: ceil(K / (32 V))
+    uint32_t nkv;              // vectors per state buffer: n K / V
+    unsigned *bar;             // barrier arrivals (zeroed by the launcher before each launch)
+};
+// threads: 384 or 512 (one CTA per SM)
+bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads);
+int grid_ctas(int cplx, int threads);  // CTAs resident at once on the device; 0: not launchable
+cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, cudaStream_t s);
 // Block partition (Sec. 4): for every pair (r, s) of rows of one diagonal block
 // (entry e: rows ent_r[e], ent_s[e] of the state) and every chain group g (chains
 // gch[g] .. gch[g+1]-1): acc[g][e] += sum over the group's chains of z_r conj(w_s), FP64.

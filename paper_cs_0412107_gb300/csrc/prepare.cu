@@ -191,6 +191,40 @@ mcinv_status prepare_matrix(int64_t n, const int64_t *row_ptr, const int32_t *co
         }
         meta[d.items] = RowMeta{-1, zo, wo, 0};
     }
+    // ---- the flat form (GridRow records) for the grid-wide sweep
+    {
+        std::vector<GridRow> grow(n + 1);
+        size_t tz = 0, tw = 0;
+        for (int64_t p = 0; p < n; ++p) {
+            tz += zdeg(perm[p]);
+            tw += wdeg(perm[p]);
+        }
+        std::vector<uint8_t> gz(std::max<size_t>(tz, 1) * ent_sz, 0), gw(std::max<size_t>(tw, 1) * ent_sz, 0);
+        int zb = 0, wb = 0;
+        for (int64_t p = 0; p < n; ++p) {
+            const int64_t i = perm[p];
+            const int np = pieces_of(i);
+            const int lg = np == 1 ? 0 : np == 2 ? 1 : 2;
+            const int dz = (int)zdeg(i), dw = (int)wdeg(i);
+            if (dz > GRID_DEG_MAX || dw > GRID_DEG_MAX)
+                return prep_fail(err, MCINV_E_UNSUPPORTED, "row %lld has more than %d off-diagonal entries", (long long)i, GRID_DEG_MAX);
+            grow[p] = GridRow{(int)i, zb, wb, lg | (dz << 2) | (dw << 17)};
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                if (col[e] == i) continue;
+                if (!cplx) ((EntR *)gz.data())[zb++] = EntR{col[e], (float)val[e]};
+                else ((EntC *)gz.data())[zb++] = EntC{col[e], (float)val[2 * e], (float)val[2 * e + 1], 0};
+            }
+            for (int64_t e = wcount[i]; e < wcount[i + 1]; ++e) {
+                if (!cplx) ((EntR *)gw.data())[wb++] = EntR{wcol[e], (float)wval[e]};
+                else ((EntC *)gw.data())[wb++] = EntC{wcol[e], (float)wval[2 * e], (float)wval[2 * e + 1], 0};
+            }
+        }
+        grow[n] = GridRow{-1, zb, wb, 0};
+        P.grow = std::move(grow);
+        P.gzent = std::move(gz);
+        P.gwent = std::move(gw);
+        P.lev_ptr = lev_ptr;
+    }
     std::vector<int32_t> pos(n);
     for (int64_t p = 0; p < n; ++p) pos[perm[p]] = (int32_t)p;
     std::vector<double> diag_pos((size_t)n * NV);

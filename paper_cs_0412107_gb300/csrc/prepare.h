@@ -19,6 +19,12 @@ struct Prepared {
     std::vector<uint8_t> stream;          // chunk blobs (constants left zero: filled on the GPU)
     std::vector<long long> cst_at;        // byte offset of each position's constants in the stream
     std::vector<double> diag_pos;         // c_ii by position (re,im for complex)
+    // the flat form of the grid-wide sweep: GridRow by position (n + 1 records),
+    // the entries of C and of C^dagger by position (EntR / EntC bytes), and the
+    // first position of every dependency level (nlev + 1)
+    std::vector<GridRow> grow;
+    std::vector<uint8_t> gzent, gwent;
+    std::vector<int32_t> lev_ptr;
 };
 
 // Validate C (MCINV_E_ARG / MCINV_E_SINGULAR_DIAG with a message), build C^dagger,

@@ -1,0 +1,411 @@
+// sweep_grid.cu -- the coupled sweep (Eqs. 4 and 5) as one cooperative grid
+// over every SM.
+//
+// The chain-sliced kernel (sweep.cu) gives each slice of 16-128 chains its own
+// CTA or cluster, which walks every row of the matrix for those chains.  Here
+// the unit of work is a (row, chain block) pair, a chain block being the
+// 32 x V chains of one warp (a 512-byte segment of z or w per gathered row),
+// and all CTAs of one cooperative launch share every dependency level:
+//   * warp g keeps one chain block, g mod nblk, for the whole launch and takes
+//     the rows g / nblk, g / nblk + R, g / nblk + 2R, ... of every level
+//     (R = warps / nblk), so everything that depends on the chains (noise
+//     column, diagonal unit, trace lane) is set up once;
+//   * a grid-wide barrier ends every level (rows of a level never read each
+//     other through C or C^dagger; a row reads z_j, j < i, written at an earlier
+//     level from this cycle's buffer and z_j, j > i, from last cycle's buffer,
+//     which is the in-place ascending sweep of Eqs. 4/5);
+//   * each entry holds the gathered vector's index from the base of the two
+//     state buffers for one cycle parity (the host resolves "j < i: this
+//     cycle's buffer" into the index), so a gather is one shuffle, one address
+//     and one 16-byte load;
+//   * the next row's record and entries are loaded while the current row's
+//     gathers are in flight, so the gathers are the only round trip on the path.
+// The arithmetic is that of the chain-sliced kernel in the same order (the
+// pieces of long rows summed as ((p0 + p1) + p2) + p3, explicit round-to-
+// nearest FMAs), so both kernels give the same bits for z, w, the diagonal
+// partials and the BF16 shadows.  Every wait is bounded (2 s of globaltimer);
+// a CTA whose wait expires sets bit 2 of the status word and stops working.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "sweep_core.cuh"
+
+namespace mcinv {
+
+namespace {
+
+// Arrive at the next grid barrier and wait until every CTA of the grid has: the
+// counter was zeroed before the launch and counts arrivals (target = barriers
+// so far x CTAs).  Thread 0 releases the CTA's writes (ordered before it by the
+// CTA barrier) and acquires everyone else's; the closing CTA barrier passes
+// that on to the whole CTA.
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned target, volatile int *abort_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*abort_flag) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        const uint64_t t0 = gtimer();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (gtimer() - t0 > 2000000000ull) {
+                *abort_flag = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int4 ldnc4(const void *p) { return __ldg((const int4 *)p); }
+__device__ __forceinline__ EntR ldg_ent(const EntR *p)
+{
+    const int2 v = __ldg((const int2 *)p);
+    return EntR{v.x, __int_as_float(v.y)};
+}
+__device__ __forceinline__ EntC ldg_ent(const EntC *p)
+{
+    const int4 v = ldnc4(p);
+    return EntC{v.x, __int_as_float(v.y), __int_as_float(v.z), v.w};
+}
+__device__ __forceinline__ CstR ldg_cst(const CstR *p)
+{
+    const float4 v = __ldg((const float4 *)p);
+    return CstR{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ CstC ldg_cst(const CstC *p)
+{
+    const float4 u = __ldg((const float4 *)p), v = __ldg((const float4 *)p + 1);
+    CstC k;
+    k.alpha = make_float2(u.x, u.y);
+    k.beta = make_float2(u.z, u.w);
+    k.inv_d = make_float2(v.x, v.y);
+    k.pad = make_float2(v.z, v.w);
+    return k;
+}
+
+template <typename Ent>
+__device__ __forceinline__ Ent ent_none()
+{
+    Ent e;
+    e.col = 0;
+    if constexpr (sizeof(Ent) == 8) e.val = 0.f;
+    else { e.re = 0.f; e.im = 0.f; e.pad = 0; }
+    return e;
+}
+
+template <typename Ent>
+__device__ __forceinline__ Ent shfl_val(const Ent &m, int src)
+{
+    Ent e;
+    e.col = 0;
+    if constexpr (sizeof(Ent) == 8) {
+        e.val = __shfl_sync(0xffffffffu, m.val, src);
+    } else {
+        e.re = __shfl_sync(0xffffffffu, m.re, src);
+        e.im = __shfl_sync(0xffffffffu, m.im, src);
+        e.pad = 0;
+    }
+    return e;
+}
+
+// Entry e (warp-uniform) of a side in the piece path: the first 32 come from the
+// lanes' registers, later ones (rows of more than 32 entries) from L1/L2;
+// `valid` says e is inside the row.
+template <typename Ent>
+__device__ __forceinline__ uint32_t ent_off(const Ent &m, const Ent *__restrict__ all, int base, int e, bool valid)
+{
+    if (e < 32) return (uint32_t)__shfl_sync(0xffffffffu, m.col, e);
+    return valid ? (uint32_t)__ldg((const int *)&all[base + e]) : 0u;
+}
+template <typename Ent>
+__device__ __forceinline__ Ent ent_val(const Ent &m, const Ent *__restrict__ all, int base, int e, bool valid)
+{
+    if (e < 32) return shfl_val(m, e);
+    return valid ? ldg_ent(&all[base + e]) : ent_none<Ent>();
+}
+
+template <bool CPLX, int V, int NT>
+__global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a, const GridArgs g)
+{
+    using P = Prec<CPLX>;
+    using L = Lane<CPLX, V>;
+    using T = typename L::T;
+    using S = typename L::S;
+    using Ent = typename P::Ent;
+    using Cst = typename P::Cst;
+    constexpr int U1 = 8;  // one batch of a whole row (at most SPLIT_ENTRIES entries a side)
+    constexpr int UP = 4;  // batches of a piece of a long row
+    __shared__ int abort_s;
+    volatile int *abort_flag = &abort_s;
+    if (threadIdx.x == 0) abort_s = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    const int tw = gridDim.x * (NT / 32);
+    const int nblk = g.nblk;
+    const int rstep = tw / nblk;       // warps per chain block
+    const int r0 = gw / nblk;          // this warp's first row of every level
+    const int blk = gw - r0 * nblk;    // and its chain block
+    const bool active = r0 < rstep;
+    const int c0 = (blk * 32 + lane) * V;
+    const bool chain_ok = c0 < a.K;
+    const uint32_t cv = (uint32_t)(c0 / V);  // the lane's vector within a row
+    const int seg = a.seg;
+    const size_t nsz = (size_t)a.n;
+    S *dpart = (S *)a.diag_part + (size_t)(c0 / (seg * V)) * nsz;
+    const bool dlead = ((lane % seg) == 0) && chain_ok && a.diag_part;
+    const uint32_t *noise_col = a.noise ? a.noise + (size_t)(c0 >> 5) * nsz : nullptr;
+    const uint32_t cshift = (uint32_t)(c0 & 31);
+    const GridRow *__restrict__ rows = g.rows;
+    const Cst *__restrict__ cstv = (const Cst *)g.cst;
+    T *const z0 = (T *)a.z[0];
+    T *const w0 = (T *)a.w[0];
+
+    bool diverged = false;
+    unsigned target = 0;
+    const int nlev = g.nlev;
+    for (int cyc = 0; cyc < a.ncyc; ++cyc) {
+        const int cur = a.cur ^ (cyc & 1);
+        const uint32_t zn_off = cur ? 0u : g.nkv;  // this cycle's buffer: the other one
+        const Ent *__restrict__ zent = (const Ent *)(cur ? g.zent[1] : g.zent[0]);
+        const Ent *__restrict__ went = (const Ent *)(cur ? g.went[1] : g.went[0]);
+        const uint32_t *noise = noise_col ? noise_col + (size_t)cyc * a.nw * nsz : nullptr;
+        const int shcol = a.cyc0_in_batch + cyc;
+        float tsum = 0.f;  // this lane's share of the cycle's trace series value
+        for (int l = 0; l < nlev; ++l) {
+            const int lb = __ldg(&g.lev_ptr[l]), le = __ldg(&g.lev_ptr[l + 1]);
+            int p = lb + r0;
+            if (!*abort_flag && active && p < le) {
+                // pipeline: this row's record and entries, the next row's record
+                int4 rec = ldnc4(&rows[p]);
+                Ent mz, mw;
+                {
+                    const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
+                    mz = lane < dz ? ldg_ent(&zent[rec.y + lane]) : ent_none<Ent>();
+                    mw = lane < dw ? ldg_ent(&went[rec.z + lane]) : ent_none<Ent>();
+                }
+                int4 nrec = p + rstep < le ? ldnc4(&rows[p + rstep]) : make_int4(0, 0, 0, 0);
+                for (; p < le; p += rstep) {
+                    // the next row's entries and the one after's record
+                    Ent nz, nw;
+                    const bool more = p + rstep < le;
+                    if (more) {
+                        const int dz = (nrec.w >> 2) & 0x7fff, dw = (nrec.w >> 17) & 0x7fff;
+                        nz = lane < dz ? ldg_ent(&zent[nrec.y + lane]) : ent_none<Ent>();
+                        nw = lane < dw ? ldg_ent(&went[nrec.z + lane]) : ent_none<Ent>();
+                    }
+                    const int4 nnrec = p + 2 * rstep < le ? ldnc4(&rows[p + 2 * rstep]) : make_int4(0, 0, 0, 0);
+
+                    const uint32_t iv = (uint32_t)rec.x;  // the row's first vector: i * K / V
+                    const int lg = rec.w & 3;
+                    const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
+                    // the epilogue's operands (their latency hides behind the gathers)
+                    const Cst k = ldg_cst(&cstv[p]);
+                    const uint32_t bits = (noise && chain_ok) ? __ldg(&noise[p]) >> cshift : 0u;
+                    S dold = P::zero();
+                    if (dlead) dold = dpart[p];
+                    int rp = -1, sp = -1;
+                    if (a.rpos && chain_ok) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
+
+                    T sz = L::zero(), sw = L::zero();
+                    if (lg == 0) {
+                        // a whole row in one batch: every gather before any FMA
+                        T xz[U1], xw[U1];
+#pragma unroll
+                        for (int u = 0; u < U1; ++u) {
+                            const uint32_t oz = (uint32_t)__shfl_sync(0xffffffffu, mz.col, u);
+                            const uint32_t ow = (uint32_t)__shfl_sync(0xffffffffu, mw.col, u);
+                            xz[u] = L::zero();
+                            xw[u] = L::zero();
+                            if (u < dz && chain_ok) xz[u] = __ldcg(&z0[oz + cv]);
+                            if (u < dw && chain_ok) xw[u] = __ldcg(&w0[ow + cv]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U1; ++u) {
+                            if (u < dz) L::fma(sz, shfl_val(mz, u), xz[u]);
+                            if (u < dw) L::fma(sw, shfl_val(mw, u), xw[u]);
+                        }
+                    } else {
+                        // 2 or 4 pieces, each a sequential sum from zero, joined in order
+                        const int np = 1 << lg;
+                        const int cz = (dz + np - 1) >> lg, cw = (dw + np - 1) >> lg;
+#pragma unroll 1
+                        for (int pk = 0; pk < np; ++pk) {
+                            const int zb = min(dz, pk * cz), zeN = min(dz, (pk + 1) * cz);
+                            const int wb = min(dw, pk * cw), weN = min(dw, (pk + 1) * cw);
+                            T pz = L::zero(), pw = L::zero();
+#pragma unroll 1
+                            for (int ez = zb, ew = wb; ez < zeN || ew < weN; ez += UP, ew += UP) {
+                                T xz[UP], xw[UP];
+#pragma unroll
+                                for (int u = 0; u < UP; ++u) {
+                                    const bool vz = ez + u < zeN, vw = ew + u < weN;
+                                    const uint32_t oz = ent_off(mz, zent, rec.y, ez + u, vz);
+                                    const uint32_t ow = ent_off(mw, went, rec.z, ew + u, vw);
+                                    xz[u] = L::zero();
+                                    xw[u] = L::zero();
+                                    if (vz && chain_ok) xz[u] = __ldcg(&z0[oz + cv]);
+                                    if (vw && chain_ok) xw[u] = __ldcg(&w0[ow + cv]);
+                                }
+#pragma unroll
+                                for (int u = 0; u < UP; ++u) {
+                                    const bool vz = ez + u < zeN, vw = ew + u < weN;
+                                    const Ent ez_ = ent_val(mz, zent, rec.y, ez + u, vz);
+                                    const Ent ew_ = ent_val(mw, went, rec.z, ew + u, vw);
+                                    if (vz) L::fma(pz, ez_, xz[u]);
+                                    if (vw) L::fma(pw, ew_, xw[u]);
+                                }
+                            }
+                            if (pk == 0) { sz = pz; sw = pw; }
+                            else { sz = L::add(sz, pz); sw = L::add(sw, pw); }
+                        }
+                    }
+
+                    // Eqs. 4/5 for the lane's V chains, then the z_i conj(w_i) partials
+                    S prod = P::zero();
+                    if (chain_ok) {
+                        const float phi_scale = noise ? 1.f : 0.f;
+                        T zv, wv;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const float phi = phi_scale * (((bits >> v) & 1u) ? -1.f : 1.f);
+                            const S zsc = P::zrow(k, phi, L::get(sz, v));
+                            const S wsc = P::wrow(k, phi, L::get(sw, v));
+                            L::set(zv, v, zsc);
+                            L::set(wv, v, wsc);
+                            diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
+                            prod = P::add(prod, P::mulconj(zsc, wsc));
+                        }
+                        if (a.tq) {
+                            float re;
+                            if constexpr (CPLX) re = prod.x;
+                            else re = prod;
+                            tsum = __fmaf_rn(__ldg(&a.tq[p]), re, tsum);
+                        }
+                        z0[zn_off + iv + cv] = zv;
+                        w0[zn_off + iv + cv] = wv;
+                        if (rp >= 0 || sp >= 0) {
+                            const size_t o = (size_t)shcol * a.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                            constexpr int NF = L::NF;
+                            if (rp >= 0) store_bf16<NF>(a.zsh + (size_t)rp * a.ldsh + o, L::f(zv));
+                            if (sp >= 0) {
+                                if constexpr (!CPLX) {
+                                    store_bf16<NF>(a.wsh + (size_t)sp * a.ldsh + o, L::f(wv));
+                                } else {
+                                    // rows 2s = [wr, wi] and 2s+1 = [-wi, wr]: one real
+                                    // contraction gives Re and Im of z conj(w) interleaved
+                                    uint16_t *wr0 = a.wsh + (size_t)(2 * sp) * a.ldsh + o;
+                                    float f0[2 * V], f1[2 * V];
+#pragma unroll
+                                    for (int v = 0; v < V; ++v) {
+                                        const S x = L::get(wv, v);
+                                        f0[2 * v] = x.x;
+                                        f0[2 * v + 1] = x.y;
+                                        f1[2 * v] = -x.y;
+                                        f1[2 * v + 1] = x.x;
+                                    }
+                                    store_bf16<2 * V>(wr0, f0);
+                                    store_bf16<2 * V>(wr0 + a.ldsh, f1);
+                                }
+                            }
+                        }
+                    }
+                    if (a.diag_part) {
+                        // the unit's sum over its seg lanes; the leader adds it to the
+                        // running partial
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1)
+                            if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
+                        if (dlead) dpart[p] = P::add(dold, prod);
+                    }
+                    if (more) { rec = nrec; mz = nz; mw = nw; }
+                    nrec = nnrec;
+                }
+            }
+            // the level's rows are written before any CTA reads them (none after the last)
+            if (!(cyc == a.ncyc - 1 && l == nlev - 1)) {
+                target += gridDim.x;
+                grid_barrier(g.bar, target, abort_flag);
+            }
+        }
+        if (a.tpart && !*abort_flag) {
+            // this warp's partial of the cycle's trace series, reduced in a fixed order
+            float v = tsum;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) a.tpart[((size_t)cyc * gridDim.x + blockIdx.x) * (NT / 32) + (threadIdx.x >> 5)] = v;
+        }
+    }
+    if (diverged) atomicOr(a.status, 1);
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(a.status, 4);
+}
+
+template <bool CPLX, int V, int NT>
+cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3((unsigned)NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cc_sweep_grid_kernel<CPLX, V, NT>, a, g);
+}
+
+template <bool CPLX, int V, int NT>
+int grid_blocks_per_sm()
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_sweep_grid_kernel<CPLX, V, NT>, NT, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
+}  // namespace
+
+bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads)
+{
+    const int v = cplx ? 2 : 4;
+    return chains_per_lane == v && K % v == 0 && (threads == 384 || threads == 512);
+}
+
+int grid_ctas(int cplx, int threads)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (threads == 384) per_sm = cplx ? grid_blocks_per_sm<true, 2, 384>() : grid_blocks_per_sm<false, 4, 384>();
+    else if (threads == 512) per_sm = cplx ? grid_blocks_per_sm<true, 2, 512>() : grid_blocks_per_sm<false, 4, 512>();
+    return per_sm * sms;
+}
+
+cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, cudaStream_t s)
+{
+    if (ctas < 1 || (long long)ctas * (threads / 32) < g.nblk) return cudaErrorInvalidConfiguration;
+    // rows of a level plus two prefetch strides stay in int; state indices in uint32
+    if ((long long)a.n + 2LL * ctas * (threads / 32) >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32))
+        return cudaErrorInvalidValue;
+    // the barrier counter starts at zero in every launch
+    cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (threads == 384) return cplx ? launch_grid_v<true, 2, 384>(a, g, ctas, s) : launch_grid_v<false, 4, 384>(a, g, ctas, s);
+    if (threads == 512) return cplx ? launch_grid_v<true, 2, 512>(a, g, ctas, s) : launch_grid_v<false, 4, 512>(a, g, ctas, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mcinv

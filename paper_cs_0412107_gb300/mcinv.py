@@ -29,6 +29,7 @@ MCINV_F_NO_DIAG = 1
 MCINV_F_AUTOTUNE = 2
 MCINV_F_COLOR_ORDER = 4
 MCINV_F_STAGED = 8
+MCINV_F_GRID = 16
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
@@ -73,7 +74,7 @@ class mcinv_info_t(ctypes.Structure):
                 ("batch_cycles", ctypes.c_int32), ("acc", ctypes.c_int32),
                 ("cycle", ctypes.c_int64), ("samples", ctypes.c_int64),
                 ("block_batches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("sweep_kernel", ctypes.c_int32), ("grid_ctas", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -41,7 +41,9 @@ def test_options_layout_matches_header(L):
     # fields, 2 x 4-byte fields
     assert ctypes.sizeof(mcinv.mcinv_options) == 104
     assert mcinv.mcinv_options.stream.offset == 56
-    assert ctypes.sizeof(mcinv.mcinv_info_t) == 104
+    # mcinv_info_t: 3 x 8, 10 x 4, 5 x 8, then sweep_kernel and grid_ctas (2 x 4)
+    assert ctypes.sizeof(mcinv.mcinv_info_t) == 112
+    assert mcinv.mcinv_info_t.sweep_kernel.offset == 104
 
 
 def _create(n, rp, col, val, **kw):
