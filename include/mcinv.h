@@ -108,6 +108,10 @@ typedef struct {
                               (default) or 512, chains_per_cta and ctas_per_slice are ignored
                               (MCINV_E_UNSUPPORTED otherwise).  MCINV_F_AUTOTUNE without this flag
                               times it beside the chain-sliced shapes. */
+#define MCINV_F_GRID_BULK 32 /* with MCINV_F_GRID: each warp stages the gathers of rows with at most
+                              8 entries a side in shared memory with bulk asynchronous copies, two
+                              rows in flight (384 threads per CTA); longer rows keep register
+                              gathers.  Same values, bit for bit. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.
@@ -270,7 +274,8 @@ typedef struct {
     int64_t block_batches;   /* batches folded into the block estimate */
     int64_t kernel_launches; /* kernels this handle has launched */
     int64_t device_bytes;    /* device memory held by the handle */
-    int32_t sweep_kernel;    /* 0: chain-sliced (registers), 1: staged, 2: grid-wide (MCINV_F_GRID) */
+    int32_t sweep_kernel;    /* 0: chain-sliced (registers), 1: staged, 2: grid-wide (MCINV_F_GRID),
+                                3: grid-wide with bulk-staged gathers (MCINV_F_GRID_BULK) */
     int32_t grid_ctas;       /* CTAs of the grid-wide sweep (0 for the others) */
 } mcinv_info_t;
 

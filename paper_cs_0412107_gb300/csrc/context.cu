@@ -29,6 +29,7 @@ struct mcinv_ctx {
     int W = 0, V = 1, LPR = 1, Q = 1, threads = 0, slices = 0, G = 0, B = 0, acc = 0, flags = 0;
     bool staged = false;  // the staged sweep kernel (sweep_staged.cu) instead of the register one
     bool grid = false;    // the grid-wide sweep kernel (sweep_grid.cu)
+    bool gbulk = false;   // its variant that stages the gathers with bulk copies
     int gctas = 0;        // its CTAs (all resident at once)
     uint64_t seed = 0;
     int64_t chain_base = 0;
@@ -230,7 +231,7 @@ static int sweep_warps(const mcinv_ctx *h) { return h->threads / 32; }
 
 static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 {
-    if (h->grid) return launch_sweep_grid(a, grid_args(h), h->cplx, h->gctas, h->threads, h->stream);
+    if (h->grid) return launch_sweep_grid(a, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
     if (h->staged) return launch_sweep_staged(a, h->LPR, h->slices, h->stream);
     return launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream);
 }
@@ -243,6 +244,7 @@ struct TunedShape {
     int W, V, LPR, Q, T;
     bool staged;
     bool grid = false;
+    bool gbulk = false;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -257,7 +259,8 @@ static mcinv_status autotune(mcinv_ctx *h)
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->grid = it->second.grid;
-            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads);
+            h->gbulk = it->second.gbulk;
+            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads, h->gbulk);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -270,7 +273,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -325,12 +328,15 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int T = 384; T <= 512; T += 128) {
-        const int ctas = grid_ctas(h->cplx, T);
-        if (!grid_supported(h->cplx, vmax, h->K, T) || ctas < 1) continue;
+    for (int variant = 0; variant < 3; ++variant) {
+        const int T = variant == 1 ? 512 : 384;
+        const bool bulk = variant == 2;
+        const int ctas = grid_ctas(h->cplx, T, bulk);
+        if (!grid_supported(h->cplx, vmax, h->K, T) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
-        const bool sG = h->grid;
+        const bool sG = h->grid, sB = h->gbulk;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
+        h->gbulk = bulk;
         h->slices = (int)((h->K + h->W - 1) / h->W);
         SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
         float ms = 1e30f;
@@ -343,14 +349,16 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
         if (e != cudaSuccess) cudaGetLastError();
         h->launches += 2;
-        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true}; }
+        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk}; }
         h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS; h->gctas = sC; h->grid = sG;
+        h->gbulk = sB;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T; h->staged = best.staged;
     h->grid = best.grid;
-    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads) : 0;
+    h->gbulk = best.gbulk;
+    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads, h->gbulk) : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -512,8 +520,9 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     }
     if (h->flags & MCINV_F_GRID) {
         const int vmax = cplx ? 2 : 4;
+        const bool bulk = (h->flags & MCINV_F_GRID_BULK) != 0;
         const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
-        const int ctas = grid_supported(cplx, vmax, opt.K, T) ? grid_ctas(cplx, T) : 0;
+        const int ctas = grid_supported(cplx, vmax, opt.K, T) && (!bulk || T == 384) ? grid_ctas(cplx, T, bulk) : 0;
         if (h->staged || ctas < 1) {
             fail(h, MCINV_E_UNSUPPORTED,
                  "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA, a resident CTA per SM "
@@ -521,6 +530,7 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
             return bail(MCINV_E_UNSUPPORTED);
         }
         h->grid = true;
+        h->gbulk = bulk;
         h->gctas = ctas;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T;
         h->slices = (int)((opt.K + h->W - 1) / h->W);
@@ -1271,7 +1281,7 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
     info->kernel_launches = h->launches; info->device_bytes = h->bytes;
-    info->sweep_kernel = h->grid ? 2 : h->staged ? 1 : 0;
+    info->sweep_kernel = h->grid ? (h->gbulk ? 3 : 2) : h->staged ? 1 : 0;
     info->grid_ctas = h->grid ? h->gctas : 0;
     return MCINV_OK;
 }

@@ -161,10 +161,13 @@ struct GridArgs {
     uint32_t nkv;              // vectors per state buffer: n K / V
     unsigned *bar;             // barrier arrivals (zeroed by the launcher before each launch)
 };
-// threads: 384 or 512 (one CTA per SM)
+// threads: 384 or 512 with the gathers in registers; bulk: 384 threads whose
+// warps stage the gathers of one-piece rows in shared memory with bulk copies.
+// One CTA per SM.
 bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads);
-int grid_ctas(int cplx, int threads);  // CTAs resident at once on the device; 0: not launchable
-cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, cudaStream_t s);
+int grid_ctas(int cplx, int threads, bool bulk);  // CTAs resident at once on the device; 0: not launchable
+cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,
+                              cudaStream_t s);
 // Block partition (Sec. 4): for every pair (r, s) of rows of one diagonal block
 // (entry e: rows ent_r[e], ent_s[e] of the state) and every chain group g (chains
 // gch[g] .. gch[g+1]-1): acc[g][e] += sum over the group's chains of z_r conj(w_s), FP64.

@@ -30,6 +30,7 @@ MCINV_F_AUTOTUNE = 2
 MCINV_F_COLOR_ORDER = 4
 MCINV_F_STAGED = 8
 MCINV_F_GRID = 16
+MCINV_F_GRID_BULK = 32
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",

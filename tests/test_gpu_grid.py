@@ -14,6 +14,7 @@ from paper_cs_0412107_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 GR = mcinv.MCINV_F_GRID
+GB = mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK
 CO = mcinv.MCINV_F_COLOR_ORDER
 
 
@@ -23,14 +24,14 @@ def _lib():
     mcinv.lib()
 
 
-def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, **kw):
+def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
     W = 64 if c.is_complex else 128
     hg = mcinv.create_from_csr(c, K=K, seed=5, acc=mcinv.MCINV_ACC_FP32_SIMT, threads_per_cta=threads,
-                               flags=flags | GR, **kw)
+                               flags=flags | grid, **kw)
     hr = mcinv.create_from_csr(c, K=K, seed=5, acc=mcinv.MCINV_ACC_FP32_SIMT, chains_per_cta=W, ctas_per_slice=1,
                                threads_per_cta=256, flags=flags, **kw)
     info = mcinv.mcinv_info(hg)
-    assert info["sweep_kernel"] == 2 and info["grid_ctas"] >= 1
+    assert info["sweep_kernel"] == (3 if grid == GB else 2) and info["grid_ctas"] >= 1
     done = 0
     for cyc in cycles:
         for h in (hg, hr):
@@ -43,35 +44,39 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, **kw):
 
 
 @pytest.mark.parametrize("flags", [0, CO])
-@pytest.mark.parametrize("K,threads", [(256, 384), (200, 512), (36, 384)])
-def test_grid_equals_chain_sliced_kernel_real(flags, K, threads):
+@pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 384, GB),
+                                            (200, 384, GB), (36, 384, GB)])
+def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
-    hg, hr = _pair(c, K, flags=flags, threads=threads)
+    hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
+@pytest.mark.parametrize("grid", [GR, GB])
 @pytest.mark.parametrize("flags", [0, CO])
-def test_grid_equals_chain_sliced_kernel_complex(flags):
+def test_grid_equals_chain_sliced_kernel_complex(flags, grid):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
-    hg, hr = _pair(c, 130, flags=flags)
+    hg, hr = _pair(c, 130, flags=flags, grid=grid)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
-def test_grid_equals_chain_sliced_kernel_wilson_dirac():
+@pytest.mark.parametrize("grid", [GR, GB])
+def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid):
     c = wl.wilson_dirac((3, 3, 3, 4), 0.1)  # 4 x 4 spinor hops, 14 nonzeros per row
-    hg, hr = _pair(c, 64, flags=CO, cycles=(3, 12))
+    hg, hr = _pair(c, 64, flags=CO, cycles=(3, 12), grid=grid)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
+@pytest.mark.parametrize("grid", [GR, GB])
 @pytest.mark.parametrize("flags", [0, CO])
-def test_grid_estimates_equal_chain_sliced_kernel(flags):
+def test_grid_estimates_equal_chain_sliced_kernel(flags, grid):
     c = wl.pedigree(3000, 1.2, 7)
     q = wl.q_diag(c.n, 1)
     kw = dict(acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=8, block_rows=np.arange(c.n), block_cols=np.arange(256))
-    hg = mcinv.create_from_csr(c, K=512, seed=2, flags=flags | GR, **kw)
+    hg = mcinv.create_from_csr(c, K=512, seed=2, flags=flags | grid, **kw)
     hr = mcinv.create_from_csr(c, K=512, seed=2, chains_per_cta=128, ctas_per_slice=1, threads_per_cta=256,
                                flags=flags, **kw)
     for h in (hg, hr):
@@ -92,13 +97,14 @@ def test_grid_estimates_equal_chain_sliced_kernel(flags):
         mcinv.mcinv_destroy(h)
 
 
+@pytest.mark.parametrize("grid", [GR, GB])
 @pytest.mark.parametrize("case", ["pedigree", "lattice"])
-def test_grid_follows_the_oracle(case):
+def test_grid_follows_the_oracle(case, grid):
     if case == "pedigree":
         c, K, cyc = wl.pedigree(2000, 1.2, 11), 64, 30
     else:
         c, K, cyc = wl.u1_lattice((12, 12), 0.12, 0.08, seed=4), 34, 40
-    h = mcinv.create_from_csr(c, K=K, seed=8, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=GR)
+    h = mcinv.create_from_csr(c, K=K, seed=8, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=grid)
     mcinv.mcinv_burnin(h, cyc)
     z, w, got = mcinv.mcinv_get_state(h)
     st, _, _ = oracle.run(c, K, seed=8, ncycles=cyc)
@@ -108,10 +114,11 @@ def test_grid_follows_the_oracle(case):
     mcinv.mcinv_destroy(h)
 
 
-def test_grid_many_cycles_in_one_launch():
+@pytest.mark.parametrize("grid", [GR, GB])
+def test_grid_many_cycles_in_one_launch(grid):
     # 64 cycles x 2 levels of grid barriers in one launch, then against the oracle
     c = wl.u1_lattice((8, 8), 0.12, 0.08, seed=6)
-    h = mcinv.create_from_csr(c, K=64, seed=3, acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=64, flags=GR | CO)
+    h = mcinv.create_from_csr(c, K=64, seed=3, acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=64, flags=grid | CO)
     mcinv.mcinv_burnin(h, 64)
     z, w, _ = mcinv.mcinv_get_state(h)
     order, _ = mcinv.mcinv_color_order(c.n, c.row_ptr, c.col)
@@ -132,6 +139,9 @@ def test_grid_rejections():
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
     with pytest.raises(mcinv.McinvError) as e:  # 256 threads
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GR)
+    assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
+    with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 512 threads
+        mcinv.create_from_csr(c, K=64, threads_per_cta=512, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
     with pytest.raises(mcinv.McinvError) as e:  # and the staged kernel
         mcinv.create_from_csr(c, K=64, flags=GR | mcinv.MCINV_F_STAGED, chains_per_cta=32)
