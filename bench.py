@@ -127,16 +127,29 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def traffic_from_profiles(kernel_file, units_per_launch):
+# the sweep kernels (mcinv_info sweep_kernel): name, the sources that define it, and
+# the committed ncu summary of its launch on pedigree50k
+SWEEP_KERNELS = {
+    0: ("cc_sweep_kernel", ("sweep.cu", "sweep_core.cuh", "internal.h"), "cc_sweep_pedigree50k.txt"),
+    1: ("cc_sweep_staged_kernel", ("sweep_staged.cu", "sweep_core.cuh", "internal.h"), None),
+    2: ("cc_sweep_grid_kernel", ("sweep_grid.cu", "sweep_core.cuh", "internal.h"), None),
+    3: ("cc_sweep_grid_kernel (bulk-staged gathers)", ("sweep_grid.cu", "sweep_core.cuh", "internal.h"),
+        "cc_sweep_grid_bulk_pedigree50k.txt"),
+}
+
+
+def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "sweep_core.cuh", "internal.h")):
     """DRAM bytes per launch of the sweep from the committed ncu summary, if the
-    summary was taken on the current source of the kernel and its chunk layout
-    (matching hash of sweep.cu, sweep_core.cuh and internal.h)."""
+    summary was taken on the current source of the kernel and its layout (matching
+    hash of its source files)."""
     import hashlib
+    if kernel_file is None:
+        return None
     p = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(p):
         return None
     src = b"".join(open(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f), "rb").read()
-                   for f in ("sweep.cu", "sweep_core.cuh", "internal.h")
+                   for f in sources
                    if os.path.exists(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f)))
     digest = hashlib.sha256(src).hexdigest()[:16]
     per_unit, ok = None, False
@@ -148,6 +161,30 @@ def traffic_from_profiles(kernel_file, units_per_launch):
     if ok and per_unit is not None:
         return per_unit * units_per_launch
     return None
+
+
+def kernel_flags(args):
+    """The sweep kernel: timed on the matrix by the autotuner (auto), or fixed: the
+    chain-sliced kernel in its default shape, the grid-wide kernel (register
+    gathers, 512 threads) or the grid-wide kernel with bulk-staged gathers."""
+    from paper_cs_0412107_gb300 import mcinv
+    if args.kernel == "auto":
+        return (0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE), {}
+    if args.kernel == "sliced":
+        return 0, {}
+    if args.kernel == "grid":
+        return mcinv.MCINV_F_GRID, {"threads_per_cta": 512}
+    return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK, {}
+
+
+def shape_kw(args):
+    """Explicit slice shape (--W, --threads) or the kernel's own."""
+    kw = dict(kernel_flags(args)[1])
+    if args.W:
+        kw["chains_per_cta"] = args.W
+    if args.threads:
+        kw["threads_per_cta"] = args.threads
+    return kw
 
 
 def order_flag(args):
@@ -173,8 +210,7 @@ def run_mine(args, world, rank, local):
     stream = torch.cuda.current_stream()
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=acc,
                               batch_cycles=args.batch, block_rows=R, block_cols=S,
-                              chains_per_cta=args.W, threads_per_cta=args.threads,
-                              flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
+                              flags=kernel_flags(args)[0] | order_flag(args), **shape_kw(args))
     info0 = mcinv.mcinv_info(h)
     B = info0["batch_cycles"]
     mcinv.mcinv_burnin(h, args.burnin)
@@ -216,6 +252,7 @@ def run_mine(args, world, rank, local):
     achieved = alg_bytes / (sw_ms / sw_launches / 1e3) / 1e9 if sw_launches else None
     compulsory_bytes = 16.0 * units_per_launch  # read + write z and w once
     bl_launches, bl_ms = prof["block"]
+    kname, ksrc, kprof = SWEEP_KERNELS[info0["sweep_kernel"]]
     gemm_flops = 2.0 * csr.n * 512 * K * B  # one contraction per batch
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -225,13 +262,14 @@ def run_mine(args, world, rank, local):
         "config": {"workload": WORKLOAD, "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
                    "cycles_per_step": B, "estimates": "diagonal + C^-1[:, 0:512]",
                    "block_accumulation": "bf16 tensor cores" if acc else "fp32 simt",
+                   "sweep_kernel": kname, "grid_ctas": info0["grid_ctas"],
                    "chains_per_cta": info0["chains_per_cta"], "threads_per_cta": info0["threads_per_cta"], "ctas_per_slice": info0["ctas_per_slice"],
                    "levels": info0["levels"], "sweep_order": args.order,
                    "l2": "inputs larger than L2 (z, w double-buffered: %.0f MB)" % (4 * 4 * csr.n * K / 1e6),
                    "parallelism": f"replicas x{world} (disjoint chains)"},
-        "roofline": {"kernel": "cc_sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm,
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
-                     "traffic": traffic_from_profiles("cc_sweep_pedigree50k.txt", units_per_launch),
+                     "traffic": traffic_from_profiles(kprof, units_per_launch, ksrc),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "bytes_per_unit": alg_bytes / units_per_launch,
@@ -249,7 +287,7 @@ def run_mine(args, world, rank, local):
         # for comparison: same kernels, 80 dependency levels instead of 7
         hn = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=acc,
                                    batch_cycles=args.batch, block_rows=R, block_cols=S,
-                                   flags=0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE)
+                                   flags=kernel_flags(args)[0], **shape_kw(args))
         mcinv.mcinv_burnin(hn, args.burnin)
         for _ in range(args.warmup):
             mcinv.mcinv_sample(hn, B)
@@ -302,7 +340,7 @@ def run_e2e(args, csr, K, acc, rank):
     def job():
         opt = mcinv.mcinv_default_options(K=K, seed=args.seed + 1, chain_base=rank * K, acc=acc,
                                           batch_cycles=args.batch,
-                                          flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
+                                          flags=kernel_flags(args)[0] | order_flag(args), **shape_kw(args))
         opt.stream = mcinv.current_stream()
         Ra = np.ascontiguousarray(R, dtype=np.int64)
         Sa = np.ascontiguousarray(S, dtype=np.int64)
@@ -566,8 +604,7 @@ def run_dirac(args, world, rank, local):
     K = args.chains
     stream = torch.cuda.current_stream()
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
-                              batch_cycles=10, chains_per_cta=args.W, threads_per_cta=args.threads,
-                              flags=(0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE) | order_flag(args))
+                              batch_cycles=10, flags=kernel_flags(args)[0] | order_flag(args), **shape_kw(args))
     info0 = mcinv.mcinv_info(h)
     mcinv.mcinv_set_trace_weights(h, np.ones(csr.n))
     mcinv.mcinv_sync(h)
@@ -614,8 +651,8 @@ def run_dirac(args, world, rank, local):
                    "effective_length": g["ess"], "exact": exact, "z": (g["mean"] - exact) / g["se"],
                    "seconds": ms_max / 1e3},
         "paper_table4": DIRAC_PAPER,
-        "roofline": {"kernel": "cc_sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm if achieved else None, "traffic": None,
+        "roofline": {"kernel": SWEEP_KERNELS[info0["sweep_kernel"]][0], "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None, "traffic": None,
                      "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_unit": 32.0,
                      "bytes": "compulsory (stencil neighbours are reuse)",
                      "gather_inclusive_gbs": gather / (sw_ms / 1e3) / 1e9 if sw_ms else None,
@@ -685,6 +722,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--order", default="colour", choices=["natural", "colour"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk"])
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--lattice-batches", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
