@@ -129,15 +129,30 @@ __device__ __forceinline__ Ent ent_val(const Ent &m, const Ent *__restrict__ all
     return valid ? ldg_ent(&all[base + e]) : ent_none<Ent>();
 }
 
-// The bulk-staged variant keeps, per warp, two stages of NSLOT 512-byte
-// segments in shared memory: while one row's gathers land in one stage (one
-// cp.async.bulk per gathered segment, completing on the stage's mbarrier), the
-// warp computes the previous row from the other.  The gathers then take no
-// registers, and every warp has two rows of gathers in flight.
-constexpr int NSLOT = 2 * SPLIT_ENTRIES;  // segments of a row with one piece (<= 8 a side)
+// The bulk-staged variant gives each warp a ring of RING 512-byte slots in
+// shared memory.  A row's gathered segments go to consecutive slots of the
+// ring (never across its end), one cp.async.bulk each, completing on one of
+// QMAX + 1 mbarriers; up to QMAX rows are in flight while the warp computes the
+// oldest, so the gathers take no registers and a warp keeps about RING segments
+// in flight.  A row of more than RING segments waits for the ring to drain and
+// then runs in rounds of RING segments on a barrier of its own.
+constexpr int RING = 32;                  // slots per warp (a power of two)
+constexpr int QMAX = 3;                   // rows in flight per warp
+constexpr int NBAR = QMAX + 2;            // QMAX + 1 for the ring rows, one for long rows
 constexpr int SEGB = 512;                 // 32 lanes x 16 bytes
 constexpr int BULK_THREADS = 384;
-constexpr size_t BULK_SMEM = (size_t)(BULK_THREADS / 32) * 2 * NSLOT * SEGB + (BULK_THREADS / 32) * 3 * sizeof(uint64_t);
+constexpr size_t BULK_SMEM = (size_t)(BULK_THREADS / 32) * RING * SEGB + (BULK_THREADS / 32) * NBAR * sizeof(uint64_t);
+
+// A row in flight in a warp's ring: its position, first vector i K / V, packed
+// counts, first slot, barrier use number, and the lane's values of its entries
+// (lane e holds entry e of each side; the offsets were used when issued).
+template <bool CPLX>
+struct RingRow {
+    int p, info;
+    uint32_t vslot;  // first slot, counted from the warp's start (slot vslot mod RING)
+    uint32_t iv, use;
+    float zr, zi, wr, wi;
+};
 
 __device__ __forceinline__ void mbar_init1(uint32_t bar)
 {
@@ -251,23 +266,23 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     T *const w0 = (T *)a.w[0];
     // bulk-staged variant: this warp's two stages and their barriers; a segment is
     // the block's vectors of one row (fewer than 32 in a last, partial block)
-    const uint32_t stage0 = smem_addr(gsm) + (uint32_t)(warp * 2 * NSLOT * SEGB);
-    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * 2 * NSLOT * SEGB + warp * 3 * sizeof(uint64_t));
+    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * RING * SEGB);
+    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * RING * SEGB + warp * NBAR * sizeof(uint64_t));
+    const uint32_t bar_long = bar0 + (NBAR - 1) * 8u;
     const uint32_t cvb = (uint32_t)(blk * 32);
     const uint32_t seg_bytes = (uint32_t)min(32, (int)(g.nkv / (uint32_t)a.n) - blk * 32) * 16u;
     if (threadIdx.x == 0) abort_s = 0;
     if (BULK && lane == 0) {
-        mbar_init1(bar0);
-        mbar_init1(bar0 + 8);
-        mbar_init1(bar0 + 16);
+        for (int b = 0; b < NBAR; ++b) mbar_init1(bar0 + 8u * b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     bool diverged = false;
     unsigned target = 0;
-    uint32_t kk = 0;  // short bulk-staged rows of this warp so far: stage kk & 1, phase (kk >> 1) & 1
-    uint32_t kb = 0;  // rounds of long rows so far: phase kb & 1 of the third barrier
+    uint32_t ic = 0;    // ring rows issued by this warp: row c waits on barrier c % (QMAX + 1), phase (c / (QMAX + 1)) & 1
+    uint32_t kb = 0;    // rounds of long rows so far: phase kb & 1 of bar_long
+    uint32_t vhead = 0; // the ring's next free slot, counted from the warp's start
     const int nlev = g.nlev;
     for (int cyc = 0; cyc < a.ncyc; ++cyc) {
         const int cur = a.cur ^ (cyc & 1);
@@ -411,86 +426,110 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
             }
             finish(p, rec, sz, sw, k, bits, dold, rp, sp);
         };
-        // bulk-staged rows: start the gathers of a one-piece row into stage st
-        auto issue = [&](const int4 &rec, const Ent &mz, const Ent &mw, uint32_t st) {
-            const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
-            const uint32_t bar = bar0 + st * 8u;
-            const uint32_t wo = (uint32_t)__shfl_sync(0xffffffffu, mw.col, (lane - dz) & 31);
-            // every lane is done reading this stage's previous row; order those
-            // generic-proxy reads before the async-proxy writes below
-            __syncwarp();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (lane == 0) mbar_expect(bar, (uint32_t)(dz + dw) * seg_bytes);
-            if (lane < dz + dw) {
-                const T *src = lane < dz ? z0 + (uint32_t)mz.col + cvb : w0 + wo + cvb;
-                bulk_g2s(stage0 + (st * NSLOT + lane) * SEGB, src, seg_bytes, bar);
-            }
-        };
-
         for (int l = 0; l < nlev; ++l) {
             const int lb = __ldg(&g.lev_ptr[l]), le = __ldg(&g.lev_ptr[l + 1]);
             int p = lb + r0;
             if (BULK && !*abort_flag && active && p < le) {
                 // the bulk copies read rows that other CTAs wrote before the grid barrier
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                // Rows of at most NSLOT segments are pipelined through the two stages,
-                // two in flight; a longer row waits for the one in flight, then takes
-                // both stages (all 2 NSLOT slots) per round of gathers.
-                int4 rec = ldnc4(&rows[p]);
-                int4 rnext = p + rstep < le ? ldnc4(&rows[p + rstep]) : make_int4(0, 0, 0, 0);
-                bool have_a = false;  // a short row in flight, number ka of this warp's short rows
-                uint32_t ka = 0;
-                int pa = 0;
-                int4 ra = make_int4(0, 0, 0, 0);
-                Ent az = ent_none<Ent>(), aw = ent_none<Ent>();
-                // compute the row in flight from its stage
-                auto finish_a = [&]() {
-                    const uint32_t st = ka & 1u;
-                    const Cst k = ldg_cst(&cstv[pa]);
-                    const uint32_t bits = (noise && chain_ok) ? __ldg(&noise[pa]) >> cshift : 0u;
-                    S dold = P::zero();
-                    if (dlead) dold = dpart[pa];
-                    int rp = -1, sp = -1;
-                    if (a.rpos && chain_ok) { rp = __ldg(&a.rpos[pa]); sp = __ldg(&a.spos[pa]); }
-                    if (!wait_chunk(bar0 + st * 8u, (ka >> 1) & 1u)) *abort_flag = 1;
-                    const uint32_t sa = stage0 + st * NSLOT * SEGB + lane * 16u;
-                    const int dz = (ra.w >> 2) & 0x7fff, dw = (ra.w >> 17) & 0x7fff;
+                RingRow<CPLX> q0{}, q1{}, q2{};  // rows in flight, oldest first
+                int qn = 0;
+                // the oldest row's epilogue operands, loaded as soon as it becomes the oldest
+                Cst ek{};
+                uint32_t ebits = 0u;
+                S edold = P::zero();
+                int erp = -1, esp = -1;
+                auto load_ep = [&](int pp) {
+                    ek = ldg_cst(&cstv[pp]);
+                    ebits = (noise && chain_ok) ? __ldg(&noise[pp]) >> cshift : 0u;
+                    edold = P::zero();
+                    if (dlead) edold = dpart[pp];
+                    erp = -1;
+                    esp = -1;
+                    if (a.rpos && chain_ok) { erp = __ldg(&a.rpos[pp]); esp = __ldg(&a.spos[pp]); }
+                };
+                // compute the oldest row in flight from its slots, which are then free
+                auto pop = [&]() {
+                    const RingRow<CPLX> r = q0;
+                    const Cst k = ek;
+                    const uint32_t bits = ebits;
+                    const S dold = edold;
+                    const int rp = erp, sp = esp;
+                    q0 = q1;
+                    q1 = q2;
+                    --qn;
+                    if (qn > 0) load_ep(q0.p);
+                    const int dz = (r.info >> 2) & 0x7fff, dw = (r.info >> 17) & 0x7fff;
+                    if (!wait_chunk(bar0 + 8u * (r.use % (QMAX + 1)), (r.use / (QMAX + 1)) & 1u)) *abort_flag = 1;
+                    Ent az, aw;
+                    az.col = 0; aw.col = 0;
+                    if constexpr (CPLX) { az.re = r.zr; az.im = r.zi; aw.re = r.wr; aw.im = r.wi; az.pad = aw.pad = 0; }
+                    else { az.val = r.zr; aw.val = r.wr; }
+                    const uint32_t zb = ring0 + (r.vslot & (RING - 1)) * SEGB + lane * 16u;
+                    const uint32_t wb = zb + (uint32_t)dz * SEGB;
                     T sz = L::zero(), sw = L::zero();
-                    if ((ra.w & 3) == 0) {
+                    if ((r.info & 3) == 0) {
 #pragma unroll
                         for (int u = 0; u < U1; ++u)
-                            if (u < dz) L::fma(sz, shfl_val(az, u), lds_vec<T>(sa + u * SEGB));
+                            if (u < dz) L::fma(sz, shfl_val(az, u), lds_vec<T>(zb + u * SEGB));
 #pragma unroll
                         for (int u = 0; u < U1; ++u)
-                            if (u < dw) L::fma(sw, shfl_val(aw, u), lds_vec<T>(sa + (dz + u) * SEGB));
+                            if (u < dw) L::fma(sw, shfl_val(aw, u), lds_vec<T>(wb + u * SEGB));
                     } else {
-                        PieceSum<L> pzs(dz, ra.w & 3), pws(dw, ra.w & 3);
-                        for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(sa + e * SEGB));
-                        for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(sa + (dz + e) * SEGB));
+                        PieceSum<L> pzs(dz, r.info & 3), pws(dw, r.info & 3);
+                        for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(zb + e * SEGB));
+                        for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(wb + e * SEGB));
                         sz = pzs.total();
                         sw = pws.total();
                     }
-                    finish(pa, ra, sz, sw, k, bits, dold, rp, sp);
-                    have_a = false;
+                    finish(r.p, make_int4((int)r.iv, 0, 0, r.info), sz, sw, k, bits, dold, rp, sp);
                 };
+                int4 rec = ldnc4(&rows[p]);
+                int4 rnext = p + rstep < le ? ldnc4(&rows[p + rstep]) : make_int4(0, 0, 0, 0);
                 for (; p < le; p += rstep) {
                     Ent mz, mw;
                     load_ents(rec, mz, mw);
                     const int4 rnn = p + 2 * rstep < le ? ldnc4(&rows[p + 2 * rstep]) : make_int4(0, 0, 0, 0);
                     const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
-                    if (dz + dw <= NSLOT) {
-                        // start this row's gathers, then finish the one in flight
-                        const uint32_t kn = kk++;
-                        issue(rec, mz, mw, kn & 1u);
-                        if (have_a) finish_a();
-                        have_a = true;
-                        ka = kn;
-                        pa = p;
-                        ra = rec;
-                        az = mz;
-                        aw = mw;
+                    const int nseg = dz + dw;
+                    if (nseg <= RING) {
+                        // the row's slots, not across the ring's end; wait for room and a barrier
+                        uint32_t v = vhead;
+                        if ((v & (RING - 1)) + nseg > RING) v = (v + RING - 1) & ~(uint32_t)(RING - 1);
+                        while (qn == QMAX || (qn > 0 && v + nseg - q0.vslot > (uint32_t)RING)) pop();
+                        const uint32_t bar = bar0 + 8u * (ic % (QMAX + 1));
+                        const uint32_t wo = (uint32_t)__shfl_sync(0xffffffffu, mw.col, (lane - dz) & 31);
+                        // every lane is done reading the slots freed above; order those
+                        // generic-proxy reads before the async-proxy writes below
+                        __syncwarp();
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        if (lane == 0) mbar_expect(bar, (uint32_t)nseg * seg_bytes);
+                        if (lane < nseg) {
+                            const T *src = lane < dz ? z0 + (uint32_t)mz.col + cvb : w0 + wo + cvb;
+                            bulk_g2s(ring0 + ((v & (RING - 1)) + lane) * SEGB, src, seg_bytes, bar);
+                        }
+                        RingRow<CPLX> r;
+                        r.p = p;
+                        r.info = rec.w;
+                        r.vslot = v;
+                        r.iv = (uint32_t)rec.x;
+                        r.use = ic;
+                        if constexpr (CPLX) { r.zr = mz.re; r.zi = mz.im; r.wr = mw.re; r.wi = mw.im; }
+                        else { r.zr = mz.val; r.zi = 0.f; r.wr = mw.val; r.wi = 0.f; }
+                        if (qn == 0) {
+                            q0 = r;
+                            load_ep(p);
+                        } else if (qn == 1) {
+                            q1 = r;
+                        } else {
+                            q2 = r;
+                        }
+                        ++qn;
+                        ++ic;
+                        vhead = v + nseg;
                     } else {
-                        if (have_a) finish_a();
+                        // a long row: drain the ring, then rounds of up to RING segments
+                        while (qn > 0) pop();
                         const Cst k = ldg_cst(&cstv[p]);
                         const uint32_t bits = (noise && chain_ok) ? __ldg(&noise[p]) >> cshift : 0u;
                         S dold = P::zero();
@@ -499,23 +538,21 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                         if (a.rpos && chain_ok) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
                         PieceSum<L> pzs(dz, rec.w & 3), pws(dw, rec.w & 3);
                         for (int ez = 0, ew = 0; ez < dz || ew < dw;) {
-                            // one round: up to 2 NSLOT segments over both stages
-                            int mzr = min(dz - ez, NSLOT);
-                            const int mwr = min(dw - ew, 2 * NSLOT - mzr);
-                            mzr = min(dz - ez, 2 * NSLOT - mwr);
-                            const uint32_t bar = bar0 + 16u;
+                            int mzr = min(dz - ez, RING / 2);
+                            const int mwr = min(dw - ew, RING - mzr);
+                            mzr = min(dz - ez, RING - mwr);
                             const uint32_t oz = ent_off_lane(mz, zent, rec.y, ez + lane, lane < mzr);
                             const uint32_t ow = ent_off_lane(mw, went, rec.z, ew + lane - mzr, lane >= mzr && lane < mzr + mwr);
                             __syncwarp();
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                            if (lane == 0) mbar_expect(bar, (uint32_t)(mzr + mwr) * seg_bytes);
+                            if (lane == 0) mbar_expect(bar_long, (uint32_t)(mzr + mwr) * seg_bytes);
                             if (lane < mzr + mwr) {
                                 const T *src = lane < mzr ? z0 + oz + cvb : w0 + ow + cvb;
-                                bulk_g2s(stage0 + lane * SEGB, src, seg_bytes, bar);
+                                bulk_g2s(ring0 + lane * SEGB, src, seg_bytes, bar_long);
                             }
-                            if (!wait_chunk(bar, kb & 1u)) *abort_flag = 1;
+                            if (!wait_chunk(bar_long, kb & 1u)) *abort_flag = 1;
                             ++kb;
-                            const uint32_t sa = stage0 + lane * 16u;
+                            const uint32_t sa = ring0 + lane * 16u;
                             for (int e = 0; e < mzr; ++e)
                                 pzs.add(ez + e, ent_val(mz, zent, rec.y, ez + e, true), lds_vec<T>(sa + e * SEGB));
                             for (int e = 0; e < mwr; ++e)
@@ -528,7 +565,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                     rec = rnext;
                     rnext = rnn;
                 }
-                if (have_a) finish_a();
+                while (qn > 0) pop();
             } else if (!BULK && !*abort_flag && active && p < le) {
                 // pipeline: this row's record and entries, the next row's record
                 int4 rec = ldnc4(&rows[p]);
