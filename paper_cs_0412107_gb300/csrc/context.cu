@@ -328,11 +328,12 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 3; ++variant) {
-        const int T = variant == 1 ? 512 : 384;
-        const bool bulk = variant == 2;
+    for (int variant = 0; variant < 5; ++variant) {
+        // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per lane
+        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : 96;
+        const bool bulk = variant >= 2;
         const int ctas = grid_ctas(h->cplx, T, bulk);
-        if (!grid_supported(h->cplx, vmax, h->K, T) || ctas < 1 || h->gnkv == 0) continue;
+        if (!grid_supported(h->cplx, vmax, h->K, T, bulk) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
         const bool sG = h->grid, sB = h->gbulk;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
@@ -522,11 +523,11 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         const int vmax = cplx ? 2 : 4;
         const bool bulk = (h->flags & MCINV_F_GRID_BULK) != 0;
         const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
-        const int ctas = grid_supported(cplx, vmax, opt.K, T) && (!bulk || T == 384) ? grid_ctas(cplx, T, bulk) : 0;
+        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) ? grid_ctas(cplx, T, bulk) : 0;
         if (h->staged || ctas < 1) {
             fail(h, MCINV_E_UNSUPPORTED,
-                 "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA, a resident CTA per SM "
-                 "and not MCINV_F_STAGED", vmax);
+                 "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA (96, 192 or 384 with "
+                 "MCINV_F_GRID_BULK), a resident CTA per SM and not MCINV_F_STAGED", vmax);
             return bail(MCINV_E_UNSUPPORTED);
         }
         h->grid = true;

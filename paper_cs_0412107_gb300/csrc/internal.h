@@ -161,10 +161,11 @@ struct GridArgs {
     uint32_t nkv;              // vectors per state buffer: n K / V
     unsigned *bar;             // barrier arrivals (zeroed by the launcher before each launch)
 };
-// threads: 384 or 512 with the gathers in registers; bulk: 384 threads whose
-// warps stage the gathers of one-piece rows in shared memory with bulk copies.
+// threads: 384 or 512 with the gathers in registers; bulk: the warps stage their
+// gathers in shared memory with bulk copies, 384 threads with 512-byte segments,
+// 192 with 1 KB or 96 with 2 KB (a warp's chain block is 1, 2 or 4 x 32 vectors).
 // One CTA per SM.
-bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads);
+bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk);
 int grid_ctas(int cplx, int threads, bool bulk);  // CTAs resident at once on the device; 0: not launchable
 cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,
                               cudaStream_t s);

@@ -141,7 +141,9 @@ constexpr int QMAX = 3;                   // rows in flight per warp
 constexpr int NBAR = QMAX + 2;            // QMAX + 1 for the ring rows, one for long rows
 constexpr int SEGB = 512;                 // 32 lanes x 16 bytes
 constexpr int BULK_THREADS = 384;
-constexpr size_t BULK_SMEM = (size_t)(BULK_THREADS / 32) * RING * SEGB + (BULK_THREADS / 32) * NBAR * sizeof(uint64_t);
+// per CTA: 12 / G warps, each a ring of RING slots of G x 512 bytes (192 KB in all)
+template <int G>
+constexpr size_t bulk_smem() { return (size_t)(BULK_THREADS / G / 32) * RING * SEGB * G + (BULK_THREADS / G / 32) * NBAR * sizeof(uint64_t); }
 
 // A row in flight in a warp's ring: its position, first vector i K / V, packed
 // counts, first slot, barrier use number, and the lane's values of its entries
@@ -167,6 +169,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
+}
+
+// Wait for a phase of a ring barrier: try_wait with a suspend-time hint, so the
+// warp sleeps in the barrier until the bytes land instead of polling; false
+// after 2 s (globaltimer).
+__device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(20000u)
+            : "memory");
+        if (ok) return true;
+        if (it == 0) t0 = gtimer();
+        else if (gtimer() - t0 > 2000000000ull) return false;
+    }
 }
 
 // one lane's 16 bytes of a staged segment
@@ -199,6 +222,7 @@ struct PieceSum {
     using T = typename L::T;
     T acc, tot;
     int k, next, c, d, np;
+    PieceSum() = default;
     __device__ __forceinline__ PieceSum(int d_, int lg) : k(0), d(d_), np(1 << lg)
     {
         c = (d + np - 1) >> lg;
@@ -227,7 +251,11 @@ struct PieceSum {
     }
 };
 
-template <bool CPLX, int V, int NT, bool BULK>
+// G: vectors per lane (BULK only; 1 with register gathers).  A warp's chain block
+// is G x 32 vectors, i.e. G x 512 contiguous bytes of a row: lane l handles the
+// vectors l, l + 32, ... of the block, each exactly as the G = 1 kernel's lane l
+// of the 32-vector block it falls in (same diagonal units, same bits).
+template <bool CPLX, int V, int NT, bool BULK, int G>
 __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a, const GridArgs g)
 {
     using P = Prec<CPLX>;
@@ -236,8 +264,10 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     using S = typename L::S;
     using Ent = typename P::Ent;
     using Cst = typename P::Cst;
+    static_assert(BULK || G == 1, "register gathers take one vector per lane");
     constexpr int U1 = 8;  // one batch of a whole row (at most SPLIT_ENTRIES entries a side)
     constexpr int UP = 4;  // batches of a piece of a long row
+    constexpr int SEGG = SEGB * G;  // bytes of one gathered segment (one ring slot)
     extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
@@ -246,31 +276,41 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (NT / 32) + warp;
     const int tw = gridDim.x * (NT / 32);
-    const int nblk = g.nblk;
+    const int kv = (int)(g.nkv / (uint32_t)a.n);  // vectors per row
+    const int nblk = (kv + 32 * G - 1) / (32 * G);
     const int rstep = tw / nblk;       // warps per chain block
     const int r0 = gw / nblk;          // this warp's first row of every level
     const int blk = gw - r0 * nblk;    // and its chain block
     const bool active = r0 < rstep;
-    const int c0 = (blk * 32 + lane) * V;
-    const bool chain_ok = c0 < a.K;
-    const uint32_t cv = (uint32_t)(c0 / V);  // the lane's vector within a row
     const int seg = a.seg;
     const size_t nsz = (size_t)a.n;
-    S *dpart = (S *)a.diag_part + (size_t)(c0 / (seg * V)) * nsz;
-    const bool dlead = ((lane % seg) == 0) && chain_ok && a.diag_part;
-    const uint32_t *noise_col = a.noise ? a.noise + (size_t)(c0 >> 5) * nsz : nullptr;
-    const uint32_t cshift = (uint32_t)(c0 & 31);
+    // per vector of the lane: its first chain, the diagonal unit, the noise word
+    int c0[G];
+    bool chain_ok[G], dlead[G];
+    uint32_t cv[G], cshift[G];
+    S *dpart[G];
+    const uint32_t *noise_col[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        cv[q] = (uint32_t)(blk * 32 * G + q * 32 + lane);
+        c0[q] = (int)cv[q] * V;
+        chain_ok[q] = c0[q] < a.K;
+        dpart[q] = (S *)a.diag_part + (size_t)(c0[q] / (seg * V)) * nsz;
+        dlead[q] = ((lane % seg) == 0) && chain_ok[q] && a.diag_part;
+        noise_col[q] = a.noise ? a.noise + (size_t)(c0[q] >> 5) * nsz : nullptr;
+        cshift[q] = (uint32_t)(c0[q] & 31);
+    }
     const GridRow *__restrict__ rows = g.rows;
     const Cst *__restrict__ cstv = (const Cst *)g.cst;
     T *const z0 = (T *)a.z[0];
     T *const w0 = (T *)a.w[0];
-    // bulk-staged variant: this warp's two stages and their barriers; a segment is
-    // the block's vectors of one row (fewer than 32 in a last, partial block)
-    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * RING * SEGB);
-    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * RING * SEGB + warp * NBAR * sizeof(uint64_t));
+    // bulk staging: this warp's ring of RING slots of SEGG bytes and its barriers;
+    // a segment is the block's vectors of one row (fewer in a last, partial block)
+    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * RING * SEGG);
+    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * RING * SEGG + warp * NBAR * sizeof(uint64_t));
     const uint32_t bar_long = bar0 + (NBAR - 1) * 8u;
-    const uint32_t cvb = (uint32_t)(blk * 32);
-    const uint32_t seg_bytes = (uint32_t)min(32, (int)(g.nkv / (uint32_t)a.n) - blk * 32) * 16u;
+    const uint32_t cvb = (uint32_t)(blk * 32 * G);
+    const uint32_t seg_bytes = (uint32_t)min(32 * G, kv - blk * 32 * G) * 16u;
     if (threadIdx.x == 0) abort_s = 0;
     if (BULK && lane == 0) {
         for (int b = 0; b < NBAR; ++b) mbar_init1(bar0 + 8u * b);
@@ -289,7 +329,8 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
         const uint32_t zn_off = cur ? 0u : g.nkv;  // this cycle's buffer: the other one
         const Ent *__restrict__ zent = (const Ent *)(cur ? g.zent[1] : g.zent[0]);
         const Ent *__restrict__ went = (const Ent *)(cur ? g.went[1] : g.went[0]);
-        const uint32_t *noise = noise_col ? noise_col + (size_t)cyc * a.nw * nsz : nullptr;
+        const bool has_noise = a.noise != nullptr;
+        const size_t noise_cyc = (size_t)cyc * a.nw * nsz;
         const int shcol = a.cyc0_in_batch + cyc;
         float tsum = 0.f;  // this lane's share of the cycle's trace series value
 
@@ -299,14 +340,16 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
             mz = lane < dz ? ldg_ent(&zent[rec.y + lane]) : ent_none<Ent>();
             mw = lane < dw ? ldg_ent(&went[rec.z + lane]) : ent_none<Ent>();
         };
-        // Eqs. 4/5 for the lane's V chains from the sums over the row's entries, the
-        // stores, the shadows and the z_i conj(w_i) partials
-        auto finish = [&](int p, const int4 &rec, const T &sz, const T &sw, const Cst &k, uint32_t bits, S dold, int rp,
-                          int sp) {
-            const uint32_t iv = (uint32_t)rec.x;  // the row's first vector: i * K / V
+        auto noise_bits = [&](int q, int p) -> uint32_t {
+            return (has_noise && chain_ok[q]) ? __ldg(&noise_col[q][noise_cyc + p]) >> cshift[q] : 0u;
+        };
+        // Eqs. 4/5 for the V chains of the lane's vector q from the sums over the row's
+        // entries, the stores, the shadows and the z_i conj(w_i) partials
+        auto finish = [&](int q, int p, uint32_t iv, const T &sz, const T &sw, const Cst &k, uint32_t bits, S dold,
+                          int rp, int sp) {
             S prod = P::zero();
-            if (chain_ok) {
-                const float phi_scale = noise ? 1.f : 0.f;
+            if (chain_ok[q]) {
+                const float phi_scale = has_noise ? 1.f : 0.f;
                 T zv, wv;
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -324,10 +367,10 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                     else re = prod;
                     tsum = __fmaf_rn(__ldg(&a.tq[p]), re, tsum);
                 }
-                z0[zn_off + iv + cv] = zv;
-                w0[zn_off + iv + cv] = wv;
+                z0[zn_off + iv + cv[q]] = zv;
+                w0[zn_off + iv + cv[q]] = wv;
                 if (rp >= 0 || sp >= 0) {
-                    const size_t o = (size_t)shcol * a.kp + (size_t)c0 * (CPLX ? 2 : 1);
+                    const size_t o = (size_t)shcol * a.kp + (size_t)c0[q] * (CPLX ? 2 : 1);
                     constexpr int NF = L::NF;
                     if (rp >= 0) store_bf16<NF>(a.zsh + (size_t)rp * a.ldsh + o, L::f(zv));
                     if (sp >= 0) {
@@ -357,22 +400,22 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1)
                     if (o < seg) prod = P::add(prod, P::shfl_xor(prod, o));
-                if (dlead) dpart[p] = P::add(dold, prod);
+                if (dlead[q]) dpart[q][p] = P::add(dold, prod);
             }
         };
-        // one row with register gathers: one batch of every gather before any FMA
-        // when it has one piece, else its 2 or 4 pieces, each a sequential sum from
-        // zero, joined in order
+        // one row with register gathers (G = 1): one batch of every gather before any
+        // FMA when it has one piece, else its 2 or 4 pieces, each a sequential sum
+        // from zero, joined in order
         auto row_regs = [&](int p, const int4 &rec, const Ent &mz, const Ent &mw) {
             const int lg = rec.w & 3;
             const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
             // the epilogue's operands (their latency hides behind the gathers)
             const Cst k = ldg_cst(&cstv[p]);
-            const uint32_t bits = (noise && chain_ok) ? __ldg(&noise[p]) >> cshift : 0u;
+            const uint32_t bits = noise_bits(0, p);
             S dold = P::zero();
-            if (dlead) dold = dpart[p];
+            if (dlead[0]) dold = dpart[0][p];
             int rp = -1, sp = -1;
-            if (a.rpos && chain_ok) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
+            if (a.rpos && chain_ok[0]) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
             T sz = L::zero(), sw = L::zero();
             if (lg == 0) {
                 T xz[U1], xw[U1];
@@ -382,8 +425,8 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                     const uint32_t ow = (uint32_t)__shfl_sync(0xffffffffu, mw.col, u);
                     xz[u] = L::zero();
                     xw[u] = L::zero();
-                    if (u < dz && chain_ok) xz[u] = __ldcg(&z0[oz + cv]);
-                    if (u < dw && chain_ok) xw[u] = __ldcg(&w0[ow + cv]);
+                    if (u < dz && chain_ok[0]) xz[u] = __ldcg(&z0[oz + cv[0]]);
+                    if (u < dw && chain_ok[0]) xw[u] = __ldcg(&w0[ow + cv[0]]);
                 }
 #pragma unroll
                 for (int u = 0; u < U1; ++u) {
@@ -408,8 +451,8 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                             const uint32_t ow = ent_off(mw, went, rec.z, ew + u, vw);
                             xz[u] = L::zero();
                             xw[u] = L::zero();
-                            if (vz && chain_ok) xz[u] = __ldcg(&z0[oz + cv]);
-                            if (vw && chain_ok) xw[u] = __ldcg(&w0[ow + cv]);
+                            if (vz && chain_ok[0]) xz[u] = __ldcg(&z0[oz + cv[0]]);
+                            if (vw && chain_ok[0]) xw[u] = __ldcg(&w0[ow + cv[0]]);
                         }
 #pragma unroll
                         for (int u = 0; u < UP; ++u) {
@@ -424,71 +467,100 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                     else { sz = L::add(sz, pz); sw = L::add(sw, pw); }
                 }
             }
-            finish(p, rec, sz, sw, k, bits, dold, rp, sp);
+            finish(0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp);
         };
+
         for (int l = 0; l < nlev; ++l) {
             const int lb = __ldg(&g.lev_ptr[l]), le = __ldg(&g.lev_ptr[l + 1]);
             int p = lb + r0;
             if (BULK && !*abort_flag && active && p < le) {
                 // the bulk copies read rows that other CTAs wrote before the grid barrier
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                RingRow<CPLX> q0{}, q1{}, q2{};  // rows in flight, oldest first
+                static_assert(QMAX >= 2 && QMAX <= 4, "queue registers");
+                RingRow<CPLX> q0{}, q1{}, q2{}, q3{};  // rows in flight, oldest first
                 int qn = 0;
                 // the oldest row's epilogue operands, loaded as soon as it becomes the oldest
                 Cst ek{};
-                uint32_t ebits = 0u;
-                S edold = P::zero();
+                uint32_t ebits[G];
+                S edold[G];
                 int erp = -1, esp = -1;
                 auto load_ep = [&](int pp) {
                     ek = ldg_cst(&cstv[pp]);
-                    ebits = (noise && chain_ok) ? __ldg(&noise[pp]) >> cshift : 0u;
-                    edold = P::zero();
-                    if (dlead) edold = dpart[pp];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) {
+                        ebits[q] = noise_bits(q, pp);
+                        edold[q] = P::zero();
+                        if (dlead[q]) edold[q] = dpart[q][pp];
+                    }
                     erp = -1;
                     esp = -1;
-                    if (a.rpos && chain_ok) { erp = __ldg(&a.rpos[pp]); esp = __ldg(&a.spos[pp]); }
+                    if (a.rpos) { erp = __ldg(&a.rpos[pp]); esp = __ldg(&a.spos[pp]); }
                 };
+#pragma unroll
+                for (int q = 0; q < G; ++q) { ebits[q] = 0u; edold[q] = P::zero(); }
                 // compute the oldest row in flight from its slots, which are then free
                 auto pop = [&]() {
                     const RingRow<CPLX> r = q0;
                     const Cst k = ek;
-                    const uint32_t bits = ebits;
-                    const S dold = edold;
+                    uint32_t bits[G];
+                    S dold[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) { bits[q] = ebits[q]; dold[q] = edold[q]; }
                     const int rp = erp, sp = esp;
                     q0 = q1;
                     q1 = q2;
+                    q2 = q3;
                     --qn;
                     if (qn > 0) load_ep(q0.p);
                     const int dz = (r.info >> 2) & 0x7fff, dw = (r.info >> 17) & 0x7fff;
-                    if (!wait_chunk(bar0 + 8u * (r.use % (QMAX + 1)), (r.use / (QMAX + 1)) & 1u)) *abort_flag = 1;
+                    if (!ring_wait(bar0 + 8u * (r.use % (QMAX + 1)), (r.use / (QMAX + 1)) & 1u)) *abort_flag = 1;
                     Ent az, aw;
                     az.col = 0; aw.col = 0;
                     if constexpr (CPLX) { az.re = r.zr; az.im = r.zi; aw.re = r.wr; aw.im = r.wi; az.pad = aw.pad = 0; }
                     else { az.val = r.zr; aw.val = r.wr; }
-                    const uint32_t zb = ring0 + (r.vslot & (RING - 1)) * SEGB + lane * 16u;
-                    const uint32_t wb = zb + (uint32_t)dz * SEGB;
-                    T sz = L::zero(), sw = L::zero();
+                    const uint32_t zb = ring0 + (r.vslot & (RING - 1)) * SEGG + lane * 16u;
+                    const uint32_t wb = zb + (uint32_t)dz * SEGG;
+                    T sz[G], sw[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) { sz[q] = L::zero(); sw[q] = L::zero(); }
                     if ((r.info & 3) == 0) {
 #pragma unroll
                         for (int u = 0; u < U1; ++u)
-                            if (u < dz) L::fma(sz, shfl_val(az, u), lds_vec<T>(zb + u * SEGB));
+                            if (u < dz) {
+                                const Ent e = shfl_val(az, u);
+#pragma unroll
+                                for (int q = 0; q < G; ++q) L::fma(sz[q], e, lds_vec<T>(zb + u * SEGG + q * SEGB));
+                            }
 #pragma unroll
                         for (int u = 0; u < U1; ++u)
-                            if (u < dw) L::fma(sw, shfl_val(aw, u), lds_vec<T>(wb + u * SEGB));
+                            if (u < dw) {
+                                const Ent e = shfl_val(aw, u);
+#pragma unroll
+                                for (int q = 0; q < G; ++q) L::fma(sw[q], e, lds_vec<T>(wb + u * SEGG + q * SEGB));
+                            }
                     } else {
-                        PieceSum<L> pzs(dz, r.info & 3), pws(dw, r.info & 3);
-                        for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(zb + e * SEGB));
-                        for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(wb + e * SEGB));
-                        sz = pzs.total();
-                        sw = pws.total();
+#pragma unroll
+                        for (int q = 0; q < G; ++q) {
+                            PieceSum<L> pzs(dz, r.info & 3), pws(dw, r.info & 3);
+                            for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(zb + e * SEGG + q * SEGB));
+                            for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(wb + e * SEGG + q * SEGB));
+                            sz[q] = pzs.total();
+                            sw[q] = pws.total();
+                        }
                     }
-                    finish(r.p, make_int4((int)r.iv, 0, 0, r.info), sz, sw, k, bits, dold, rp, sp);
+#pragma unroll
+                    for (int q = 0; q < G; ++q) finish(q, r.p, r.iv, sz[q], sw[q], k, bits[q], dold[q], rp, sp);
                 };
+                // pipeline: this row's record and entries, the next row's record
                 int4 rec = ldnc4(&rows[p]);
+                Ent mz, mw;
+                load_ents(rec, mz, mw);
                 int4 rnext = p + rstep < le ? ldnc4(&rows[p + rstep]) : make_int4(0, 0, 0, 0);
                 for (; p < le; p += rstep) {
-                    Ent mz, mw;
-                    load_ents(rec, mz, mw);
+                    // the next row's entries and the record of the one after
+                    Ent nz, nw;
+                    const bool more = p + rstep < le;
+                    if (more) load_ents(rnext, nz, nw);
                     const int4 rnn = p + 2 * rstep < le ? ldnc4(&rows[p + 2 * rstep]) : make_int4(0, 0, 0, 0);
                     const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
                     const int nseg = dz + dw;
@@ -506,7 +578,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                         if (lane == 0) mbar_expect(bar, (uint32_t)nseg * seg_bytes);
                         if (lane < nseg) {
                             const T *src = lane < dz ? z0 + (uint32_t)mz.col + cvb : w0 + wo + cvb;
-                            bulk_g2s(ring0 + ((v & (RING - 1)) + lane) * SEGB, src, seg_bytes, bar);
+                            bulk_g2s(ring0 + ((v & (RING - 1)) + lane) * SEGG, src, seg_bytes, bar);
                         }
                         RingRow<CPLX> r;
                         r.p = p;
@@ -521,8 +593,10 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                             load_ep(p);
                         } else if (qn == 1) {
                             q1 = r;
-                        } else {
+                        } else if (QMAX == 3 || qn == 2) {
                             q2 = r;
+                        } else {
+                            q3 = r;
                         }
                         ++qn;
                         ++ic;
@@ -531,12 +605,19 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                         // a long row: drain the ring, then rounds of up to RING segments
                         while (qn > 0) pop();
                         const Cst k = ldg_cst(&cstv[p]);
-                        const uint32_t bits = (noise && chain_ok) ? __ldg(&noise[p]) >> cshift : 0u;
-                        S dold = P::zero();
-                        if (dlead) dold = dpart[p];
+                        uint32_t bits[G];
+                        S dold[G];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) {
+                            bits[q] = noise_bits(q, p);
+                            dold[q] = P::zero();
+                            if (dlead[q]) dold[q] = dpart[q][p];
+                        }
                         int rp = -1, sp = -1;
-                        if (a.rpos && chain_ok) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
-                        PieceSum<L> pzs(dz, rec.w & 3), pws(dw, rec.w & 3);
+                        if (a.rpos) { rp = __ldg(&a.rpos[p]); sp = __ldg(&a.spos[p]); }
+                        PieceSum<L> pzs[G], pws[G];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) { pzs[q] = PieceSum<L>(dz, rec.w & 3); pws[q] = PieceSum<L>(dw, rec.w & 3); }
                         for (int ez = 0, ew = 0; ez < dz || ew < dw;) {
                             int mzr = min(dz - ez, RING / 2);
                             const int mwr = min(dw - ew, RING - mzr);
@@ -548,21 +629,29 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                             if (lane == 0) mbar_expect(bar_long, (uint32_t)(mzr + mwr) * seg_bytes);
                             if (lane < mzr + mwr) {
                                 const T *src = lane < mzr ? z0 + oz + cvb : w0 + ow + cvb;
-                                bulk_g2s(ring0 + lane * SEGB, src, seg_bytes, bar_long);
+                                bulk_g2s(ring0 + lane * SEGG, src, seg_bytes, bar_long);
                             }
-                            if (!wait_chunk(bar_long, kb & 1u)) *abort_flag = 1;
+                            if (!ring_wait(bar_long, kb & 1u)) *abort_flag = 1;
                             ++kb;
                             const uint32_t sa = ring0 + lane * 16u;
-                            for (int e = 0; e < mzr; ++e)
-                                pzs.add(ez + e, ent_val(mz, zent, rec.y, ez + e, true), lds_vec<T>(sa + e * SEGB));
-                            for (int e = 0; e < mwr; ++e)
-                                pws.add(ew + e, ent_val(mw, went, rec.z, ew + e, true), lds_vec<T>(sa + (mzr + e) * SEGB));
+                            for (int e = 0; e < mzr; ++e) {
+                                const Ent en = ent_val(mz, zent, rec.y, ez + e, true);
+#pragma unroll
+                                for (int q = 0; q < G; ++q) pzs[q].add(ez + e, en, lds_vec<T>(sa + e * SEGG + q * SEGB));
+                            }
+                            for (int e = 0; e < mwr; ++e) {
+                                const Ent en = ent_val(mw, went, rec.z, ew + e, true);
+#pragma unroll
+                                for (int q = 0; q < G; ++q) pws[q].add(ew + e, en, lds_vec<T>(sa + (mzr + e) * SEGG + q * SEGB));
+                            }
                             ez += mzr;
                             ew += mwr;
                         }
-                        finish(p, rec, pzs.total(), pws.total(), k, bits, dold, rp, sp);
+#pragma unroll
+                        for (int q = 0; q < G; ++q)
+                            finish(q, p, (uint32_t)rec.x, pzs[q].total(), pws[q].total(), k, bits[q], dold[q], rp, sp);
                     }
-                    rec = rnext;
+                    if (more) { rec = rnext; mz = nz; mw = nw; }
                     rnext = rnn;
                 }
                 while (qn > 0) pop();
@@ -606,11 +695,11 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     }
 }
 
-template <bool CPLX, int V, int NT, bool BULK>
+template <bool CPLX, int V, int NT, bool BULK, int G>
 cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaStream_t s)
 {
-    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK>;
-    const size_t smem = BULK ? BULK_SMEM : 0;
+    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G>;
+    const size_t smem = BULK ? bulk_smem<G>() : 0;
     if (BULK) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -628,11 +717,11 @@ cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaS
     return cudaLaunchKernelEx(&cfg, kern, a, g);
 }
 
-template <bool CPLX, int V, int NT, bool BULK>
+template <bool CPLX, int V, int NT, bool BULK, int G>
 int grid_blocks_per_sm()
 {
-    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK>;
-    const size_t smem = BULK ? BULK_SMEM : 0;
+    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G>;
+    const size_t smem = BULK ? bulk_smem<G>() : 0;
     int per_sm = 0;
     if ((BULK && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) {
@@ -644,10 +733,12 @@ int grid_blocks_per_sm()
 
 }  // namespace
 
-bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads)
+bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk)
 {
     const int v = cplx ? 2 : 4;
-    return chains_per_lane == v && K % v == 0 && (threads == 384 || threads == 512);
+    if (chains_per_lane != v || K % v != 0) return false;
+    if (bulk) return threads == BULK_THREADS || threads == BULK_THREADS / 2 || threads == BULK_THREADS / 4;
+    return threads == 384 || threads == 512;
 }
 
 int grid_ctas(int cplx, int threads, bool bulk)
@@ -660,11 +751,17 @@ int grid_ctas(int cplx, int threads, bool bulk)
     int per_sm = 0;
     if (bulk) {
         if (threads == BULK_THREADS)
-            per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS, true>() : grid_blocks_per_sm<false, 4, BULK_THREADS, true>();
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS, true, 1>() : grid_blocks_per_sm<false, 4, BULK_THREADS, true, 1>();
+        else if (threads == BULK_THREADS / 2)
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS / 2, true, 2>()
+                          : grid_blocks_per_sm<false, 4, BULK_THREADS / 2, true, 2>();
+        else if (threads == BULK_THREADS / 4)
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS / 4, true, 4>()
+                          : grid_blocks_per_sm<false, 4, BULK_THREADS / 4, true, 4>();
     } else if (threads == 384) {
-        per_sm = cplx ? grid_blocks_per_sm<true, 2, 384, false>() : grid_blocks_per_sm<false, 4, 384, false>();
+        per_sm = cplx ? grid_blocks_per_sm<true, 2, 384, false, 1>() : grid_blocks_per_sm<false, 4, 384, false, 1>();
     } else if (threads == 512) {
-        per_sm = cplx ? grid_blocks_per_sm<true, 2, 512, false>() : grid_blocks_per_sm<false, 4, 512, false>();
+        per_sm = cplx ? grid_blocks_per_sm<true, 2, 512, false, 1>() : grid_blocks_per_sm<false, 4, 512, false, 1>();
     }
     return per_sm * sms;
 }
@@ -672,21 +769,29 @@ int grid_ctas(int cplx, int threads, bool bulk)
 cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,
                               cudaStream_t s)
 {
-    const int nt = threads;
-    if (ctas < 1 || (long long)ctas * (nt / 32) < g.nblk) return cudaErrorInvalidConfiguration;
+    if (ctas < 1 || threads < 32) return cudaErrorInvalidConfiguration;
     // rows of a level plus two prefetch strides stay in int; state indices in uint32
-    if ((long long)a.n + 2LL * ctas * (nt / 32) >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32))
+    if ((long long)a.n + 2LL * ctas * (threads / 32) >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32))
         return cudaErrorInvalidValue;
+    const int G = bulk ? BULK_THREADS / threads : 1;
+    if ((long long)ctas * (threads / 32) < (g.nblk + G - 1) / G) return cudaErrorInvalidConfiguration;
     // the barrier counter starts at zero in every launch
     cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     if (bulk) {
-        if (threads != BULK_THREADS) return cudaErrorInvalidValue;
-        return cplx ? launch_grid_v<true, 2, BULK_THREADS, true>(a, g, ctas, s)
-                    : launch_grid_v<false, 4, BULK_THREADS, true>(a, g, ctas, s);
+        if (threads == BULK_THREADS)
+            return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, BULK_THREADS, true, 1>(a, g, ctas, s);
+        if (threads == BULK_THREADS / 2)
+            return cplx ? launch_grid_v<true, 2, BULK_THREADS / 2, true, 2>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, BULK_THREADS / 2, true, 2>(a, g, ctas, s);
+        if (threads == BULK_THREADS / 4)
+            return cplx ? launch_grid_v<true, 2, BULK_THREADS / 4, true, 4>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, BULK_THREADS / 4, true, 4>(a, g, ctas, s);
+        return cudaErrorInvalidValue;
     }
-    if (threads == 384) return cplx ? launch_grid_v<true, 2, 384, false>(a, g, ctas, s) : launch_grid_v<false, 4, 384, false>(a, g, ctas, s);
-    if (threads == 512) return cplx ? launch_grid_v<true, 2, 512, false>(a, g, ctas, s) : launch_grid_v<false, 4, 512, false>(a, g, ctas, s);
+    if (threads == 384) return cplx ? launch_grid_v<true, 2, 384, false, 1>(a, g, ctas, s) : launch_grid_v<false, 4, 384, false, 1>(a, g, ctas, s);
+    if (threads == 512) return cplx ? launch_grid_v<true, 2, 512, false, 1>(a, g, ctas, s) : launch_grid_v<false, 4, 512, false, 1>(a, g, ctas, s);
     return cudaErrorInvalidValue;
 }
 

@@ -45,7 +45,8 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
 
 @pytest.mark.parametrize("flags", [0, CO])
 @pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 384, GB),
-                                            (200, 384, GB), (36, 384, GB)])
+                                            (200, 384, GB), (36, 384, GB), (1024, 192, GB), (520, 192, GB),
+                                            (1024, 96, GB), (900, 96, GB), (36, 96, GB)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -53,30 +54,30 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid", [GR, GB])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
-def test_grid_equals_chain_sliced_kernel_complex(flags, grid):
+def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
-    hg, hr = _pair(c, 130, flags=flags, grid=grid)
+    hg, hr = _pair(c, 130 if threads == 384 else 520, flags=flags, grid=grid, threads=threads)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid", [GR, GB])
-def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid):
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 96)])
+def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
     c = wl.wilson_dirac((3, 3, 3, 4), 0.1)  # 4 x 4 spinor hops, 14 nonzeros per row
-    hg, hr = _pair(c, 64, flags=CO, cycles=(3, 12), grid=grid)
+    hg, hr = _pair(c, 64 if threads == 384 else 320, flags=CO, cycles=(3, 12), grid=grid, threads=threads)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid", [GR, GB])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
-def test_grid_estimates_equal_chain_sliced_kernel(flags, grid):
+def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
     q = wl.q_diag(c.n, 1)
     kw = dict(acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=8, block_rows=np.arange(c.n), block_cols=np.arange(256))
-    hg = mcinv.create_from_csr(c, K=512, seed=2, flags=flags | grid, **kw)
+    hg = mcinv.create_from_csr(c, K=512, seed=2, flags=flags | grid, threads_per_cta=threads, **kw)
     hr = mcinv.create_from_csr(c, K=512, seed=2, chains_per_cta=128, ctas_per_slice=1, threads_per_cta=256,
                                flags=flags, **kw)
     for h in (hg, hr):
@@ -99,7 +100,7 @@ def test_grid_estimates_equal_chain_sliced_kernel(flags, grid):
 
 @pytest.mark.parametrize("grid", [GR, GB])
 @pytest.mark.parametrize("case", ["pedigree", "lattice"])
-def test_grid_follows_the_oracle(case, grid):
+def test_grid_follows_the_oracle(case, grid):  # the default thread count, 384
     if case == "pedigree":
         c, K, cyc = wl.pedigree(2000, 1.2, 11), 64, 30
     else:
@@ -140,7 +141,7 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # 256 threads
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GR)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
-    with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 512 threads
+    with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 512 threads (96, 192 or 384)
         mcinv.create_from_csr(c, K=64, threads_per_cta=512, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
     with pytest.raises(mcinv.McinvError) as e:  # and the staged kernel
