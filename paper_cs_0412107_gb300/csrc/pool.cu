@@ -10,7 +10,11 @@
 // (burn-in or sampling by its own schedule) with a fixed sequence of
 // persistent kernels that read their work from device tables:
 //   noise  : (slot, 128-row block) entries -> Philox noise planes
-//   sweep  : (slot, chain slice) work items pulled from a device queue
+//   sweep  : (slot, chain slice) work items pulled from a device queue: the
+//            chain-sliced row arithmetic over the chunk stream, or (the ring
+//            form) a CTA per (slot, 128-chain block) whose warps take the rows
+//            of each level with bulk-staged gathers (sweep_ring.cuh), a CTA
+//            barrier between levels
 //   block  : grouped tcgen05 contraction over (slot, 128x256 tile) entries
 //   fold   : block and diagonal FP64 folds over (slot, range) segments
 // so the step is captured once as a CUDA graph and replayed whatever the
@@ -31,6 +35,7 @@
 #include "internal.h"
 #include "prepare.h"
 #include "sweep_core.cuh"
+#include "sweep_ring.cuh"
 #include "tc_gemm.h"
 
 namespace mcinv {
@@ -42,7 +47,15 @@ struct PoolSlotDev {
     const uint8_t *stream;
     const ChunkDesc *chunks;
     const int *perm, *pos;
-    float *z[2], *w[2];
+    float *z[2], *w[2];          // z[1] = z[0] + n K (one allocation), same for w
+    // the flat form for the ring form (see internal.h GridRow): records with
+    // .row = i K / 4, entries per cycle parity (.col: vector index from z[0]),
+    // constants by position, the first position of every level
+    const GridRow *grows;
+    const EntR *gzent[2], *gwent[2];
+    const CstR *gcst;
+    const int *levptr;
+    int nlev;
     uint32_t *noise;    // [B][nw][n] by position
     float *dpart;       // [units][n] by position
     double *dacc;       // [G][n] by row
@@ -220,6 +233,91 @@ __global__ void __launch_bounds__(512, 1) pool_sweep_kernel(const PoolSlotDev *_
     }
 }
 
+// The ring form of the sweep: a CTA of 12 warps takes a (slot, 128-chain block)
+// item from the device queue and runs the slot's cycles of this step; warp w
+// takes the rows lb + w, lb + w + 12, ... of each level with bulk-staged
+// gathers (ring::level_bulk, the same arithmetic), and a CTA barrier ends every
+// level: the whole chain block of the matrix is this CTA's.  The warps' rings,
+// barriers and their phases persist across items.
+constexpr int POOL_RING_THREADS = 384;
+constexpr size_t POOL_RING_SMEM = (size_t)(POOL_RING_THREADS / 32) * ring::RING * ring::SEGB +
+                                  (POOL_RING_THREADS / 32) * ring::NBAR * sizeof(uint64_t);
+
+__global__ void __launch_bounds__(POOL_RING_THREADS, 1) pool_ring_kernel(const PoolSlotDev *__restrict__ slots,
+                                                                        const PoolItem *__restrict__ items,
+                                                                        PoolCounts *cnt, int K, int nw, int seg,
+                                                                        int *status)
+{
+    using namespace ring;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int item_s, abort_s;
+    volatile int *abort_flag = &abort_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NWARP = POOL_RING_THREADS / 32;
+    const uint32_t ring0 = smem_addr(smem) + (uint32_t)(warp * RING * SEGB);
+    const uint32_t bar0 = smem_addr(smem) + (uint32_t)(NWARP * RING * SEGB + warp * NBAR * sizeof(uint64_t));
+    if (lane == 0) {
+        for (int b = 0; b < NBAR; ++b) mbar_init1(bar0 + 8u * b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x == 0) abort_s = 0;
+    __syncthreads();
+    Lanes<false, 4, 1> w;
+    w.init(lane, 0, 1, K, 1, seg, nullptr, nullptr, ring0, bar0);  // the ring; the block is set per item
+    const int kv = K / 4;
+    bool diverged = false;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(&cnt->queue, 1);
+        __syncthreads();
+        const int it = item_s;
+        if (it >= cnt->items || *abort_flag) break;
+        const PoolItem item = items[it];
+        const PoolSlotDev &S = slots[item.slot];
+        const int ncyc = S.nb + S.ns;
+        Mat<false> m;
+        m.rows = S.grows;
+        m.cst = S.gcst;
+        m.z0 = S.z[0];
+        m.w0 = S.w[0];
+        m.has_noise = true;
+        m.zsh = S.zsh;
+        m.wsh = S.wsh;
+        m.ldsh = S.ldsh;
+        m.kp = S.kp;
+        m.tq = nullptr;
+        float tdummy = 0.f;
+        for (int cyc = 0; cyc < ncyc && !*abort_flag; ++cyc) {
+            const bool acc = cyc >= S.nb;
+            // the item's chain block; diagonal partials while sampling
+            w.set_block(item.slice, kv, K, S.n, acc ? (void *)S.dpart : nullptr, S.noise);
+            const int cur = S.cur ^ (cyc & 1);
+            m.zn_off = cur ? 0u : (uint32_t)S.n * (uint32_t)kv;
+            m.zent = cur ? S.gzent[1] : S.gzent[0];
+            m.went = cur ? S.gwent[1] : S.gwent[0];
+            m.noise_cyc = (size_t)cyc * nw * (size_t)S.n;
+            const bool sh = acc && S.inverse;
+            m.rpos = sh ? S.perm : nullptr;  // full inverse: R = S = every row in order
+            m.spos = sh ? S.perm : nullptr;
+            m.shcol = cyc - S.nb;
+            for (int l = 0; l < S.nlev; ++l) {
+                // the last level's state stores (this CTA's) before this level's bulk reads
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                if (!*abort_flag)
+                    level_bulk<false, 4, 1>(w, m, __ldg(&S.levptr[l]) + warp, __ldg(&S.levptr[l + 1]), NWARP, tdummy,
+                                            diverged, abort_flag);
+                __syncthreads();
+            }
+        }
+    }
+    if (diverged) atomicOr(status, 1);
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicOr(status, 4);
+        const uint64_t t0 = gtimer();  // let copies still in flight land before exit
+        while (gtimer() - t0 < 10000000ull) {
+        }
+    }
+}
+
 // Folds after the contraction: block segments add the FP32 batch product to
 // the FP64 sums and batch-mean moments; diagonal segments add the units'
 // partials of each group to the FP64 group sums (by row) and clear them.
@@ -231,11 +329,29 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
         const PoolSeg sg = segs[e];
         const PoolSlotDev &S = slots[sg.slot];
         if (sg.kind == 0) {
-            for (long long k = threadIdx.x; k < sg.count; k += blockDim.x) {
+            // four elements a thread per step (segments start at multiples of 2^16),
+            // explicit round-to-nearest double operations as in the single-matrix fold
+            const long long q4 = sg.count / 4;
+            for (long long k = threadIdx.x; k < q4; k += blockDim.x) {
+                const long long x = sg.begin + 4 * k;
+                const float4 v = *(const float4 *)&S.D[x];
+                const double vs[4] = {(double)v.x, (double)v.y, (double)v.z, (double)v.w};
+                double2 a = *(double2 *)&S.bsum[x], b = *(double2 *)&S.bsum[x + 2];
+                double2 c = *(double2 *)&S.bsq[x], d = *(double2 *)&S.bsq[x + 2];
+                a.x = __dadd_rn(a.x, vs[0]); a.y = __dadd_rn(a.y, vs[1]);
+                b.x = __dadd_rn(b.x, vs[2]); b.y = __dadd_rn(b.y, vs[3]);
+                c.x = __fma_rn(__dmul_rn(vs[0], vs[0]), S.scale_sq, c.x);
+                c.y = __fma_rn(__dmul_rn(vs[1], vs[1]), S.scale_sq, c.y);
+                d.x = __fma_rn(__dmul_rn(vs[2], vs[2]), S.scale_sq, d.x);
+                d.y = __fma_rn(__dmul_rn(vs[3], vs[3]), S.scale_sq, d.y);
+                *(double2 *)&S.bsum[x] = a; *(double2 *)&S.bsum[x + 2] = b;
+                *(double2 *)&S.bsq[x] = c; *(double2 *)&S.bsq[x + 2] = d;
+            }
+            for (long long k = 4 * q4 + threadIdx.x; k < sg.count; k += blockDim.x) {
                 const long long x = sg.begin + k;
                 const double v = S.D[x];
-                S.bsum[x] += v;
-                S.bsq[x] += v * v * S.scale_sq;
+                S.bsum[x] = __dadd_rn(S.bsum[x], v);
+                S.bsq[x] = __fma_rn(__dmul_rn(v, v), S.scale_sq, S.bsq[x]);
             }
         } else {
             const int upg = units / G;
@@ -278,6 +394,13 @@ static cudaError_t launch_pool_sweep(int LPR, int V, const PoolSlotDev *slots, c
                                      int K, int nw, int blob_max, int seg, int *status, int grid, int threads,
                                      cudaStream_t s)
 {
+    if (LPR == 32 && threads == POOL_RING_THREADS) {
+        // the ring form
+        cudaError_t e = cudaFuncSetAttribute(pool_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POOL_RING_SMEM);
+        if (e != cudaSuccess) return e;
+        pool_ring_kernel<<<grid, POOL_RING_THREADS, POOL_RING_SMEM, s>>>(slots, items, cnt, K, nw, seg, status);
+        return cudaGetLastError();
+    }
     switch (LPR) {
     case 1: return launch_pool_sweep_l<1>(V, slots, items, cnt, K, nw, blob_max, seg, status, grid, threads, s);
     case 2: return launch_pool_sweep_l<2>(V, slots, items, cnt, K, nw, blob_max, seg, status, grid, threads, s);
@@ -548,19 +671,29 @@ static void slot_parts(const mcinv_pool_ctx *p, const Prepared &P, int inverse, 
     parts.push_back(P.chunks.size() * sizeof(ChunkDesc));          // 1 chunks
     parts.push_back(n * 4);                                        // 2 perm
     parts.push_back(n * 4);                                        // 3 pos
-    for (int k = 0; k < 4; ++k) parts.push_back(n * K * 4);        // 4..7 z0 z1 w0 w1
-    parts.push_back((size_t)p->B * p->nw * n * 4);                 // 8 noise
-    parts.push_back((size_t)p->units * n * 4);                     // 9 dpart
-    parts.push_back((size_t)p->G * n * 8);                         // 10 dacc
+    parts.push_back(2 * n * K * 4);                                // 4 z (both buffers)
+    parts.push_back(2 * n * K * 4);                                // 5 w (both buffers)
+    parts.push_back((size_t)p->B * p->nw * n * 4);                 // 6 noise
+    parts.push_back((size_t)p->units * n * 4);                     // 7 dpart
+    parts.push_back((size_t)p->G * n * 8);                         // 8 dacc
     if (inverse) {
         const size_t ld = (size_t)p->B * kp;
-        parts.push_back((n + 127) / 128 * 128 * ld * 2);          // 11 zsh
-        parts.push_back((n + 255) / 256 * 256 * ld * 2);          // 12 wsh
-        parts.push_back(n * n * 4);                                // 13 D
-        parts.push_back(n * n * 8);                                // 14 bsum
-        parts.push_back(n * n * 8);                                // 15 bsq
+        parts.push_back((n + 127) / 128 * 128 * ld * 2);          // 9 zsh
+        parts.push_back((n + 255) / 256 * 256 * ld * 2);          // 10 wsh
+        parts.push_back(n * n * 4);                                // 11 D
+        parts.push_back(n * n * 8);                                // 12 bsum
+        parts.push_back(n * n * 8);                                // 13 bsq
     }
+    // the flat form of the ring form (kGridParts parts, last)
+    parts.push_back(P.grow.size() * sizeof(GridRow));              // records
+    parts.push_back(P.gzent.size());                               // C entries, cycles from buffer 0
+    parts.push_back(P.gzent.size());                               // C entries, cycles from buffer 1
+    parts.push_back(P.gwent.size());                               // C^dagger entries, buffer 0
+    parts.push_back(P.gwent.size());                               // C^dagger entries, buffer 1
+    parts.push_back(n * sizeof(CstR));                             // constants by position
+    parts.push_back(P.lev_ptr.size() * 4);                         // level starts
 }
+static constexpr int kGridParts = 7;
 
 extern "C" mcinv_status mcinv_pool_footprint(mcinv_pool_t p, int64_t n, int64_t nnz, int32_t want_inverse, int64_t *bytes)
 {
@@ -568,7 +701,7 @@ extern "C" mcinv_status mcinv_pool_footprint(mcinv_pool_t p, int64_t n, int64_t 
     // an estimate from the shapes alone (the stream is bounded by ~48 B per row + 16 B per entry x 2)
     const size_t K = (size_t)p->K, un = (size_t)n;
     size_t b = un * 48 + (size_t)nnz * 32 + 4096 + 8 * un + 4 * un * K * 4 + (size_t)p->B * p->nw * un * 4 +
-               (size_t)p->units * un * 4 + (size_t)p->G * un * 8;
+               (size_t)p->units * un * 4 + (size_t)p->G * un * 8 + un * 36 + (size_t)nnz * 32 + 8 * 256;
     if (want_inverse) {
         const size_t ld = (size_t)p->B * ((K + 63) / 64 * 64);
         b += (un + 127) / 128 * 128 * ld * 2 + (un + 255) / 256 * 256 * ld * 2 + un * un * 20;
@@ -611,6 +744,8 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
         col = col2.data();
         val = val2.data();
     }
+    if (2.0 * (double)n * (double)(p->K / 4) >= 4294967296.0)
+        return pfail(p, MCINV_E_UNSUPPORTED, "n K too large for the pool's 32-bit state indices");
     mcinv_status st = prepare_matrix(n, row_ptr, col, val, 0, p->blob_max, P, &why);
     if (st != MCINV_OK) return pfail(p, st, "%s", why.c_str());
     if (P.blob_max > p->blob_max) return pfail(p, MCINV_E_UNSUPPORTED, "a row has too many entries for the pool's chunks");
@@ -636,7 +771,37 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     PCUDA(p, cudaMemcpyAsync(at(1), P.chunks.data(), P.chunks.size() * sizeof(ChunkDesc), cudaMemcpyHostToDevice, str));
     PCUDA(p, cudaMemcpyAsync(at(2), P.perm.data(), n * 4, cudaMemcpyHostToDevice, str));
     PCUDA(p, cudaMemcpyAsync(at(3), P.pos.data(), n * 4, cudaMemcpyHostToDevice, str));
-    for (int k = 4; k < (int)parts.size(); ++k) PCUDA(p, cudaMemsetAsync(at(k), 0, parts[k], str));
+    const int gp = (int)parts.size() - kGridParts;  // the flat form's first part
+    for (int k = 4; k < gp; ++k) PCUDA(p, cudaMemsetAsync(at(k), 0, parts[k], str));
+    // the flat form: records (.row = i K / 4), entries for each cycle parity (.col =
+    // vector index of the gathered segment from z[0] / w[0]: this cycle's buffer
+    // for j < i, last cycle's for j > i), level starts
+    const uint32_t kv = (uint32_t)(p->K / 4), nkv = (uint32_t)n * kv;
+    std::vector<GridRow> grow = P.grow;
+    for (int64_t q = 0; q < n; ++q) grow[q].row = (int)((uint32_t)P.grow[q].row * kv);
+    std::vector<uint8_t> gent[4];
+    for (int par = 0; par < 2; ++par) {
+        const uint32_t off_new = par ? 0u : nkv, off_old = par ? nkv : 0u;
+        gent[par] = P.gzent;
+        gent[2 + par] = P.gwent;
+        for (int64_t q = 0; q < n; ++q) {
+            const int i = P.grow[q].row;
+            auto fix = [&](std::vector<uint8_t> &v, int b, int e) {
+                for (int x = b; x < e; ++x) {
+                    int *c = (int *)(v.data() + (size_t)x * sizeof(EntR));
+                    *c = (int)((*c < i ? off_new : off_old) + (uint32_t)*c * kv);
+                }
+            };
+            fix(gent[par], P.grow[q].zb, P.grow[q + 1].zb);
+            fix(gent[2 + par], P.grow[q].wb, P.grow[q + 1].wb);
+        }
+    }
+    PCUDA(p, cudaMemcpyAsync(at(gp), grow.data(), grow.size() * sizeof(GridRow), cudaMemcpyHostToDevice, str));
+    PCUDA(p, cudaMemcpyAsync(at(gp + 1), gent[0].data(), gent[0].size(), cudaMemcpyHostToDevice, str));
+    PCUDA(p, cudaMemcpyAsync(at(gp + 2), gent[1].data(), gent[1].size(), cudaMemcpyHostToDevice, str));
+    PCUDA(p, cudaMemcpyAsync(at(gp + 3), gent[2].data(), gent[2].size(), cudaMemcpyHostToDevice, str));
+    PCUDA(p, cudaMemcpyAsync(at(gp + 4), gent[3].data(), gent[3].size(), cudaMemcpyHostToDevice, str));
+    PCUDA(p, cudaMemcpyAsync(at(gp + 6), P.lev_ptr.data(), P.lev_ptr.size() * 4, cudaMemcpyHostToDevice, str));
     // constants in FP64 on the GPU, written into the stream
     double *d_diag = nullptr;
     long long *d_at = nullptr;
@@ -649,6 +814,11 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     PCUDA(p, cudaMemcpyAsync(d_at, P.cst_at.data(), n * 8, cudaMemcpyHostToDevice, str));
     PCUDA(p, cudaMemcpyAsync(d_bad, &big, 4, cudaMemcpyHostToDevice, str));
     PCUDA(p, launch_constants((int)n, d_diag, 0, at(0), d_at, d_bad, str));
+    // the same constants by position for the ring form
+    std::vector<long long> cat((size_t)n);
+    for (int64_t q = 0; q < n; ++q) cat[q] = (long long)(q * (int64_t)sizeof(CstR));
+    PCUDA(p, cudaMemcpyAsync(d_at, cat.data(), n * 8, cudaMemcpyHostToDevice, str));
+    PCUDA(p, launch_constants((int)n, d_diag, 0, at(gp + 5), d_at, d_bad, str));
     int bad = big;
     PCUDA(p, cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, str));
     PCUDA(p, cudaFreeAsync(d_diag, str));
@@ -675,10 +845,19 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     d.chunks = (const ChunkDesc *)at(1);
     d.perm = (const int *)at(2);
     d.pos = (const int *)at(3);
-    d.z[0] = (float *)at(4); d.z[1] = (float *)at(5); d.w[0] = (float *)at(6); d.w[1] = (float *)at(7);
-    d.noise = (uint32_t *)at(8);
-    d.dpart = (float *)at(9);
-    d.dacc = (double *)at(10);
+    d.z[0] = (float *)at(4); d.z[1] = d.z[0] + (size_t)n * p->K;
+    d.w[0] = (float *)at(5); d.w[1] = d.w[0] + (size_t)n * p->K;
+    d.noise = (uint32_t *)at(6);
+    d.dpart = (float *)at(7);
+    d.dacc = (double *)at(8);
+    d.grows = (const GridRow *)at(gp);
+    d.gzent[0] = (const EntR *)at(gp + 1);
+    d.gzent[1] = (const EntR *)at(gp + 2);
+    d.gwent[0] = (const EntR *)at(gp + 3);
+    d.gwent[1] = (const EntR *)at(gp + 4);
+    d.gcst = (const CstR *)at(gp + 5);
+    d.levptr = (const int *)at(gp + 6);
+    d.nlev = (int)P.nlev;
     d.n = (int)n;
     d.nchunks = s.nchunks;
     d.matrix_id = matrix_id;
@@ -687,11 +866,11 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     d.kp = kp;
     d.ldsh = (long long)p->B * kp;
     if (s.inverse) {
-        d.zsh = (uint16_t *)at(11);
-        d.wsh = (uint16_t *)at(12);
-        d.D = (float *)at(13);
-        d.bsum = (double *)at(14);
-        d.bsq = (double *)at(15);
+        d.zsh = (uint16_t *)at(9);
+        d.wsh = (uint16_t *)at(10);
+        d.D = (float *)at(11);
+        d.bsum = (double *)at(12);
+        d.bsq = (double *)at(13);
         const char *w = nullptr;
         if (!tc_encode_operand(&s.maps[0], d.zsh, (n + 127) / 128 * 128, d.ldsh, d.ldsh, false, &w) ||
             !tc_encode_operand(&s.maps[1], d.wsh, (n + 255) / 256 * 256, d.ldsh, d.ldsh, true, &w)) {
@@ -790,7 +969,8 @@ static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count)
 
 // Time one step per candidate slice shape on the pool's current members (the
 // results are the same whichever shape runs: same arithmetic per chain).
-static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}};
+// {32, 384} is the ring form (a CTA of 12 warps per 128-chain block)
+static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}};
 
 extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
 {

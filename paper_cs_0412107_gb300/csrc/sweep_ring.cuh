@@ -238,6 +238,16 @@ struct Lanes {
     {
         lane = lane_;
         seg = seg_;
+        ring0 = ring0_;
+        bar0 = bar0_;
+        bar_long = bar0 + (NBAR - 1) * 8u;
+        ic = kb = vhead = 0;
+        set_block(blk, kv, K, n, dp, noise);
+    }
+    // the chain block, the diagonal partials and the noise plane (the ring and its
+    // state are kept)
+    __device__ __forceinline__ void set_block(int blk, int kv, int K, int n, void *dp, const uint32_t *noise)
+    {
         diag = dp != nullptr;
 #pragma unroll
         for (int q = 0; q < G; ++q) {
@@ -249,12 +259,8 @@ struct Lanes {
             noise_col[q] = noise ? noise + (size_t)(c0[q] >> 5) * (size_t)n : nullptr;
             cshift[q] = (uint32_t)(c0[q] & 31);
         }
-        ring0 = ring0_;
-        bar0 = bar0_;
-        bar_long = bar0 + (NBAR - 1) * 8u;
         cvb = (uint32_t)(blk * 32 * G);
         seg_bytes = (uint32_t)min(32 * G, kv - blk * 32 * G) * 16u;
-        ic = kb = vhead = 0;
     }
     // the noise word of vector q at position p in the cycle starting noise_cyc words in
     __device__ __forceinline__ uint32_t bits(int q, int p, size_t noise_cyc) const

@@ -160,3 +160,46 @@ def test_pool_colour_order_follows_the_oracle_on_the_permuted_matrices():
         # the inverse's diagonal is the diagonal estimate, in the rows of C (BF16 products)
         assert np.abs(np.diag(inv) - dm).max() < 2e-2 * np.abs(dm).max()
     mcinv.mcinv_pool_destroy(pool)
+
+
+@pytest.mark.parametrize("flags", [0, mcinv.MCINV_F_COLOR_ORDER])
+def test_pool_ring_form_equals_chain_sliced_form(flags):
+    # the ring form (a CTA of 12 warps per 128-chain block, bulk-staged gathers) and the
+    # chain-sliced form compute the same arithmetic: states and estimates bit for bit
+    K, B, burn, samp = 192, 4, 5, 11
+    mats = [wl.random_dominant(n, 4, 1.5, 40 + n) for n in (70, 333, 1200)] + [wl.pedigree(900, 1.2, 5)]
+    res = {}
+    for name, shape in (("ring", dict(chains_per_cta=128, threads_per_cta=384)),
+                        ("sliced", dict(chains_per_cta=32, threads_per_cta=512))):
+        pool = mcinv.mcinv_pool_create(K=K, seed=2, mem_budget=1 << 29, max_slots=8, batch_cycles=B, flags=flags,
+                                       **shape)
+        tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=7 + k, burnin=burn, samples=samp, want_inverse=True)
+                   for k, c in enumerate(mats)]
+        run_until_done(pool, tickets)
+        info = mcinv.mcinv_pool_info(pool)
+        assert info["chains_per_cta"] == shape["chains_per_cta"] and info["threads_per_cta"] == shape["threads_per_cta"]
+        res[name] = [(mcinv.mcinv_pool_get_state(pool, t, c.n),
+                      mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, c.n),
+                      mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)) for c, t in zip(mats, tickets)]
+        mcinv.mcinv_pool_destroy(pool)
+    for (sr, dr, br), (ss, ds, bs) in zip(res["ring"], res["sliced"]):
+        assert np.array_equal(sr[0], ss[0]) and np.array_equal(sr[1], ss[1]) and sr[2] == ss[2]
+        assert np.array_equal(dr[0], ds[0]) and np.array_equal(dr[1], ds[1])
+        assert np.array_equal(br[0], bs[0]) and np.array_equal(br[1], bs[1])
+
+
+def test_pool_ring_form_follows_the_oracle():
+    K, B, burn, samp = 64, 4, 6, 7
+    mats = [wl.random_dominant(n, 4, 1.5, seed) for n, seed in ((64, 1), (517, 3))] + [wl.pedigree(700, 1.2, 2)]
+    pool = mcinv.mcinv_pool_create(K=K, seed=11, mem_budget=1 << 28, max_slots=8, batch_cycles=B,
+                                   chains_per_cta=128, threads_per_cta=384)
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=100 + k, burnin=burn, samples=samp)
+               for k, c in enumerate(mats)]
+    run_until_done(pool, tickets)
+    for k, (c, t) in enumerate(zip(mats, tickets)):
+        z, w, cyc = mcinv.mcinv_pool_get_state(pool, t, c.n)
+        assert cyc == burn + samp
+        st, dacc, _ = oracle.run(c, K, seed=11, matrix=100 + k, ncycles=burn + samp, acc_from=burn)
+        assert rel_err(z, st.z.real) < TOL and rel_err(w, st.w.real) < TOL
+        dm, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, c.n)
+        assert rel_err(dm, dacc.sum(0).real / (K * samp)) < TOL
