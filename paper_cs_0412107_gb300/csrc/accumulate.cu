@@ -124,31 +124,40 @@ cudaError_t launch_block_simt(int cplx, int K, const void *z, const void *w, con
 
 // sum += blk; sq += blk^2 * scale_sq (scale_sq = 1/(K^2 B) makes sq the
 // batch-length-weighted second moment of the batch means); optionally blk = 0.
-// sum += x, sq += x^2 scale for the FP32 batch product x, four elements a thread
-// per step (16-byte loads of the product, 16-byte loads and stores of the sums)
+// sum += x, sq += x^2 scale for the FP32 batch product x, eight elements a
+// thread per step with every load issued before the stores (16-byte accesses)
 // to keep enough bytes in flight; explicit round-to-nearest double operations.
-__device__ __forceinline__ void fold4(const float4 x, double2 *sum, double2 *sq, double scale_sq)
-{
-    const double xs[4] = {(double)x.x, (double)x.y, (double)x.z, (double)x.w};
-    double2 a = sum[0], b = sum[1], c = sq[0], d = sq[1];
-    a.x = __dadd_rn(a.x, xs[0]); a.y = __dadd_rn(a.y, xs[1]);
-    b.x = __dadd_rn(b.x, xs[2]); b.y = __dadd_rn(b.y, xs[3]);
-    c.x = __fma_rn(__dmul_rn(xs[0], xs[0]), scale_sq, c.x); c.y = __fma_rn(__dmul_rn(xs[1], xs[1]), scale_sq, c.y);
-    d.x = __fma_rn(__dmul_rn(xs[2], xs[2]), scale_sq, d.x); d.y = __fma_rn(__dmul_rn(xs[3], xs[3]), scale_sq, d.y);
-    sum[0] = a; sum[1] = b; sq[0] = c; sq[1] = d;
-}
-
 __global__ void block_fold_kernel(long long elems, double scale_sq, float *__restrict__ blk,
                                   double *__restrict__ sum, double *__restrict__ sq, int zero_blk, int vec)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long n4 = vec ? elems / 4 : 0;  // whole quads first when the arrays are 16-byte aligned
-    for (long long e = e0; e < n4; e += stride) {
-        fold4(((const float4 *)blk)[e], (double2 *)sum + 2 * e, (double2 *)sq + 2 * e, scale_sq);
-        if (zero_blk) ((float4 *)blk)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long n8 = vec ? elems / 8 : 0;  // whole octets first when the arrays are 16-byte aligned
+    float4 *__restrict__ D4 = (float4 *)blk;
+    double2 *__restrict__ s2 = (double2 *)sum;
+    double2 *__restrict__ q2 = (double2 *)sq;
+    for (long long e = e0; e < n8; e += stride) {
+        const float4 v0 = D4[2 * e], v1 = D4[2 * e + 1];
+        double2 a[4], c[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) { a[h] = s2[4 * e + h]; c[h] = q2[4 * e + h]; }
+        const double x[8] = {(double)v0.x, (double)v0.y, (double)v0.z, (double)v0.w,
+                             (double)v1.x, (double)v1.y, (double)v1.z, (double)v1.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            a[h].x = __dadd_rn(a[h].x, x[2 * h]);
+            a[h].y = __dadd_rn(a[h].y, x[2 * h + 1]);
+            c[h].x = __fma_rn(__dmul_rn(x[2 * h], x[2 * h]), scale_sq, c[h].x);
+            c[h].y = __fma_rn(__dmul_rn(x[2 * h + 1], x[2 * h + 1]), scale_sq, c[h].y);
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) { s2[4 * e + h] = a[h]; q2[4 * e + h] = c[h]; }
+        if (zero_blk) {
+            D4[2 * e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            D4[2 * e + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
-    for (long long e = 4 * n4 + e0; e < elems; e += stride) {
+    for (long long e = 8 * n8 + e0; e < elems; e += stride) {
         const double x = blk[e];
         sum[e] = __dadd_rn(sum[e], x);
         sq[e] = __fma_rn(__dmul_rn(x, x), scale_sq, sq[e]);
@@ -161,8 +170,8 @@ cudaError_t launch_block_fold(int cplx, long long elems, double scale_sq, float 
 {
     const long long total = elems * (cplx ? 2 : 1);
     const int vec = ((uintptr_t)blk % 16 == 0 && (uintptr_t)sum % 16 == 0 && (uintptr_t)sq % 16 == 0) ? 1 : 0;
-    long long blocks = ((vec ? total / 4 : total) + 255) / 256;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    long long blocks = ((vec ? total / 8 : total) + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
     if (blocks < 1) blocks = 1;
     block_fold_kernel<<<(unsigned)blocks, 256, 0, s>>>(total, scale_sq, blk, sum, sq, zero_blk, vec);
     return cudaGetLastError();

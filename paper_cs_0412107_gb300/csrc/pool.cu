@@ -329,25 +329,32 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
         const PoolSeg sg = segs[e];
         const PoolSlotDev &S = slots[sg.slot];
         if (sg.kind == 0) {
-            // four elements a thread per step (segments start at multiples of 2^16),
-            // explicit round-to-nearest double operations as in the single-matrix fold
-            const long long q4 = sg.count / 4;
-            for (long long k = threadIdx.x; k < q4; k += blockDim.x) {
-                const long long x = sg.begin + 4 * k;
-                const float4 v = *(const float4 *)&S.D[x];
-                const double vs[4] = {(double)v.x, (double)v.y, (double)v.z, (double)v.w};
-                double2 a = *(double2 *)&S.bsum[x], b = *(double2 *)&S.bsum[x + 2];
-                double2 c = *(double2 *)&S.bsq[x], d = *(double2 *)&S.bsq[x + 2];
-                a.x = __dadd_rn(a.x, vs[0]); a.y = __dadd_rn(a.y, vs[1]);
-                b.x = __dadd_rn(b.x, vs[2]); b.y = __dadd_rn(b.y, vs[3]);
-                c.x = __fma_rn(__dmul_rn(vs[0], vs[0]), S.scale_sq, c.x);
-                c.y = __fma_rn(__dmul_rn(vs[1], vs[1]), S.scale_sq, c.y);
-                d.x = __fma_rn(__dmul_rn(vs[2], vs[2]), S.scale_sq, d.x);
-                d.y = __fma_rn(__dmul_rn(vs[3], vs[3]), S.scale_sq, d.y);
-                *(double2 *)&S.bsum[x] = a; *(double2 *)&S.bsum[x + 2] = b;
-                *(double2 *)&S.bsq[x] = c; *(double2 *)&S.bsq[x + 2] = d;
+            // eight elements a thread per step, every load issued before the stores
+            // (segments start at multiples of 2^16), explicit round-to-nearest double
+            // operations as in the single-matrix fold
+            const float4 *__restrict__ D4 = (const float4 *)(S.D + sg.begin);
+            double2 *__restrict__ s2 = (double2 *)(S.bsum + sg.begin);
+            double2 *__restrict__ q2 = (double2 *)(S.bsq + sg.begin);
+            const double sc = S.scale_sq;
+            const long long q8 = sg.count / 8;
+            for (long long k = threadIdx.x; k < q8; k += blockDim.x) {
+                const float4 v0 = D4[2 * k], v1 = D4[2 * k + 1];
+                double2 a[4], c[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) { a[h] = s2[4 * k + h]; c[h] = q2[4 * k + h]; }
+                const double x[8] = {(double)v0.x, (double)v0.y, (double)v0.z, (double)v0.w,
+                                     (double)v1.x, (double)v1.y, (double)v1.z, (double)v1.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    a[h].x = __dadd_rn(a[h].x, x[2 * h]);
+                    a[h].y = __dadd_rn(a[h].y, x[2 * h + 1]);
+                    c[h].x = __fma_rn(__dmul_rn(x[2 * h], x[2 * h]), sc, c[h].x);
+                    c[h].y = __fma_rn(__dmul_rn(x[2 * h + 1], x[2 * h + 1]), sc, c[h].y);
+                }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) { s2[4 * k + h] = a[h]; q2[4 * k + h] = c[h]; }
             }
-            for (long long k = 4 * q4 + threadIdx.x; k < sg.count; k += blockDim.x) {
+            for (long long k = 8 * q8 + threadIdx.x; k < sg.count; k += blockDim.x) {
                 const long long x = sg.begin + k;
                 const double v = S.D[x];
                 S.bsum[x] = __dadd_rn(S.bsum[x], v);
@@ -961,7 +968,7 @@ static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count)
     PCUDA(p, launch_pool_sweep(p->LPR, p->V, p->d_slots, p->d_items, p->d_cnt, (int)p->K, p->nw, p->blob_max, p->seg,
                                p->d_status, p->grid_sweep, p->threads, s));
     PCUDA(p, tc_gemm_grouped_run(p->d_tiles, &p->d_cnt->tiles, p->d_maps, p->d_outs, 152, p->d_status, s));
-    pool_fold_kernel<<<4 * 152, 256, 0, s>>>(p->d_slots, p->d_segs, p->d_cnt, p->units, p->G);
+    pool_fold_kernel<<<8 * 152, 256, 0, s>>>(p->d_slots, p->d_segs, p->d_cnt, p->units, p->G);
     PCUDA(p, cudaGetLastError());
     if (count) p->launches += 4;
     return MCINV_OK;

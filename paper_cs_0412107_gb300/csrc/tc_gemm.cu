@@ -276,8 +276,9 @@ bool encode(CUtensorMap *map, const uint16_t *base, size_t rows, long long ld, i
 // table (matrix, m0, n0); each matrix has its own pair of tensor maps in
 // global memory and its own output.  Warps: 0 = TMA producer, 1 = MMA issuer,
 // 2..5 = epilogue (warp w reads TMEM lanes 32*(w%4) .. +31).  The smem ring's
-// stage/phase counters run on across tiles; tmem_full / tmem_empty hand the
-// single 256-column accumulator between the MMA issuer and the epilogue.
+// stage/phase counters run on across tiles.  Two 256-column accumulators in
+// TMEM alternate between tiles (tmem_full / tmem_empty per accumulator), so
+// the MMAs of one tile run while the epilogue drains the previous one.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_grouped_kernel(const GroupTile *__restrict__ tiles, const int *__restrict__ ntiles_p,
@@ -289,9 +290,9 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *sB = smem + STAGES * A_BYTES;
     uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;
-    uint64_t *tempty = tfull + 1;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
+    uint64_t *tfull = empty + STAGES;  // [2]
+    uint64_t *tempty = tfull + 2;       // [2]
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = *ntiles_p;
@@ -301,14 +302,16 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(tfull), 1);
-        mbar_init(smem_u32(tempty), 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), 4);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(2 * TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
@@ -337,8 +340,10 @@ __global__ void __launch_bounds__(192, 1)
             int kg = 0, tl = 0;
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
                 const int kt_n = outs[tiles[t].slot].ktiles;
-                // the epilogue must have drained the accumulator of the previous tile
-                if (tl > 0 && !mbar_wait(smem_u32(tempty), (uint32_t)(tl - 1) & 1u, abort_flag)) break;
+                const int ab = tl & 1;  // this tile's accumulator
+                const uint32_t acc = tmem + (uint32_t)(ab * TMEM_COLS);
+                // the epilogue must have drained this accumulator (two tiles ago)
+                if (tl >= 2 && !mbar_wait(smem_u32(&tempty[ab]), (uint32_t)((tl >> 1) - 1) & 1u, abort_flag)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool ok = true;
                 for (int kt = 0; kt < kt_n; ++kt, ++kg) {
@@ -350,11 +355,11 @@ __global__ void __launch_bounds__(192, 1)
                     const uint64_t b = sdesc(smem_u32(sB + s * B_BYTES));
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
-                        mma_bf16(tmem, a + 2 * kk, b + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(acc, a + 2 * kk, b + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
                     mma_commit(smem_u32(&empty[s]));
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(tfull));
+                mma_commit(smem_u32(&tfull[ab]));
             }
         }
     } else {
@@ -364,14 +369,15 @@ __global__ void __launch_bounds__(192, 1)
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
             const GroupTile tile = tiles[t];
             const GroupOut o = outs[tile.slot];
-            const bool have = __all_sync(0xffffffffu, mbar_wait(smem_u32(tfull), (uint32_t)tl & 1u, abort_flag));
+            const int ab = tl & 1;
+            const bool have = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[ab]), (uint32_t)(tl >> 1) & 1u, abort_flag));
             if (!have) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = tile.m0 + q * 32 + lane;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld32(tmem + (uint32_t)(ab * TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
                 if (row < o.M) {
                     float *dst = o.D + (size_t)row * o.N + tile.n0 + c0;
                     if (tile.n0 + c0 + 32 <= o.N && (o.N & 3) == 0) {
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty)) : "memory");
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[ab])) : "memory");
         }
     }
     __syncwarp();
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
 }
 
 }  // namespace
