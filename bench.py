@@ -440,6 +440,8 @@ def run_batch(args, world, rank, local):
     # accumulation, launches issued one by one), RMS checked on every 64th matrix
     if args.rms_samples > 0:
         res["time_to_rms"] = time_to_rms(args, mats, burn, K, B, budget, rank)
+    if args.serve_requests <= 0:
+        return res
     # serving: Poisson arrivals at 50% and 90% of the batch throughput (matrices/s)
     rate_max = len(mats) / dt
     serving = {}

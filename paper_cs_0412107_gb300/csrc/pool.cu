@@ -960,13 +960,16 @@ static void build_tables(mcinv_pool_ctx *p, StepTables &T)
         for (int sl = 0; sl < slices; ++sl) T.items.push_back(PoolItem{o.second, sl});
 }
 
-static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count)
+// One step's kernels on stream s; with ev, the sweep is bracketed by ev[0], ev[1].
+static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count, cudaEvent_t *ev = nullptr)
 {
     PCUDA(p, cudaMemsetAsync(&p->d_cnt->queue, 0, sizeof(int), s));
     pool_noise_kernel<<<4 * 152, 128, 0, s>>>(p->d_slots, p->d_rbs, p->d_cnt, p->seed, (uint64_t)p->chain_base, (int)p->K, p->nw);
     PCUDA(p, cudaGetLastError());
+    if (ev) PCUDA(p, cudaEventRecord(ev[0], s));
     PCUDA(p, launch_pool_sweep(p->LPR, p->V, p->d_slots, p->d_items, p->d_cnt, (int)p->K, p->nw, p->blob_max, p->seg,
                                p->d_status, p->grid_sweep, p->threads, s));
+    if (ev) PCUDA(p, cudaEventRecord(ev[1], s));
     PCUDA(p, tc_gemm_grouped_run(p->d_tiles, &p->d_cnt->tiles, p->d_maps, p->d_outs, 152, p->d_status, s));
     pool_fold_kernel<<<8 * 152, 256, 0, s>>>(p->d_slots, p->d_segs, p->d_cnt, p->units, p->G);
     PCUDA(p, cudaGetLastError());
@@ -974,8 +977,10 @@ static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count)
     return MCINV_OK;
 }
 
-// Time one step per candidate slice shape on the pool's current members (the
-// results are the same whichever shape runs: same arithmetic per chain).
+// Time the sweep of one step per candidate shape on the pool's current members
+// (the results are the same whichever shape runs: same arithmetic per chain);
+// the score is the sweep's time per unit of sweep work, so burn-in and sampling
+// steps compare alike.
 // {32, 384} is the ring form (a CTA of 12 warps per 128-chain block)
 static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}};
 
@@ -1046,17 +1051,15 @@ extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
         // shape computes the same values), the fastest per unit of work is kept
         const int k = k_tune;
         p->tune_next++;
-        cudaEvent_t ea, eb;
-        PCUDA(p, cudaEventCreate(&ea));
-        PCUDA(p, cudaEventCreate(&eb));
-        PCUDA(p, cudaEventRecord(ea, s));
-        const mcinv_status st = launch_step(p, s, true);
-        PCUDA(p, cudaEventRecord(eb, s));
-        PCUDA(p, cudaEventSynchronize(eb));
+        cudaEvent_t ev[2];
+        PCUDA(p, cudaEventCreate(&ev[0]));
+        PCUDA(p, cudaEventCreate(&ev[1]));
+        const mcinv_status st = launch_step(p, s, true, ev);
+        PCUDA(p, cudaEventSynchronize(ev[1]));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ea, eb);
-        cudaEventDestroy(ea);
-        cudaEventDestroy(eb);
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
         if (st != MCINV_OK) return st;
         double work = 0;
         for (int si = 0; si < p->max_slots; ++si)
