@@ -112,6 +112,12 @@ typedef struct {
                               8 entries a side in shared memory with bulk asynchronous copies, two
                               rows in flight (384 threads per CTA); longer rows keep register
                               gathers.  Same values, bit for bit. */
+#define MCINV_F_GRID_NOPAIR 64 /* with MCINV_F_GRID_BULK: keep z and w in separate buffers.  Without it,
+                              for a structurally symmetric C (row i of C and of C^dagger name the
+                              same columns) the bulk sweep keeps the state in the pair layout, a
+                              chain block's z and w of a row side by side, so one 1 KB copy
+                              gathers both; readers of the state (mcinv_get_state, the CUDA-core
+                              block accumulation) see the usual layout.  Same values, bit for bit. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.
@@ -275,7 +281,8 @@ typedef struct {
     int64_t kernel_launches; /* kernels this handle has launched */
     int64_t device_bytes;    /* device memory held by the handle */
     int32_t sweep_kernel;    /* 0: chain-sliced (registers), 1: staged, 2: grid-wide (MCINV_F_GRID),
-                                3: grid-wide with bulk-staged gathers (MCINV_F_GRID_BULK) */
+                                3: grid-wide with bulk-staged gathers (MCINV_F_GRID_BULK),
+                                4: the same on the pair layout (structurally symmetric C) */
     int32_t grid_ctas;       /* CTAs of the grid-wide sweep (0 for the others) */
 } mcinv_info_t;
 

@@ -30,6 +30,9 @@ struct mcinv_ctx {
     bool staged = false;  // the staged sweep kernel (sweep_staged.cu) instead of the register one
     bool grid = false;    // the grid-wide sweep kernel (sweep_grid.cu)
     bool gbulk = false;   // its variant that stages the gathers with bulk copies
+    bool gpair = false;   // ... on the pair layout of the state (z and w of a chain block side by side)
+    bool pair_able = false;  // structurally symmetric, the pair form built
+    bool canon_ok = true, pair_ok = false;  // which layout holds the current state
     int gctas = 0;        // its CTAs (all resident at once)
     uint64_t seed = 0;
     int64_t chain_base = 0;
@@ -44,6 +47,12 @@ struct mcinv_ctx {
     GridRow *d_grow = nullptr;
     uint8_t *d_gzent[2] = {nullptr, nullptr}, *d_gwent[2] = {nullptr, nullptr}, *d_gcst = nullptr;
     uint32_t gnkv = 0;
+    // the pair form: records (.row = i x 2 kvp), entries with pair-layout offsets, the
+    // two pair-layout state buffers (n x 2 kvp vectors each, one allocation)
+    GridRow *d_grow_p = nullptr;
+    uint8_t *d_gpzent[2] = {nullptr, nullptr}, *d_gpwent[2] = {nullptr, nullptr};
+    void *d_x = nullptr;
+    uint32_t gpnkv = 0;
     int *d_levptr = nullptr;
     unsigned *d_gbar = nullptr;
     int nchunks = 0, blob_max = 0, seg = 1, units = 0;
@@ -212,10 +221,13 @@ static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumula
 static GridArgs grid_args(mcinv_ctx *h)
 {
     GridArgs g{};
-    g.rows = h->d_grow;
-    g.zent[0] = h->d_gzent[0]; g.zent[1] = h->d_gzent[1];
-    g.went[0] = h->d_gwent[0]; g.went[1] = h->d_gwent[1];
-    g.nkv = h->gnkv;
+    const bool pair = h->gbulk && h->gpair;
+    g.pair = pair ? 1 : 0;
+    g.rows = pair ? h->d_grow_p : h->d_grow;
+    g.zent[0] = pair ? h->d_gpzent[0] : h->d_gzent[0]; g.zent[1] = pair ? h->d_gpzent[1] : h->d_gzent[1];
+    g.went[0] = pair ? h->d_gpwent[0] : h->d_gwent[0]; g.went[1] = pair ? h->d_gpwent[1] : h->d_gwent[1];
+    g.nkv = pair ? h->gpnkv : h->gnkv;
+    g.kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
     g.cst = h->d_gcst;
     g.lev_ptr = h->d_levptr;
     g.nlev = h->nlev;
@@ -229,8 +241,37 @@ static GridArgs grid_args(mcinv_ctx *h)
 static int sweep_ctas(const mcinv_ctx *h) { return h->grid ? h->gctas : h->slices * h->Q; }
 static int sweep_warps(const mcinv_ctx *h) { return h->threads / 32; }
 
+// The state in the canonical layout (z[n][K], w[n][K]) again, after sweeps on the
+// pair layout; every reader of the state calls this first.
+static cudaError_t ensure_canonical(mcinv_ctx *h)
+{
+    if (h->canon_ok) return cudaSuccess;
+    const size_t nx = (size_t)h->gpnkv * 16;  // bytes of one pair-layout buffer
+    cudaError_t e = launch_pair_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
+                                     (int)(h->K * (h->cplx ? 8 : 4) / 16), 1, h->stream);
+    if (e == cudaSuccess) h->canon_ok = true;
+    return e;
+}
+
 static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 {
+    if (h->grid && h->gbulk && h->gpair) {
+        // the pair layout: packed from the canonical state when that is the newer
+        const size_t nx = (size_t)h->gpnkv * 16;
+        if (!h->pair_ok) {
+            cudaError_t e = launch_pair_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n,
+                                             (int)(h->K * (h->cplx ? 8 : 4) / 16), 0, h->stream);
+            if (e != cudaSuccess) return e;
+            h->pair_ok = true;
+        }
+        SweepArgs b = a;
+        b.z[0] = h->d_x;
+        b.z[1] = (char *)h->d_x + nx;
+        b.w[0] = b.z[0];
+        b.w[1] = b.z[1];
+        h->canon_ok = false;
+        return launch_sweep_grid(b, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
+    }
     if (h->grid) return launch_sweep_grid(a, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
     if (h->staged) return launch_sweep_staged(a, h->LPR, h->slices, h->stream);
     return launch_sweep(a, h->cplx, h->LPR, h->V, h->slices, h->threads, h->stream);
@@ -245,6 +286,7 @@ struct TunedShape {
     bool staged;
     bool grid = false;
     bool gbulk = false;
+    bool gpair = false;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -260,6 +302,7 @@ static mcinv_status autotune(mcinv_ctx *h)
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->grid = it->second.grid;
             h->gbulk = it->second.gbulk;
+            h->gpair = it->second.gpair && h->d_x;
             if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads, h->gbulk);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
@@ -273,7 +316,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk, h->gpair};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -328,16 +371,20 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 5; ++variant) {
-        // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per lane
-        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : 96;
+    for (int variant = 0; variant < 6; ++variant) {
+        // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
+        // lane; bulk-staged on the pair layout (structurally symmetric matrices)
+        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : variant == 4 ? 96 : 384;
         const bool bulk = variant >= 2;
+        const bool pair = variant == 5;
+        if (pair && !h->d_x) continue;
         const int ctas = grid_ctas(h->cplx, T, bulk);
         if (!grid_supported(h->cplx, vmax, h->K, T, bulk) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
-        const bool sG = h->grid, sB = h->gbulk;
+        const bool sG = h->grid, sB = h->gbulk, sP = h->gpair;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
         h->gbulk = bulk;
+        h->gpair = pair;
         h->slices = (int)((h->K + h->W - 1) / h->W);
         SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
         float ms = 1e30f;
@@ -350,15 +397,17 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
         if (e != cudaSuccess) cudaGetLastError();
         h->launches += 2;
-        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk}; }
+        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk, pair}; }
         h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS; h->gctas = sC; h->grid = sG;
         h->gbulk = sB;
+        h->gpair = sP;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->W = best.W; h->V = best.V; h->LPR = best.LPR; h->Q = best.Q; h->threads = best.T; h->staged = best.staged;
     h->grid = best.grid;
     h->gbulk = best.gbulk;
+    h->gpair = best.gpair;
     h->gctas = h->grid ? grid_ctas(h->cplx, h->threads, h->gbulk) : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
@@ -370,6 +419,8 @@ static mcinv_status autotune(mcinv_ctx *h)
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->cur = 0;
+    h->canon_ok = true;
+    h->pair_ok = false;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best;
     return MCINV_OK;
@@ -586,6 +637,42 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         }
         for (int64_t p = 0; p < n; ++p) grow[p].row = (int)((uint32_t)P.grow[p].row * kv);
         SETUP(upload(h, &h->d_grow, grow));
+        // the pair form, for structurally symmetric matrices (row i of C and of
+        // C^dagger name the same columns in the same order): offsets into the pair
+        // layout, rows of 2 kvp vectors (kvp: kv rounded up to a whole chain block)
+        const uint32_t kvp = (kv + 31) / 32 * 32;
+        bool sym = P.gzent.size() == P.gwent.size() && 2.0 * 2.0 * (double)n * kvp < 4294967296.0;
+        for (int64_t p = 0; p < n && sym; ++p) {
+            const int zb = P.grow[p].zb, ze = P.grow[p + 1].zb, wb = P.grow[p].wb, we = P.grow[p + 1].wb;
+            if (ze - zb != we - wb) { sym = false; break; }
+            for (int q = 0; q < ze - zb; ++q)
+                if (*(const int *)(P.gzent.data() + (size_t)(zb + q) * esz_ent) !=
+                    *(const int *)(P.gwent.data() + (size_t)(wb + q) * esz_ent)) { sym = false; break; }
+        }
+        if (sym) {
+            h->gpnkv = (uint32_t)n * 2u * kvp;
+            for (int par = 0; par < 2; ++par) {
+                const uint32_t off_new = par ? 0u : h->gpnkv, off_old = par ? h->gpnkv : 0u;
+                std::vector<uint8_t> ez = P.gzent, ew = P.gwent;
+                for (int64_t p = 0; p < n; ++p) {
+                    const int i = P.grow[p].row;
+                    auto fix = [&](std::vector<uint8_t> &v, int b, int e) {
+                        for (int q = b; q < e; ++q) {
+                            int *c = (int *)(v.data() + (size_t)q * esz_ent);
+                            *c = (int)((*c < i ? off_new : off_old) + (uint32_t)*c * 2u * kvp);
+                        }
+                    };
+                    fix(ez, P.grow[p].zb, P.grow[p + 1].zb);
+                    fix(ew, P.grow[p].wb, P.grow[p + 1].wb);
+                }
+                SETUP(upload(h, &h->d_gpzent[par], ez));
+                SETUP(upload(h, &h->d_gpwent[par], ew));
+            }
+            std::vector<GridRow> growp = P.grow;
+            for (int64_t p = 0; p < n; ++p) growp[p].row = (int)((uint32_t)P.grow[p].row * 2u * kvp);
+            SETUP(upload(h, &h->d_grow_p, growp));
+            h->pair_able = true;
+        }
         SETUP(upload(h, &h->d_levptr, P.lev_ptr));
         SETUP(dalloc(h, &h->d_gbar, 1));
         const size_t csz = cplx ? sizeof(CstC) : sizeof(CstR);
@@ -611,6 +698,14 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     h->d_w[1] = (char *)h->d_w[0] + state * esz;
     SETUP(cudaMemsetAsync(h->d_z[0], 0, 2 * state * esz, h->stream));
     SETUP(cudaMemsetAsync(h->d_w[0], 0, 2 * state * esz, h->stream));
+    // the pair-layout buffers, when the bulk sweep may run on them
+    const bool want_pair = h->pair_able && !(h->flags & MCINV_F_GRID_NOPAIR) &&
+                           (((h->flags & MCINV_F_GRID) && h->gbulk && h->threads == 384) ||
+                            ((h->flags & MCINV_F_AUTOTUNE) && !(h->flags & MCINV_F_GRID)));
+    if (want_pair) {
+        SETUP(dalloc(h, (char **)&h->d_x, 2 * (size_t)h->gpnkv * 16));
+        if (h->grid) h->gpair = true;
+    }
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
     SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
@@ -745,6 +840,9 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         if (h->d_diag_acc) SETUP(dalloc(h, &h->d_acc_est, (size_t)h->G * n * NV));
     }
     SETUP(cudaStreamSynchronize(h->stream));
+    // the block accumulation on CUDA cores and the partition's block sums read the
+    // state after every cycle: keep it in the canonical layout for them
+    if (h->gpair && ((h->nR > 0 && h->acc == MCINV_ACC_FP32_SIMT) || h->nent > 0)) h->gpair = false;
     *out = h;
     return MCINV_OK;
 #undef SETUP
@@ -812,6 +910,7 @@ static mcinv_status run_cycles(mcinv_ctx *h, int64_t cycles, bool accumulate)
                     if (st != MCINV_OK) return st;
                 }
                 h->cur ^= 1;
+                CUDA_TRY(h, ensure_canonical(h));
                 if (simt_block)
                     LAUNCH_K(h, MCINV_KERNEL_BLOCK, launch_block_simt(h->cplx, (int)h->K, h->d_z[h->cur], h->d_w[h->cur], h->d_R,
                                                 (int)h->nR, h->d_S, (int)h->nS, h->d_blk, h->stream));
@@ -1200,6 +1299,7 @@ extern "C" mcinv_status mcinv_get_state(mcinv_t h, int64_t chain0, int64_t nchai
     const size_t esz = NV * sizeof(float);
     std::vector<float> tmp((size_t)h->n * nchains * NV);
     double *dst[2] = {z, w};
+    CUDA_TRY(h, ensure_canonical(h));
     void *src[2] = {h->d_z[h->cur], h->d_w[h->cur]};
     for (int v = 0; v < 2; ++v) {
         if (!dst[v] || nchains == 0) continue;
@@ -1268,6 +1368,8 @@ extern "C" mcinv_status mcinv_set_state(mcinv_t h, const double *z, const double
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    h->canon_ok = true;  // the pair layout (if any) is stale now
+    h->pair_ok = false;
     h->cycle = cycle;
     return mcinv_reset_estimates(h);
 }
@@ -1282,7 +1384,7 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
     info->kernel_launches = h->launches; info->device_bytes = h->bytes;
-    info->sweep_kernel = h->grid ? (h->gbulk ? 3 : 2) : h->staged ? 1 : 0;
+    info->sweep_kernel = h->grid ? (h->gbulk ? (h->gpair ? 4 : 3) : 2) : h->staged ? 1 : 0;
     info->grid_ctas = h->grid ? h->gctas : 0;
     return MCINV_OK;
 }

@@ -158,7 +158,9 @@ struct GridArgs {
     const int *lev_ptr;        // [nlev + 1]: first position of each level
     int nlev;
     int nblk;                  // chain blocks per row: ceil(K / (32 V))
-    uint32_t nkv;              // vectors per state buffer: n K / V
+    int kv;                    // 16-byte vectors per row of z (or of w): K / V
+    uint32_t nkv;              // vectors per state buffer: n K / V (pair layout: n x 2 x 32 nblk)
+    int pair;                  // bulk staging on the pair layout (a.z[0]: its two buffers)
     unsigned *bar;             // barrier arrivals (zeroed by the launcher before each launch)
 };
 // threads: 384 or 512 with the gathers in registers; bulk: the warps stage their
@@ -169,6 +171,11 @@ bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool 
 int grid_ctas(int cplx, int threads, bool bulk);  // CTAs resident at once on the device; 0: not launchable
 cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,
                               cudaStream_t s);
+// The pair layout of the chain state for the grid-wide bulk sweep of structurally
+// symmetric matrices: row j, chain block k (32 vectors of 16 bytes) holds the
+// block's z vectors, then the same chains' w vectors (rows of 64 ceil(kv / 32)
+// vectors).  unpack = 0: canonical z, w ([n][kv] vectors each) -> x; 1: back.
+cudaError_t launch_pair_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s);
 // Block partition (Sec. 4): for every pair (r, s) of rows of one diagonal block
 // (entry e: rows ent_r[e], ent_s[e] of the state) and every chain group g (chains
 // gch[g] .. gch[g+1]-1): acc[g][e] += sum over the group's chains of z_r conj(w_s), FP64.

@@ -76,10 +76,11 @@ constexpr size_t bulk_smem()
 // launch and takes the rows g / nblk, g / nblk + R, ... of every level (R =
 // warps / nblk); a grid barrier ends each level.  G: vectors per lane (BULK
 // only; 1 with register gathers).
-template <bool CPLX, int V, int NT, bool BULK, int G>
+template <bool CPLX, int V, int NT, bool BULK, int G, bool PAIR = false>
 __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a, const GridArgs g)
 {
     static_assert(BULK || G == 1, "register gathers take one vector per lane");
+    static_assert(!PAIR || (BULK && G == 1), "the pair layout is read with bulk copies, one vector per lane");
     extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     const int warp = threadIdx.x >> 5;
     const int gw = blockIdx.x * (NT / 32) + warp;
     const int tw = gridDim.x * (NT / 32);
-    const int kv = (int)(g.nkv / (uint32_t)a.n);  // vectors per row
+    const int kv = g.kv;  // vectors per row of z (or of w)
     const int nblk = (kv + 32 * G - 1) / (32 * G);
     const int rstep = tw / nblk;       // warps per chain block
     const int r0 = gw / nblk;          // this warp's first row of every level
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     Lanes<CPLX, V, G> w;
     const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * RING * SEGB * G);
     const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * RING * SEGB * G + warp * NBAR * sizeof(uint64_t));
-    w.init(lane, blk, kv, a.K, a.n, a.seg, a.diag_part, a.noise, ring0, bar0);
+    w.init(lane, blk, kv, a.K, a.n, a.seg, a.diag_part, a.noise, ring0, bar0, PAIR);
     if (threadIdx.x == 0) abort_s = 0;
     if (BULK && lane == 0) {
         for (int b = 0; b < NBAR; ++b) mbar_init1(bar0 + 8u * b);
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     m.rows = g.rows;
     m.cst = (const typename Prec<CPLX>::Cst *)g.cst;
     m.z0 = a.z[0];
-    m.w0 = a.w[0];
+    m.w0 = PAIR ? a.z[0] : a.w[0];  // the pair layout holds w beside z
     m.has_noise = a.noise != nullptr;
     m.rpos = a.rpos;
     m.spos = a.spos;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                 if constexpr (BULK) {
                     // the bulk copies read rows that other CTAs wrote before the grid barrier
                     asm volatile("fence.proxy.async.global;" ::: "memory");
-                    level_bulk<CPLX, V, G>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
+                    level_bulk<CPLX, V, G, PAIR>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
                 } else {
                     level_regs<CPLX, V>(w, m, lb + r0, le, rstep, tsum, diverged);
                 }
@@ -163,10 +164,10 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     }
 }
 
-template <bool CPLX, int V, int NT, bool BULK, int G>
+template <bool CPLX, int V, int NT, bool BULK, int G, bool PAIR = false>
 cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaStream_t s)
 {
-    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G>;
+    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G, PAIR>;
     const size_t smem = BULK ? bulk_smem<G>() : 0;
     if (BULK) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -199,7 +200,39 @@ int grid_blocks_per_sm()
     return per_sm;
 }
 
+// The pair layout of the state: row j, chain block k (32 vectors of 16 bytes:
+// V chains each) holds the block's z vectors, then the same chains' w vectors;
+// rows are nblk x 64 vectors (the last block padded).  Pack: canonical z, w
+// ([n][kv] vectors each) -> x; unpack: x -> z, w.
+__global__ void pair_pack_kernel(const float4 *__restrict__ z, const float4 *__restrict__ w, float4 *__restrict__ x,
+                                 long long n, int kv, int kvp, int unpack)
+{
+    const long long total = n * (long long)kvp;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long j = t / kvp;
+        const int v = (int)(t - j * kvp);
+        const long long xo = j * 2 * kvp + (v >> 5) * 64 + (v & 31);
+        if (!unpack) {
+            x[xo] = v < kv ? z[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[xo + 32] = v < kv ? w[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (v < kv) {
+            ((float4 *)z)[j * kv + v] = x[xo];
+            ((float4 *)w)[j * kv + v] = x[xo + 32];
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pair_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s)
+{
+    const int kvp = (kv + 31) / 32 * 32;
+    long long blocks = (n * kvp + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks < 1) blocks = 1;
+    pair_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)z, (const float4 *)w, (float4 *)x, n, kv, kvp, unpack);
+    return cudaGetLastError();
+}
 
 bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk)
 {
@@ -247,6 +280,11 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
     cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     if (bulk) {
+        if (g.pair) {
+            if (threads != BULK_THREADS) return cudaErrorInvalidValue;
+            return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1, true>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, BULK_THREADS, true, 1, true>(a, g, ctas, s);
+        }
         if (threads == BULK_THREADS)
             return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1>(a, g, ctas, s)
                         : launch_grid_v<false, 4, BULK_THREADS, true, 1>(a, g, ctas, s);

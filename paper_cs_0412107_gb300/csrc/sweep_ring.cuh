@@ -226,6 +226,7 @@ struct Lanes {
     uint32_t cv[G], cshift[G];
     S *dpart[G];
     const uint32_t *noise_col[G];   // the lane's noise words of cycle 0, by position, or null
+    uint32_t zo[G], wo[G];          // the lane's z and w vectors within a row of the state
     uint32_t ring0, bar0, bar_long; // the ring and its barriers (bulk staging)
     uint32_t cvb, seg_bytes;        // the block's first vector in a row; bytes of one segment
     uint32_t ic, kb, vhead;         // ring rows issued, long-row rounds, next free slot
@@ -233,8 +234,9 @@ struct Lanes {
     // blk: the warp's chain block (G x 32 vectors); kv: vectors per row; K chains;
     // dp: diagonal partials [units][n] by position, or null; noise: [cycle][nw][n]
     // by position, or null
+    // pair: the state is in the pair layout (see PairLayout below; G = 1)
     __device__ __forceinline__ void init(int lane_, int blk, int kv, int K, int n, int seg_, void *dp,
-                                         const uint32_t *noise, uint32_t ring0_, uint32_t bar0_)
+                                         const uint32_t *noise, uint32_t ring0_, uint32_t bar0_, bool pair = false)
     {
         lane = lane_;
         seg = seg_;
@@ -242,11 +244,12 @@ struct Lanes {
         bar0 = bar0_;
         bar_long = bar0 + (NBAR - 1) * 8u;
         ic = kb = vhead = 0;
-        set_block(blk, kv, K, n, dp, noise);
+        set_block(blk, kv, K, n, dp, noise, pair);
     }
     // the chain block, the diagonal partials and the noise plane (the ring and its
     // state are kept)
-    __device__ __forceinline__ void set_block(int blk, int kv, int K, int n, void *dp, const uint32_t *noise)
+    __device__ __forceinline__ void set_block(int blk, int kv, int K, int n, void *dp, const uint32_t *noise,
+                                              bool pair = false)
     {
         diag = dp != nullptr;
 #pragma unroll
@@ -259,8 +262,18 @@ struct Lanes {
             noise_col[q] = noise ? noise + (size_t)(c0[q] >> 5) * (size_t)n : nullptr;
             cshift[q] = (uint32_t)(c0[q] & 31);
         }
-        cvb = (uint32_t)(blk * 32 * G);
-        seg_bytes = (uint32_t)min(32 * G, kv - blk * 32 * G) * 16u;
+        if (pair) {
+            // a row's block blk: 32 z vectors, then the same chains' 32 w vectors
+            zo[0] = (uint32_t)(blk * 64 + lane);
+            wo[0] = zo[0] + 32u;
+            cvb = (uint32_t)(blk * 64);
+            seg_bytes = 2u * SEGB;
+        } else {
+#pragma unroll
+            for (int q = 0; q < G; ++q) zo[q] = wo[q] = cv[q];
+            cvb = (uint32_t)(blk * 32 * G);
+            seg_bytes = (uint32_t)min(32 * G, kv - blk * 32 * G) * 16u;
+        }
     }
     // the noise word of vector q at position p in the cycle starting noise_cyc words in
     __device__ __forceinline__ uint32_t bits(int q, int p, size_t noise_cyc) const
@@ -320,8 +333,8 @@ __device__ __forceinline__ void finish(const Lanes<CPLX, V, G> &w, const Mat<CPL
             else re = prod;
             tsum = __fmaf_rn(__ldg(&m.tq[p]), re, tsum);
         }
-        ((T *)m.z0)[m.zn_off + iv + w.cv[q]] = zv;
-        ((T *)m.w0)[m.zn_off + iv + w.cv[q]] = wv;
+        ((T *)m.z0)[m.zn_off + iv + w.zo[q]] = zv;
+        ((T *)m.w0)[m.zn_off + iv + w.wo[q]] = wv;
         if (rp >= 0 || sp >= 0) {
             const size_t o = (size_t)m.shcol * m.kp + (size_t)w.c0[q] * (CPLX ? 2 : 1);
             constexpr int NF = L::NF;
@@ -402,8 +415,8 @@ __device__ __forceinline__ void row_regs(const Lanes<CPLX, V, 1> &w, const Mat<C
             const uint32_t ow = (uint32_t)__shfl_sync(0xffffffffu, mw.col, u);
             xz[u] = L::zero();
             xw[u] = L::zero();
-            if (u < dz && w.ok[0]) xz[u] = __ldcg(&z0[oz + w.cv[0]]);
-            if (u < dw && w.ok[0]) xw[u] = __ldcg(&w0[ow + w.cv[0]]);
+            if (u < dz && w.ok[0]) xz[u] = __ldcg(&z0[oz + w.zo[0]]);
+            if (u < dw && w.ok[0]) xw[u] = __ldcg(&w0[ow + w.wo[0]]);
         }
 #pragma unroll
         for (int u = 0; u < U1; ++u) {
@@ -428,8 +441,8 @@ __device__ __forceinline__ void row_regs(const Lanes<CPLX, V, 1> &w, const Mat<C
                     const uint32_t ow = ent_off(mw, m.went, rec.z, ew + u, vw);
                     xz[u] = L::zero();
                     xw[u] = L::zero();
-                    if (vz && w.ok[0]) xz[u] = __ldcg(&z0[oz + w.cv[0]]);
-                    if (vw && w.ok[0]) xw[u] = __ldcg(&w0[ow + w.cv[0]]);
+                    if (vz && w.ok[0]) xz[u] = __ldcg(&z0[oz + w.zo[0]]);
+                    if (vw && w.ok[0]) xw[u] = __ldcg(&w0[ow + w.wo[0]]);
                 }
 #pragma unroll
                 for (int u = 0; u < UP; ++u) {
@@ -478,7 +491,13 @@ __device__ __forceinline__ void level_regs(const Lanes<CPLX, V, 1> &w, const Mat
 // has ordered the last level's state stores before these async-proxy reads
 // (fence.proxy.async after the level barrier).  On an expired wait *abort_flag
 // is set and the rows are finished with whatever landed.
-template <bool CPLX, int V, int G>
+//
+// PAIR: the state is in the pair layout (the chain block's z vectors of a row
+// followed by its w vectors, one allocation for both) and the matrix is
+// structurally symmetric (row i of C and of C^dagger name the same j, in the
+// same order), so z_j and w_j of a neighbour are one 1 KB segment: one copy,
+// one slot of 2 x 512 bytes (RING / 2 slots of the same ring bytes).
+template <bool CPLX, int V, int G, bool PAIR = false>
 __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int p, int le, int rstep,
                                            float &tsum, bool &diverged, volatile int *abort_flag)
 {
@@ -489,7 +508,10 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
     using Ent = typename P::Ent;
     using Cst = typename P::Cst;
     constexpr int U1 = 8;
-    constexpr int SEGG = SEGB * G;
+    static_assert(!PAIR || G == 1, "pairs take one vector per lane");
+    constexpr int SEGG = PAIR ? 2 * SEGB : SEGB * G;  // bytes of one slot
+    constexpr int RN = PAIR ? RING / 2 : RING;        // slots of the warp's ring
+    constexpr int WOFF = PAIR ? SEGB : 0;             // the w half of a slot (pairs)
     static_assert(QMAX >= 2 && QMAX <= 4, "queue registers");
     if (p >= le) return;
     const int lane = w.lane;
@@ -536,8 +558,8 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
         az.col = 0; aw.col = 0;
         if constexpr (CPLX) { az.re = r.zr; az.im = r.zi; aw.re = r.wr; aw.im = r.wi; az.pad = aw.pad = 0; }
         else { az.val = r.zr; aw.val = r.wr; }
-        const uint32_t zb = w.ring0 + (r.vslot & (RING - 1)) * SEGG + lane * 16u;
-        const uint32_t wb = zb + (uint32_t)dz * SEGG;
+        const uint32_t zb = w.ring0 + (r.vslot & (RN - 1)) * SEGG + lane * 16u;
+        const uint32_t wb = PAIR ? zb + WOFF : zb + (uint32_t)dz * SEGG;
         T sz[G], sw[G];
 #pragma unroll
         for (int q = 0; q < G; ++q) { sz[q] = L::zero(); sw[q] = L::zero(); }
@@ -581,12 +603,12 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
         if (more) load_ents(m, lane, rnext, nz, nw);
         const int4 rnn = p + 2 * rstep < le ? ldnc4(&m.rows[p + 2 * rstep]) : make_int4(0, 0, 0, 0);
         const int dz = (rec.w >> 2) & 0x7fff, dw = (rec.w >> 17) & 0x7fff;
-        const int nseg = dz + dw;
-        if (nseg <= RING) {
+        const int nseg = PAIR ? dz : dz + dw;
+        if (nseg <= RN) {
             // the row's slots, not across the ring's end; wait for room and a barrier
             uint32_t v = w.vhead;
-            if ((v & (RING - 1)) + nseg > RING) v = (v + RING - 1) & ~(uint32_t)(RING - 1);
-            while (qn == QMAX || (qn > 0 && v + nseg - q0.vslot > (uint32_t)RING)) pop();
+            if ((v & (RN - 1)) + nseg > RN) v = (v + RN - 1) & ~(uint32_t)(RN - 1);
+            while (qn == QMAX || (qn > 0 && v + nseg - q0.vslot > (uint32_t)RN)) pop();
             const uint32_t bar = w.bar0 + 8u * (w.ic % (QMAX + 1));
             const uint32_t wo = (uint32_t)__shfl_sync(0xffffffffu, mw.col, (lane - dz) & 31);
             // every lane is done reading the slots freed above; order those
@@ -595,8 +617,8 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (lane == 0) mbar_expect(bar, (uint32_t)nseg * w.seg_bytes);
             if (lane < nseg) {
-                const T *src = lane < dz ? z0 + (uint32_t)mz.col + w.cvb : w0 + wo + w.cvb;
-                bulk_g2s(w.ring0 + ((v & (RING - 1)) + lane) * SEGG, src, w.seg_bytes, bar);
+                const T *src = (PAIR || lane < dz) ? z0 + (uint32_t)mz.col + w.cvb : w0 + wo + w.cvb;
+                bulk_g2s(w.ring0 + ((v & (RN - 1)) + lane) * SEGG, src, w.seg_bytes, bar);
             }
             RingRow<CPLX> r;
             r.p = p;
@@ -637,16 +659,23 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
 #pragma unroll
             for (int q = 0; q < G; ++q) { pzs[q] = PieceSum<L>(dz, rec.w & 3); pws[q] = PieceSum<L>(dw, rec.w & 3); }
             for (int ez = 0, ew = 0; ez < dz || ew < dw;) {
-                int mzr = min(dz - ez, RING / 2);
-                const int mwr = min(dw - ew, RING - mzr);
-                mzr = min(dz - ez, RING - mwr);
+                // one round: z and w segments (or pairs) of the next entries
+                int mzr, mwr;
+                if constexpr (PAIR) {
+                    mzr = mwr = min(dz - ez, RN);
+                } else {
+                    mzr = min(dz - ez, RING / 2);
+                    mwr = min(dw - ew, RING - mzr);
+                    mzr = min(dz - ez, RING - mwr);
+                }
+                const int ncp = PAIR ? mzr : mzr + mwr;
                 const uint32_t oz = ent_off_lane(mz, m.zent, rec.y, ez + lane, lane < mzr);
-                const uint32_t ow = ent_off_lane(mw, m.went, rec.z, ew + lane - mzr, lane >= mzr && lane < mzr + mwr);
+                const uint32_t ow = PAIR ? 0u : ent_off_lane(mw, m.went, rec.z, ew + lane - mzr, lane >= mzr && lane < mzr + mwr);
                 __syncwarp();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (lane == 0) mbar_expect(w.bar_long, (uint32_t)(mzr + mwr) * w.seg_bytes);
-                if (lane < mzr + mwr) {
-                    const T *src = lane < mzr ? z0 + oz + w.cvb : w0 + ow + w.cvb;
+                if (lane == 0) mbar_expect(w.bar_long, (uint32_t)ncp * w.seg_bytes);
+                if (lane < ncp) {
+                    const T *src = (PAIR || lane < mzr) ? z0 + oz + w.cvb : w0 + ow + w.cvb;
                     bulk_g2s(w.ring0 + lane * SEGG, src, w.seg_bytes, w.bar_long);
                 }
                 if (!ring_wait(w.bar_long, w.kb & 1u)) *abort_flag = 1;
@@ -660,7 +689,8 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
                 for (int e = 0; e < mwr; ++e) {
                     const Ent en = ent_val(mw, m.went, rec.z, ew + e, true);
 #pragma unroll
-                    for (int q = 0; q < G; ++q) pws[q].add(ew + e, en, lds_vec<T>(sa + (mzr + e) * SEGG + q * SEGB));
+                    for (int q = 0; q < G; ++q)
+                        pws[q].add(ew + e, en, lds_vec<T>(sa + (PAIR ? e * SEGG + WOFF : (mzr + e) * SEGG) + q * SEGB));
                 }
                 ez += mzr;
                 ew += mwr;

@@ -15,6 +15,7 @@ from paper_cs_0412107_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 GR = mcinv.MCINV_F_GRID
 GB = mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK
+GBS = GB | mcinv.MCINV_F_GRID_NOPAIR  # bulk staging, z and w in separate buffers
 CO = mcinv.MCINV_F_COLOR_ORDER
 
 
@@ -31,7 +32,9 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
     hr = mcinv.create_from_csr(c, K=K, seed=5, acc=mcinv.MCINV_ACC_FP32_SIMT, chains_per_cta=W, ctas_per_slice=1,
                                threads_per_cta=256, flags=flags, **kw)
     info = mcinv.mcinv_info(hg)
-    assert info["sweep_kernel"] == (3 if grid == GB else 2) and info["grid_ctas"] >= 1
+    # the pair layout where C is structurally symmetric (bulk staging, 384 threads)
+    want = (3, 4) if grid == GB else (3,) if grid == GBS else (2,)
+    assert info["sweep_kernel"] in want and info["grid_ctas"] >= 1
     done = 0
     for cyc in cycles:
         for h in (hg, hr):
@@ -45,8 +48,9 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
 
 @pytest.mark.parametrize("flags", [0, CO])
 @pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 384, GB),
-                                            (200, 384, GB), (36, 384, GB), (1024, 192, GB), (520, 192, GB),
-                                            (1024, 96, GB), (900, 96, GB), (36, 96, GB)])
+                                            (200, 384, GB), (36, 384, GB), (256, 384, GBS), (200, 384, GBS),
+                                            (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
+                                            (36, 96, GB)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -54,7 +58,7 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
@@ -63,7 +67,7 @@ def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 96)])
 def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
     c = wl.wilson_dirac((3, 3, 3, 4), 0.1)  # 4 x 4 spinor hops, 14 nonzeros per row
     hg, hr = _pair(c, 64 if threads == 384 else 320, flags=CO, cycles=(3, 12), grid=grid, threads=threads)
@@ -71,7 +75,7 @@ def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
@@ -147,3 +151,27 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # and the staged kernel
         mcinv.create_from_csr(c, K=64, flags=GR | mcinv.MCINV_F_STAGED, chains_per_cta=32)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
+
+
+def test_pair_layout_is_used_and_survives_state_round_trips():
+    # a structurally symmetric matrix runs on the pair layout; reading the state
+    # between launches, writing it back and resuming give the uninterrupted run's bits
+    c = wl.pedigree(4000, 1.2, 9)
+    h = mcinv.create_from_csr(c, K=256, seed=6, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=GB | CO, batch_cycles=3)
+    assert mcinv.mcinv_info(h)["sweep_kernel"] == 4
+    g = mcinv.create_from_csr(c, K=256, seed=6, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=GBS | CO, batch_cycles=3)
+    assert mcinv.mcinv_info(g)["sweep_kernel"] == 3
+    mcinv.mcinv_burnin(h, 7)
+    z, w, cyc = mcinv.mcinv_get_state(h)
+    mcinv.mcinv_set_state(h, z, w, cyc)
+    mcinv.mcinv_burnin(h, 5)
+    mcinv.mcinv_burnin(g, 12)
+    zh, wh, _ = mcinv.mcinv_get_state(h)
+    zg, wg, _ = mcinv.mcinv_get_state(g)
+    assert np.array_equal(zh, zg) and np.array_equal(wh, wg)
+    # a matrix that is not structurally symmetric keeps separate buffers
+    r = wl.random_dominant(300, 4, 1.5, 2)
+    hr = mcinv.create_from_csr(r, K=64, flags=GB)
+    assert mcinv.mcinv_info(hr)["sweep_kernel"] == 3
+    for x in (h, g, hr):
+        mcinv.mcinv_destroy(x)
