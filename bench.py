@@ -132,9 +132,11 @@ def max_over_ranks(x, world):
 SWEEP_KERNELS = {
     0: ("cc_sweep_kernel", ("sweep.cu", "sweep_core.cuh", "internal.h"), "cc_sweep_pedigree50k.txt"),
     1: ("cc_sweep_staged_kernel", ("sweep_staged.cu", "sweep_core.cuh", "internal.h"), None),
-    2: ("cc_sweep_grid_kernel", ("sweep_grid.cu", "sweep_core.cuh", "internal.h"), None),
-    3: ("cc_sweep_grid_kernel (bulk-staged gathers)", ("sweep_grid.cu", "sweep_core.cuh", "internal.h"),
+    2: ("cc_sweep_grid_kernel", ("sweep_grid.cu", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), None),
+    3: ("cc_sweep_grid_kernel (bulk-staged gathers)", ("sweep_grid.cu", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"),
         "cc_sweep_grid_bulk_pedigree50k.txt"),
+    4: ("cc_sweep_grid_kernel (bulk-staged gathers, pair layout)",
+        ("sweep_grid.cu", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), "cc_sweep_grid_pair_pedigree50k.txt"),
 }
 
 
@@ -166,7 +168,8 @@ def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "s
 def kernel_flags(args):
     """The sweep kernel: timed on the matrix by the autotuner (auto), or fixed: the
     chain-sliced kernel in its default shape, the grid-wide kernel (register
-    gathers, 512 threads) or the grid-wide kernel with bulk-staged gathers."""
+    gathers, 512 threads), the grid-wide kernel with bulk-staged gathers on
+    separate z, w buffers (bulk) or on the pair layout (pair)."""
     from paper_cs_0412107_gb300 import mcinv
     if args.kernel == "auto":
         return (0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE), {}
@@ -174,6 +177,8 @@ def kernel_flags(args):
         return 0, {}
     if args.kernel == "grid":
         return mcinv.MCINV_F_GRID, {"threads_per_cta": 512}
+    if args.kernel == "bulk":
+        return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_NOPAIR, {}
     return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK, {}
 
 
@@ -724,7 +729,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--order", default="colour", choices=["natural", "colour"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair"])
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--lattice-batches", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
