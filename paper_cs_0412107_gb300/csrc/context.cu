@@ -374,7 +374,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     for (int variant = 0; variant < 6; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
         // lane; bulk-staged on the pair layout (structurally symmetric matrices)
-        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : variant == 4 ? 96 : 384;
+        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : variant == 4 ? 96 : 512;
         const bool bulk = variant >= 2;
         const bool pair = variant == 5;
         if (pair && !h->d_x) continue;
@@ -574,7 +574,8 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         const int vmax = cplx ? 2 : 4;
         const bool bulk = (h->flags & MCINV_F_GRID_BULK) != 0;
         const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
-        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) ? grid_ctas(cplx, T, bulk) : 0;
+        // (512 threads with bulk staging belong to the pair layout, chosen below when it applies)
+        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) && !(bulk && T == 512) ? grid_ctas(cplx, T, bulk) : 0;
         if (h->staged || ctas < 1) {
             fail(h, MCINV_E_UNSUPPORTED,
                  "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA (96, 192 or 384 with "
@@ -700,11 +701,19 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     SETUP(cudaMemsetAsync(h->d_w[0], 0, 2 * state * esz, h->stream));
     // the pair-layout buffers, when the bulk sweep may run on them
     const bool want_pair = h->pair_able && !(h->flags & MCINV_F_GRID_NOPAIR) &&
-                           (((h->flags & MCINV_F_GRID) && h->gbulk && h->threads == 384) ||
+                           (((h->flags & MCINV_F_GRID) && h->gbulk && opt.threads_per_cta <= 0) ||
                             ((h->flags & MCINV_F_AUTOTUNE) && !(h->flags & MCINV_F_GRID)));
     if (want_pair) {
-        SETUP(dalloc(h, (char **)&h->d_x, 2 * (size_t)h->gpnkv * 16));
-        if (h->grid) h->gpair = true;
+        const int pc = grid_ctas(cplx, 512, true);
+        if (pc > 0) {
+            SETUP(dalloc(h, (char **)&h->d_x, 2 * (size_t)h->gpnkv * 16));
+            if (h->grid) {
+                // the pair layout: 16 warps a CTA
+                h->gpair = true;
+                h->threads = 512;
+                h->gctas = pc;
+            }
+        }
     }
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
@@ -842,7 +851,11 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     SETUP(cudaStreamSynchronize(h->stream));
     // the block accumulation on CUDA cores and the partition's block sums read the
     // state after every cycle: keep it in the canonical layout for them
-    if (h->gpair && ((h->nR > 0 && h->acc == MCINV_ACC_FP32_SIMT) || h->nent > 0)) h->gpair = false;
+    if (h->gpair && ((h->nR > 0 && h->acc == MCINV_ACC_FP32_SIMT) || h->nent > 0)) {
+        h->gpair = false;
+        h->threads = 384;
+        h->gctas = grid_ctas(h->cplx, 384, true);
+    }
     *out = h;
     return MCINV_OK;
 #undef SETUP

@@ -165,8 +165,8 @@ struct GridArgs {
 };
 // threads: 384 or 512 with the gathers in registers; bulk: the warps stage their
 // gathers in shared memory with bulk copies, 384 threads with 512-byte segments,
-// 192 with 1 KB or 96 with 2 KB (a warp's chain block is 1, 2 or 4 x 32 vectors).
-// One CTA per SM.
+// 192 with 1 KB or 96 with 2 KB (a warp's chain block is 1, 2 or 4 x 32 vectors),
+// or 512 on the pair layout (GridArgs.pair).  One CTA per SM.
 bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk);
 int grid_ctas(int cplx, int threads, bool bulk);  // CTAs resident at once on the device; 0: not launchable
 cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,

@@ -65,12 +65,14 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned target, vol
 using namespace ring;
 
 constexpr int BULK_THREADS = 384;
-// per CTA: 12 / G warps, each a ring of RING slots of G x 512 bytes (192 KB in all)
-template <int G>
-constexpr size_t bulk_smem()
-{
-    return (size_t)(BULK_THREADS / G / 32) * RING * SEGB * G + (BULK_THREADS / G / 32) * NBAR * sizeof(uint64_t);
-}
+constexpr int PAIR_THREADS = 512;
+// ring bytes of one warp: RING slots of G x 512 bytes, or PAIR_RN slots of 1 KB
+template <int G, bool PAIR>
+constexpr int ring_bytes() { return PAIR ? PAIR_RN * 2 * SEGB : RING * SEGB * G; }
+// per CTA: 12 / G warps, each a ring of RING slots of G x 512 bytes (192 KB in
+// all), or 16 warps of PAIR_RN 1 KB slots (the pair layout)
+template <int NT, int G, bool PAIR>
+constexpr size_t bulk_smem() { return (size_t)(NT / 32) * (ring_bytes<G, PAIR>() + NBAR * sizeof(uint64_t)); }
 
 // The grid-wide sweep: warp g keeps the chain block g mod nblk for the whole
 // launch and takes the rows g / nblk, g / nblk + R, ... of every level (R =
@@ -96,8 +98,8 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     const int blk = gw - r0 * nblk;    // and its chain block
     const bool active = r0 < rstep;
     Lanes<CPLX, V, G> w;
-    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * RING * SEGB * G);
-    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * RING * SEGB * G + warp * NBAR * sizeof(uint64_t));
+    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * ring_bytes<G, PAIR>());
+    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * ring_bytes<G, PAIR>() + warp * NBAR * sizeof(uint64_t));
     w.init(lane, blk, kv, a.K, a.n, a.seg, a.diag_part, a.noise, ring0, bar0, PAIR);
     if (threadIdx.x == 0) abort_s = 0;
     if (BULK && lane == 0) {
@@ -168,7 +170,7 @@ template <bool CPLX, int V, int NT, bool BULK, int G, bool PAIR = false>
 cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaStream_t s)
 {
     auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G, PAIR>;
-    const size_t smem = BULK ? bulk_smem<G>() : 0;
+    const size_t smem = BULK ? bulk_smem<NT, G, PAIR>() : 0;
     if (BULK) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -186,11 +188,11 @@ cudaError_t launch_grid_v(const SweepArgs &a, const GridArgs &g, int ctas, cudaS
     return cudaLaunchKernelEx(&cfg, kern, a, g);
 }
 
-template <bool CPLX, int V, int NT, bool BULK, int G>
+template <bool CPLX, int V, int NT, bool BULK, int G, bool PAIR = false>
 int grid_blocks_per_sm()
 {
-    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G>;
-    const size_t smem = BULK ? bulk_smem<G>() : 0;
+    auto kern = cc_sweep_grid_kernel<CPLX, V, NT, BULK, G, PAIR>;
+    const size_t smem = BULK ? bulk_smem<NT, G, PAIR>() : 0;
     int per_sm = 0;
     if ((BULK && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) {
@@ -238,7 +240,9 @@ bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool 
 {
     const int v = cplx ? 2 : 4;
     if (chains_per_lane != v || K % v != 0) return false;
-    if (bulk) return threads == BULK_THREADS || threads == BULK_THREADS / 2 || threads == BULK_THREADS / 4;
+    if (bulk)
+        return threads == BULK_THREADS || threads == BULK_THREADS / 2 || threads == BULK_THREADS / 4 ||
+               threads == PAIR_THREADS;
     return threads == 384 || threads == 512;
 }
 
@@ -251,7 +255,10 @@ int grid_ctas(int cplx, int threads, bool bulk)
     }
     int per_sm = 0;
     if (bulk) {
-        if (threads == BULK_THREADS)
+        if (threads == PAIR_THREADS)
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, PAIR_THREADS, true, 1, true>()
+                          : grid_blocks_per_sm<false, 4, PAIR_THREADS, true, 1, true>();
+        else if (threads == BULK_THREADS)
             per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS, true, 1>() : grid_blocks_per_sm<false, 4, BULK_THREADS, true, 1>();
         else if (threads == BULK_THREADS / 2)
             per_sm = cplx ? grid_blocks_per_sm<true, 2, BULK_THREADS / 2, true, 2>()
@@ -281,10 +288,11 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
     if (e != cudaSuccess) return e;
     if (bulk) {
         if (g.pair) {
-            if (threads != BULK_THREADS) return cudaErrorInvalidValue;
-            return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1, true>(a, g, ctas, s)
-                        : launch_grid_v<false, 4, BULK_THREADS, true, 1, true>(a, g, ctas, s);
+            if (threads != PAIR_THREADS) return cudaErrorInvalidValue;
+            return cplx ? launch_grid_v<true, 2, PAIR_THREADS, true, 1, true>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, PAIR_THREADS, true, 1, true>(a, g, ctas, s);
         }
+        if (threads == PAIR_THREADS) return cudaErrorInvalidValue;  // 512 threads: the pair layout only
         if (threads == BULK_THREADS)
             return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1>(a, g, ctas, s)
                         : launch_grid_v<false, 4, BULK_THREADS, true, 1>(a, g, ctas, s);

@@ -104,6 +104,7 @@ constexpr int RING = 32;                  // slots per warp (a power of two)
 constexpr int QMAX = 3;                   // rows in flight per warp
 constexpr int NBAR = QMAX + 2;            // QMAX + 1 for the ring rows, one for long rows
 constexpr int SEGB = 512;                 // 32 lanes x 16 bytes
+constexpr int PAIR_RN = 12;               // 1 KB slots per warp on the pair layout (16 warps per CTA)
 
 // A row in flight in a warp's ring: its position, first vector i K / V, packed
 // counts, first slot, barrier use number, and the lane's values of its entries
@@ -496,7 +497,7 @@ __device__ __forceinline__ void level_regs(const Lanes<CPLX, V, 1> &w, const Mat
 // followed by its w vectors, one allocation for both) and the matrix is
 // structurally symmetric (row i of C and of C^dagger name the same j, in the
 // same order), so z_j and w_j of a neighbour are one 1 KB segment: one copy,
-// one slot of 2 x 512 bytes (RING / 2 slots of the same ring bytes).
+// one slot of 2 x 512 bytes, PAIR_RN slots a warp.
 template <bool CPLX, int V, int G, bool PAIR = false>
 __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int p, int le, int rstep,
                                            float &tsum, bool &diverged, volatile int *abort_flag)
@@ -510,7 +511,7 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
     constexpr int U1 = 8;
     static_assert(!PAIR || G == 1, "pairs take one vector per lane");
     constexpr int SEGG = PAIR ? 2 * SEGB : SEGB * G;  // bytes of one slot
-    constexpr int RN = PAIR ? RING / 2 : RING;        // slots of the warp's ring
+    constexpr int RN = PAIR ? PAIR_RN : RING;         // slots of the warp's ring
     constexpr int WOFF = PAIR ? SEGB : 0;             // the w half of a slot (pairs)
     static_assert(QMAX >= 2 && QMAX <= 4, "queue registers");
     if (p >= le) return;
@@ -558,7 +559,7 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
         az.col = 0; aw.col = 0;
         if constexpr (CPLX) { az.re = r.zr; az.im = r.zi; aw.re = r.wr; aw.im = r.wi; az.pad = aw.pad = 0; }
         else { az.val = r.zr; aw.val = r.wr; }
-        const uint32_t zb = w.ring0 + (r.vslot & (RN - 1)) * SEGG + lane * 16u;
+        const uint32_t zb = w.ring0 + (r.vslot % RN) * SEGG + lane * 16u;
         const uint32_t wb = PAIR ? zb + WOFF : zb + (uint32_t)dz * SEGG;
         T sz[G], sw[G];
 #pragma unroll
@@ -607,7 +608,7 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
         if (nseg <= RN) {
             // the row's slots, not across the ring's end; wait for room and a barrier
             uint32_t v = w.vhead;
-            if ((v & (RN - 1)) + nseg > RN) v = (v + RN - 1) & ~(uint32_t)(RN - 1);
+            if ((v % RN) + nseg > RN) v = (v / RN + 1) * RN;
             while (qn == QMAX || (qn > 0 && v + nseg - q0.vslot > (uint32_t)RN)) pop();
             const uint32_t bar = w.bar0 + 8u * (w.ic % (QMAX + 1));
             const uint32_t wo = (uint32_t)__shfl_sync(0xffffffffu, mw.col, (lane - dz) & 31);
@@ -618,7 +619,7 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
             if (lane == 0) mbar_expect(bar, (uint32_t)nseg * w.seg_bytes);
             if (lane < nseg) {
                 const T *src = (PAIR || lane < dz) ? z0 + (uint32_t)mz.col + w.cvb : w0 + wo + w.cvb;
-                bulk_g2s(w.ring0 + ((v & (RN - 1)) + lane) * SEGG, src, w.seg_bytes, bar);
+                bulk_g2s(w.ring0 + ((v % RN) + lane) * SEGG, src, w.seg_bytes, bar);
             }
             RingRow<CPLX> r;
             r.p = p;

@@ -27,13 +27,14 @@ def _lib():
 
 def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
     W = 64 if c.is_complex else 128
+    # threads 0: the kernel's own (bulk staging: the pair layout where C is structurally symmetric)
     hg = mcinv.create_from_csr(c, K=K, seed=5, acc=mcinv.MCINV_ACC_FP32_SIMT, threads_per_cta=threads,
                                flags=flags | grid, **kw)
     hr = mcinv.create_from_csr(c, K=K, seed=5, acc=mcinv.MCINV_ACC_FP32_SIMT, chains_per_cta=W, ctas_per_slice=1,
                                threads_per_cta=256, flags=flags, **kw)
     info = mcinv.mcinv_info(hg)
-    # the pair layout where C is structurally symmetric (bulk staging, 384 threads)
-    want = (3, 4) if grid == GB else (3,) if grid == GBS else (2,)
+    # the pair layout where C is structurally symmetric (bulk staging, default threads)
+    want = (3, 4) if grid == GB and threads == 0 else (3,) if grid in (GB, GBS) else (2,)
     assert info["sweep_kernel"] in want and info["grid_ctas"] >= 1
     done = 0
     for cyc in cycles:
@@ -47,8 +48,8 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
 
 
 @pytest.mark.parametrize("flags", [0, CO])
-@pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 384, GB),
-                                            (200, 384, GB), (36, 384, GB), (256, 384, GBS), (200, 384, GBS),
+@pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 0, GB),
+                                            (200, 0, GB), (36, 0, GB), (256, 384, GB), (200, 0, GBS),
                                             (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
                                             (36, 96, GB)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
@@ -58,24 +59,24 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
-    hg, hr = _pair(c, 130 if threads == 384 else 520, flags=flags, grid=grid, threads=threads)
+    hg, hr = _pair(c, 130 if threads in (0, 384) else 520, flags=flags, grid=grid, threads=threads)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 96)])
 def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
     c = wl.wilson_dirac((3, 3, 3, 4), 0.1)  # 4 x 4 spinor hops, 14 nonzeros per row
-    hg, hr = _pair(c, 64 if threads == 384 else 320, flags=CO, cycles=(3, 12), grid=grid, threads=threads)
+    hg, hr = _pair(c, 64 if threads in (0, 384) else 320, flags=CO, cycles=(3, 12), grid=grid, threads=threads)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 384), (GBS, 384), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
