@@ -108,13 +108,16 @@ typedef struct {
                               (default) or 512, chains_per_cta and ctas_per_slice are ignored
                               (MCINV_E_UNSUPPORTED otherwise).  MCINV_F_AUTOTUNE without this flag
                               times it beside the chain-sliced shapes. */
-#define MCINV_F_GRID_BULK 32 /* with MCINV_F_GRID: each warp stages the gathers of rows with at most
-                              8 entries a side in shared memory with bulk asynchronous copies, two
-                              rows in flight (384 threads per CTA); longer rows keep register
-                              gathers.  Same values, bit for bit. */
+#define MCINV_F_GRID_BULK 32 /* with MCINV_F_GRID: each warp stages its rows' gathered segments in a
+                              ring of shared-memory slots with bulk asynchronous copies, up to three
+                              rows in flight; a row longer than the ring runs in rounds.
+                              threads_per_cta 384 (default: 12 warps of 32 slots), 192 or 96 (2 or
+                              4 vectors a lane), or 512 (16 warps of 24 slots).  Same values, bit
+                              for bit. */
 #define MCINV_F_GRID_NOPAIR 64 /* with MCINV_F_GRID_BULK: keep z and w in separate buffers.  Without it,
                               for a structurally symmetric C (row i of C and of C^dagger name the
-                              same columns) the bulk sweep keeps the state in the pair layout, a
+                              same columns) and threads_per_cta 0 the bulk sweep keeps the state
+                              in the pair layout (16 warps of 12 slots of 1 KB), a
                               chain block's z and w of a row side by side, so one 1 KB copy
                               gathers both; readers of the state (mcinv_get_state, the CUDA-core
                               block accumulation) see the usual layout.  Same values, bit for bit. */

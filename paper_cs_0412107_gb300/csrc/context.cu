@@ -371,10 +371,12 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 6; ++variant) {
+    for (int variant = 0; variant < 7; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
-        // lane; bulk-staged on the pair layout (structurally symmetric matrices)
-        const int T = variant == 0 ? 384 : variant == 1 ? 512 : variant == 2 ? 384 : variant == 3 ? 192 : variant == 4 ? 96 : 512;
+        // lane (12 warps of 32 slots) or 1 (16 warps of 24 slots); bulk-staged on the pair
+        // layout (structurally symmetric matrices)
+        static const int kT[7] = {384, 512, 384, 192, 96, 512, 512};
+        const int T = kT[variant];
         const bool bulk = variant >= 2;
         const bool pair = variant == 5;
         if (pair && !h->d_x) continue;
@@ -574,12 +576,12 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         const int vmax = cplx ? 2 : 4;
         const bool bulk = (h->flags & MCINV_F_GRID_BULK) != 0;
         const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
-        // (512 threads with bulk staging belong to the pair layout, chosen below when it applies)
-        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) && !(bulk && T == 512) ? grid_ctas(cplx, T, bulk) : 0;
+        // (with bulk staging and no explicit shape the pair layout is chosen below when it applies)
+        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) ? grid_ctas(cplx, T, bulk) : 0;
         if (h->staged || ctas < 1) {
             fail(h, MCINV_E_UNSUPPORTED,
-                 "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA (96, 192 or 384 with "
-                 "MCINV_F_GRID_BULK), a resident CTA per SM and not MCINV_F_STAGED", vmax);
+                 "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA (96, 192, 384 or 512 "
+                 "with MCINV_F_GRID_BULK), a resident CTA per SM and not MCINV_F_STAGED", vmax);
             return bail(MCINV_E_UNSUPPORTED);
         }
         h->grid = true;

@@ -233,29 +233,35 @@ __global__ void __launch_bounds__(512, 1) pool_sweep_kernel(const PoolSlotDev *_
     }
 }
 
-// The ring form of the sweep: a CTA of 12 warps takes a (slot, 128-chain block)
-// item from the device queue and runs the slot's cycles of this step; warp w
-// takes the rows lb + w, lb + w + 12, ... of each level with bulk-staged
-// gathers (ring::level_bulk, the same arithmetic), and a CTA barrier ends every
-// level: the whole chain block of the matrix is this CTA's.  The warps' rings,
+// The ring form of the sweep: a CTA of NT / 32 warps (12 with 32-slot rings or
+// 16 with 24-slot rings) takes a (slot, 128-chain block) item from the device
+// queue and runs the slot's cycles of this step; warp w takes the rows lb + w,
+// lb + w + NT / 32, ... of each level with bulk-staged gathers
+// (ring::level_bulk, the same arithmetic), and a CTA barrier ends every level:
+// the whole chain block of the matrix is this CTA's.  The warps' rings,
 // barriers and their phases persist across items.
-constexpr int POOL_RING_THREADS = 384;
-constexpr size_t POOL_RING_SMEM = (size_t)(POOL_RING_THREADS / 32) * ring::RING * ring::SEGB +
-                                  (POOL_RING_THREADS / 32) * ring::NBAR * sizeof(uint64_t);
+template <int NT>
+constexpr int pool_ring_slots() { return NT == 512 ? ring::RING16 : ring::RING; }
+template <int NT>
+constexpr size_t pool_ring_smem()
+{
+    return (size_t)(NT / 32) * (pool_ring_slots<NT>() * ring::SEGB + ring::NBAR * sizeof(uint64_t));
+}
 
-__global__ void __launch_bounds__(POOL_RING_THREADS, 1) pool_ring_kernel(const PoolSlotDev *__restrict__ slots,
-                                                                        const PoolItem *__restrict__ items,
-                                                                        PoolCounts *cnt, int K, int nw, int seg,
-                                                                        int *status)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__restrict__ slots,
+                                                          const PoolItem *__restrict__ items, PoolCounts *cnt, int K,
+                                                          int nw, int seg, int *status)
 {
     using namespace ring;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int item_s, abort_s;
     volatile int *abort_flag = &abort_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NWARP = POOL_RING_THREADS / 32;
-    const uint32_t ring0 = smem_addr(smem) + (uint32_t)(warp * RING * SEGB);
-    const uint32_t bar0 = smem_addr(smem) + (uint32_t)(NWARP * RING * SEGB + warp * NBAR * sizeof(uint64_t));
+    constexpr int NWARP = NT / 32;
+    constexpr int RB = pool_ring_slots<NT>() * SEGB;  // ring bytes of a warp
+    const uint32_t ring0 = smem_addr(smem) + (uint32_t)(warp * RB);
+    const uint32_t bar0 = smem_addr(smem) + (uint32_t)(NWARP * RB + warp * NBAR * sizeof(uint64_t));
     if (lane == 0) {
         for (int b = 0; b < NBAR; ++b) mbar_init1(bar0 + 8u * b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -303,8 +309,9 @@ __global__ void __launch_bounds__(POOL_RING_THREADS, 1) pool_ring_kernel(const P
                 // the last level's state stores (this CTA's) before this level's bulk reads
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 if (!*abort_flag)
-                    level_bulk<false, 4, 1>(w, m, __ldg(&S.levptr[l]) + warp, __ldg(&S.levptr[l + 1]), NWARP, tdummy,
-                                            diverged, abort_flag);
+                    level_bulk<false, 4, 1, false, pool_ring_slots<NT>()>(w, m, __ldg(&S.levptr[l]) + warp,
+                                                                          __ldg(&S.levptr[l + 1]), NWARP, tdummy,
+                                                                          diverged, abort_flag);
                 __syncthreads();
             }
         }
@@ -401,11 +408,13 @@ static cudaError_t launch_pool_sweep(int LPR, int V, const PoolSlotDev *slots, c
                                      int K, int nw, int blob_max, int seg, int *status, int grid, int threads,
                                      cudaStream_t s)
 {
-    if (LPR == 32 && threads == POOL_RING_THREADS) {
+    if (LPR == 32 && (threads == 384 || threads == 512)) {
         // the ring form
-        cudaError_t e = cudaFuncSetAttribute(pool_ring_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POOL_RING_SMEM);
+        auto kern = threads == 384 ? pool_ring_kernel<384> : pool_ring_kernel<512>;
+        const size_t smem = threads == 384 ? pool_ring_smem<384>() : pool_ring_smem<512>();
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        pool_ring_kernel<<<grid, POOL_RING_THREADS, POOL_RING_SMEM, s>>>(slots, items, cnt, K, nw, seg, status);
+        kern<<<grid, threads, smem, s>>>(slots, items, cnt, K, nw, seg, status);
         return cudaGetLastError();
     }
     switch (LPR) {
@@ -981,8 +990,8 @@ static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count, c
 // (the results are the same whichever shape runs: same arithmetic per chain);
 // the score is the sweep's time per unit of sweep work, so burn-in and sampling
 // steps compare alike.
-// {32, 384} is the ring form (a CTA of 12 warps per 128-chain block)
-static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}};
+// {32, 384} and {32, 512} are the ring form (a CTA of 12 or 16 warps per 128-chain block)
+static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}, {32, 512}};
 
 extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
 {

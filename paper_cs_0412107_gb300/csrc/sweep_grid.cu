@@ -66,13 +66,17 @@ using namespace ring;
 
 constexpr int BULK_THREADS = 384;
 constexpr int PAIR_THREADS = 512;
-// ring bytes of one warp: RING slots of G x 512 bytes, or PAIR_RN slots of 1 KB
-template <int G, bool PAIR>
-constexpr int ring_bytes() { return PAIR ? PAIR_RN * 2 * SEGB : RING * SEGB * G; }
-// per CTA: 12 / G warps, each a ring of RING slots of G x 512 bytes (192 KB in
-// all), or 16 warps of PAIR_RN 1 KB slots (the pair layout)
+// slots of one warp's ring: RING with 12 / G warps a CTA, RING16 with 16 warps
+// (separate z and w buffers), PAIR_RN on the pair layout (16 warps)
+template <int NT, bool PAIR>
+constexpr int ring_slots() { return PAIR ? PAIR_RN : NT == 512 ? RING16 : RING; }
+// ring bytes of one warp: slots of G x 512 bytes, or of 1 KB on the pair layout
 template <int NT, int G, bool PAIR>
-constexpr size_t bulk_smem() { return (size_t)(NT / 32) * (ring_bytes<G, PAIR>() + NBAR * sizeof(uint64_t)); }
+constexpr int ring_bytes() { return PAIR ? PAIR_RN * 2 * SEGB : ring_slots<NT, PAIR>() * SEGB * G; }
+// per CTA: 12 / G warps of 32 slots of G x 512 bytes (192 KB in all), or 16
+// warps of 12 KB each
+template <int NT, int G, bool PAIR>
+constexpr size_t bulk_smem() { return (size_t)(NT / 32) * (ring_bytes<NT, G, PAIR>() + NBAR * sizeof(uint64_t)); }
 
 // The grid-wide sweep: warp g keeps the chain block g mod nblk for the whole
 // launch and takes the rows g / nblk, g / nblk + R, ... of every level (R =
@@ -98,8 +102,8 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
     const int blk = gw - r0 * nblk;    // and its chain block
     const bool active = r0 < rstep;
     Lanes<CPLX, V, G> w;
-    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * ring_bytes<G, PAIR>());
-    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * ring_bytes<G, PAIR>() + warp * NBAR * sizeof(uint64_t));
+    const uint32_t ring0 = smem_addr(gsm) + (uint32_t)(warp * ring_bytes<NT, G, PAIR>());
+    const uint32_t bar0 = smem_addr(gsm) + (uint32_t)((NT / 32) * ring_bytes<NT, G, PAIR>() + warp * NBAR * sizeof(uint64_t));
     w.init(lane, blk, kv, a.K, a.n, a.seg, a.diag_part, a.noise, ring0, bar0, PAIR);
     if (threadIdx.x == 0) abort_s = 0;
     if (BULK && lane == 0) {
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                 if constexpr (BULK) {
                     // the bulk copies read rows that other CTAs wrote before the grid barrier
                     asm volatile("fence.proxy.async.global;" ::: "memory");
-                    level_bulk<CPLX, V, G, PAIR>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
+                    level_bulk<CPLX, V, G, PAIR, ring_slots<NT, PAIR>()>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
                 } else {
                     level_regs<CPLX, V>(w, m, lb + r0, le, rstep, tsum, diverged);
                 }
@@ -236,6 +240,9 @@ cudaError_t launch_pair_pack(const void *z, const void *w, void *x, long long n,
     return cudaGetLastError();
 }
 
+static_assert(bulk_smem<PAIR_THREADS, 1, true>() == bulk_smem<PAIR_THREADS, 1, false>(),
+              "the 16-warp forms share one occupancy");
+
 bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk)
 {
     const int v = cplx ? 2 : 4;
@@ -255,7 +262,7 @@ int grid_ctas(int cplx, int threads, bool bulk)
     }
     int per_sm = 0;
     if (bulk) {
-        if (threads == PAIR_THREADS)
+        if (threads == PAIR_THREADS)  // the pair and the 16-warp separate forms: the same 12 KB rings
             per_sm = cplx ? grid_blocks_per_sm<true, 2, PAIR_THREADS, true, 1, true>()
                           : grid_blocks_per_sm<false, 4, PAIR_THREADS, true, 1, true>();
         else if (threads == BULK_THREADS)
@@ -281,7 +288,7 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
     // rows of a level plus two prefetch strides stay in int; state indices in uint32
     if ((long long)a.n + 2LL * ctas * (threads / 32) >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32))
         return cudaErrorInvalidValue;
-    const int G = bulk ? BULK_THREADS / threads : 1;
+    const int G = bulk && threads <= BULK_THREADS ? BULK_THREADS / threads : 1;
     if ((long long)ctas * (threads / 32) < (g.nblk + G - 1) / G) return cudaErrorInvalidConfiguration;
     // the barrier counter starts at zero in every launch
     cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);
@@ -292,7 +299,9 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
             return cplx ? launch_grid_v<true, 2, PAIR_THREADS, true, 1, true>(a, g, ctas, s)
                         : launch_grid_v<false, 4, PAIR_THREADS, true, 1, true>(a, g, ctas, s);
         }
-        if (threads == PAIR_THREADS) return cudaErrorInvalidValue;  // 512 threads: the pair layout only
+        if (threads == PAIR_THREADS)  // 16 warps of RING16 slots
+            return cplx ? launch_grid_v<true, 2, PAIR_THREADS, true, 1>(a, g, ctas, s)
+                        : launch_grid_v<false, 4, PAIR_THREADS, true, 1>(a, g, ctas, s);
         if (threads == BULK_THREADS)
             return cplx ? launch_grid_v<true, 2, BULK_THREADS, true, 1>(a, g, ctas, s)
                         : launch_grid_v<false, 4, BULK_THREADS, true, 1>(a, g, ctas, s);

@@ -93,14 +93,16 @@ __device__ __forceinline__ Ent ent_val(const Ent &m, const Ent *__restrict__ all
     return valid ? ldg_ent(&all[base + e]) : ent_none<Ent>();
 }
 
-// The bulk-staged variant gives each warp a ring of RING 512-byte slots in
+// The bulk-staged variant gives each warp a ring of 512-byte slots (RING or RING16) in
 // shared memory.  A row's gathered segments go to consecutive slots of the
 // ring (never across its end), one cp.async.bulk each, completing on one of
 // QMAX + 1 mbarriers; up to QMAX rows are in flight while the warp computes the
-// oldest, so the gathers take no registers and a warp keeps about RING segments
-// in flight.  A row of more than RING segments waits for the ring to drain and
-// then runs in rounds of RING segments on a barrier of its own.
-constexpr int RING = 32;                  // slots per warp (a power of two)
+// oldest, so the gathers take no registers and a warp keeps about a ring of
+// segments in flight.  A row of more segments than the ring has slots waits for
+// the ring to drain and then runs in rounds of a ring each on a barrier of its
+// own.  Every slot index is taken modulo the ring's slot count.
+constexpr int RING = 32;                  // slots per warp (12 warps a CTA)
+constexpr int RING16 = 24;                // slots per warp with 16 warps a CTA (same 12 KB a warp as PAIR_RN)
 constexpr int QMAX = 3;                   // rows in flight per warp
 constexpr int NBAR = QMAX + 2;            // QMAX + 1 for the ring rows, one for long rows
 constexpr int SEGB = 512;                 // 32 lanes x 16 bytes
@@ -112,7 +114,7 @@ constexpr int PAIR_RN = 12;               // 1 KB slots per warp on the pair lay
 template <bool CPLX>
 struct RingRow {
     int p, info;
-    uint32_t vslot;  // first slot, counted from the warp's start (slot vslot mod RING)
+    uint32_t vslot;  // first slot, counted from the warp's start (slot vslot mod the ring's slots)
     uint32_t iv, use;
     float zr, zi, wr, wi;
 };
@@ -485,10 +487,10 @@ __device__ __forceinline__ void level_regs(const Lanes<CPLX, V, 1> &w, const Mat
 }
 
 // The rows p, p + rstep, ... (< le) of one level with bulk-staged gathers: a row
-// of at most RING segments goes to consecutive slots of the warp's ring (never
-// across its end), its segments one cp.async.bulk each, completing on one of
-// QMAX + 1 barriers; up to QMAX rows are in flight while the oldest is computed.
-// A longer row drains the ring and runs in rounds of RING segments.  The caller
+// of at most RNS segments goes to consecutive slots of the warp's ring of RNS
+// slots (never across its end), its segments one cp.async.bulk each, completing
+// on one of QMAX + 1 barriers; up to QMAX rows are in flight while the oldest is
+// computed.  A longer row drains the ring and runs in rounds of RNS segments.  The caller
 // has ordered the last level's state stores before these async-proxy reads
 // (fence.proxy.async after the level barrier).  On an expired wait *abort_flag
 // is set and the rows are finished with whatever landed.
@@ -498,7 +500,7 @@ __device__ __forceinline__ void level_regs(const Lanes<CPLX, V, 1> &w, const Mat
 // structurally symmetric (row i of C and of C^dagger name the same j, in the
 // same order), so z_j and w_j of a neighbour are one 1 KB segment: one copy,
 // one slot of 2 x 512 bytes, PAIR_RN slots a warp.
-template <bool CPLX, int V, int G, bool PAIR = false>
+template <bool CPLX, int V, int G, bool PAIR = false, int RNS = RING>
 __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int p, int le, int rstep,
                                            float &tsum, bool &diverged, volatile int *abort_flag)
 {
@@ -511,9 +513,10 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
     constexpr int U1 = 8;
     static_assert(!PAIR || G == 1, "pairs take one vector per lane");
     constexpr int SEGG = PAIR ? 2 * SEGB : SEGB * G;  // bytes of one slot
-    constexpr int RN = PAIR ? PAIR_RN : RING;         // slots of the warp's ring
+    constexpr int RN = PAIR ? PAIR_RN : RNS;          // slots of the warp's ring
     constexpr int WOFF = PAIR ? SEGB : 0;             // the w half of a slot (pairs)
     static_assert(QMAX >= 2 && QMAX <= 4, "queue registers");
+    static_assert(RN >= 2 && RN <= 32, "a ring's copies take a lane each");
     if (p >= le) return;
     const int lane = w.lane;
     T *const z0 = (T *)m.z0;
@@ -643,7 +646,7 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
             ++w.ic;
             w.vhead = v + nseg;
         } else {
-            // a long row: drain the ring, then rounds of up to RING segments
+            // a long row: drain the ring, then rounds of up to RN segments
             while (qn > 0) pop();
             const Cst k = ldg_cst(&m.cst[p]);
             uint32_t bits[G];
@@ -665,9 +668,9 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
                 if constexpr (PAIR) {
                     mzr = mwr = min(dz - ez, RN);
                 } else {
-                    mzr = min(dz - ez, RING / 2);
-                    mwr = min(dw - ew, RING - mzr);
-                    mzr = min(dz - ez, RING - mwr);
+                    mzr = min(dz - ez, RN / 2);
+                    mwr = min(dw - ew, RN - mzr);
+                    mzr = min(dz - ez, RN - mwr);
                 }
                 const int ncp = PAIR ? mzr : mzr + mwr;
                 const uint32_t oz = ent_off_lane(mz, m.zent, rec.y, ez + lane, lane < mzr);

@@ -51,7 +51,7 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
 @pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 0, GB),
                                             (200, 0, GB), (36, 0, GB), (256, 384, GB), (200, 0, GBS),
                                             (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
-                                            (36, 96, GB)])
+                                            (36, 96, GB), (256, 512, GB), (200, 512, GBS), (36, 512, GBS)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -59,7 +59,7 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
@@ -68,7 +68,7 @@ def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 96), (GBS, 512)])
 def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
     c = wl.wilson_dirac((3, 3, 3, 4), 0.1)  # 4 x 4 spinor hops, 14 nonzeros per row
     hg, hr = _pair(c, 64 if threads in (0, 384) else 320, flags=CO, cycles=(3, 12), grid=grid, threads=threads)
@@ -76,7 +76,7 @@ def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
@@ -146,8 +146,8 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # 256 threads
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GR)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
-    with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 512 threads (96, 192 or 384)
-        mcinv.create_from_csr(c, K=64, threads_per_cta=512, flags=GB)
+    with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 256 threads (96, 192, 384 or 512)
+        mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
     with pytest.raises(mcinv.McinvError) as e:  # and the staged kernel
         mcinv.create_from_csr(c, K=64, flags=GR | mcinv.MCINV_F_STAGED, chains_per_cta=32)

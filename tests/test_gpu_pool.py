@@ -162,14 +162,17 @@ def test_pool_colour_order_follows_the_oracle_on_the_permuted_matrices():
     mcinv.mcinv_pool_destroy(pool)
 
 
-@pytest.mark.parametrize("flags", [0, mcinv.MCINV_F_COLOR_ORDER])
-def test_pool_ring_form_equals_chain_sliced_form(flags):
-    # the ring form (a CTA of 12 warps per 128-chain block, bulk-staged gathers) and the
-    # chain-sliced form compute the same arithmetic: states and estimates bit for bit
+@pytest.mark.parametrize("flags,ring_threads", [(0, 384), (mcinv.MCINV_F_COLOR_ORDER, 384),
+                                                (0, 512), (mcinv.MCINV_F_COLOR_ORDER, 512)])
+def test_pool_ring_form_equals_chain_sliced_form(flags, ring_threads):
+    # the ring form (a CTA of 12 or 16 warps per 128-chain block, bulk-staged gathers) and
+    # the chain-sliced form compute the same arithmetic: states and estimates bit for bit
     K, B, burn, samp = 192, 4, 5, 11
-    mats = [wl.random_dominant(n, 4, 1.5, 40 + n) for n in (70, 333, 1200)] + [wl.pedigree(900, 1.2, 5)]
+    # 30 entries a row: rows longer than a 24-slot ring run in rounds
+    mats = [wl.random_dominant(n, 4, 1.5, 40 + n) for n in (70, 333, 1200)] + [wl.pedigree(900, 1.2, 5),
+                                                                                 wl.random_dominant(300, 30, 1.5, 8)]
     res = {}
-    for name, shape in (("ring", dict(chains_per_cta=128, threads_per_cta=384)),
+    for name, shape in (("ring", dict(chains_per_cta=128, threads_per_cta=ring_threads)),
                         ("sliced", dict(chains_per_cta=32, threads_per_cta=512))):
         pool = mcinv.mcinv_pool_create(K=K, seed=2, mem_budget=1 << 29, max_slots=8, batch_cycles=B, flags=flags,
                                        **shape)
