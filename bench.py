@@ -140,10 +140,11 @@ SWEEP_KERNELS = {
 }
 
 
-def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "sweep_core.cuh", "internal.h")):
+def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "sweep_core.cuh", "internal.h"),
+                          threads=None):
     """DRAM bytes per launch of the sweep from the committed ncu summary, if the
     summary was taken on the current source of the kernel and its layout (matching
-    hash of its source files)."""
+    hash of its source files) and, where it names one, the same CTA shape."""
     import hashlib
     if kernel_file is None:
         return None
@@ -154,13 +155,15 @@ def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "s
                    for f in sources
                    if os.path.exists(os.path.join(ROOT, "paper_cs_0412107_gb300", "csrc", f)))
     digest = hashlib.sha256(src).hexdigest()[:16]
-    per_unit, ok = None, False
+    per_unit, ok, shape_ok = None, False, True
     for line in open(p):
         if line.startswith("source_sha256_16:"):
             ok = line.split(":", 1)[1].strip() == digest
+        if line.startswith("threads_per_cta:") and threads is not None:
+            shape_ok = int(line.split(":", 1)[1]) == threads
         if line.startswith("dram_bytes_per_unit:"):
             per_unit = float(line.split(":", 1)[1])
-    if ok and per_unit is not None:
+    if ok and shape_ok and per_unit is not None:
         return per_unit * units_per_launch
     return None
 
@@ -274,7 +277,7 @@ def run_mine(args, world, rank, local):
                    "parallelism": f"replicas x{world} (disjoint chains)"},
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
-                     "traffic": traffic_from_profiles(kprof, units_per_launch, ksrc),
+                     "traffic": traffic_from_profiles(kprof, units_per_launch, ksrc, info0["threads_per_cta"]),
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "bytes_per_unit": alg_bytes / units_per_launch,

@@ -117,10 +117,16 @@ typedef struct {
 #define MCINV_F_GRID_NOPAIR 64 /* with MCINV_F_GRID_BULK: keep z and w in separate buffers.  Without it,
                               for a structurally symmetric C (row i of C and of C^dagger name the
                               same columns) and threads_per_cta 0 the bulk sweep keeps the state
-                              in the pair layout (16 warps of 12 slots of 1 KB), a
-                              chain block's z and w of a row side by side, so one 1 KB copy
-                              gathers both; readers of the state (mcinv_get_state, the CUDA-core
-                              block accumulation) see the usual layout.  Same values, bit for bit. */
+                              in the pair layout, a 32-vector chain block's z and w of a row side
+                              by side, so one copy gathers both: 12 warps a CTA, each taking two
+                              adjacent blocks (2 KB copies into 9 slots).  Readers of the state
+                              (mcinv_get_state, the CUDA-core block accumulation) see the usual
+                              layout.  Same values, bit for bit. */
+#define MCINV_F_GRID_PAIR 128 /* with MCINV_F_GRID_BULK: the pair layout with the shape that
+                              threads_per_cta names: 512 (16 warps, one block a warp, 12 slots of
+                              1 KB), 384 (the default) or 256 (8 warps, two blocks a warp, 13 slots
+                              of 2 KB).  MCINV_E_UNSUPPORTED when C is not structurally symmetric;
+                              MCINV_E_ARG with MCINV_F_GRID_NOPAIR or another thread count. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.

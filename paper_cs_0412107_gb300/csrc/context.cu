@@ -297,13 +297,14 @@ static mcinv_status autotune(mcinv_ctx *h)
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
+        // (a shape on the pair layout is for handles that hold the pair buffers)
+        if (it != g_tune_cache.end() && (!it->second.gpair || h->d_x)) {
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->grid = it->second.grid;
             h->gbulk = it->second.gbulk;
-            h->gpair = it->second.gpair && h->d_x;
-            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads, h->gbulk);
+            h->gpair = it->second.gpair;
+            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -371,17 +372,18 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 7; ++variant) {
+    for (int variant = 0; variant < 9; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
         // lane (12 warps of 32 slots) or 1 (16 warps of 24 slots); bulk-staged on the pair
-        // layout (structurally symmetric matrices)
-        static const int kT[7] = {384, 512, 384, 192, 96, 512, 512};
+        // layout (structurally symmetric matrices) with one vector a lane (16 warps) or two
+        // (12 or 8 warps)
+        static const int kT[9] = {384, 512, 384, 192, 96, 512, 512, 384, 256};
         const int T = kT[variant];
         const bool bulk = variant >= 2;
-        const bool pair = variant == 5;
+        const bool pair = variant == 5 || variant >= 7;
         if (pair && !h->d_x) continue;
-        const int ctas = grid_ctas(h->cplx, T, bulk);
-        if (!grid_supported(h->cplx, vmax, h->K, T, bulk) || ctas < 1 || h->gnkv == 0) continue;
+        const int ctas = grid_ctas(h->cplx, T, bulk, pair);
+        if (!grid_supported(h->cplx, vmax, h->K, pair ? 512 : T, bulk) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
         const bool sG = h->grid, sB = h->gbulk, sP = h->gpair;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
@@ -410,7 +412,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     h->grid = best.grid;
     h->gbulk = best.gbulk;
     h->gpair = best.gpair;
-    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads, h->gbulk) : 0;
+    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair) : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -563,6 +565,10 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         h->Q = q;
     }
 
+    if ((h->flags & MCINV_F_GRID_PAIR) && !((h->flags & MCINV_F_GRID) && (h->flags & MCINV_F_GRID_BULK))) {
+        fail(h, MCINV_E_ARG, "MCINV_F_GRID_PAIR needs MCINV_F_GRID and MCINV_F_GRID_BULK");
+        return bail(MCINV_E_ARG);
+    }
     if (h->flags & MCINV_F_STAGED) {
         if (!staged_supported(cplx, h->LPR, h->V, opt.K, h->blob_max)) {
             fail(h, MCINV_E_UNSUPPORTED,
@@ -576,8 +582,14 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         const int vmax = cplx ? 2 : 4;
         const bool bulk = (h->flags & MCINV_F_GRID_BULK) != 0;
         const int T = opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
-        // (with bulk staging and no explicit shape the pair layout is chosen below when it applies)
-        const int ctas = grid_supported(cplx, vmax, opt.K, T, bulk) ? grid_ctas(cplx, T, bulk) : 0;
+        // (with bulk staging and no explicit shape, or MCINV_F_GRID_PAIR, the pair layout is
+        // chosen below when it applies)
+        const bool fpair = (h->flags & MCINV_F_GRID_PAIR) != 0;
+        if (fpair && ((h->flags & MCINV_F_GRID_NOPAIR) || (T != 512 && T != 384 && T != 256))) {
+            fail(h, MCINV_E_ARG, "MCINV_F_GRID_PAIR takes 512, 384 or 256 threads per CTA, not MCINV_F_GRID_NOPAIR");
+            return bail(MCINV_E_ARG);
+        }
+        const int ctas = grid_supported(cplx, vmax, opt.K, fpair ? 512 : T, bulk) ? grid_ctas(cplx, T, bulk, fpair) : 0;
         if (h->staged || ctas < 1) {
             fail(h, MCINV_E_UNSUPPORTED,
                  "the grid-wide sweep needs K a multiple of %d, 384 or 512 threads per CTA (96, 192, 384 or 512 "
@@ -702,19 +714,29 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     SETUP(cudaMemsetAsync(h->d_z[0], 0, 2 * state * esz, h->stream));
     SETUP(cudaMemsetAsync(h->d_w[0], 0, 2 * state * esz, h->stream));
     // the pair-layout buffers, when the bulk sweep may run on them
+    const bool fpair = (h->flags & MCINV_F_GRID_PAIR) != 0;
+    if (fpair && !h->pair_able) {
+        fail(h, MCINV_E_UNSUPPORTED, "MCINV_F_GRID_PAIR needs a structurally symmetric C (row i of C and of "
+                                     "C^dagger naming the same columns)");
+        return bail(MCINV_E_UNSUPPORTED);
+    }
     const bool want_pair = h->pair_able && !(h->flags & MCINV_F_GRID_NOPAIR) &&
-                           (((h->flags & MCINV_F_GRID) && h->gbulk && opt.threads_per_cta <= 0) ||
+                           (((h->flags & MCINV_F_GRID) && h->gbulk && (opt.threads_per_cta <= 0 || fpair)) ||
                             ((h->flags & MCINV_F_AUTOTUNE) && !(h->flags & MCINV_F_GRID)));
     if (want_pair) {
-        const int pc = grid_ctas(cplx, 512, true);
+        // the pair layout: 12 warps a CTA, two 32-vector blocks a warp, by default
+        const int pt = fpair && opt.threads_per_cta > 0 ? opt.threads_per_cta : 384;
+        const int pc = grid_ctas(cplx, pt, true, true);
         if (pc > 0) {
             SETUP(dalloc(h, (char **)&h->d_x, 2 * (size_t)h->gpnkv * 16));
             if (h->grid) {
-                // the pair layout: 16 warps a CTA
                 h->gpair = true;
-                h->threads = 512;
+                h->threads = pt;
                 h->gctas = pc;
             }
+        } else if (fpair) {
+            fail(h, MCINV_E_UNSUPPORTED, "the pair-layout sweep with %d threads per CTA has no resident CTA", pt);
+            return bail(MCINV_E_UNSUPPORTED);
         }
     }
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));

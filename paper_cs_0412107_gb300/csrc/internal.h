@@ -164,11 +164,13 @@ struct GridArgs {
     unsigned *bar;             // barrier arrivals (zeroed by the launcher before each launch)
 };
 // threads: 384 or 512 with the gathers in registers; bulk: the warps stage their
-// gathers in shared memory with bulk copies, 384 threads with 512-byte segments,
-// 192 with 1 KB or 96 with 2 KB (a warp's chain block is 1, 2 or 4 x 32 vectors),
-// or 512 on the pair layout (GridArgs.pair).  One CTA per SM.
+// gathers in shared memory with bulk copies, 384 or 512 threads with 512-byte
+// segments, 192 with 1 KB or 96 with 2 KB (a warp's chain block is 1, 2 or 4 x 32
+// vectors); on the pair layout (GridArgs.pair, pair = true) 512 threads with 1 KB
+// segments (z and w of a 32-vector block) or 384 or 256 with 2 KB (two blocks).
+// One CTA per SM.
 bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool bulk);
-int grid_ctas(int cplx, int threads, bool bulk);  // CTAs resident at once on the device; 0: not launchable
+int grid_ctas(int cplx, int threads, bool bulk, bool pair = false);  // CTAs resident at once on the device; 0: not launchable
 cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, int ctas, int threads, bool bulk,
                               cudaStream_t s);
 // The pair layout of the chain state for the grid-wide bulk sweep of structurally

@@ -66,17 +66,25 @@ using namespace ring;
 
 constexpr int BULK_THREADS = 384;
 constexpr int PAIR_THREADS = 512;
-// slots of one warp's ring: RING with 12 / G warps a CTA, RING16 with 16 warps
-// (separate z and w buffers), PAIR_RN on the pair layout (16 warps)
-template <int NT, bool PAIR>
-constexpr int ring_slots() { return PAIR ? PAIR_RN : NT == 512 ? RING16 : RING; }
-// ring bytes of one warp: slots of G x 512 bytes, or of 1 KB on the pair layout
+// slots of one warp's ring.  Separate z and w buffers: RING with 12 / G warps
+// a CTA, RING16 with 16 warps.  The pair layout: PAIR_RN slots of 1 KB with 16
+// warps (G = 1); with G = 2 (two adjacent blocks a warp, 2 KB slots) 9 slots
+// with 12 warps or 13 with 8.
 template <int NT, int G, bool PAIR>
-constexpr int ring_bytes() { return PAIR ? PAIR_RN * 2 * SEGB : ring_slots<NT, PAIR>() * SEGB * G; }
-// per CTA: 12 / G warps of 32 slots of G x 512 bytes (192 KB in all), or 16
-// warps of 12 KB each
+constexpr int ring_slots()
+{
+    return PAIR ? (G == 1 ? PAIR_RN : NT == 384 ? 9 : 13) : NT == 512 ? RING16 : RING;
+}
+// ring bytes of one warp: slots of G x 512 bytes, or of G x 1 KB on the pair layout
+template <int NT, int G, bool PAIR>
+constexpr int ring_bytes() { return ring_slots<NT, G, PAIR>() * (PAIR ? 2 : 1) * SEGB * G; }
 template <int NT, int G, bool PAIR>
 constexpr size_t bulk_smem() { return (size_t)(NT / 32) * (ring_bytes<NT, G, PAIR>() + NBAR * sizeof(uint64_t)); }
+// the threads of a CTA and the vectors a lane of the bulk-staged forms
+constexpr int bulk_g(int threads, bool pair)
+{
+    return pair ? (threads == PAIR_THREADS ? 1 : 2) : threads <= BULK_THREADS ? BULK_THREADS / threads : 1;
+}
 
 // The grid-wide sweep: warp g keeps the chain block g mod nblk for the whole
 // launch and takes the rows g / nblk, g / nblk + R, ... of every level (R =
@@ -86,7 +94,8 @@ template <bool CPLX, int V, int NT, bool BULK, int G, bool PAIR = false>
 __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a, const GridArgs g)
 {
     static_assert(BULK || G == 1, "register gathers take one vector per lane");
-    static_assert(!PAIR || (BULK && G == 1), "the pair layout is read with bulk copies, one vector per lane");
+    static_assert(!PAIR || (BULK && G <= 2), "the pair layout is read with bulk copies, one or two vectors a lane");
+    static_assert(!BULK || bulk_smem<NT, G, PAIR>() <= 227u * 1024u, "rings fit the shared memory of a CTA");
     extern __shared__ __align__(128) uint8_t gsm[];
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
                 if constexpr (BULK) {
                     // the bulk copies read rows that other CTAs wrote before the grid barrier
                     asm volatile("fence.proxy.async.global;" ::: "memory");
-                    level_bulk<CPLX, V, G, PAIR, ring_slots<NT, PAIR>()>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
+                    level_bulk<CPLX, V, G, PAIR, ring_slots<NT, G, PAIR>()>(w, m, lb + r0, le, rstep, tsum, diverged, abort_flag);
                 } else {
                     level_regs<CPLX, V>(w, m, lb + r0, le, rstep, tsum, diverged);
                 }
@@ -253,7 +262,7 @@ bool grid_supported(int cplx, int chains_per_lane, int64_t K, int threads, bool 
     return threads == 384 || threads == 512;
 }
 
-int grid_ctas(int cplx, int threads, bool bulk)
+int grid_ctas(int cplx, int threads, bool bulk, bool pair)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -261,7 +270,12 @@ int grid_ctas(int cplx, int threads, bool bulk)
         return 0;
     }
     int per_sm = 0;
-    if (bulk) {
+    if (bulk && pair && threads != PAIR_THREADS) {
+        if (threads == 384)
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, 384, true, 2, true>() : grid_blocks_per_sm<false, 4, 384, true, 2, true>();
+        else if (threads == 256)
+            per_sm = cplx ? grid_blocks_per_sm<true, 2, 256, true, 2, true>() : grid_blocks_per_sm<false, 4, 256, true, 2, true>();
+    } else if (bulk) {
         if (threads == PAIR_THREADS)  // the pair and the 16-warp separate forms: the same 12 KB rings
             per_sm = cplx ? grid_blocks_per_sm<true, 2, PAIR_THREADS, true, 1, true>()
                           : grid_blocks_per_sm<false, 4, PAIR_THREADS, true, 1, true>();
@@ -288,13 +302,19 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
     // rows of a level plus two prefetch strides stay in int; state indices in uint32
     if ((long long)a.n + 2LL * ctas * (threads / 32) >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32))
         return cudaErrorInvalidValue;
-    const int G = bulk && threads <= BULK_THREADS ? BULK_THREADS / threads : 1;
+    const int G = bulk ? bulk_g(threads, g.pair != 0) : 1;
     if ((long long)ctas * (threads / 32) < (g.nblk + G - 1) / G) return cudaErrorInvalidConfiguration;
     // the barrier counter starts at zero in every launch
     cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     if (bulk) {
         if (g.pair) {
+            if (threads == 384)
+                return cplx ? launch_grid_v<true, 2, 384, true, 2, true>(a, g, ctas, s)
+                            : launch_grid_v<false, 4, 384, true, 2, true>(a, g, ctas, s);
+            if (threads == 256)
+                return cplx ? launch_grid_v<true, 2, 256, true, 2, true>(a, g, ctas, s)
+                            : launch_grid_v<false, 4, 256, true, 2, true>(a, g, ctas, s);
             if (threads != PAIR_THREADS) return cudaErrorInvalidValue;
             return cplx ? launch_grid_v<true, 2, PAIR_THREADS, true, 1, true>(a, g, ctas, s)
                         : launch_grid_v<false, 4, PAIR_THREADS, true, 1, true>(a, g, ctas, s);

@@ -266,11 +266,15 @@ struct Lanes {
             cshift[q] = (uint32_t)(c0[q] & 31);
         }
         if (pair) {
-            // a row's block blk: 32 z vectors, then the same chains' 32 w vectors
-            zo[0] = (uint32_t)(blk * 64 + lane);
-            wo[0] = zo[0] + 32u;
-            cvb = (uint32_t)(blk * 64);
-            seg_bytes = 2u * SEGB;
+            // a row's 32-vector block b: 32 z vectors, then the same chains' 32 w
+            // vectors; the warp's G blocks are adjacent (the last may be past the row)
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                zo[q] = (uint32_t)((blk * G + q) * 64 + lane);
+                wo[q] = zo[q] + 32u;
+            }
+            cvb = (uint32_t)(blk * G * 64);
+            seg_bytes = (uint32_t)min(G, (kv + 31) / 32 - blk * G) * 2u * SEGB;
         } else {
 #pragma unroll
             for (int q = 0; q < G; ++q) zo[q] = wo[q] = cv[q];
@@ -511,10 +515,10 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
     using Ent = typename P::Ent;
     using Cst = typename P::Cst;
     constexpr int U1 = 8;
-    static_assert(!PAIR || G == 1, "pairs take one vector per lane");
-    constexpr int SEGG = PAIR ? 2 * SEGB : SEGB * G;  // bytes of one slot
-    constexpr int RN = PAIR ? PAIR_RN : RNS;          // slots of the warp's ring
-    constexpr int WOFF = PAIR ? SEGB : 0;             // the w half of a slot (pairs)
+    constexpr int SEGG = PAIR ? 2 * SEGB * G : SEGB * G;  // bytes of one slot
+    constexpr int RN = RNS;                               // slots of the warp's ring
+    constexpr int WOFF = PAIR ? SEGB : 0;                 // the w half of a block's pair
+    constexpr int QOFF = PAIR ? 2 * SEGB : SEGB;          // vector q of a lane, from vector 0
     static_assert(QMAX >= 2 && QMAX <= 4, "queue registers");
     static_assert(RN >= 2 && RN <= 32, "a ring's copies take a lane each");
     if (p >= le) return;
@@ -573,21 +577,21 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
                 if (u < dz) {
                     const Ent e = shfl_val(az, u);
 #pragma unroll
-                    for (int q = 0; q < G; ++q) L::fma(sz[q], e, lds_vec<T>(zb + u * SEGG + q * SEGB));
+                    for (int q = 0; q < G; ++q) L::fma(sz[q], e, lds_vec<T>(zb + u * SEGG + q * QOFF));
                 }
 #pragma unroll
             for (int u = 0; u < U1; ++u)
                 if (u < dw) {
                     const Ent e = shfl_val(aw, u);
 #pragma unroll
-                    for (int q = 0; q < G; ++q) L::fma(sw[q], e, lds_vec<T>(wb + u * SEGG + q * SEGB));
+                    for (int q = 0; q < G; ++q) L::fma(sw[q], e, lds_vec<T>(wb + u * SEGG + q * QOFF));
                 }
         } else {
 #pragma unroll
             for (int q = 0; q < G; ++q) {
                 PieceSum<L> pzs(dz, r.info & 3), pws(dw, r.info & 3);
-                for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(zb + e * SEGG + q * SEGB));
-                for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(wb + e * SEGG + q * SEGB));
+                for (int e = 0; e < dz; ++e) pzs.add(e, shfl_val(az, e), lds_vec<T>(zb + e * SEGG + q * QOFF));
+                for (int e = 0; e < dw; ++e) pws.add(e, shfl_val(aw, e), lds_vec<T>(wb + e * SEGG + q * QOFF));
                 sz[q] = pzs.total();
                 sw[q] = pws.total();
             }
@@ -688,13 +692,13 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
                 for (int e = 0; e < mzr; ++e) {
                     const Ent en = ent_val(mz, m.zent, rec.y, ez + e, true);
 #pragma unroll
-                    for (int q = 0; q < G; ++q) pzs[q].add(ez + e, en, lds_vec<T>(sa + e * SEGG + q * SEGB));
+                    for (int q = 0; q < G; ++q) pzs[q].add(ez + e, en, lds_vec<T>(sa + e * SEGG + q * QOFF));
                 }
                 for (int e = 0; e < mwr; ++e) {
                     const Ent en = ent_val(mw, m.went, rec.z, ew + e, true);
 #pragma unroll
                     for (int q = 0; q < G; ++q)
-                        pws[q].add(ew + e, en, lds_vec<T>(sa + (PAIR ? e * SEGG + WOFF : (mzr + e) * SEGG) + q * SEGB));
+                        pws[q].add(ew + e, en, lds_vec<T>(sa + (PAIR ? e * SEGG + WOFF : (mzr + e) * SEGG) + q * QOFF));
                 }
                 ez += mzr;
                 ew += mwr;

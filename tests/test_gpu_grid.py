@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 GR = mcinv.MCINV_F_GRID
 GB = mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK
 GBS = GB | mcinv.MCINV_F_GRID_NOPAIR  # bulk staging, z and w in separate buffers
+GP = GB | mcinv.MCINV_F_GRID_PAIR  # bulk staging on the pair layout, in the shape threads names
 CO = mcinv.MCINV_F_COLOR_ORDER
 
 
@@ -34,7 +35,7 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
                                threads_per_cta=256, flags=flags, **kw)
     info = mcinv.mcinv_info(hg)
     # the pair layout where C is structurally symmetric (bulk staging, default threads)
-    want = (3, 4) if grid == GB and threads == 0 else (3,) if grid in (GB, GBS) else (2,)
+    want = (3, 4) if grid == GB and threads == 0 else (4,) if grid == GP else (3,) if grid in (GB, GBS) else (2,)
     assert info["sweep_kernel"] in want and info["grid_ctas"] >= 1
     done = 0
     for cyc in cycles:
@@ -51,7 +52,9 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
 @pytest.mark.parametrize("K,threads,grid", [(256, 384, GR), (200, 512, GR), (36, 384, GR), (256, 0, GB),
                                             (200, 0, GB), (36, 0, GB), (256, 384, GB), (200, 0, GBS),
                                             (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
-                                            (36, 96, GB), (256, 512, GB), (200, 512, GBS), (36, 512, GBS)])
+                                            (36, 96, GB), (256, 512, GB), (200, 512, GBS), (36, 512, GBS),
+                                            (256, 512, GP), (200, 384, GP), (36, 384, GP), (1024, 384, GP),
+                                            (520, 256, GP), (900, 256, GP)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -59,7 +62,8 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
+                                          (GP, 384), (GP, 256)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
@@ -76,7 +80,8 @@ def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512)])
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
+                                          (GP, 256)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
@@ -149,6 +154,13 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 256 threads (96, 192, 384 or 512)
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
+    for flags, threads in ((GP, 192), (GP | mcinv.MCINV_F_GRID_NOPAIR, 384), (GR | mcinv.MCINV_F_GRID_PAIR, 384)):
+        with pytest.raises(mcinv.McinvError) as e:  # the pair shapes: 512, 384 or 256 threads, bulk staging
+            mcinv.create_from_csr(wl.pedigree(500, 1.2, 1), K=64, threads_per_cta=threads, flags=flags)
+        assert e.value.status == mcinv.MCINV_E_ARG
+    with pytest.raises(mcinv.McinvError) as e:  # the pair layout of a matrix that is not structurally symmetric
+        mcinv.create_from_csr(c, K=64, threads_per_cta=384, flags=GP)
+    assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
     with pytest.raises(mcinv.McinvError) as e:  # and the staged kernel
         mcinv.create_from_csr(c, K=64, flags=GR | mcinv.MCINV_F_STAGED, chains_per_cta=32)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
@@ -159,7 +171,8 @@ def test_pair_layout_is_used_and_survives_state_round_trips():
     # between launches, writing it back and resuming give the uninterrupted run's bits
     c = wl.pedigree(4000, 1.2, 9)
     h = mcinv.create_from_csr(c, K=256, seed=6, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=GB | CO, batch_cycles=3)
-    assert mcinv.mcinv_info(h)["sweep_kernel"] == 4
+    info = mcinv.mcinv_info(h)
+    assert info["sweep_kernel"] == 4 and info["threads_per_cta"] == 384  # 12 warps, two blocks a warp
     g = mcinv.create_from_csr(c, K=256, seed=6, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=GBS | CO, batch_cycles=3)
     assert mcinv.mcinv_info(g)["sweep_kernel"] == 3
     mcinv.mcinv_burnin(h, 7)
