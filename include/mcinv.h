@@ -341,7 +341,10 @@ typedef struct {
     int32_t max_slots;      /* matrices resident at once */
     int32_t batch_cycles;   /* B: cycles every matrix advances per step; 0 = 8 */
     int32_t groups;         /* SE groups of the diagonal; 0 = 32 */
-    int32_t chains_per_cta; /* 0 = the first steps time the candidate shapes */
+    int32_t chains_per_cta; /* 0 = the first steps time the candidate shapes; 4 x a power of two
+                               <= 128 (a chain slice per CTA; 128 with 384 or 512 threads: the
+                               bulk-staged ring form), or 256 (the ring form, two vectors a lane,
+                               384 threads) */
     int32_t threads_per_cta;
     int32_t flags;
     void *stream;

@@ -233,33 +233,36 @@ __global__ void __launch_bounds__(512, 1) pool_sweep_kernel(const PoolSlotDev *_
     }
 }
 
-// The ring form of the sweep: a CTA of NT / 32 warps (12 with 32-slot rings or
-// 16 with 24-slot rings) takes a (slot, 128-chain block) item from the device
-// queue and runs the slot's cycles of this step; warp w takes the rows lb + w,
-// lb + w + NT / 32, ... of each level with bulk-staged gathers
-// (ring::level_bulk, the same arithmetic), and a CTA barrier ends every level:
-// the whole chain block of the matrix is this CTA's.  The warps' rings,
-// barriers and their phases persist across items.
-template <int NT>
-constexpr int pool_ring_slots() { return NT == 512 ? ring::RING16 : ring::RING; }
-template <int NT>
+// The ring form of the sweep: a CTA of NT / 32 warps takes a (slot, chain
+// block) item from the device queue and runs the slot's cycles of this step;
+// warp w takes the rows lb + w, lb + w + NT / 32, ... of each level with
+// bulk-staged gathers (ring::level_bulk, the same arithmetic), and a CTA
+// barrier ends every level: the whole chain block of the matrix is this CTA's.
+// Shapes: 12 warps of 32 slots or 16 warps of 24 slots of 512 bytes for a
+// 128-chain block (G = 1), or 12 warps of 18 slots of 1 KB for a 256-chain
+// block (G = 2: two vectors a lane, the row's fixed work paid once for both).
+// The warps' rings, barriers and their phases persist across items.
+template <int NT, int G>
+constexpr int pool_ring_slots() { return G == 2 ? 18 : NT == 512 ? ring::RING16 : ring::RING; }
+template <int NT, int G>
 constexpr size_t pool_ring_smem()
 {
-    return (size_t)(NT / 32) * (pool_ring_slots<NT>() * ring::SEGB + ring::NBAR * sizeof(uint64_t));
+    return (size_t)(NT / 32) * (pool_ring_slots<NT, G>() * ring::SEGB * G + ring::NBAR * sizeof(uint64_t));
 }
 
-template <int NT>
+template <int NT, int G>
 __global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__restrict__ slots,
                                                           const PoolItem *__restrict__ items, PoolCounts *cnt, int K,
                                                           int nw, int seg, int *status)
 {
     using namespace ring;
+    static_assert(pool_ring_smem<NT, G>() <= 227u * 1024u, "rings fit the shared memory of a CTA");
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int item_s, abort_s;
     volatile int *abort_flag = &abort_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NWARP = NT / 32;
-    constexpr int RB = pool_ring_slots<NT>() * SEGB;  // ring bytes of a warp
+    constexpr int RB = pool_ring_slots<NT, G>() * SEGB * G;  // ring bytes of a warp
     const uint32_t ring0 = smem_addr(smem) + (uint32_t)(warp * RB);
     const uint32_t bar0 = smem_addr(smem) + (uint32_t)(NWARP * RB + warp * NBAR * sizeof(uint64_t));
     if (lane == 0) {
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__r
     }
     if (threadIdx.x == 0) abort_s = 0;
     __syncthreads();
-    Lanes<false, 4, 1> w;
+    Lanes<false, 4, G> w;
     w.init(lane, 0, 1, K, 1, seg, nullptr, nullptr, ring0, bar0);  // the ring; the block is set per item
     const int kv = K / 4;
     bool diverged = false;
@@ -309,9 +312,9 @@ __global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__r
                 // the last level's state stores (this CTA's) before this level's bulk reads
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 if (!*abort_flag)
-                    level_bulk<false, 4, 1, false, pool_ring_slots<NT>()>(w, m, __ldg(&S.levptr[l]) + warp,
-                                                                          __ldg(&S.levptr[l + 1]), NWARP, tdummy,
-                                                                          diverged, abort_flag);
+                    level_bulk<false, 4, G, false, pool_ring_slots<NT, G>()>(w, m, __ldg(&S.levptr[l]) + warp,
+                                                                             __ldg(&S.levptr[l + 1]), NWARP, tdummy,
+                                                                             diverged, abort_flag);
                 __syncthreads();
             }
         }
@@ -408,10 +411,10 @@ static cudaError_t launch_pool_sweep(int LPR, int V, const PoolSlotDev *slots, c
                                      int K, int nw, int blob_max, int seg, int *status, int grid, int threads,
                                      cudaStream_t s)
 {
-    if (LPR == 32 && (threads == 384 || threads == 512)) {
-        // the ring form
-        auto kern = threads == 384 ? pool_ring_kernel<384> : pool_ring_kernel<512>;
-        const size_t smem = threads == 384 ? pool_ring_smem<384>() : pool_ring_smem<512>();
+    if ((LPR == 32 && (threads == 384 || threads == 512)) || (LPR == 64 && threads == 384)) {
+        // the ring form: 128-chain blocks (12 or 16 warps) or 256-chain blocks (12 warps)
+        auto kern = LPR == 64 ? pool_ring_kernel<384, 2> : threads == 384 ? pool_ring_kernel<384, 1> : pool_ring_kernel<512, 1>;
+        const size_t smem = LPR == 64 ? pool_ring_smem<384, 2>() : threads == 384 ? pool_ring_smem<384, 1>() : pool_ring_smem<512, 1>();
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, threads, smem, s>>>(slots, items, cnt, K, nw, seg, status);
@@ -615,15 +618,17 @@ extern "C" mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_op
     p->V = 4;
     if (o.chains_per_cta > 0) {
         p->LPR = o.chains_per_cta / 4;
-        if (p->LPR < 1 || p->LPR > 32 || (p->LPR & (p->LPR - 1))) {
+        const bool ring2 = p->LPR == 64 && o.chains_per_cta == 256 && (o.threads_per_cta == 0 || o.threads_per_cta == 384);
+        if (!ring2 && (p->LPR < 1 || p->LPR > 32 || (p->LPR & (p->LPR - 1)) || o.chains_per_cta != 4 * p->LPR)) {
             delete p;
-            return pfail(nullptr, MCINV_E_ARG, "chains_per_cta must be 4 x a power of two <= 128");
+            return pfail(nullptr, MCINV_E_ARG,
+                         "chains_per_cta must be 4 x a power of two <= 128, or 256 (the ring form, 384 threads)");
         }
         p->fixed_shape = true;
     } else {
         p->LPR = 8;  // 32-chain slices; the first steps time the alternatives
     }
-    p->threads = o.threads_per_cta > 0 ? o.threads_per_cta : 512;
+    p->threads = o.threads_per_cta > 0 ? o.threads_per_cta : p->LPR == 64 ? 384 : 512;
     if (p->threads % 32 || p->threads > 512) {
         delete p;
         return pfail(nullptr, MCINV_E_ARG, "threads_per_cta must be a multiple of 32, <= 512");
@@ -632,7 +637,7 @@ extern "C" mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_op
     // SE units: seg lanes (seg x 4 chains) with seg <= every candidate slice's lanes (>= 2)
     const int Greq = o.groups > 0 ? o.groups : 32;
     int seg = 1;
-    const int minL = p->fixed_shape ? p->LPR : 2;
+    const int minL = p->fixed_shape ? std::min(p->LPR, 32) : 2;
     while (seg * 2 <= minL && (int64_t)seg * 2 * 4 * Greq <= o.K) seg *= 2;
     p->seg = seg;
     p->units = (int)((o.K + seg * 4 - 1) / (seg * 4));
@@ -990,8 +995,10 @@ static mcinv_status launch_step(mcinv_pool_ctx *p, cudaStream_t s, bool count, c
 // (the results are the same whichever shape runs: same arithmetic per chain);
 // the score is the sweep's time per unit of sweep work, so burn-in and sampling
 // steps compare alike.
-// {32, 384} and {32, 512} are the ring form (a CTA of 12 or 16 warps per 128-chain block)
-static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}, {32, 512}};
+// {32, 384} and {32, 512} are the ring form (a CTA of 12 or 16 warps per 128-chain block),
+// {64, 384} the ring form with 256-chain blocks (two vectors a lane)
+static const int kTuneL[][2] = {{2, 512}, {4, 512}, {8, 512}, {8, 256}, {16, 256}, {32, 256}, {32, 384}, {32, 512},
+                                {64, 384}};
 
 extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
 {

@@ -162,17 +162,19 @@ def test_pool_colour_order_follows_the_oracle_on_the_permuted_matrices():
     mcinv.mcinv_pool_destroy(pool)
 
 
-@pytest.mark.parametrize("flags,ring_threads", [(0, 384), (mcinv.MCINV_F_COLOR_ORDER, 384),
-                                                (0, 512), (mcinv.MCINV_F_COLOR_ORDER, 512)])
-def test_pool_ring_form_equals_chain_sliced_form(flags, ring_threads):
-    # the ring form (a CTA of 12 or 16 warps per 128-chain block, bulk-staged gathers) and
-    # the chain-sliced form compute the same arithmetic: states and estimates bit for bit
+@pytest.mark.parametrize("flags,ring_threads,ring_chains", [(0, 384, 128), (mcinv.MCINV_F_COLOR_ORDER, 384, 128),
+                                                            (0, 512, 128), (mcinv.MCINV_F_COLOR_ORDER, 512, 128),
+                                                            (0, 384, 256), (mcinv.MCINV_F_COLOR_ORDER, 384, 256)])
+def test_pool_ring_form_equals_chain_sliced_form(flags, ring_threads, ring_chains):
+    # the ring form (a CTA of 12 or 16 warps per 128-chain block, or 12 warps per 256-chain
+    # block, bulk-staged gathers) and the chain-sliced form compute the same arithmetic:
+    # states and estimates bit for bit (K = 192: a 256-chain block that the chains fill in part)
     K, B, burn, samp = 192, 4, 5, 11
     # 30 entries a row: rows longer than a 24-slot ring run in rounds
     mats = [wl.random_dominant(n, 4, 1.5, 40 + n) for n in (70, 333, 1200)] + [wl.pedigree(900, 1.2, 5),
                                                                                  wl.random_dominant(300, 30, 1.5, 8)]
     res = {}
-    for name, shape in (("ring", dict(chains_per_cta=128, threads_per_cta=ring_threads)),
+    for name, shape in (("ring", dict(chains_per_cta=ring_chains, threads_per_cta=ring_threads)),
                         ("sliced", dict(chains_per_cta=32, threads_per_cta=512))):
         pool = mcinv.mcinv_pool_create(K=K, seed=2, mem_budget=1 << 29, max_slots=8, batch_cycles=B, flags=flags,
                                        **shape)
@@ -191,11 +193,12 @@ def test_pool_ring_form_equals_chain_sliced_form(flags, ring_threads):
         assert np.array_equal(br[0], bs[0]) and np.array_equal(br[1], bs[1])
 
 
-def test_pool_ring_form_follows_the_oracle():
+@pytest.mark.parametrize("ring_chains", [128, 256])
+def test_pool_ring_form_follows_the_oracle(ring_chains):
     K, B, burn, samp = 64, 4, 6, 7
     mats = [wl.random_dominant(n, 4, 1.5, seed) for n, seed in ((64, 1), (517, 3))] + [wl.pedigree(700, 1.2, 2)]
     pool = mcinv.mcinv_pool_create(K=K, seed=11, mem_budget=1 << 28, max_slots=8, batch_cycles=B,
-                                   chains_per_cta=128, threads_per_cta=384)
+                                   chains_per_cta=ring_chains, threads_per_cta=384)
     tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=100 + k, burnin=burn, samples=samp)
                for k, c in enumerate(mats)]
     run_until_done(pool, tickets)
@@ -206,3 +209,16 @@ def test_pool_ring_form_follows_the_oracle():
         assert rel_err(z, st.z.real) < TOL and rel_err(w, st.w.real) < TOL
         dm, _ = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, c.n)
         assert rel_err(dm, dacc.sum(0).real / (K * samp)) < TOL
+
+
+def test_pool_shape_rejections():
+    # chain slices of 4 x a power of two <= 128, or the 256-chain ring form with 384 threads
+    for shape in (dict(chains_per_cta=256, threads_per_cta=512), dict(chains_per_cta=96),
+                  dict(chains_per_cta=512)):
+        with pytest.raises(mcinv.McinvError) as e:
+            mcinv.mcinv_pool_create(K=256, seed=1, mem_budget=1 << 26, max_slots=2, **shape)
+        assert e.value.status == mcinv.MCINV_E_ARG
+    pool = mcinv.mcinv_pool_create(K=256, seed=1, mem_budget=1 << 26, max_slots=2, chains_per_cta=256)
+    info = mcinv.mcinv_pool_info(pool)
+    assert info["chains_per_cta"] == 256 and info["threads_per_cta"] == 384
+    mcinv.mcinv_pool_destroy(pool)
