@@ -41,7 +41,10 @@ typedef enum {
     MCINV_E_SINGULAR_DIAG = 2, /* a c_ii is missing, zero or non-finite (D must be
                                   non-singular, Sec. 2.2) */
     MCINV_E_DIVERGED = 3,      /* a chain went non-finite or beyond 1e30: the sweep
-                                  does not converge (sp(T) >= 1 or sp(S) >= 1, Sec. 2.2) */
+                                  does not converge (sp(T) >= 1 or sp(S) >= 1, Sec. 2.2).
+                                  The grid-wide and pool ring sweeps look at the last
+                                  cycle of each launch (a diverging chain stays beyond
+                                  the bound), the chain-sliced sweep at every cycle */
     MCINV_E_NOMEM = 4,         /* device memory could not be allocated */
     MCINV_E_CUDA = 5,          /* a CUDA runtime error; see mcinv_last_error */
     MCINV_E_TIMEOUT = 6,       /* a bounded device-side wait expired */

@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__r
             m.rpos = sh ? S.perm : nullptr;  // full inverse: R = S = every row in order
             m.spos = sh ? S.perm : nullptr;
             m.shcol = cyc - S.nb;
+            m.check_div = cyc == ncyc - 1;
             for (int l = 0; l < S.nlev; ++l) {
                 // the last level's state stores (this CTA's) before this level's bulk reads
                 asm volatile("fence.proxy.async.global;" ::: "memory");

@@ -25,6 +25,11 @@ template <> struct Prec<false> {
     // all template instantiations (any slice shape) give the same bits
     static __device__ __forceinline__ T zrow(const Cst &k, float phi, T s) { return __fmaf_rn(-k.inv_d, s, phi * k.alpha); }
     static __device__ __forceinline__ T wrow(const Cst &k, float phi, T s) { return __fmaf_rn(-k.inv_d, s, phi * k.beta); }
+    // the same with phi * alpha (phi * beta) given: phi = +-1 only flips the sign bit
+    static __device__ __forceinline__ T zrow_a(const Cst &k, T pa, T s) { return __fmaf_rn(-k.inv_d, s, pa); }
+    static __device__ __forceinline__ T wrow_a(const Cst &k, T pb, T s) { return __fmaf_rn(-k.inv_d, s, pb); }
+    static __device__ __forceinline__ T flip(T a, uint32_t sign) { return __int_as_float(__float_as_int(a) ^ (int)sign); }
+    static __device__ __forceinline__ T times_zero(T a) { return 0.f * a; }
     static __device__ __forceinline__ T mulconj(T a, T b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ T add(T a, T b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
@@ -52,6 +57,24 @@ template <> struct Prec<true> {
         const float im = __fmaf_rn(-k.inv_d.y, s.x, __fmul_rn(k.inv_d.x, s.y));
         return make_float2(__fsub_rn(phi * k.beta.x, re), __fsub_rn(phi * k.beta.y, im));
     }
+    // the same with phi * alpha (phi * beta) given
+    static __device__ __forceinline__ T zrow_a(const Cst &k, T pa, T s)
+    {
+        const float re = __fmaf_rn(-k.inv_d.y, s.y, __fmul_rn(k.inv_d.x, s.x));
+        const float im = __fmaf_rn(k.inv_d.y, s.x, __fmul_rn(k.inv_d.x, s.y));
+        return make_float2(__fsub_rn(pa.x, re), __fsub_rn(pa.y, im));
+    }
+    static __device__ __forceinline__ T wrow_a(const Cst &k, T pb, T s)
+    {
+        const float re = __fmaf_rn(k.inv_d.y, s.y, __fmul_rn(k.inv_d.x, s.x));
+        const float im = __fmaf_rn(-k.inv_d.y, s.x, __fmul_rn(k.inv_d.x, s.y));
+        return make_float2(__fsub_rn(pb.x, re), __fsub_rn(pb.y, im));
+    }
+    static __device__ __forceinline__ T flip(T a, uint32_t sign)
+    {
+        return make_float2(__int_as_float(__float_as_int(a.x) ^ (int)sign), __int_as_float(__float_as_int(a.y) ^ (int)sign));
+    }
+    static __device__ __forceinline__ T times_zero(T a) { return make_float2(0.f * a.x, 0.f * a.y); }
     static __device__ __forceinline__ T mulconj(T a, T b)
     {   // a conj(b)
         return make_float2(__fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)), __fmaf_rn(-a.x, b.y, __fmul_rn(a.y, b.x)));

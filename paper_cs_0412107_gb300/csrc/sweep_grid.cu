@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(NT, 1) cc_sweep_grid_kernel(const SweepArgs a,
         m.went = (const typename Prec<CPLX>::Ent *)(cur ? g.went[1] : g.went[0]);
         m.noise_cyc = (size_t)cyc * a.nw * (size_t)a.n;
         m.shcol = a.cyc0_in_batch + cyc;
+        m.check_div = cyc == a.ncyc - 1;
         float tsum = 0.f;  // this lane's share of the cycle's trace series value
         for (int l = 0; l < nlev; ++l) {
             const int lb = __ldg(&g.lev_ptr[l]), le = __ldg(&g.lev_ptr[l + 1]);

@@ -300,6 +300,7 @@ struct Mat {
     uint32_t zn_off;                      // this cycle's buffer, in vectors from z0
     size_t noise_cyc;                     // this cycle's noise words, from the lanes' noise_col
     bool has_noise;
+    bool check_div;                       // this cycle checks for diverged chains (the launch's last)
     const int *rpos, *spos;               // BF16 shadows: by position, index in R / S or -1; or null
     uint16_t *zsh, *wsh;
     long long ldsh, kp;
@@ -322,17 +323,25 @@ __device__ __forceinline__ void finish(const Lanes<CPLX, V, G> &w, const Mat<CPL
     using S = typename L::S;
     S prod = P::zero();
     if (w.ok[q]) {
-        const float phi_scale = m.has_noise ? 1.f : 0.f;
+        // phi alpha and phi beta (Eq. 5): phi = +-1 flips the sign bit; no noise: phi = +0
+        const S a0 = m.has_noise ? k.alpha : P::times_zero(k.alpha);
+        const S b0 = m.has_noise ? k.beta : P::times_zero(k.beta);
         T zv, wv;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const float phi = phi_scale * (((bits >> v) & 1u) ? -1.f : 1.f);
-            const S zsc = P::zrow(k, phi, L::get(sz, v));
-            const S wsc = P::wrow(k, phi, L::get(sw, v));
-            L::set(zv, v, zsc);
-            L::set(wv, v, wsc);
-            diverged |= !(P::finite_bounded(zsc) && P::finite_bounded(wsc));
-            prod = P::add(prod, P::mulconj(zsc, wsc));
+            const uint32_t sign = ((bits >> v) & 1u) << 31;
+            L::set(zv, v, P::zrow_a(k, P::flip(a0, sign), L::get(sz, v)));
+            L::set(wv, v, P::wrow_a(k, P::flip(b0, sign), L::get(sw, v)));
+        }
+        // a diverging chain stays beyond the bound, so the launch's last cycle tells
+        if (m.check_div) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                diverged |= !(P::finite_bounded(L::get(zv, v)) && P::finite_bounded(L::get(wv, v)));
+        }
+        if (w.diag || m.tq) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) prod = P::add(prod, P::mulconj(L::get(zv, v), L::get(wv, v)));
         }
         if (m.tq) {
             float re;
