@@ -581,20 +581,37 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
 #pragma unroll
         for (int q = 0; q < G; ++q) { sz[q] = L::zero(); sw[q] = L::zero(); }
         if ((r.info & 3) == 0) {
+            // entries 0..3, then 4..7 where the row has them (one branch for both sides)
 #pragma unroll
-            for (int u = 0; u < U1; ++u)
+            for (int u = 0; u < U1 / 2; ++u)
                 if (u < dz) {
                     const Ent e = shfl_val(az, u);
 #pragma unroll
                     for (int q = 0; q < G; ++q) L::fma(sz[q], e, lds_vec<T>(zb + u * SEGG + q * QOFF));
                 }
 #pragma unroll
-            for (int u = 0; u < U1; ++u)
+            for (int u = 0; u < U1 / 2; ++u)
                 if (u < dw) {
                     const Ent e = shfl_val(aw, u);
 #pragma unroll
                     for (int q = 0; q < G; ++q) L::fma(sw[q], e, lds_vec<T>(wb + u * SEGG + q * QOFF));
                 }
+            if (dz > U1 / 2 || dw > U1 / 2) {
+#pragma unroll
+                for (int u = U1 / 2; u < U1; ++u)
+                    if (u < dz) {
+                        const Ent e = shfl_val(az, u);
+#pragma unroll
+                        for (int q = 0; q < G; ++q) L::fma(sz[q], e, lds_vec<T>(zb + u * SEGG + q * QOFF));
+                    }
+#pragma unroll
+                for (int u = U1 / 2; u < U1; ++u)
+                    if (u < dw) {
+                        const Ent e = shfl_val(aw, u);
+#pragma unroll
+                        for (int q = 0; q < G; ++q) L::fma(sw[q], e, lds_vec<T>(wb + u * SEGG + q * QOFF));
+                    }
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < G; ++q) {
