@@ -573,6 +573,86 @@ def run_lattice(args, world, rank, local):
     res["speedup_to_3e-3"] = (b["seconds_to_3e-3"] / a["seconds_to_3e-3"]) if a["seconds_to_3e-3"] and b["seconds_to_3e-3"] else None
     return res
 
+def run_lattice2d(args, world, rank, local):
+    """The complex 2D lattice (L = 128, K = 4096 chains, diagonal and tr(QC^-1) with q ~ U(0,1)):
+    coupled updates per second of the sampling step, with the sweep's bytes against the
+    copy bandwidth both as gathered (every stored c_ij of C and of C^dagger reads one
+    complex64 z_j / w_j) and as compulsory (z and w read and written once a cycle)."""
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    from paper_cs_0412107_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    w = wl.WORKLOADS["lattice2d128"]
+    csr = w.build()
+    K = w.K
+    h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
+                              batch_cycles=args.batch, flags=kernel_flags(args)[0] | order_flag(args),
+                              **shape_kw(args))
+    mcinv.mcinv_set_trace_weights(h, wl.q_diag(csr.n, args.seed))
+    info0 = mcinv.mcinv_info(h)
+    B = info0["batch_cycles"]
+    mcinv.mcinv_burnin(h, args.burnin)
+    for _ in range(args.warmup):
+        mcinv.mcinv_sample(h, B)
+    mcinv.mcinv_sync(h)
+    launches0 = mcinv.mcinv_info(h)["kernel_launches"]
+    mcinv.mcinv_profile(h, True)
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            mcinv.mcinv_sample(h, B)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    mcinv.mcinv_sync(h)
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), world)
+    prof = {mcinv.KERNEL_NAMES[k]: mcinv.mcinv_profile_read(h, k) for k in range(5)}
+    launches = mcinv.mcinv_info(h)["kernel_launches"] - launches0
+    tr, tse = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_TRACE, q_diag=wl.q_diag(csr.n, args.seed))
+    mcinv.mcinv_destroy(h)
+    cycles = args.steps * B
+    hbm, _, _, peak_kind = read_peaks()
+    sw_launches, sw_ms = prof["sweep"]
+    cyc_per_launch = cycles / max(sw_launches, 1)
+    units_per_launch = csr.n * K * cyc_per_launch
+    nnz_off = csr.nnz - csr.n
+    alg_bytes = 8.0 * (2 * nnz_off + 2 * csr.n) * K * cyc_per_launch
+    compulsory_bytes = 32.0 * units_per_launch
+    t_launch = sw_ms / sw_launches / 1e3 if sw_launches else None
+    achieved = alg_bytes / t_launch / 1e9 if t_launch else None
+    kname, ksrc, kprof = SWEEP_KERNELS[info0["sweep_kernel"]]
+    kprof = {4: "cc_sweep_grid_pair_lattice2d128.txt"}.get(info0["sweep_kernel"])
+    return {
+        "metric": METRIC, "value": float(csr.nnz) * K * cycles * world / (ms_max / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic (seeded U(1) lattice, Philox noise)",
+        "config": {"workload": "lattice2d128", "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
+                   "estimates": "diagonal + tr(QC^-1), q ~ U(0,1)", "sweep_kernel": kname,
+                   "threads_per_cta": info0["threads_per_cta"], "levels": info0["levels"],
+                   "sweep_order": args.order,
+                   "l2": "inputs larger than L2 (z, w double-buffered: %.0f MB)" % (4 * 8 * csr.n * K / 1e6)},
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm if achieved else None, "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": traffic_from_profiles(kprof, units_per_launch, ksrc, info0["threads_per_cta"]),
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_unit": alg_bytes / units_per_launch,
+                     "units_per_launch": units_per_launch, "compulsory_bytes_per_launch": compulsory_bytes,
+                     "compulsory_frac": compulsory_bytes / t_launch / 1e9 / hbm if t_launch else None},
+        "trace": {"re": float(np.real(tr)), "im": float(np.imag(tr)), "se_re": float(np.real(tse)),
+                  "se_im": float(np.imag(tse)), "cycles": args.burnin + (args.warmup + args.steps) * B},
+        "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+
+
 def cpu_baseline(csr, K, seconds, workload=WORKLOAD):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     `chains` chains (one OpenMP thread per chain group) for `cycles` cycles."""
@@ -724,7 +804,8 @@ def main():
     ap.add_argument("--e2e-burnin", type=int, default=500)
     ap.add_argument("--e2e-samples", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18", "lattice4d16"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18", "lattice4d16",
+                                                             "lattice2d128"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-burnin", type=int, default=200)
     ap.add_argument("--batch-samples", type=int, default=2000)
@@ -747,6 +828,8 @@ def main():
         res = run_dirac(args, world, rank, local)
     elif args.workload == "lattice4d16":
         res = run_lattice(args, world, rank, local)
+    elif args.workload == "lattice2d128":
+        res = run_lattice2d(args, world, rank, local)
     else:
         res = run_mine(args, world, rank, local)
     if rank == 0 and res is not None:
