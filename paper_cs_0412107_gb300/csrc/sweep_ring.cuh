@@ -106,7 +106,7 @@ constexpr int RING16 = 24;                // slots per warp with 16 warps a CTA 
 constexpr int QMAX = 3;                   // rows in flight per warp
 constexpr int NBAR = QMAX + 2;            // QMAX + 1 for the ring rows, one for long rows
 constexpr int SEGB = 512;                 // 32 lanes x 16 bytes
-constexpr int PAIR_RN = 12;               // 1 KB slots per warp on the pair layout (16 warps per CTA)
+constexpr int PAIR_RN = 12;               // 1 KB slots per warp on the pair layout with 16 warps a CTA
 
 // A row in flight in a warp's ring: its position, first vector i K / V, packed
 // counts, first slot, barrier use number, and the lane's values of its entries
@@ -511,8 +511,8 @@ __device__ __forceinline__ void level_regs(const Lanes<CPLX, V, 1> &w, const Mat
 // PAIR: the state is in the pair layout (the chain block's z vectors of a row
 // followed by its w vectors, one allocation for both) and the matrix is
 // structurally symmetric (row i of C and of C^dagger name the same j, in the
-// same order), so z_j and w_j of a neighbour are one 1 KB segment: one copy,
-// one slot of 2 x 512 bytes, PAIR_RN slots a warp.
+// same order), so z_j and w_j of a neighbour's 32-vector block are one 1 KB
+// segment, and the G adjacent blocks of the warp one G KB copy into one slot.
 template <bool CPLX, int V, int G, bool PAIR = false, int RNS = RING>
 __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int p, int le, int rstep,
                                            float &tsum, bool &diverged, volatile int *abort_flag)
