@@ -189,3 +189,18 @@ def test_pair_layout_is_used_and_survives_state_round_trips():
     assert mcinv.mcinv_info(hr)["sweep_kernel"] == 3
     for x in (h, g, hr):
         mcinv.mcinv_destroy(x)
+
+
+@pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 384), (GBS, 512), (GP, 256)])
+@pytest.mark.parametrize("batch", [1, 8])
+def test_grid_reports_divergence(grid, threads, batch):
+    """C = [[1, 3], [4, 1]]: sp(T) > 1, the chains blow up (Sec. 2.2).  The grid-wide sweep
+    checks the bound on each launch's last cycle; a diverging chain is still beyond it there."""
+    csr = wl.csr_from_coo(2, [0, 0, 1, 1], [0, 1, 0, 1], np.array([1.0, 3.0, 4.0, 1.0]))
+    h = mcinv.create_from_csr(csr, K=8, seed=1, acc=mcinv.MCINV_ACC_FP32_SIMT, flags=grid, threads_per_cta=threads,
+                              batch_cycles=batch)
+    mcinv.mcinv_burnin(h, 64)
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_sync(h)
+    assert e.value.status == mcinv.MCINV_E_DIVERGED
+    mcinv.mcinv_destroy(h)

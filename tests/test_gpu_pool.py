@@ -222,3 +222,18 @@ def test_pool_shape_rejections():
     info = mcinv.mcinv_pool_info(pool)
     assert info["chains_per_cta"] == 256 and info["threads_per_cta"] == 384
     mcinv.mcinv_pool_destroy(pool)
+
+
+@pytest.mark.parametrize("shape", [dict(chains_per_cta=128, threads_per_cta=384), dict(chains_per_cta=256),
+                                   dict(chains_per_cta=32, threads_per_cta=512)])
+def test_pool_reports_divergence(shape):
+    # C = [[1, 3], [4, 1]]: sp(T) > 1 (Sec. 2.2); the ring form checks the bound on the last
+    # cycle of each step, where a diverging chain is still beyond it
+    csr = wl.csr_from_coo(2, [0, 0, 1, 1], [0, 1, 0, 1], np.array([1.0, 3.0, 4.0, 1.0]))
+    pool = mcinv.mcinv_pool_create(K=64, seed=1, mem_budget=1 << 26, max_slots=2, batch_cycles=8, **shape)
+    t = mcinv.mcinv_pool_submit(pool, csr, matrix_id=1, burnin=64, samples=8, want_inverse=False)
+    run_until_done(pool, [t])
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_DIAG, csr.n)
+    assert e.value.status == mcinv.MCINV_E_DIVERGED
+    mcinv.mcinv_pool_destroy(pool)
