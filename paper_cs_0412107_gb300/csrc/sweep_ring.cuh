@@ -261,7 +261,13 @@ struct Lanes {
             c0[q] = (int)cv[q] * V;
             ok[q] = c0[q] < K;
             dpart[q] = (S *)dp + (size_t)(c0[q] / (seg * V)) * (size_t)n;
-            dlead[q] = ((lane % seg) == 0) && ok[q] && diag;
+            // the lane that adds the unit's sum to its partial: the unit's first lane; with
+            // two vectors a lane and units of two or more lanes, vector 1's unit sum ends in
+            // the unit's second lane (diag_pair), which stores it if the unit has chains
+            if (G == 2 && q == 1 && seg >= 2)
+                dlead[q] = ((lane % seg) == 1) && (c0[q] - V < K) && diag;
+            else
+                dlead[q] = ((lane % seg) == 0) && ok[q] && diag;
             noise_col[q] = noise ? noise + (size_t)(c0[q] >> 5) * (size_t)n : nullptr;
             cshift[q] = (uint32_t)(c0[q] & 31);
         }
@@ -309,10 +315,10 @@ struct Mat {
 };
 
 // Eqs. 4/5 for the V chains of the lane's vector q from the sums over the row's
-// entries, the stores, the shadows and the z_i conj(w_i) partials.  Every lane
-// of the warp calls it (the diagonal sums shuffle).
+// entries, the stores, the shadows and the trace term; returns the lane's
+// z_i conj(w_i) partial for the diagonal (diag_one / diag_pair).
 template <bool CPLX, int V, int G>
-__device__ __forceinline__ void finish(const Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int q, int p, uint32_t iv,
+__device__ __forceinline__ typename Prec<CPLX>::T finish(const Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int q, int p, uint32_t iv,
                                        const typename Lane<CPLX, V>::T &sz, const typename Lane<CPLX, V>::T &sw,
                                        const typename Prec<CPLX>::Cst &k, uint32_t bits, typename Prec<CPLX>::T dold,
                                        int rp, int sp, float &tsum, bool &diverged)
@@ -377,13 +383,51 @@ __device__ __forceinline__ void finish(const Lanes<CPLX, V, G> &w, const Mat<CPL
             }
         }
     }
-    if (w.diag) {
-        // the unit's sum over its seg lanes; the leader adds it to the running partial
+    return prod;
+}
+
+// The unit's sum of the lanes' z_i conj(w_i) over its seg lanes (xor butterfly:
+// every lane of the unit ends with the same sum); its leader adds it to the
+// running partial.
+template <bool CPLX, int V, int G>
+__device__ __forceinline__ void diag_one(const Lanes<CPLX, V, G> &w, int q, int p, typename Prec<CPLX>::T prod,
+                                         typename Prec<CPLX>::T dold)
+{
+    using P = Prec<CPLX>;
+    if (!w.diag) return;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1)
-            if (o < w.seg) prod = P::add(prod, P::shfl_xor(prod, o));
-        if (w.dlead[q]) w.dpart[q][p] = P::add(dold, prod);
+    for (int o = 1; o < 32; o <<= 1)
+        if (o < w.seg) prod = P::add(prod, P::shfl_xor(prod, o));
+    if (w.dlead[q]) w.dpart[q][p] = P::add(dold, prod);
+}
+
+// The same for both vectors of a two-vector lane at once: at the first level
+// even lanes keep vector 0's pair sum and odd lanes vector 1's (each lane sends
+// the other), then one butterfly over the unit's lanes of the same parity.  The
+// additions are those of two separate butterflies (a + b = b + a), so the unit
+// sums are the same bits, in the unit's even lanes for vector 0 and odd lanes
+// for vector 1.
+template <bool CPLX, int V>
+__device__ __forceinline__ void diag_pair(const Lanes<CPLX, V, 2> &w, int p, typename Prec<CPLX>::T pr0,
+                                          typename Prec<CPLX>::T pr1, typename Prec<CPLX>::T dold0,
+                                          typename Prec<CPLX>::T dold1)
+{
+    using P = Prec<CPLX>;
+    using S = typename P::T;
+    if (!w.diag) return;
+    if (w.seg == 1) {
+        if (w.dlead[0]) w.dpart[0][p] = P::add(dold0, pr0);
+        if (w.dlead[1]) w.dpart[1][p] = P::add(dold1, pr1);
+        return;
     }
+    const bool odd = (w.lane & 1) != 0;
+    S keep = odd ? pr1 : pr0;
+    keep = P::add(keep, P::shfl_xor(odd ? pr0 : pr1, 1));
+#pragma unroll
+    for (int o = 2; o < 32; o <<= 1)
+        if (o < w.seg) keep = P::add(keep, P::shfl_xor(keep, o));
+    if (w.dlead[0]) w.dpart[0][p] = P::add(dold0, keep);
+    if (w.dlead[1]) w.dpart[1][p] = P::add(dold1, keep);
 }
 
 // this lane's share of row p's entries: lane e holds entry e of each side
@@ -473,7 +517,7 @@ __device__ __forceinline__ void row_regs(const Lanes<CPLX, V, 1> &w, const Mat<C
             else { sz = L::add(sz, pz); sw = L::add(sw, pw); }
         }
     }
-    finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp, tsum, diverged);
+    diag_one(w, 0, p, finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp, tsum, diverged), dold);
 }
 
 // The rows p, p + rstep, ... (< le) of one level with register gathers, the next
@@ -623,7 +667,16 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
             }
         }
 #pragma unroll
-        for (int q = 0; q < G; ++q) finish<CPLX, V, G>(w, m, q, r.p, r.iv, sz[q], sw[q], k, bits[q], dold[q], rp, sp, tsum, diverged);
+        S pr[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+            pr[q] = finish<CPLX, V, G>(w, m, q, r.p, r.iv, sz[q], sw[q], k, bits[q], dold[q], rp, sp, tsum, diverged);
+        if constexpr (G == 2) {
+            diag_pair<CPLX, V>(w, r.p, pr[0], pr[1], dold[0], dold[1]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < G; ++q) diag_one(w, q, r.p, pr[q], dold[q]);
+        }
     };
     // pipeline: this row's record and entries, the next row's record
     int4 rec = ldnc4(&m.rows[p]);
@@ -729,10 +782,17 @@ __device__ __forceinline__ void level_bulk(Lanes<CPLX, V, G> &w, const Mat<CPLX>
                 ez += mzr;
                 ew += mwr;
             }
+            S pr[G];
 #pragma unroll
             for (int q = 0; q < G; ++q)
-                finish<CPLX, V, G>(w, m, q, p, (uint32_t)rec.x, pzs[q].total(), pws[q].total(), k, bits[q], dold[q], rp,
-                                   sp, tsum, diverged);
+                pr[q] = finish<CPLX, V, G>(w, m, q, p, (uint32_t)rec.x, pzs[q].total(), pws[q].total(), k, bits[q],
+                                           dold[q], rp, sp, tsum, diverged);
+            if constexpr (G == 2) {
+                diag_pair<CPLX, V>(w, p, pr[0], pr[1], dold[0], dold[1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < G; ++q) diag_one(w, q, p, pr[q], dold[q]);
+            }
         }
         if (more) { rec = rnext; mz = nz; mw = nw; }
         rnext = rnn;
