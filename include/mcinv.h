@@ -464,10 +464,13 @@ void mcinv_server_destroy(mcinv_server_t s);
  * nothing needs clearing): calls whose work overlaps on the GPU -- different
  * streams or host threads -- race; calls on one stream do not.  The first call
  * on a device looks up the array's device address with that device current;
- * make that first call before any stream capture.  The call waits for its
- * stream before returning.  No cudaMalloc, cudaFree or other allocation.
- * On failure *error (when error is not NULL) points to a static message.
- * MCINV_E_UNSUPPORTED off sm_103a; MCINV_E_TIMEOUT if a bounded wait expired.
+ * make that first call before any stream capture.  The address is kept until
+ * the process exits, so do not use this entry point across a cudaDeviceReset.
+ * The call waits for its stream before returning.  No cudaMalloc, cudaFree or
+ * other allocation.  On failure *error (when error is not NULL) points to a
+ * static message.  MCINV_E_UNSUPPORTED off sm_103a; MCINV_E_TIMEOUT if a
+ * bounded wait in the contraction expired, in which case sum and sq are left
+ * unchanged (the fold is skipped).
  */
 mcinv_status mcinv_block_accumulate_noalloc(int64_t M, int64_t N, int64_t inner, const uint16_t *A,
                                             int64_t lda, const uint16_t *B, int64_t ldb,

@@ -221,14 +221,17 @@ def group_estimate(acc, counts, samples):
     return m, se(mg, m)
 
 
-def geyer_ips(x):
-    """Geyer's (1992) initial positive sequence estimator for a stationary series.
+def geyer_ims(x):
+    """Geyer's (1992) initial monotone sequence estimator for a stationary series
+    (the effective length Sec. 2.3 and Sec. 3.1 take from Geyer).
 
-    gamma(k): lag-k autocovariance (divided by M); Gamma_j = gamma(2j) + gamma(2j+1),
-    summed while positive and made non-increasing; asymptotic variance
-    sigma^2 = -gamma(0) + 2 sum Gamma_j; effective length M gamma(0) / sigma^2;
-    standard error of the mean sqrt(sigma^2 / M) = sqrt(gamma(0) / ess).
-    Returns dict(mean, var, ess, se).
+    gamma(k): lag-k autocovariance (divided by M); the pair sums
+    Gamma_j = gamma(2j) + gamma(2j+1) are taken while positive (the initial
+    positive sequence), and each is then capped by the one before it, so the
+    summed sequence is non-increasing (the monotone refinement);
+    asymptotic variance sigma^2 = -gamma(0) + 2 sum Gamma_j; effective length
+    M gamma(0) / sigma^2; standard error of the mean
+    sqrt(sigma^2 / M) = sqrt(gamma(0) / ess).  Returns dict(mean, var, ess, se).
     """
     x = np.asarray(x, dtype=np.float64)
     M = len(x)

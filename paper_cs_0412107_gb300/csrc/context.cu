@@ -1242,9 +1242,10 @@ extern "C" mcinv_status mcinv_set_trace_weights(mcinv_t h, const double *q)
     return MCINV_OK;
 }
 
-// Geyer (1992) initial positive sequence estimate on the per-cycle series:
-// gamma(k) the lag-k autocovariance, Gamma_j = gamma(2j) + gamma(2j+1) summed
-// while positive (and made monotone), asymptotic variance
+// Geyer (1992) initial monotone sequence estimate on the per-cycle series:
+// gamma(k) the lag-k autocovariance, Gamma_j = gamma(2j) + gamma(2j+1) taken
+// while positive, each capped by the one before (the monotone refinement of
+// the initial positive sequence), asymptotic variance
 // sigma^2 = -gamma(0) + 2 sum_j Gamma_j, effective length M gamma(0) / sigma^2,
 // Monte Carlo SE = sqrt(gamma(0) / effective length) (Sec. 2.3, Sec. 3.1).
 static void geyer(const std::vector<double> &x, double *mean, double *var, double *ess, double *se)

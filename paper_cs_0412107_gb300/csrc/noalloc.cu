@@ -30,7 +30,10 @@ std::mutex g_mu;
 unsigned char *g_ptr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device, looked up once per
-// device (in host code the symbol is only a host-side stand-in).
+// device (in host code the symbol is only a host-side stand-in).  The address
+// is kept for the life of the process: after a cudaDeviceReset the module is
+// loaded again and the kept address may no longer be the array's, so the
+// entry point must not be used across a device reset.
 cudaError_t scratch_on_current_device(unsigned char **out)
 {
     int dev = 0;
@@ -46,6 +49,24 @@ cudaError_t scratch_on_current_device(unsigned char **out)
     }
     *out = g_ptr[dev];
     return cudaSuccess;
+}
+
+// sum += D, sq += D^2 * scale_sq over the M*N product, unless the contraction
+// reported a failure in *status: then the caller's accumulators are left as
+// they were (tiles abandoned after an expired wait were never written, so D
+// still holds an earlier call's product there).  One element a thread per
+// step, explicit round-to-nearest double operations as in the handle's fold.
+__global__ void guarded_fold_kernel(long long elems, double scale_sq, const float *__restrict__ D,
+                                    double *__restrict__ sum, double *__restrict__ sq,
+                                    const int *__restrict__ status)
+{
+    if (*(const volatile int *)status != 0) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < elems; e += stride) {
+        const double x = D[e];
+        sum[e] = __dadd_rn(sum[e], x);
+        sq[e] = __fma_rn(__dmul_rn(x, x), scale_sq, sq[e]);
+    }
 }
 
 }  // namespace
@@ -97,7 +118,10 @@ extern "C" mcinv_status mcinv_block_accumulate_noalloc(int64_t M, int64_t N, int
         msg = (why && *why) ? why : "tensor-core contraction launch failed";
         return e == cudaErrorNotSupported ? MCINV_E_UNSUPPORTED : MCINV_E_CUDA;
     }
-    if (mcinv::launch_block_fold(0, M * N, scale_sq, D, sum, sq, 0, s) != cudaSuccess) {
+    long long blocks = (M * N + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    guarded_fold_kernel<<<(unsigned)blocks, 256, 0, s>>>(M * N, scale_sq, D, sum, sq, status);
+    if (cudaGetLastError() != cudaSuccess) {
         msg = "fold launch failed";
         return MCINV_E_CUDA;
     }
@@ -108,7 +132,7 @@ extern "C" mcinv_status mcinv_block_accumulate_noalloc(int64_t M, int64_t N, int
         return MCINV_E_CUDA;
     }
     if (st) {
-        msg = "a bounded wait in the tensor-core contraction expired";
+        msg = "a bounded wait in the tensor-core contraction expired (sum and sq were left unchanged)";
         return MCINV_E_TIMEOUT;
     }
     msg = "";

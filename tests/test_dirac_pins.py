@@ -87,7 +87,7 @@ def test_oracle_trace_estimate_on_a_small_lattice():
     K, burn, samp = 32, 40, 160
     series = []
     oracle.run(c, K, seed=5, ncycles=burn + samp, acc_from=burn, q=np.ones(c.n), series_out=series)
-    g = oracle.geyer_ips(np.array(series))
+    g = oracle.geyer_ims(np.array(series))
     assert abs(g["mean"] - exact) < 4 * g["se"]
     assert g["se"] < 0.01 * exact
 

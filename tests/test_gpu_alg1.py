@@ -83,7 +83,7 @@ def test_trace_series_matches_oracle(complex_):
     assert len(s_gpu) == samp
     assert np.abs(s_gpu - s_orc).max() <= 1e-4 * np.abs(s_orc).max()
     g = mcinv.mcinv_trace_mc_error(h)
-    g_orc = oracle.geyer_ips(s_gpu)  # the oracle's estimator on the GPU's own series
+    g_orc = oracle.geyer_ims(s_gpu)  # the oracle's estimator on the GPU's own series
     for key in ("mean", "var", "ess", "se"):
         assert abs(g[key] - g_orc[key]) <= 1e-9 * abs(g_orc[key]), key
 

@@ -54,3 +54,45 @@ def test_sampled_chains_match_the_oracle(name, order):
         zr, wr = (z[o], w[o]) if o is not None else (z, w)
         assert _rel(zr, st.z) <= TOL and _rel(wr, st.w) <= TOL, (name, order, c0, _rel(zr, st.z), _rel(wr, st.w))
     mcinv.mcinv_destroy(h)
+
+
+def _bench_handle(name, c, K):
+    """The handle as the benchmark creates it for this workload: autotuned kernel,
+    colour order, and the workload's estimates accumulated while sampling."""
+    flags = mcinv.MCINV_F_AUTOTUNE | mcinv.MCINV_F_COLOR_ORDER
+    if name == "pedigree50k":  # diagonal + C^-1[:, 0:512] on the tensor cores
+        return mcinv.create_from_csr(c, K=K, seed=11, acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=8, flags=flags,
+                                     block_rows=np.arange(c.n), block_cols=np.arange(512))
+    if name == "lattice4d16":  # C^-1[0:4096, 0:4096] on the tensor cores
+        R = np.arange(4096)
+        return mcinv.create_from_csr(c, K=K, seed=11, acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=8, flags=flags,
+                                     block_rows=R, block_cols=R)
+    # lattice2d128 and the Wilson-Dirac matrix: diagonal and trace
+    h = mcinv.create_from_csr(c, K=K, seed=11, acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=8, flags=flags)
+    mcinv.mcinv_set_trace_weights(h, wl.q_diag(c.n, 0))
+    return h
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sampled_chains_follow_the_oracle_for_100_cycles(name):
+    """Same-draw parity at full size over 100 cycles (20 burn-in, then 80 sampling
+    cycles with the estimates accumulated) in the benchmark's configuration, for
+    two chains in the middle of the chain range, checked after cycles 20 and 100."""
+    make, K, _ = CASES[name]
+    c = make()
+    h = _bench_handle(name, c, K)
+    o, _ = greedy_order(c)
+    cref = permuted(c, o)
+    c0, nch = K // 2 + 1, 2
+    st = None
+    for done, todo in ((0, 20), (20, 80)):
+        if done == 0:
+            mcinv.mcinv_burnin(h, todo)
+        else:
+            mcinv.mcinv_sample(h, todo)
+        z, w, cyc = mcinv.mcinv_get_state(h, c0, nch)
+        assert cyc == done + todo
+        st, _, _ = oracle.run(cref, nch, seed=11, chain0=c0, cycle0=done, ncycles=todo, diag=False, state=st)
+        ez, ew = _rel(z[o], st.z), _rel(w[o], st.w)
+        assert ez <= TOL and ew <= TOL, (name, cyc, ez, ew)
+    mcinv.mcinv_destroy(h)

@@ -296,7 +296,7 @@ def test_paper_tables_se_is_sqrt_var_over_effective_length():
         assert abs(np.sqrt(var / eff) - se) <= 0.0006 * se + 5e-4
 
 
-@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9])
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9, -0.5])
 def test_geyer_effective_length_of_ar1(rho):
     """AR(1) with coefficient rho: effective length M (1 - rho)/(1 + rho)."""
     rng = np.random.default_rng(2)
@@ -306,11 +306,28 @@ def test_geyer_effective_length_of_ar1(rho):
     x[0] = e[0]
     for t in range(1, M):
         x[t] = rho * x[t - 1] + e[t]
-    g = oracle.geyer_ips(x)
+    g = oracle.geyer_ims(x)
     want = M * (1 - rho) / (1 + rho)
     assert abs(g["ess"] / want - 1) < 0.08
     assert abs(g["se"] - np.sqrt(g["var"] / g["ess"])) < 1e-12
     assert abs(g["var"] - 1 / (1 - rho ** 2)) < 0.05 / (1 - rho ** 2)
+
+
+def test_geyer_takes_the_initial_monotone_sequence():
+    """x_t = cos(0.8 pi t): gamma(k) -> cos(0.8 pi k) / 2, so the pair sums are
+    Gamma_0 = (1 + cos 0.8pi)/2, Gamma_1 = (cos 1.6pi + cos 2.4pi)/2 (larger),
+    Gamma_2 = (cos 3.2pi + 1)/2, and Gamma_3 = (cos 4.8pi + cos 5.6pi)/2 < 0 ends the
+    sequence.  The initial positive sequence sums Gamma_0..2 as they are (sigma^2 =
+    gamma(0), effective length M); the initial monotone sequence caps Gamma_1 and
+    Gamma_2 at Gamma_0, which gives sigma^2 = -1/2 + 6 Gamma_0 and an effective
+    length of about 6.85 M.  Geyer (1992) as read for Sec. 2.3: the monotone one."""
+    M = 10_000  # a whole number of periods (5 samples = 2 periods): the mean is 0
+    x = np.cos(0.8 * np.pi * np.arange(M))
+    g = oracle.geyer_ims(x)
+    g0 = 0.5 * (1 + np.cos(0.8 * np.pi))
+    want = M * 0.5 / (-0.5 + 6 * g0)
+    assert abs(g["ess"] / want - 1) < 0.01
+    assert g["ess"] > 6 * M  # the initial positive sequence would give about M
 
 
 def test_trace_series_mean_is_the_diagonal_trace():

@@ -53,9 +53,18 @@ def test_noalloc_block_accumulation_matches_allocating_path():
     s_dev = torch.zeros(M * N, dtype=torch.float64, device="cuda")
     q_dev = torch.zeros(M * N, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    mem = None
     for call in (1, 2):
         mcinv.mcinv_block_accumulate_noalloc(M, N, inner, A_dev.data_ptr(), lda, B_dev.data_ptr(), ldb, scale,
                                              s_dev.data_ptr(), q_dev.data_ptr(), stream)
+        torch.cuda.synchronize()
+        if call == 1:
+            # the first call loads the library's module on this device; after it,
+            # a call must leave the device's free memory and torch's pool as they were
+            mem = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
+        else:
+            assert (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()) == mem
         s = s_dev.cpu().numpy().reshape(M, N)
         q = q_dev.cpu().numpy().reshape(M, N)
         assert np.all(np.abs(s - call * D) <= call * bound)
