@@ -316,11 +316,98 @@ def run_mine(args, world, rank, local):
         result["natural_order"] = {"value": float(csr.nnz) * K * nsteps * B * world / (msn / 1e3),
                                    "ms_per_step": msn / nsteps, "steps": nsteps, "levels": ni["levels"],
                                    "sweep_gbs": ach_n, "sweep_frac": ach_n / hbm if ach_n else None}
+    if rank == 0 and world == 1 and args.order == "colour" and not args.no_natural and not args.no_extras:
+        result["order_efficiency"] = guarded(order_efficiency, args, csr)
     if rank == 0 and not args.no_e2e:
         result["e2e"] = run_e2e(args, csr, K, acc, rank)
     if rank == 0 and world == 1 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(csr, K, args.cpu_seconds)
+        base, accuracy = cpu_baseline_and_accuracy(args, csr, kernel_flags(args)[0] | order_flag(args),
+                                                   shape_kw(args))
+        result["cpu_baseline"] = base
+        result["accuracy"] = accuracy
+    if rank == 0 and world == 1 and not args.no_extras:
+        result["configs"] = run_configs(args, local)
     return result
+
+
+def order_efficiency(args, csr):
+    """Statistical efficiency of the two sweep orders on the pedigree workload.
+
+    The colour order (Sec. 4's reordering: the sampler of P C P^T) sweeps faster than
+    the given order, but the order changes the Gauss-Seidel contraction and so the
+    autocorrelation of the chains; updates per second only mean faster answers if
+    the error per sampling cycle stays about the same.  Both orders run the
+    benchmark's handle (K chains, 500 burn-in cycles, BF16 block) and, after a
+    doubling series of sampling cycles, the RMS errors of the diagonal on 24 sampled
+    rows and of C^-1[:, 0:512] on 16 sampled columns are taken against FP64 BiCGSTAB
+    solves (the clock stops while they are read).  Reported: the curves, seconds to
+    each error, and the error variance per sampling cycle (RMS^2 x cycles, the Monte
+    Carlo part), whose ratio is the statistical efficiency of one order against
+    the other."""
+    import scipy.sparse.linalg as spl
+    import torch
+
+    from paper_cs_0412107_gb300 import mcinv
+    n = csr.n
+    rows = np.linspace(0, n - 1, 24).astype(np.int64)
+    cols = np.linspace(0, 511, 16).astype(np.int64)
+    A = csr.to_scipy().tocsr()
+
+    def column(j):
+        e = np.zeros(n)
+        e[j] = 1.0
+        x, info = spl.bicgstab(A, e, rtol=1e-12, atol=0.0, maxiter=2000)
+        assert info == 0, info
+        return x
+
+    dtruth = np.array([column(j)[j] for j in rows])
+    btruth = np.stack([column(j) for j in cols], axis=1)
+    K, B, burn = args.chains, 8, 500
+    checks = [8, 16, 32, 64, 128, 256, 512, 1024, 2048]
+    rms = lambda d: float(np.sqrt(np.mean(d ** 2)))
+    out = {"K": K, "burnin": burn, "diag_rows": len(rows), "block_columns": len(cols),
+           "truth": "FP64 BiCGSTAB columns of C^-1 (rtol 1e-12)"}
+    for name, oflag in (("colour", mcinv.MCINV_F_COLOR_ORDER), ("given", 0)):
+        h = mcinv.create_from_csr(csr, K=K, seed=args.seed + 202, acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=B,
+                                  block_rows=np.arange(n), block_cols=np.arange(512),
+                                  flags=kernel_flags(args)[0] | oflag, **shape_kw(args))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mcinv.mcinv_burnin(h, burn)
+        mcinv.mcinv_sync(h)
+        t_burn = time.perf_counter() - t0
+        t, done, curve = t_burn, 0, []
+        for c in checks:
+            t0 = time.perf_counter()
+            mcinv.mcinv_sample(h, c - done)
+            mcinv.mcinv_sync(h)
+            t += time.perf_counter() - t0
+            done = c
+            dm, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_DIAG)
+            bm, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+            curve.append({"sampling_cycles": c, "seconds": t, "rms_diag": rms(dm[rows] - dtruth),
+                          "rms_block": rms(bm[:, cols] - btruth)})
+        levels = mcinv.mcinv_info(h)["levels"]
+        mcinv.mcinv_destroy(h)
+        tail = curve[-4:]
+        out[name] = {"levels": levels, "burnin_seconds": t_burn, "curve": curve,
+                     "seconds_per_sampling_cycle": (curve[-1]["seconds"] - curve[0]["seconds"]) /
+                                                   (checks[-1] - checks[0]),
+                     "diag_error_var_per_cycle": float(np.mean([p["rms_diag"] ** 2 * p["sampling_cycles"]
+                                                                for p in tail])),
+                     "block_error_var_per_cycle": float(np.mean([p["rms_block"] ** 2 * p["sampling_cycles"]
+                                                                 for p in tail]))}
+        for eps in (3e-3, 1e-3):
+            for est in ("diag", "block"):
+                hit = next((p["seconds"] for p in curve if p[f"rms_{est}"] <= eps), None)
+                out[name][f"seconds_to_{est}_rms_{eps:g}"] = hit
+    c, g = out["colour"], out["given"]
+    for est in ("diag", "block"):
+        eff = g[f"{est}_error_var_per_cycle"] / c[f"{est}_error_var_per_cycle"]
+        out[f"{est}_statistical_efficiency_colour_over_given"] = eff
+        out[f"{est}_effective_speedup_colour_over_given"] = eff * g["seconds_per_sampling_cycle"] / \
+            c["seconds_per_sampling_cycle"]
+    return out
 
 
 def run_e2e(args, csr, K, acc, rank):
@@ -412,15 +499,17 @@ def run_batch(args, world, rank, local):
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
                                    max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
-    t_admit = time.perf_counter() - t0
-    steps = 0
-    while not all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
-        mcinv.mcinv_pool_step(pool)
-        steps += 1
-    mcinv.mcinv_pool_sync(pool)
-    dt = time.perf_counter() - t0
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp)
+                   for k, c in enumerate(mats)]
+        t_admit = time.perf_counter() - t0
+        steps = 0
+        while not all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
+            mcinv.mcinv_pool_step(pool)
+            steps += 1
+        mcinv.mcinv_pool_sync(pool)
+        dt = time.perf_counter() - t0
     info = mcinv.mcinv_pool_info(pool)
     # accuracy on a few members against the dense inverse
     errs = []
@@ -442,7 +531,7 @@ def run_batch(args, world, rank, local):
            "seconds": dt, "admission_seconds": t_admit, "steps": steps,
            "block_tflops_effective": flops / dt / 1e12,
            "rms_error_vs_dense_inverse": {"median": float(np.median(errs)), "max": float(np.max(errs))},
-           "kernel_launches": info["kernel_launches"]}
+           "kernel_launches": info["kernel_launches"], "clocks": clocks.summary()}
     # time to 1e-2 RMS error of every inverse: the same schedule through the batched
     # BF16 pool and through the plain path (one FP32 handle per matrix, SIMT
     # accumulation, launches issued one by one), RMS checked on every 64th matrix
@@ -475,46 +564,99 @@ def run_batch(args, world, rank, local):
     return res
 
 
-def time_to_rms(args, mats, burn, K, B, budget, rank):
+def time_to_rms(args, mats, burn, K, B, budget, rank, target=1e-2, max_samples=2000):
+    """Time to an RMS inverse error <= target on every monitored matrix (every 64th,
+    against its dense inverse), checked after every B sampling cycles, for the batched
+    BF16 form and for the plain path (one handle per matrix, FP32 CUDA-core
+    accumulation, launches issued one matrix at a time).  Both forms draw the same
+    noise (seed, matrix id), so they need about the same number of cycles; the clock
+    stops while the error is checked.  Setup (pool creation and admission, or handle
+    creation and destruction) is reported apart from accumulation (burn-in, sampling
+    and the estimate)."""
     import torch
 
     from paper_cs_0412107_gb300 import mcinv
-    samp = args.rms_samples
     check = list(range(0, len(mats), 64))
     truth = {k: np.linalg.inv(mats[k].to_dense()) for k in check}
-    out = {"target_rms": 1e-2, "burnin": burn, "samples": samp, "checked_matrices": len(check)}
-    # batched form
+    rms = lambda k, m: float(np.sqrt(np.mean((m - truth[k]) ** 2)))
+    out = {"target_rms": target, "burnin": burn, "checked_every_cycles": B, "monitored_matrices": len(check)}
+    # batched form: every matrix admitted at once, steps until the monitored ones reach the target
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
                                    max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=samp) for k, c in enumerate(mats)]
-    while not all(mcinv.mcinv_pool_poll(pool, t) for t in tickets):
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=max_samples)
+               for k, c in enumerate(mats)]
+    mcinv.mcinv_pool_sync(pool)
+    t_setup = time.perf_counter() - t0
+    t_acc, cycles, worst = 0.0, 0, None
+    while cycles < burn + max_samples:
+        t0 = time.perf_counter()
         mcinv.mcinv_pool_step(pool)
-    est = {k: mcinv.mcinv_pool_estimate(pool, tickets[k], mcinv.MCINV_EST_BLOCK, mats[k].n)[0] for k in check}
-    t_pool = time.perf_counter() - t0
-    mcinv.mcinv_pool_destroy(pool)
-    rms_pool = [float(np.sqrt(np.mean((est[k] - truth[k]) ** 2))) for k in check]
-    # plain path: every matrix on its own handle, FP32 CUDA-core accumulation of the full inverse
-    torch.cuda.synchronize()
+        mcinv.mcinv_pool_sync(pool)
+        t_acc += time.perf_counter() - t0
+        cycles += B
+        if cycles <= burn:
+            continue
+        worst = max(rms(k, mcinv.mcinv_pool_estimate(pool, tickets[k], mcinv.MCINV_EST_BLOCK, mats[k].n)[0])
+                    for k in check)  # the check: not timed
+        if worst <= target:
+            break
     t0 = time.perf_counter()
-    rms_plain = []
-    for k, c in enumerate(mats):
+    for k, c in enumerate(mats):  # the answer: every matrix's inverse and its SE, read back
+        mcinv.mcinv_pool_estimate(pool, tickets[k], mcinv.MCINV_EST_BLOCK, c.n)
+    t_acc += time.perf_counter() - t0
+    mcinv.mcinv_pool_destroy(pool)
+    out["batched_bf16"] = {"seconds": t_setup + t_acc, "setup_seconds": t_setup, "accumulation_seconds": t_acc,
+                           "sampling_cycles": cycles - burn, "rms_max": worst}
+    # plain path: the monitored matrices first, each until it reaches the target, which
+    # fixes the sampling cycles every other matrix then runs
+    torch.cuda.synchronize()
+    t_setup = t_acc = 0.0
+    need, rms_plain = 0, []
+
+    def plain(k, c, samples=None):
+        nonlocal t_setup, t_acc, need
+        t0 = time.perf_counter()
         h = mcinv.create_from_csr(c, K=K, seed=args.seed, chain_base=rank * K, matrix_id=k,
                                   acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=B, flags=order_flag(args),
                                   block_rows=np.arange(c.n), block_cols=np.arange(c.n))
+        mcinv.mcinv_sync(h)
+        t1 = time.perf_counter()
         mcinv.mcinv_burnin(h, burn)
-        mcinv.mcinv_sample(h, samp)
-        m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+        t_check = 0.0
+        if samples is not None:
+            mcinv.mcinv_sample(h, samples)
+            mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)  # the answer (synchronises)
+        else:
+            done = 0
+            while True:
+                mcinv.mcinv_sample(h, B)
+                done += B
+                tc = time.perf_counter()
+                m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+                tc = time.perf_counter() - tc
+                if rms(k, m) <= target or done >= max_samples:
+                    rms_plain.append(rms(k, m))
+                    need = max(need, done)
+                    break
+                t_check += tc  # an estimate taken only to check: not timed
+        t2 = time.perf_counter()
         mcinv.mcinv_destroy(h)
-        if k in truth:
-            rms_plain.append(float(np.sqrt(np.mean((m - truth[k]) ** 2))))
-    t_plain = time.perf_counter() - t0
-    out["batched_bf16"] = {"seconds": t_pool, "rms_max": max(rms_pool), "rms_median": float(np.median(rms_pool))}
-    out["plain_fp32"] = {"seconds": t_plain, "rms_max": max(rms_plain), "rms_median": float(np.median(rms_plain))}
-    out["speedup"] = t_plain / t_pool
-    return out
+        t3 = time.perf_counter()
+        t_setup += (t1 - t0) + (t3 - t2)
+        t_acc += t2 - t1 - t_check
 
+    for k in check:
+        plain(k, mats[k])
+    for k, c in enumerate(mats):
+        if k not in truth:
+            plain(k, c, samples=need)
+    out["plain_fp32"] = {"seconds": t_setup + t_acc, "setup_seconds": t_setup, "accumulation_seconds": t_acc,
+                         "sampling_cycles": need, "rms_max": max(rms_plain)}
+    out["speedup"] = out["plain_fp32"]["seconds"] / out["batched_bf16"]["seconds"]
+    out["speedup_accumulation"] = out["plain_fp32"]["accumulation_seconds"] / out["batched_bf16"]["accumulation_seconds"]
+    return out
 
 
 def lattice_truth(csr, cols):
@@ -557,20 +699,24 @@ def run_lattice(args, world, rank, local):
         h = mcinv.create_from_csr(csr, K=K, seed=args.seed, acc=acc, batch_cycles=B, block_rows=R, block_cols=R,
                                   flags=mcinv.MCINV_F_AUTOTUNE | order_flag(args))
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mcinv.mcinv_burnin(h, burn)
-        curve = []
-        for k in range(nb):
-            mcinv.mcinv_sample(h, B)
-            m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)  # synchronises
-            rms = float(np.sqrt(np.mean(np.abs(m[:, check] - truth) ** 2)))
-            curve.append({"cycles": burn + (k + 1) * B, "seconds": time.perf_counter() - t0, "rms": rms})
+        with ClockSampler(local) as clocks:
+            t0 = time.perf_counter()
+            mcinv.mcinv_burnin(h, burn)
+            curve = []
+            for k in range(nb):
+                mcinv.mcinv_sample(h, B)
+                m, _ = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)  # synchronises
+                rms = float(np.sqrt(np.mean(np.abs(m[:, check] - truth) ** 2)))
+                curve.append({"cycles": burn + (k + 1) * B, "seconds": time.perf_counter() - t0, "rms": rms})
         mcinv.mcinv_destroy(h)
         first = lambda tgt: next((c["seconds"] for c in curve if c["rms"] <= tgt), None)
-        res["forms"][name] = {"curve": curve, "seconds_to_1e-2": first(1e-2), "seconds_to_3e-3": first(3e-3)}
+        res["forms"][name] = {"curve": curve, "seconds_to_1e-2": first(1e-2), "seconds_to_3e-3": first(3e-3),
+                              "clocks": clocks.summary()}
     a, b = res["forms"]["bf16_tensor_cores"], res["forms"]["fp32_cuda_cores"]
     res["value"] = a["seconds_to_3e-3"]
-    res["speedup_to_3e-3"] = (b["seconds_to_3e-3"] / a["seconds_to_3e-3"]) if a["seconds_to_3e-3"] and b["seconds_to_3e-3"] else None
+    for t in ("1e-2", "3e-3"):
+        ta, tb = a[f"seconds_to_{t}"], b[f"seconds_to_{t}"]
+        res[f"speedup_to_{t}"] = tb / ta if ta and tb else None
     return res
 
 def run_lattice2d(args, world, rank, local):
@@ -671,6 +817,111 @@ def cpu_baseline(csr, K, seconds, workload=WORKLOAD):
             "seconds": dt}
 
 
+def cpu_baseline_and_accuracy(args, csr, flags, shape):
+    """The CPU-baseline leg of the pedigree line.
+
+    The FP64 oracle is timed on a bounded sample of the workload: Ks chains of the
+    colour-ordered matrix P C P^T for 16 burn-in and 112 sampling cycles, with the
+    diagonal and 256 sampled rows x 512 columns of the block C^-1[:, 0:512]
+    accumulated, on every host core (one OpenMP thread per chain group).  A second,
+    smaller sample (no accumulation) is timed on one core.
+
+    The same all-core run is the FP64 reference of the accuracy report (the error of
+    each result against the oracle, next to its Monte Carlo standard error): a GPU
+    handle in the benchmark's configuration (FP32 sweep, BF16 tensor-core block,
+    FP64 folds, colour order, autotuned kernel) runs the same Ks chains, and its
+    diagonal and block estimates are compared entry by entry with the oracle's."""
+    import oracle
+    from oracle.colour import greedy_order, permuted
+    from paper_cs_0412107_gb300 import mcinv
+    nproc = os.cpu_count() or 1
+    Ks, B, burn, samp = 128, 8, 16, 112
+    seed = args.seed + 101
+    order, _ = greedy_order(csr)
+    cp = permuted(csr, order)
+    pos = np.empty(csr.n, dtype=np.int64)
+    pos[order] = np.arange(csr.n)  # row r of C is row pos[r] of P C P^T
+    R = np.linspace(0, csr.n - 1, 256).astype(np.int64)
+    S = np.arange(512)
+    cpg = max(1, Ks // nproc)
+    t0 = time.perf_counter()
+    _, dacc, bacc = oracle.run(cp, Ks, seed=seed, ncycles=burn + samp, acc_from=burn, cpg=cpg, R=pos[R], S=pos[S],
+                               threads=nproc)
+    t_all = time.perf_counter() - t0
+    od = dacc.sum(0).real[pos] / (Ks * samp)
+    ob = bacc.sum(0).real / (Ks * samp)
+    # one core: 8 chains, no accumulation, sized to about 5 s
+    t0 = time.perf_counter()
+    oracle.run(cp, 8, seed=seed, ncycles=1, diag=False, threads=1)
+    c1 = max(1, int(5.0 / max(time.perf_counter() - t0, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(cp, 8, seed=seed, ncycles=c1, diag=False, threads=1)
+    t_one = time.perf_counter() - t0
+    base = {"value": float(csr.nnz) * Ks * (burn + samp) / t_all, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "nproc": nproc,
+            "sample": f"{Ks} chains x {burn + samp} cycles of {WORKLOAD} in colour order, diagonal and 256 x 512 "
+                      f"entries of C^-1[:, 0:512] accumulated over the last {samp} (of K={args.chains})",
+            "seconds": t_all,
+            "one_core": {"value": float(csr.nnz) * 8 * c1 / t_one, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"8 chains x {c1} cycles of {WORKLOAD} in colour order, no accumulation",
+                         "seconds": t_one}}
+    h = mcinv.create_from_csr(csr, K=Ks, seed=seed, acc=mcinv.MCINV_ACC_BF16_TC, batch_cycles=B,
+                              block_rows=np.arange(csr.n), block_cols=S, flags=flags, **shape)
+    mcinv.mcinv_burnin(h, burn)
+    mcinv.mcinv_sample(h, samp)
+    dm, dse = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_DIAG)
+    bm, bse = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
+    info = mcinv.mcinv_info(h)
+    mcinv.mcinv_destroy(h)
+    bm, bse = bm[R], bse[R]
+
+    def report(m, se, ref):
+        err = np.abs(m - ref)
+        return {"max_abs_error": float(err.max()), "rms_error": float(np.sqrt(np.mean(err ** 2))),
+                "max_rel_error": float(err.max() / np.abs(ref).max()),
+                "mc_se_median": float(np.median(se)), "mc_se_min": float(np.min(se)),
+                "max_error_over_se": float(np.max(err / se))}
+
+    acc = {"reference": "FP64 oracle, same draws (the CPU-baseline sample)", "K": Ks, "burnin": burn,
+           "samples": samp, "batch_cycles": B, "sweep_kernel": SWEEP_KERNELS[info["sweep_kernel"]][0],
+           "diagonal": dict(report(dm, dse, od), precision="FP32 sweep partials, FP64 fold", entries=int(csr.n)),
+           "block": dict(report(bm, bse, ob), precision="BF16 operands on the tensor cores, FP32 accumulation, "
+                                                        "FP64 fold", entries=f"{len(R)} sampled rows x {len(S)}")}
+    return base, acc
+
+
+def guarded(fn, *a, **kw):
+    """Run one sub-record; a failure is reported in the record, not raised."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 -- the main line must still print
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def run_configs(args, local):
+    """The other workloads of the benchmark, each one bounded: the complex 2D lattice's
+    update rate and roofline, the 4D lattice's time to 1e-2 and 3e-3 RMS error with the
+    tensor cores against CUDA-core accumulation, and the batched form (throughput,
+    time to 1e-2 RMS against the plain path, serving latency)."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.batch, a.burnin = 20, 5, 8, 20
+    a.kernel, a.order, a.W, a.threads, a.no_autotune = "auto", "colour", 0, 0, False
+    r = guarded(run_lattice2d, a, 1, 0, local)
+    if "error" not in r:
+        r = {k: r[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config",
+                               "roofline", "trace", "kernels_ms", "gpu_launches", "clocks")}
+    out["lattice2d128"] = r
+    a = copy.copy(args)
+    a.lattice_batches, a.order = 6, "colour"
+    out["lattice4d16"] = guarded(run_lattice, a, 1, 0, local)
+    a = copy.copy(args)
+    a.order = "colour"
+    out["batch512"] = guarded(run_batch, a, 1, 0, local)
+    return out
+
+
 DIRAC_PAPER = {"exact": 413007.84, "cc_cycles": 10832 + 18, "cc_se": 4.128, "cpu_seconds": 10859.0}
 
 
@@ -704,14 +955,17 @@ def run_dirac(args, world, rank, local):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    evm = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         ev0.record(stream)
         p = mcinv.mcinv_burnin_coupled(h, 1e-5, 1000)
+        evm.record(stream)
         used = mcinv.mcinv_sample_until(h, 1e-5, 100, 100_000)
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
     ms = ev0.elapsed_time(ev1)
+    ms_sampling = evm.elapsed_time(ev1)
     prof = {mcinv.KERNEL_NAMES[k]: mcinv.mcinv_profile_read(h, k) for k in range(5)}
     mcinv.mcinv_profile(h, False)
     g = mcinv.mcinv_trace_mc_error(h)
@@ -739,7 +993,9 @@ def run_dirac(args, world, rank, local):
                    "l2": "inputs larger than L2 (z, w double-buffered: %.1f GB)" % (4 * 8 * csr.n * K / 1e9)},
         "result": {"burnin_cycles": p, "sampling_cycles": used, "trace": g["mean"], "mc_error": g["se"],
                    "effective_length": g["ess"], "exact": exact, "z": (g["mean"] - exact) / g["se"],
-                   "seconds": ms_max / 1e3},
+                   "seconds": ms_max / 1e3, "sampling_seconds": ms_sampling / 1e3,
+                   "effective_samples_per_second": g["ess"] / (ms_sampling / 1e3),
+                   "effective_length_per_cycle": g["ess"] / used},
         "paper_table4": DIRAC_PAPER,
         "roofline": {"kernel": SWEEP_KERNELS[info0["sweep_kernel"]][0], "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None, "traffic": None,
@@ -793,7 +1049,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--acc", default="tc", choices=["tc", "simt"])
     ap.add_argument("--chains", type=int, default=1024)
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=128, help="cycles per sampling batch = per step")
     ap.add_argument("--burnin", type=int, default=20)
     ap.add_argument("--W", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -815,6 +1071,7 @@ def main():
     ap.add_argument("--order", default="colour", choices=["natural", "colour"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair"])
     ap.add_argument("--no-natural", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--lattice-batches", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

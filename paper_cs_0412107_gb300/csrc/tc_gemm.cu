@@ -3,18 +3,22 @@
 // (chains x cycles along `inner`), B = BF16 shadows of w rows, D in FP32.
 // This is the sum over chains and cycles of z_r conj(w_s) of Eq. 1/C.
 //
-// One CTA per 128 x 256 output tile, 128 threads:
+// tc_gemm_kernel (the allocation-free path) runs one CTA per 128 x 256 output
+// tile, 128 threads:
 //   warp 0 lane 0  TMA producer: 64-wide K slices of A and B into a 4-stage
 //                  ring of 128B-swizzled shared-memory tiles (mbarrier tx counts)
 //   warp 1 lane 0  MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
 //                  M=128, N=256, K=16, accumulator in TMEM (256 columns);
 //                  tcgen05.commit frees ring slots and finally signals the epilogue
 //   warps 0-3      epilogue: tcgen05.ld 32 lanes x 32 columns at a time -> D
+// tc_gemm_persistent_kernel (the handle's path) runs one CTA per SM over all
+// tiles with two TMEM accumulators (below).
 // Every wait is bounded (globaltimer); on expiry the CTA records a timeout in
 // `status`, abandons the tile, releases TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "tc_gemm.h"
@@ -235,6 +239,229 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Persistent single-matrix contraction: one CTA per SM walks the 128 x 256
+// tiles (t = CTA, CTA + grid, ...; the column tiles of one row band are
+// neighbours in t, so they run at the same time and the band's A rows are read
+// from DRAM once).  Warps: 0 = TMA producer, 1 = MMA issuer, 2..5 = epilogue.
+// Two 256-column TMEM accumulators alternate between a CTA's tiles, so the
+// epilogue of one tile runs under the MMAs of the next.
+//
+// When the tiles leave a last, partly filled wave of at most half the grid,
+// those remaining tiles are split along the contraction dimension into s
+// parts each (one part per CTA): a part writes its FP32 partial tile to a
+// workspace, and the warp that completes the count of a tile's parts sums
+// them in part order into D.  The sum order is fixed, so the result does not
+// depend on which CTA finishes last.
+// ---------------------------------------------------------------------------
+struct PersistSched {
+    int NT;       // column tiles
+    int Tfull;    // tiles computed whole (t < Tfull)
+    int s;        // parts of each remaining tile (1: none remain)
+    int npieces;  // (tiles - Tfull) * s
+    int ktiles;   // 64-wide slices of the contraction dimension
+};
+
+// Work item idx of CTA b: a whole tile, or (last) its part of a split tile.
+__device__ __forceinline__ bool persist_item(const PersistSched &S, int b, int G, int idx, int &m0, int &n0, int &k0,
+                                             int &k1, int &piece)
+{
+    const int nfull = b < S.Tfull ? (S.Tfull - 1 - b) / G + 1 : 0;
+    int t;
+    if (idx < nfull) {
+        t = b + idx * G;
+        k0 = 0;
+        k1 = S.ktiles;
+        piece = -1;
+    } else if (idx == nfull && b < S.npieces) {
+        t = S.Tfull + b / S.s;
+        const int q = b % S.s;
+        k0 = (int)((long long)q * S.ktiles / S.s);
+        k1 = (int)((long long)(q + 1) * S.ktiles / S.s);
+        piece = b;
+    } else {
+        return false;
+    }
+    m0 = (t / S.NT) * BM;
+    n0 = (t % S.NT) * BN;
+    return true;
+}
+
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                              float *__restrict__ D, int M, int N, const PersistSched S, float *__restrict__ work,
+                              int *__restrict__ cnt, int *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * A_BYTES;
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;  // [2]
+    uint64_t *tempty = tfull + 2;       // [2]
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x, G = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(smem_u32(&full[st]), 1);
+            mbar_init(smem_u32(&empty[st]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&tfull[a]), 1);
+            mbar_init(smem_u32(&tempty[a]), 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    int m0, n0, k0, k1, piece;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int kg = 0;  // k-slices issued so far (ring position)
+            for (int idx = 0; !*abort_flag && persist_item(S, b, G, idx, m0, n0, k0, k1, piece); ++idx) {
+                bool ok = true;
+                for (int kt = k0; kt < k1; ++kt, ++kg) {
+                    const int st = kg % STAGES;
+                    const uint32_t phase = (uint32_t)(kg / STAGES) & 1u;
+                    if (kg >= STAGES && !mbar_wait(smem_u32(&empty[st]), phase ^ 1u, abort_flag)) { ok = false; break; }
+                    mbar_expect_tx(smem_u32(&full[st]), STAGE_BYTES);
+                    tma_load_2d(smem_u32(sA + st * A_BYTES), &ta, smem_u32(&full[st]), kt * BK, m0);
+                    tma_load_2d(smem_u32(sB + st * B_BYTES), &tb, smem_u32(&full[st]), kt * BK, n0);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int kg = 0, tl = 0;
+            for (int idx = 0; !*abort_flag && persist_item(S, b, G, idx, m0, n0, k0, k1, piece); ++idx, ++tl) {
+                const int ab = tl & 1;  // this item's accumulator
+                const uint32_t acc = tmem + (uint32_t)(ab * TMEM_COLS);
+                // the epilogue must have drained this accumulator (two items ago)
+                if (tl >= 2 && !mbar_wait(smem_u32(&tempty[ab]), (uint32_t)((tl >> 1) - 1) & 1u, abort_flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool ok = true;
+                for (int kt = k0; kt < k1; ++kt, ++kg) {
+                    const int st = kg % STAGES;
+                    const uint32_t phase = (uint32_t)(kg / STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(&full[st]), phase, abort_flag)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t a = sdesc(smem_u32(sA + st * A_BYTES));
+                    const uint64_t bd = sdesc(smem_u32(sB + st * B_BYTES));
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(acc, a + 2 * kk, bd + 2 * kk, (kt > k0 || kk > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty[st]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&tfull[ab]));
+            }
+        }
+    } else {
+        // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows)
+        const int q = warp & 3;
+        const int rt = q * 32 + lane;  // row within the tile
+        int tl = 0;
+        for (int idx = 0; persist_item(S, b, G, idx, m0, n0, k0, k1, piece); ++idx, ++tl) {
+            const int ab = tl & 1;
+            const bool have =
+                __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[ab]), (uint32_t)(tl >> 1) & 1u, abort_flag));
+            if (!have) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = m0 + rt;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(ab * TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                if (piece >= 0) {
+                    float *wp = work + (size_t)piece * BM * BN + (size_t)rt * BN + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *(float4 *)(wp + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                          __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                } else if (row < M) {
+                    float *dst = D + (size_t)row * N + n0 + c0;
+                    if (n0 + c0 + 32 <= N && (N & 3) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[ab])) : "memory");
+            if (piece >= 0) {
+                // count this warp's rows of the part in; the warp completing the tile's
+                // 4 s arrivals sums the parts in part order (no barrier between warps)
+                const int tt = piece / S.s;
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) {
+                    const int old = atomicAdd(&cnt[tt], 1);
+                    last = (old == 4 * S.s - 1);
+                    if (last) cnt[tt] = 0;  // ready for the next launch
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();
+                    const float *w0 = work + (size_t)tt * S.s * BM * BN;
+#pragma unroll 1
+                    for (int f = lane; f < BM * BN / 4; f += 32) {
+                        const int tr = f / (BN / 4), tc = (f % (BN / 4)) * 4;
+                        float4 v = __ldcg((const float4 *)(w0 + (size_t)tr * BN + tc));
+                        for (int j = 1; j < S.s; ++j) {
+                            const float4 u = __ldcg((const float4 *)(w0 + (size_t)j * BM * BN + (size_t)tr * BN + tc));
+                            v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+                        }
+                        const int grow = m0 + tr;
+                        if (grow < M) {
+                            float *dst = D + (size_t)grow * N + n0 + tc;
+                            if (n0 + tc + 4 <= N && (N & 3) == 0) {
+                                *(float4 *)dst = v;
+                            } else {
+                                const float vv[4] = {v.x, v.y, v.z, v.w};
+                                for (int j = 0; j < 4; ++j)
+                                    if (n0 + tc + j < N) dst[j] = vv[j];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicOr(status, 2);
+        // give TMA copies still in flight time to land before the CTA exits
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -449,6 +676,9 @@ struct TcGemmPlan {
     CUtensorMap ta, tb;
     float *D;
     long long M, N, ld;
+    int sms;        // CTAs of the persistent grid (one per SM)
+    float *work;    // sms partial 128 x 256 tiles of a split last wave
+    int *cnt;       // arrivals per split tile
 };
 
 TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t *B, size_t b_rows,
@@ -475,8 +705,22 @@ TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t
         delete p;
         return nullptr;
     }
-    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(tc_gemm_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+            cudaSuccess) {
         if (why) *why = "cannot reserve shared memory";
+        delete p;
+        return nullptr;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    p->sms = sms;
+    if (cudaMalloc((void **)&p->work, (size_t)sms * BM * BN * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void **)&p->cnt, (size_t)sms * sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->cnt, 0, (size_t)sms * sizeof(int)) != cudaSuccess) {
+        if (why) *why = "cannot allocate the split-tile workspace";
+        cudaFree(p->work);
+        cudaFree(p->cnt);
         delete p;
         return nullptr;
     }
@@ -490,13 +734,38 @@ TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t
 cudaError_t tc_gemm_run(TcGemmPlan *p, long long inner, int *status, cudaStream_t s)
 {
     if (!p || inner <= 0 || inner % BK || inner > p->ld) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((p->N + BN - 1) / BN), (unsigned)((p->M + BM - 1) / BM));
-    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(p->ta, p->tb, p->D, (int)p->M, (int)p->N, (int)(inner / BK),
-                                                 status);
+    const long long MT = (p->M + BM - 1) / BM, NT = (p->N + BN - 1) / BN, T = MT * NT;
+    if (T > (1LL << 30)) return cudaErrorInvalidValue;
+    const int ktiles = (int)(inner / BK);
+    const int G = (int)std::min<long long>(T, p->sms);
+    const long long R = T / G, r = T % G;
+    PersistSched S;
+    S.NT = (int)NT;
+    S.ktiles = ktiles;
+    S.s = 1;
+    S.Tfull = (int)T;
+    S.npieces = 0;
+    if (R >= 1 && r > 0 && 2 * r <= G && ktiles >= 2) {
+        // a last wave of r tiles on G CTAs: split each into G / r parts
+        S.s = (int)std::min<long long>(G / r, ktiles);
+        S.Tfull = (int)(R * G);
+        S.npieces = (int)(r * S.s);
+        // a contraction abandoned after an expired wait leaves its counts behind
+        cudaError_t e = cudaMemsetAsync(p->cnt, 0, (size_t)r * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    tc_gemm_persistent_kernel<<<G, 192, SMEM_BYTES, s>>>(p->ta, p->tb, p->D, (int)p->M, (int)p->N, S, p->work,
+                                                         p->cnt, status);
     return cudaGetLastError();
 }
 
-void tc_gemm_plan_destroy(TcGemmPlan *p) { delete p; }
+void tc_gemm_plan_destroy(TcGemmPlan *p)
+{
+    if (!p) return;
+    cudaFree(p->work);
+    cudaFree(p->cnt);
+    delete p;
+}
 
 cudaError_t tc_gemm_run_direct(const uint16_t *A, long long lda, const uint16_t *B, long long ldb, long long M,
                                long long N, long long inner, float *D, int *status, cudaStream_t s,

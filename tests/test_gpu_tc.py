@@ -36,7 +36,11 @@ def from_bf16_bits(b):
     return (b.astype(np.uint32) << 16).view(np.float32)
 
 
-@pytest.mark.parametrize("M,N,inner", [(128, 256, 64), (300, 200, 192), (1000, 600, 1024), (129, 513, 64 * 37)])
+@pytest.mark.parametrize("M,N,inner", [(128, 256, 64), (300, 200, 192), (1000, 600, 1024), (129, 513, 64 * 37),
+                                       # more tiles than SMs (152 on GB300): a last wave of 8 tiles split in
+                                       # 19 parts each; 3 tiles in 40 (capped by the 40 k-slices); and 100
+                                       # tiles, more than half a wave, run whole as an extra round
+                                       (10240, 512, 2048), (19500, 300, 64 * 40), (16100, 512, 256)])
 def test_tc_contraction_matches_fp64(M, N, inner):
     rng = np.random.default_rng(M + N + inner)
     A = to_bf16_bits(rng.normal(size=(M, inner)))
