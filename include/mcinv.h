@@ -344,6 +344,10 @@ typedef struct {
     int32_t max_slots;      /* matrices resident at once */
     int32_t batch_cycles;   /* B: cycles every matrix advances per step; 0 = 8 */
     int32_t groups;         /* SE groups of the diagonal; 0 = 32 */
+    int32_t fold_steps;     /* F: sampling steps whose block products are summed in FP32 before
+                               each FP64 fold, so a block batch (for the batch-means SE) is the
+                               sampling cycles of F steps (fewer at a member's end); 0 = 4, at
+                               most 1024 */
     int32_t chains_per_cta; /* 0 = the first steps time the candidate shapes; 4 x a power of two
                                <= 128 (a chain slice per CTA; 128 with 384 or 512 threads: the
                                bulk-staged ring form), or 256 (the ring form, two vectors a lane,
@@ -355,7 +359,7 @@ typedef struct {
 
 typedef struct {
     int64_t K, steps, kernel_launches, arena_bytes, arena_used;
-    int32_t chains_per_cta, threads_per_cta, groups, batch_cycles, active, tuned;
+    int32_t chains_per_cta, threads_per_cta, groups, batch_cycles, active, tuned, fold_steps;
 } mcinv_pool_info_t;
 
 void mcinv_pool_default_options(mcinv_pool_options *opt);

@@ -508,6 +508,8 @@ struct HostSlot {
     int64_t burnin = 0, samples = 0;  // schedule
     int64_t cycle = 0;                // cycles run
     int64_t sampled = 0, batches = 0; // samples accumulated, block batches folded
+    int64_t pend = 0, folded = 0;     // sampling cycles in the FP32 product not yet folded; folded
+    int pend_steps = 0;               // sampling steps summed in the FP32 product since the last fold
     int inverse = 0;
     int cur = 0;
     std::vector<int32_t> ord;  // MCINV_F_COLOR_ORDER: row k of the sampled P C P^T is row ord[k] of C
@@ -524,6 +526,7 @@ struct mcinv_pool_ctx {
     uint64_t seed = 0;
     int64_t chain_base = 0;
     int B = 8, G = 32, units = 0, seg = 1, nw = 0;
+    int F = 4;                         // steps whose block products are summed before a fold
     int LPR = 8, V = 4, threads = 512, grid_sweep = 152;
     int blob_max = 48 * 1024;
     int max_slots = 0;
@@ -612,6 +615,11 @@ extern "C" mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_op
     p->seed = o.seed;
     p->chain_base = o.chain_base;
     p->B = o.batch_cycles > 0 ? o.batch_cycles : 8;
+    if (o.fold_steps < 0 || o.fold_steps > 1024) {
+        delete p;
+        return pfail(nullptr, MCINV_E_ARG, "fold_steps must be in [0, 1024]");
+    }
+    p->F = o.fold_steps > 0 ? o.fold_steps : 4;
     p->max_slots = (int)o.max_slots;
     p->stream = (cudaStream_t)o.stream;
     p->color = (o.flags & MCINV_F_COLOR_ORDER) != 0;
@@ -930,6 +938,7 @@ struct StepTables {
     std::vector<GroupTile> tiles;
     std::vector<GroupOut> outs;
     std::vector<PoolSeg> segs;
+    std::vector<char> fold;  // per slot: the block product is folded after this step
 };
 
 static void build_tables(mcinv_pool_ctx *p, StepTables &T)
@@ -940,6 +949,7 @@ static void build_tables(mcinv_pool_ctx *p, StepTables &T)
     T.slots.assign(p->max_slots, PoolSlotDev{});
     T.items.clear(); T.rbs.clear(); T.tiles.clear(); T.segs.clear();
     T.outs.assign(p->max_slots, GroupOut{});
+    T.fold.assign(p->max_slots, 0);
     const long long kp = (p->K + 63) / 64 * 64;
     std::vector<std::pair<double, int>> order;
     for (int si = 0; si < p->max_slots; ++si) {
@@ -954,17 +964,23 @@ static void build_tables(mcinv_pool_ctx *p, StepTables &T)
         d.cur = s.cur;
         d.nb = (int)nb;
         d.ns = (int)ns;
-        d.scale_sq = ns > 0 ? 1.0 / ((double)p->K * (double)p->K * (double)ns) : 0.0;
+        // the block products of F sampling steps (fewer at the member's end) are summed
+        // in FP32 by the contraction's epilogue, then folded once: a batch of pend + ns cycles
+        const bool fold = ns > 0 && (s.pend_steps + 1 >= p->F || ns == todo - nb);
+        d.scale_sq = fold ? 1.0 / ((double)p->K * (double)p->K * (double)(s.pend + ns)) : 0.0;
         T.slots[si] = d;
+        T.fold[si] = fold ? 1 : 0;
         order.push_back({(double)(s.nnz + s.n) * (double)(nb + ns), si});
         for (int rb = 0; rb < (s.n + 127) / 128; ++rb) T.rbs.push_back(PoolRB{si, rb});
         if (ns > 0) {
             if (s.inverse) {
-                T.outs[si] = GroupOut{d.D, (int)s.n, (int)s.n, (int)((ns * kp + 63) / 64), 0};
+                T.outs[si] = GroupOut{d.D, (int)s.n, (int)s.n, (int)((ns * kp + 63) / 64), s.pend > 0 ? 1 : 0};
                 for (int m0 = 0; m0 < s.n; m0 += 128)
                     for (int n0 = 0; n0 < s.n; n0 += 256) T.tiles.push_back(GroupTile{si, m0, n0, 0});
                 const long long el = (long long)s.n * s.n;
-                for (long long b = 0; b < el; b += 1 << 16) T.segs.push_back(PoolSeg{si, 0, b, std::min<long long>(1 << 16, el - b)});
+                if (fold)
+                    for (long long b = 0; b < el; b += 1 << 16)
+                        T.segs.push_back(PoolSeg{si, 0, b, std::min<long long>(1 << 16, el - b)});
             }
             for (long long b = 0; b < s.n; b += 4096) T.segs.push_back(PoolSeg{si, 1, b, std::min<long long>(4096, s.n - b)});
         }
@@ -1121,7 +1137,14 @@ extern "C" mcinv_status mcinv_pool_step(mcinv_pool_t p)
         hs.cur ^= (d.nb + d.ns) & 1;
         if (d.ns > 0) {
             hs.sampled += d.ns;
-            hs.batches += 1;
+            hs.pend += d.ns;
+            hs.pend_steps += 1;
+            if (T.fold[si]) {
+                hs.batches += 1;
+                hs.folded += hs.pend;
+                hs.pend = 0;
+                hs.pend_steps = 0;
+            }
         }
     }
     p->steps++;
@@ -1159,6 +1182,7 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
     else if (kind == MCINV_EST_TRACE) elems = 2;
     else if (kind == MCINV_EST_BLOCK) {
         if (!s.inverse) return pfail(p, MCINV_E_STATE, "the full inverse was not requested for this matrix");
+        if (s.folded == 0) return pfail(p, MCINV_E_STATE, "no block batch folded yet");
         elems = n * n;
     } else return pfail(p, MCINV_E_ARG, "unknown estimate kind");
     // scratch for the estimate from the arena (bookkeeping only)
@@ -1183,7 +1207,8 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
                  (e = cudaStreamSynchronize(str)) == cudaSuccess)
             e = launch_trace_estimate(0, (int)n, p->G, p->d_counts, (double)s.sampled, s.dev.dacc, dq, mean, str);
     } else {
-        e = launch_block_estimate(0, (long long)(n * n), (double)p->K, (double)s.sampled, (double)s.batches, s.dev.bsum,
+        // the samples folded so far (a product still being summed joins at its fold)
+        e = launch_block_estimate(0, (long long)(n * n), (double)p->K, (double)s.folded, (double)s.batches, s.dev.bsum,
                                   s.dev.bsq, mean, se, str);
     }
     if (st == MCINV_OK && e == cudaSuccess) {
@@ -1262,6 +1287,7 @@ extern "C" mcinv_status mcinv_pool_info(mcinv_pool_t p, mcinv_pool_info_t *info)
     info->threads_per_cta = p->threads;
     info->groups = p->G;
     info->batch_cycles = p->B;
+    info->fold_steps = p->F;
     info->steps = p->steps;
     info->kernel_launches = p->launches;
     info->arena_bytes = (int64_t)p->arena_bytes;

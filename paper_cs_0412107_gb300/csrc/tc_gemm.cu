@@ -608,14 +608,25 @@ __global__ void __launch_bounds__(192, 1)
                 if (row < o.M) {
                     float *dst = o.D + (size_t)row * o.N + tile.n0 + c0;
                     if (tile.n0 + c0 + 32 <= o.N && (o.N & 3) == 0) {
+                        if (o.add) {
+                            float4 v[8];
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                            for (int j = 0; j < 8; ++j) v[j] = *(const float4 *)(dst + 4 * j);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                *(float4 *)(dst + 4 * j) =
+                                    make_float4(v[j].x + __uint_as_float(r[4 * j]), v[j].y + __uint_as_float(r[4 * j + 1]),
+                                                v[j].z + __uint_as_float(r[4 * j + 2]), v[j].w + __uint_as_float(r[4 * j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        }
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (tile.n0 + c0 + j < o.N) dst[j] = __uint_as_float(r[j]);
+                            if (tile.n0 + c0 + j < o.N) dst[j] = o.add ? dst[j] + __uint_as_float(r[j]) : __uint_as_float(r[j]);
                     }
                 }
             }

@@ -21,7 +21,7 @@ struct GroupOut {
     float *D;   // M x N row-major FP32
     int M, N;
     int ktiles; // 64-wide slices of the contraction dimension this step
-    int pad;
+    int add;    // 0: D = A B^T; 1: D += A B^T (the product of an earlier step is kept)
 };
 bool tc_encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, long long ld, long long inner,
                        bool is_b, const char **why);

@@ -86,7 +86,7 @@ class mcinv_info_t(ctypes.Structure):
 class mcinv_pool_options(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int64), ("seed", ctypes.c_uint64), ("chain_base", ctypes.c_int64),
                 ("mem_budget", ctypes.c_int64), ("max_slots", ctypes.c_int32),
-                ("batch_cycles", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("batch_cycles", ctypes.c_int32), ("groups", ctypes.c_int32), ("fold_steps", ctypes.c_int32),
                 ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
@@ -96,7 +96,7 @@ class mcinv_pool_info_t(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
                 ("chains_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("groups", ctypes.c_int32), ("batch_cycles", ctypes.c_int32), ("active", ctypes.c_int32),
-                ("tuned", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("fold_steps", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -478,10 +478,12 @@ def mcinv_pool_default_options(**overrides) -> mcinv_pool_options:
 
 
 def mcinv_pool_create(*, K=256, seed=0, chain_base=0, mem_budget=1 << 32, max_slots=512, batch_cycles=8,
-                      groups=32, chains_per_cta=0, threads_per_cta=0, flags=0, stream="current") -> Pool:
+                      groups=32, fold_steps=0, chains_per_cta=0, threads_per_cta=0, flags=0,
+                      stream="current") -> Pool:
     o = mcinv_pool_default_options(K=K, seed=seed, chain_base=chain_base, mem_budget=mem_budget,
                                    max_slots=max_slots, batch_cycles=batch_cycles, groups=groups,
-                                   chains_per_cta=chains_per_cta, threads_per_cta=threads_per_cta, flags=flags)
+                                   fold_steps=fold_steps, chains_per_cta=chains_per_cta,
+                                   threads_per_cta=threads_per_cta, flags=flags)
     o.stream = current_stream() if stream == "current" else stream
     p = ctypes.c_void_p()
     _pcheck(lib().mcinv_pool_create(ctypes.byref(p), ctypes.byref(o)))

@@ -8,10 +8,14 @@ alone or alongside others that join later; its full inverse equals the
 single-matrix handle's; admission refuses what does not fit in the arena
 and accepts it after a release; the batch estimates cover the dense inverse.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
-import oracle
+sys.path.insert(0, os.path.dirname(__file__))
+import oracle  # noqa: E402
 from paper_cs_0412107_gb300 import build as libbuild
 from paper_cs_0412107_gb300 import mcinv
 from paper_cs_0412107_gb300 import workloads as wl
@@ -83,9 +87,10 @@ def test_pool_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_pool_full_inverse_equals_single_handle():
+    # one step's product a batch (fold_steps 1), as the handle folds every batch
     K, B, burn, samp = 128, 4, 8, 16
     c = wl.random_dominant(256, 4, 1.5, 0)
-    pool = mcinv.mcinv_pool_create(K=K, seed=9, mem_budget=1 << 28, max_slots=4, batch_cycles=B)
+    pool = mcinv.mcinv_pool_create(K=K, seed=9, mem_budget=1 << 28, max_slots=4, batch_cycles=B, fold_steps=1)
     t = mcinv.mcinv_pool_submit(pool, c, matrix_id=4, burnin=burn, samples=samp)
     run_until_done(pool, [t])
     pm, pse = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
@@ -97,6 +102,29 @@ def test_pool_full_inverse_equals_single_handle():
     hm, hse = mcinv.mcinv_estimate(h, mcinv.MCINV_EST_BLOCK)
     assert np.abs(pm - hm).max() <= 1e-12 * np.abs(hm).max()
     assert np.abs(pse - hse).max() <= 1e-9 * np.abs(hse).max()
+
+
+@pytest.mark.parametrize("F", [1, 3])
+def test_pool_folded_batches_follow_the_oracle(F):
+    """The block products of F steps summed in FP32 by the contraction's epilogue and
+    folded once (the batch-means SE over batches of F x B cycles, shorter at a member's
+    start and end): mean and SE of each member's full inverse equal the oracle's from
+    the same draws, its states rounded to the BF16 operands, within 1e-4 of the largest
+    entry.  Burn-ins that end inside a step give a short first batch."""
+    import _block_oracle
+    K, B = 64, 4
+    mats = [(wl.random_dominant(n, 4, 1.5, seed), burn, samp)
+            for n, seed, burn, samp in ((130, 1, 6, 33), (300, 2, 4, 16), (77, 3, 9, 50))]
+    pool = mcinv.mcinv_pool_create(K=K, seed=17, mem_budget=1 << 28, max_slots=4, batch_cycles=B, fold_steps=F)
+    assert mcinv.mcinv_pool_info(pool)["fold_steps"] == F
+    tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=40 + k, burnin=burn, samples=samp)
+               for k, (c, burn, samp) in enumerate(mats)]
+    run_until_done(pool, tickets)
+    for k, ((c, burn, samp), t) in enumerate(zip(mats, tickets)):
+        m, se = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
+        om, ose = _block_oracle.block_estimate(c, K, 17, 40 + k, burn, samp, B, F)
+        assert rel_err(m, om) <= 1e-4 and rel_err(se, ose) <= 1e-4, (F, k, rel_err(m, om), rel_err(se, ose))
+    mcinv.mcinv_pool_destroy(pool)
 
 
 def test_pool_admission_by_device_memory():

@@ -13,6 +13,7 @@ import time
 import numpy as np
 import pytest
 
+import _block_oracle
 import oracle
 from paper_cs_0412107_gb300 import build as libbuild
 from paper_cs_0412107_gb300 import mcinv
@@ -87,26 +88,18 @@ def test_trace_request_matches_diagonal_request():
     assert abs(float(tres[0]) - float((q * dres[0]).sum())) <= 1e-10 * abs(float(tres[0]))
 
 
-def _bf16(x):
-    """Round to BF16 (nearest, ties to even) through FP32, as the sweep rounds its FP32
-    chain values into the tensor-core operands."""
-    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    b = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint32) << 16
-    return b.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
 def _rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
 
 
-def _oracle_result(c, mid, burn, samp, kind, q, G):
+def _oracle_result(c, mid, burn, samp, kind, q, G, F):
     """The FP64 oracle's estimate and SE for one request, from the same draws (the
     request's matrix id keys the noise; chains 0..K-1; cycles counted from 0 at
     admission).  Diagonal and trace: Eq. 1/C and Eq. tr over the sampling cycles,
     SE from the G contiguous chain groups.  Block (the full inverse): the batch
-    means of the pool's schedule (a step advances B cycles, so the first sampling
-    batch ends where the burn-in's last step does), each cycle's product formed from
-    the oracle's states rounded to the BF16 operands the tensor cores multiply."""
+    means of the pool's schedule (B cycles a step, F steps' products a batch), each
+    cycle's product formed from the oracle's states rounded to the BF16 operands
+    the tensor cores multiply."""
     cpg = K // G
     if kind != mcinv.MCINV_EST_BLOCK:
         _, dacc, _ = oracle.run(c, K, seed=SEED, matrix=mid, ncycles=burn + samp, acc_from=burn, cpg=cpg)
@@ -114,19 +107,7 @@ def _oracle_result(c, mid, burn, samp, kind, q, G):
         if kind == mcinv.MCINV_EST_TRACE:
             dacc = (dacc * q[None, :]).sum(axis=1)
         return oracle.group_estimate(dacc, np.full(G, cpg), samp)
-    st, _, _ = oracle.run(c, K, seed=SEED, matrix=mid, ncycles=burn)
-    sums, lens = [], []
-    cyc = burn
-    while cyc < burn + samp:
-        end = min((cyc // B + 1) * B, burn + samp)
-        X = np.zeros((c.n, c.n))
-        for t in range(cyc, end):
-            st, _, _ = oracle.run(c, K, seed=SEED, matrix=mid, cycle0=t, ncycles=1, state=st)
-            X += _bf16(st.z.real) @ _bf16(st.w.real).T
-        sums.append(X)
-        lens.append(end - cyc)
-        cyc = end
-    return oracle.group_estimate(np.array(sums), np.array(lens, dtype=np.float64), K)
+    return _block_oracle.block_estimate(c, K, SEED, mid, burn, samp, B, F)
 
 
 def test_served_results_match_the_oracle():
@@ -136,7 +117,7 @@ def test_served_results_match_the_oracle():
     (Eq. 1/C, Eq. tr) within 1e-4 of its largest entry."""
     reqs = _requests()
     probe = mcinv.mcinv_pool_create(K=K, mem_budget=1 << 24, max_slots=2, batch_cycles=B)
-    G = mcinv.mcinv_pool_info(probe)["groups"]
+    G, F = mcinv.mcinv_pool_info(probe)["groups"], mcinv.mcinv_pool_info(probe)["fold_steps"]
     need = [mcinv.mcinv_pool_footprint(probe, c.n, c.nnz, kind == mcinv.MCINV_EST_BLOCK)
             for c, _, _, _, kind, _ in reqs]
     mcinv.mcinv_pool_destroy(probe)
@@ -145,7 +126,7 @@ def test_served_results_match_the_oracle():
     kinds = set()
     for k, (c, mid, burn, samp, kind, q) in enumerate(reqs):
         m, se, _ = mixed[k]
-        om, ose = _oracle_result(c, mid, burn, samp, kind, q, G)
+        om, ose = _oracle_result(c, mid, burn, samp, kind, q, G, F)
         assert _rel(m, om) <= 1e-4, (k, kind, _rel(m, om))
         assert _rel(se, ose) <= 1e-4, (k, kind, _rel(se, ose))
         kinds.add(kind)
