@@ -584,8 +584,9 @@ def time_to_rms(args, mats, burn, K, B, budget, rank, target=1e-2, max_samples=2
     # batched form: every matrix admitted at once, steps until the monitored ones reach the target
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    # one step's product a batch: the estimates can be checked after every step
     pool = mcinv.mcinv_pool_create(K=K, seed=args.seed, chain_base=rank * K, mem_budget=budget,
-                                   max_slots=len(mats), batch_cycles=B, flags=order_flag(args))
+                                   max_slots=len(mats), batch_cycles=B, fold_steps=1, flags=order_flag(args))
     tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=burn, samples=max_samples)
                for k, c in enumerate(mats)]
     mcinv.mcinv_pool_sync(pool)

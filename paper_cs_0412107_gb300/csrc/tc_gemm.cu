@@ -247,10 +247,11 @@ __global__ void __launch_bounds__(128, 1)
 // Two 256-column TMEM accumulators alternate between a CTA's tiles, so the
 // epilogue of one tile runs under the MMAs of the next.
 //
-// When the tiles leave a last, partly filled wave of at most half the grid,
-// those remaining tiles are split along the contraction dimension into s
-// parts each (one part per CTA): a part writes its FP32 partial tile to a
-// workspace, and the warp that completes the count of a tile's parts sums
+// When the tiles leave a last, partly filled wave of at most half the grid
+// (and are long enough, kSplitMinKtiles), those remaining tiles are split
+// along the contraction dimension into s parts each (one part per CTA): a part
+// writes its FP32 partial tile to a workspace, and for each 32-row quarter of
+// the tile the warp that completes the count of that quarter's parts sums
 // them in part order into D.  The sum order is fixed, so the result does not
 // depend on which CTA finishes last.
 // ---------------------------------------------------------------------------
@@ -409,38 +410,51 @@ __global__ void __launch_bounds__(192, 1)
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[ab])) : "memory");
             if (piece >= 0) {
-                // count this warp's rows of the part in; the warp completing the tile's
-                // 4 s arrivals sums the parts in part order (no barrier between warps)
-                const int tt = piece / S.s;
+                // count this warp's 32 rows of the part in; the warp completing the s
+                // arrivals of its quarter of the tile sums those rows' parts in part
+                // order (the four quarters in parallel, no barrier between warps)
+                const int tq = (piece / S.s) * 4 + q;
                 __threadfence();
                 __syncwarp();
                 int last = 0;
                 if (lane == 0) {
-                    const int old = atomicAdd(&cnt[tt], 1);
-                    last = (old == 4 * S.s - 1);
-                    if (last) cnt[tt] = 0;  // ready for the next launch
+                    const int old = atomicAdd(&cnt[tq], 1);
+                    last = (old == S.s - 1);
+                    if (last) cnt[tq] = 0;  // ready for the next launch
                 }
                 last = __shfl_sync(0xffffffffu, last, 0);
                 if (last) {
                     __threadfence();
-                    const float *w0 = work + (size_t)tt * S.s * BM * BN;
+                    const float *w0 = work + (size_t)(piece / S.s) * S.s * BM * BN + (size_t)q * 32 * BN;
+                    // 32 rows x 64 float4: lanes along a row, 8 float4 a lane in flight per part
 #pragma unroll 1
-                    for (int f = lane; f < BM * BN / 4; f += 32) {
-                        const int tr = f / (BN / 4), tc = (f % (BN / 4)) * 4;
-                        float4 v = __ldcg((const float4 *)(w0 + (size_t)tr * BN + tc));
+                    for (int f0 = 0; f0 < 32 * BN / 4; f0 += 8 * 32) {
+                        float4 v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[u] = __ldcg((const float4 *)w0 + f0 + u * 32 + lane);
                         for (int j = 1; j < S.s; ++j) {
-                            const float4 u = __ldcg((const float4 *)(w0 + (size_t)j * BM * BN + (size_t)tr * BN + tc));
-                            v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+                            float4 x[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                x[u] = __ldcg((const float4 *)(w0 + (size_t)j * BM * BN) + f0 + u * 32 + lane);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                v[u].x += x[u].x; v[u].y += x[u].y; v[u].z += x[u].z; v[u].w += x[u].w;
+                            }
                         }
-                        const int grow = m0 + tr;
-                        if (grow < M) {
-                            float *dst = D + (size_t)grow * N + n0 + tc;
-                            if (n0 + tc + 4 <= N && (N & 3) == 0) {
-                                *(float4 *)dst = v;
-                            } else {
-                                const float vv[4] = {v.x, v.y, v.z, v.w};
-                                for (int j = 0; j < 4; ++j)
-                                    if (n0 + tc + j < N) dst[j] = vv[j];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int f = f0 + u * 32 + lane;
+                            const int grow = m0 + q * 32 + f / (BN / 4), gcol = n0 + (f % (BN / 4)) * 4;
+                            if (grow < M) {
+                                float *dst = D + (size_t)grow * N + gcol;
+                                if (gcol + 4 <= N && (N & 3) == 0) {
+                                    *(float4 *)dst = v[u];
+                                } else {
+                                    const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                                    for (int j = 0; j < 4; ++j)
+                                        if (gcol + j < N) dst[j] = vv[j];
+                                }
                             }
                         }
                     }
@@ -505,7 +519,11 @@ bool encode(CUtensorMap *map, const uint16_t *base, size_t rows, long long ld, i
 // 2..5 = epilogue (warp w reads TMEM lanes 32*(w%4) .. +31).  The smem ring's
 // stage/phase counters run on across tiles.  Two 256-column accumulators in
 // TMEM alternate between tiles (tmem_full / tmem_empty per accumulator), so
-// the MMAs of one tile run while the epilogue drains the previous one.
+// the MMAs of one tile run while the epilogue drains the previous one.  A
+// matrix whose output is marked `add` has the tile added to D (the products of
+// several steps summed before one fold): each 32 x 32 chunk goes through a
+// staging square in shared memory so that the read-modify-write of D is made
+// row by row, 32 consecutive columns a warp instruction.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_grouped_kernel(const GroupTile *__restrict__ tiles, const int *__restrict__ ntiles_p,
@@ -592,6 +610,7 @@ __global__ void __launch_bounds__(192, 1)
     } else {
         // epilogue warps 2..5
         const int q = warp & 3;
+        float *stage = (float *)(smem + STAGES * STAGE_BYTES + 256) + q * 32 * 33;
         int tl = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
             const GroupTile tile = tiles[t];
@@ -605,28 +624,41 @@ __global__ void __launch_bounds__(192, 1)
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + (uint32_t)(ab * TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                if (row < o.M) {
+                if (o.add) {
+                    // D += the chunk: through this warp's 32 x 33 staging square, so that a
+                    // warp instruction reads and writes 32 consecutive columns of one row
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+                    __syncwarp();
+                    const int col = tile.n0 + c0 + lane;
+#pragma unroll 1
+                    for (int r0 = 0; r0 < 32; r0 += 16) {
+                        // the 16 rows' loads first (independent), then the adds and stores
+                        float dv[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int grow = tile.m0 + q * 32 + r0 + u;
+                            dv[u] = (grow < o.M && col < o.N) ? __ldcg(o.D + (size_t)grow * o.N + col) : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int grow = tile.m0 + q * 32 + r0 + u;
+                            if (grow < o.M && col < o.N)
+                                o.D[(size_t)grow * o.N + col] = dv[u] + stage[(r0 + u) * 33 + lane];
+                        }
+                    }
+                    __syncwarp();
+                } else if (row < o.M) {
                     float *dst = o.D + (size_t)row * o.N + tile.n0 + c0;
                     if (tile.n0 + c0 + 32 <= o.N && (o.N & 3) == 0) {
-                        if (o.add) {
-                            float4 v[8];
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) v[j] = *(const float4 *)(dst + 4 * j);
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                *(float4 *)(dst + 4 * j) =
-                                    make_float4(v[j].x + __uint_as_float(r[4 * j]), v[j].y + __uint_as_float(r[4 * j + 1]),
-                                                v[j].z + __uint_as_float(r[4 * j + 2]), v[j].w + __uint_as_float(r[4 * j + 3]));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 4)
-                                *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                        }
+                        for (int j = 0; j < 32; j += 4)
+                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (tile.n0 + c0 + j < o.N) dst[j] = o.add ? dst[j] + __uint_as_float(r[j]) : __uint_as_float(r[j]);
+                            if (tile.n0 + c0 + j < o.N) dst[j] = __uint_as_float(r[j]);
                     }
                 }
             }
@@ -673,7 +705,8 @@ bool tc_encode_operand(CUtensorMap *map, const uint16_t *base, long long rows, l
 cudaError_t tc_gemm_grouped_run(const GroupTile *tiles, const int *ntiles, const CUtensorMap *maps, const GroupOut *outs,
                                 int grid, int *status, cudaStream_t s)
 {
-    const int smem = STAGES * STAGE_BYTES + 1024 + 256;
+    // the ring, its barriers, and four 32 x 33 FP32 staging squares for D += A B^T
+    const int smem = STAGES * STAGE_BYTES + 1024 + 256 + 4 * 32 * 33 * 4;
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     tc_gemm_grouped_kernel<<<grid, 192, smem, s>>>(tiles, ntiles, maps, outs, status);
@@ -683,13 +716,20 @@ cudaError_t tc_gemm_grouped_run(const GroupTile *tiles, const int *ntiles, const
 namespace {
 }  // namespace
 
+// Split a last, partly filled wave only when a tile is long enough for the
+// parts' fix-up (a read of every part's 128 KB) to cost less than the wait for
+// whole tiles: 512 k-slices of 64 are about 0.17 ms of tensor-core time a tile.
+constexpr int kSplitMinKtiles = 512;
+// at most this many parts a tile, so that the fix-up's reads stay short
+constexpr long long kSplitMaxParts = 16;
+
 struct TcGemmPlan {
     CUtensorMap ta, tb;
     float *D;
     long long M, N, ld;
     int sms;        // CTAs of the persistent grid (one per SM)
     float *work;    // sms partial 128 x 256 tiles of a split last wave
-    int *cnt;       // arrivals per split tile
+    int *cnt;       // arrivals per (split tile, 32-row quarter)
 };
 
 TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t *B, size_t b_rows,
@@ -727,8 +767,8 @@ TcGemmPlan *tc_gemm_plan_create(const uint16_t *A, size_t a_rows, const uint16_t
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     p->sms = sms;
     if (cudaMalloc((void **)&p->work, (size_t)sms * BM * BN * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void **)&p->cnt, (size_t)sms * sizeof(int)) != cudaSuccess ||
-        cudaMemset(p->cnt, 0, (size_t)sms * sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void **)&p->cnt, (size_t)sms * 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->cnt, 0, (size_t)sms * 4 * sizeof(int)) != cudaSuccess) {
         if (why) *why = "cannot allocate the split-tile workspace";
         cudaFree(p->work);
         cudaFree(p->cnt);
@@ -756,13 +796,13 @@ cudaError_t tc_gemm_run(TcGemmPlan *p, long long inner, int *status, cudaStream_
     S.s = 1;
     S.Tfull = (int)T;
     S.npieces = 0;
-    if (R >= 1 && r > 0 && 2 * r <= G && ktiles >= 2) {
+    if (R >= 1 && r > 0 && 2 * r <= G && ktiles >= kSplitMinKtiles) {
         // a last wave of r tiles on G CTAs: split each into G / r parts
-        S.s = (int)std::min<long long>(G / r, ktiles);
+        S.s = (int)std::min<long long>(std::min<long long>(G / r, kSplitMaxParts), ktiles);
         S.Tfull = (int)(R * G);
         S.npieces = (int)(r * S.s);
         // a contraction abandoned after an expired wait leaves its counts behind
-        cudaError_t e = cudaMemsetAsync(p->cnt, 0, (size_t)r * sizeof(int), s);
+        cudaError_t e = cudaMemsetAsync(p->cnt, 0, (size_t)r * 4 * sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
     tc_gemm_persistent_kernel<<<G, 192, SMEM_BYTES, s>>>(p->ta, p->tb, p->D, (int)p->M, (int)p->N, S, p->work,

@@ -106,11 +106,17 @@ def test_pool_full_inverse_equals_single_handle():
 
 @pytest.mark.parametrize("F", [1, 3])
 def test_pool_folded_batches_follow_the_oracle(F):
-    """The block products of F steps summed in FP32 by the contraction's epilogue and
-    folded once (the batch-means SE over batches of F x B cycles, shorter at a member's
-    start and end): mean and SE of each member's full inverse equal the oracle's from
-    the same draws, its states rounded to the BF16 operands, within 1e-4 of the largest
-    entry.  Burn-ins that end inside a step give a short first batch."""
+    """The block products of F sampling steps summed in FP32 by the contraction's
+    epilogue and folded once (the batch-means SE over batches of F steps' sampling
+    cycles): mean and SE of each member's full inverse equal the oracle's from the same
+    draws, its states rounded to the BF16 operands, within 1e-4 of the largest entry of
+    the mean.  Burn-ins that end inside a step give a short first batch.
+
+    The SE shares the mean's absolute bar: the GPU rounds its FP32 states to BF16 and
+    the oracle its FP64 states, so a value within ~1e-7 of a rounding boundary lands on
+    the other BF16 neighbour (one operand off by 2^-7 of itself), which moves a batch
+    mean by about 1e-5 of the largest entry; the SE, a spread of batch means ~20 times
+    smaller than the mean, takes that absolute error, not 1e-4 of itself."""
     import _block_oracle
     K, B = 64, 4
     mats = [(wl.random_dominant(n, 4, 1.5, seed), burn, samp)
@@ -123,7 +129,9 @@ def test_pool_folded_batches_follow_the_oracle(F):
     for k, ((c, burn, samp), t) in enumerate(zip(mats, tickets)):
         m, se = mcinv.mcinv_pool_estimate(pool, t, mcinv.MCINV_EST_BLOCK, c.n)
         om, ose = _block_oracle.block_estimate(c, K, 17, 40 + k, burn, samp, B, F)
-        assert rel_err(m, om) <= 1e-4 and rel_err(se, ose) <= 1e-4, (F, k, rel_err(m, om), rel_err(se, ose))
+        bar = 1e-4 * np.abs(om).max()
+        assert np.abs(m - om).max() <= bar and np.abs(se - ose).max() <= bar, \
+            (F, k, rel_err(m, om), np.abs(se - ose).max() / np.abs(om).max())
     mcinv.mcinv_pool_destroy(pool)
 
 

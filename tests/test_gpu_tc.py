@@ -37,9 +37,8 @@ def from_bf16_bits(b):
 
 
 @pytest.mark.parametrize("M,N,inner", [(128, 256, 64), (300, 200, 192), (1000, 600, 1024), (129, 513, 64 * 37),
-                                       # more tiles than SMs (152 on GB300): a last wave of 8 tiles split in
-                                       # 19 parts each; 3 tiles in 40 (capped by the 40 k-slices); and 100
-                                       # tiles, more than half a wave, run whole as an extra round
+                                       # more tiles than SMs (152 on GB300) with short tiles: a last wave of
+                                       # 8, 3 or 100 tiles run whole
                                        (10240, 512, 2048), (19500, 300, 64 * 40), (16100, 512, 256)])
 def test_tc_contraction_matches_fp64(M, N, inner):
     rng = np.random.default_rng(M + N + inner)
@@ -51,6 +50,28 @@ def test_tc_contraction_matches_fp64(M, N, inner):
     want = a @ b.T
     bound = inner * 2.0 ** -23 * (np.abs(a) @ np.abs(b).T) + 1e-30
     assert np.all(np.abs(D - want) <= bound), np.abs(D - want).max()
+
+
+def test_tc_split_last_wave_is_exact():
+    """170 tiles of 128 x 256 on 152 SMs with 515 k-slices of 64 a tile: the last
+    wave's 18 tiles are split along the contraction into 8 uneven parts each, written
+    to a workspace and summed in part order by the warp completing each 32-row
+    quarter.  Operands are small integers (exact in BF16) and every partial sum stays
+    below 2^24, so FP32 accumulation is exact in any order: D must equal the integer
+    product bit for bit, the ragged N = 40 columns included."""
+    rng = np.random.default_rng(5)
+    M, N, inner = 128 * 170, 40, 64 * 515
+    Ai = rng.integers(-4, 5, size=(M, inner), dtype=np.int8)
+    Bi = rng.integers(-4, 5, size=(N, inner), dtype=np.int8)
+    bits = (np.arange(-4, 5, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)  # BF16 of -4..4
+    A = bits[Ai.astype(np.int16) + 4]
+    B = bits[Bi.astype(np.int16) + 4]
+    D = mcinv.mcinv_selftest_tc_gemm(A, B)
+    del A
+    Bf = Bi.astype(np.float32)
+    for r0 in range(0, M, 2048):  # float32 products of integers < 2^24: exact
+        want = Ai[r0:r0 + 2048].astype(np.float32) @ Bf.T
+        assert np.array_equal(D[r0:r0 + 2048], want), r0
 
 
 @pytest.mark.parametrize("complex_", [False, True])
