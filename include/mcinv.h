@@ -346,7 +346,7 @@ typedef struct {
     int32_t groups;         /* SE groups of the diagonal; 0 = 32 */
     int32_t fold_steps;     /* F: sampling steps whose block products are summed in FP32 before
                                each FP64 fold, so a block batch (for the batch-means SE) is the
-                               sampling cycles of F steps (fewer at a member's end); 0 = 4, at
+                               sampling cycles of F steps (fewer at a member's end); 0 = 8, at
                                most 1024 */
     int32_t chains_per_cta; /* 0 = the first steps time the candidate shapes; 4 x a power of two
                                <= 128 (a chain slice per CTA; 128 with 384 or 512 threads: the

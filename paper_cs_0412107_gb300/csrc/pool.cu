@@ -390,6 +390,24 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
     }
 }
 
+// The full inverse of P C P^T back to the rows and columns of C: entry (r, c)
+// of C^-1 is entry (pos[r], pos[c]) of the sampled matrix's inverse (pos: the
+// position of each row of C in the colour order).  Reads gathered within a row,
+// writes coalesced.
+__global__ void block_unpermute_kernel(long long n, const int *__restrict__ pos, const double *__restrict__ mean_p,
+                                       const double *__restrict__ se_p, double *__restrict__ mean_c,
+                                       double *__restrict__ se_c)
+{
+    const long long total = n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / n, c = e - r * n;
+        const long long src = (long long)pos[r] * n + pos[c];
+        mean_c[e] = mean_p[src];
+        se_c[e] = se_p[src];
+    }
+}
+
 template <int LPR>
 static cudaError_t launch_pool_sweep_l(int V, const PoolSlotDev *slots, const PoolItem *items, PoolCounts *cnt, int K,
                                        int nw, int blob_max, int seg, int *status, int grid, int threads, cudaStream_t s)
@@ -526,7 +544,7 @@ struct mcinv_pool_ctx {
     uint64_t seed = 0;
     int64_t chain_base = 0;
     int B = 8, G = 32, units = 0, seg = 1, nw = 0;
-    int F = 4;                         // steps whose block products are summed before a fold
+    int F = 8;                         // steps whose block products are summed before a fold
     int LPR = 8, V = 4, threads = 512, grid_sweep = 152;
     int blob_max = 48 * 1024;
     int max_slots = 0;
@@ -619,7 +637,7 @@ extern "C" mcinv_status mcinv_pool_create(mcinv_pool_t *out, const mcinv_pool_op
         delete p;
         return pfail(nullptr, MCINV_E_ARG, "fold_steps must be in [0, 1024]");
     }
-    p->F = o.fold_steps > 0 ? o.fold_steps : 4;
+    p->F = o.fold_steps > 0 ? o.fold_steps : 8;
     p->max_slots = (int)o.max_slots;
     p->stream = (cudaStream_t)o.stream;
     p->color = (o.flags & MCINV_F_COLOR_ORDER) != 0;
@@ -1190,6 +1208,8 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
     a.bytes = 2 * elems * 8 + (kind == MCINV_EST_TRACE ? n * 8 : 0);
     if (!p->heap.alloc(a.bytes, &a.off)) return pfail(p, MCINV_E_NOMEM, "no arena space for the estimate");
     double *mean = (double *)(p->arena + a.off), *se = mean + elems;
+    Alloc g;                   // scratch of the unpermuted inverse, when it fits
+    bool unpermuted = false;   // the inverse is in the rows of C already
     mcinv_status st = MCINV_OK;
     cudaError_t e = cudaSuccess;
     if (kind == MCINV_EST_DIAG) {
@@ -1210,6 +1230,24 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
         // the samples folded so far (a product still being summed joins at its fold)
         e = launch_block_estimate(0, (long long)(n * n), (double)p->K, (double)s.folded, (double)s.batches, s.dev.bsum,
                                   s.dev.bsq, mean, se, str);
+        if (e == cudaSuccess && !s.ord.empty() && p->heap.alloc(2 * elems * 8 + n * 4, &g.off)) {
+            // back to the rows and columns of C on the device (else on the host, below)
+            g.bytes = 2 * elems * 8 + n * 4;
+            double *mc = (double *)(p->arena + g.off), *sc = mc + elems;
+            int *dpos = (int *)(sc + elems);
+            std::vector<int> pos(n);
+            for (size_t k = 0; k < n; ++k) pos[s.ord[k]] = (int)k;
+            if ((e = cudaMemcpyAsync(dpos, pos.data(), n * 4, cudaMemcpyHostToDevice, str)) == cudaSuccess &&
+                (e = cudaStreamSynchronize(str)) == cudaSuccess) {
+                long long blocks = (long long)((elems + 255) / 256);
+                if (blocks > 152LL * 16) blocks = 152LL * 16;
+                block_unpermute_kernel<<<(unsigned)blocks, 256, 0, str>>>((long long)n, dpos, mean, se, mc, sc);
+                e = cudaGetLastError();
+            }
+            mean = mc;
+            se = sc;
+            unpermuted = true;
+        }
     }
     if (st == MCINV_OK && e == cudaSuccess) {
         if (kind == MCINV_EST_TRACE) {
@@ -1222,9 +1260,10 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
         if (e == cudaSuccess) e = cudaStreamSynchronize(str);
     }
     p->heap.release(a.off, a.bytes);
+    if (g.bytes) p->heap.release(g.off, g.bytes);
     if (st != MCINV_OK) return st;
     if (e != cudaSuccess) return pfail(p, MCINV_E_CUDA, "estimate: %s", cudaGetErrorString(e));
-    if (!s.ord.empty() && kind != MCINV_EST_TRACE) {
+    if (!s.ord.empty() && kind != MCINV_EST_TRACE && !unpermuted) {
         // rows (and, for the inverse, columns) of P C^-1 P^T back to those of C^-1
         for (double *x : {out, se_out}) {
             if (!x) continue;

@@ -521,9 +521,9 @@ bool encode(CUtensorMap *map, const uint16_t *base, size_t rows, long long ld, i
 // TMEM alternate between tiles (tmem_full / tmem_empty per accumulator), so
 // the MMAs of one tile run while the epilogue drains the previous one.  A
 // matrix whose output is marked `add` has the tile added to D (the products of
-// several steps summed before one fold): each 32 x 32 chunk goes through a
-// staging square in shared memory so that the read-modify-write of D is made
-// row by row, 32 consecutive columns a warp instruction.
+// several steps summed before one fold).  Each 32 x 32 chunk of the epilogue
+// goes through a staging square in shared memory, so that D is written (and,
+// to add, read) row by row, 32 consecutive columns a warp instruction.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_grouped_kernel(const GroupTile *__restrict__ tiles, const int *__restrict__ ntiles_p,
@@ -619,48 +619,33 @@ __global__ void __launch_bounds__(192, 1)
             const bool have = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[ab]), (uint32_t)(tl >> 1) & 1u, abort_flag));
             if (!have) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = tile.m0 + q * 32 + lane;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + (uint32_t)(ab * TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                if (o.add) {
-                    // D += the chunk: through this warp's 32 x 33 staging square, so that a
-                    // warp instruction reads and writes 32 consecutive columns of one row
+                // D = (or +=) the chunk, through this warp's 32 x 33 staging square, so
+                // that a warp instruction reads and writes 32 consecutive columns of one row
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
-                    __syncwarp();
-                    const int col = tile.n0 + c0 + lane;
+                for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+                __syncwarp();
+                const int col = tile.n0 + c0 + lane;
 #pragma unroll 1
-                    for (int r0 = 0; r0 < 32; r0 += 16) {
-                        // the 16 rows' loads first (independent), then the adds and stores
-                        float dv[16];
+                for (int r0 = 0; r0 < 32; r0 += 16) {
+                    // the 16 rows' loads first (independent), then the adds and stores
+                    float dv[16];
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int grow = tile.m0 + q * 32 + r0 + u;
-                            dv[u] = (grow < o.M && col < o.N) ? __ldcg(o.D + (size_t)grow * o.N + col) : 0.f;
-                        }
-#pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int grow = tile.m0 + q * 32 + r0 + u;
-                            if (grow < o.M && col < o.N)
-                                o.D[(size_t)grow * o.N + col] = dv[u] + stage[(r0 + u) * 33 + lane];
-                        }
+                    for (int u = 0; u < 16; ++u) {
+                        const int grow = tile.m0 + q * 32 + r0 + u;
+                        dv[u] = (o.add && grow < o.M && col < o.N) ? __ldcg(o.D + (size_t)grow * o.N + col) : 0.f;
                     }
-                    __syncwarp();
-                } else if (row < o.M) {
-                    float *dst = o.D + (size_t)row * o.N + tile.n0 + c0;
-                    if (tile.n0 + c0 + 32 <= o.N && (o.N & 3) == 0) {
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (tile.n0 + c0 + j < o.N) dst[j] = __uint_as_float(r[j]);
+                    for (int u = 0; u < 16; ++u) {
+                        const int grow = tile.m0 + q * 32 + r0 + u;
+                        if (grow < o.M && col < o.N)
+                            o.D[(size_t)grow * o.N + col] = dv[u] + stage[(r0 + u) * 33 + lane];
                     }
                 }
+                __syncwarp();
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
