@@ -83,7 +83,7 @@ def test_pool_result_is_the_same_alone_and_in_the_mix():
     run_until_done(mix, [tm, t1, t2])
     for k, (m, se) in ref.items():
         m2, se2 = mcinv.mcinv_pool_estimate(mix, tm, k, a.n)
-        assert np.array_equal(m, m2) and np.array_equal(se, se2), k
+        assert np.array_equal(m, m2) and np.array_equal(se, se2, equal_nan=True), k
 
 
 def test_pool_full_inverse_equals_single_handle():
@@ -154,7 +154,8 @@ def test_pool_admission_by_device_memory():
 def test_pool_batch_estimates_cover_the_dense_inverse():
     sizes = wl.batch_sizes(6, 64, 160, seed=1)
     mats = [wl.random_dominant(int(n), 4, 1.5, 1000 + k) for k, n in enumerate(sizes)]
-    pool = mcinv.mcinv_pool_create(K=256, seed=0, mem_budget=1 << 30, max_slots=16, batch_cycles=8)
+    # 100 sampling steps, two a batch: 50 batch means, so the z-scores are nearly normal
+    pool = mcinv.mcinv_pool_create(K=256, seed=0, mem_budget=1 << 30, max_slots=16, batch_cycles=8, fold_steps=2)
     tickets = [mcinv.mcinv_pool_submit(pool, c, matrix_id=k, burnin=80, samples=800) for k, c in enumerate(mats)]
     run_until_done(pool, tickets)
     zs = []
