@@ -182,7 +182,8 @@ def kernel_flags(args):
         return mcinv.MCINV_F_GRID, {"threads_per_cta": 512}
     if args.kernel == "bulk":
         return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_NOPAIR, {}
-    return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK, {}
+    # the pair layout in the shape --threads names (384 by default)
+    return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_PAIR, {}
 
 
 def shape_kw(args):

@@ -54,7 +54,7 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
                                             (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
                                             (36, 96, GB), (256, 512, GB), (200, 512, GBS), (36, 512, GBS),
                                             (256, 512, GP), (200, 384, GP), (36, 384, GP), (1024, 384, GP),
-                                            (520, 256, GP), (900, 256, GP)])
+                                            (520, 256, GP), (900, 256, GP), (1024, 192, GP), (520, 192, GP)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -63,11 +63,20 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
 
 
 @pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
-                                          (GP, 384), (GP, 256)])
+                                          (GP, 384), (GP, 256), (GP, 192)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
     hg, hr = _pair(c, 130 if threads in (0, 384) else 520, flags=flags, grid=grid, threads=threads)
+    for h in (hg, hr):
+        mcinv.mcinv_destroy(h)
+
+
+@pytest.mark.parametrize("threads", [384, 256, 192])
+def test_pair_shapes_on_a_4d_lattice(threads):
+    # 8 neighbours a row: one row in flight a warp with 9 or 13 slots, two with 16
+    c = wl.u1_lattice((4, 6, 4, 4), 0.06, 0.04, seed=3)
+    hg, hr = _pair(c, 520, flags=CO, cycles=(2, 9), grid=GP, threads=threads)
     for h in (hg, hr):
         mcinv.mcinv_destroy(h)
 
@@ -81,7 +90,7 @@ def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
 
 
 @pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
-                                          (GP, 256)])
+                                          (GP, 256), (GP, 192)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
