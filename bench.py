@@ -727,7 +727,8 @@ def run_lattice(args, world, rank, local):
     return res
 
 def run_lattice2d(args, world, rank, local):
-    """The complex 2D lattice (L = 128, K = 4096 chains, diagonal and tr(QC^-1) with q ~ U(0,1)):
+    """The complex 2D lattice (L = 128, K = 4096 chains, diagonal and tr(QC^-1) with q ~ U(0,1)),
+    or with --workload lattice4d16-rate the 4D one (16^4, K = 8192, the same estimates):
     coupled updates per second of the sampling step, with the sweep's bytes against the
     copy bandwidth both as gathered (every stored c_ij of C and of C^dagger reads one
     complex64 z_j / w_j) and as compulsory (z and w read and written once a cycle)."""
@@ -737,7 +738,8 @@ def run_lattice2d(args, world, rank, local):
     from paper_cs_0412107_gb300 import workloads as wl
 
     torch.cuda.set_device(local)
-    w = wl.WORKLOADS["lattice2d128"]
+    name = "lattice4d16" if args.workload == "lattice4d16-rate" else "lattice2d128"
+    w = wl.WORKLOADS[name]
     csr = w.build()
     K = w.K
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
@@ -781,13 +783,13 @@ def run_lattice2d(args, world, rank, local):
     t_launch = sw_ms / sw_launches / 1e3 if sw_launches else None
     achieved = alg_bytes / t_launch / 1e9 if t_launch else None
     kname, ksrc, kprof = SWEEP_KERNELS[info0["sweep_kernel"]]
-    kprof = {4: "cc_sweep_grid_pair_lattice2d128.txt"}.get(info0["sweep_kernel"])
+    kprof = {4: f"cc_sweep_grid_pair_{name}.txt"}.get(info0["sweep_kernel"])
     return {
         "metric": METRIC, "value": float(csr.nnz) * K * cycles * world / (ms_max / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (seeded U(1) lattice, Philox noise)",
-        "config": {"workload": "lattice2d128", "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
+        "config": {"workload": name, "n": csr.n, "nnz": csr.nnz, "K": K, "batch_cycles": B,
                    "estimates": "diagonal + tr(QC^-1), q ~ U(0,1)", "sweep_kernel": kname,
                    "threads_per_cta": info0["threads_per_cta"], "levels": info0["levels"],
                    "sweep_order": args.order,
@@ -1068,7 +1070,8 @@ def main():
     ap.add_argument("--e2e-samples", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch512", "dirac18", "lattice4d16",
-                                                             "lattice2d128"])
+                                                             "lattice2d128", "lattice4d16-rate"],
+                    help="lattice4d16: time to RMS error; lattice4d16-rate: the update rate, as lattice2d128")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-burnin", type=int, default=200)
     ap.add_argument("--batch-samples", type=int, default=2000)
@@ -1092,7 +1095,7 @@ def main():
         res = run_dirac(args, world, rank, local)
     elif args.workload == "lattice4d16":
         res = run_lattice(args, world, rank, local)
-    elif args.workload == "lattice2d128":
+    elif args.workload in ("lattice2d128", "lattice4d16-rate"):
         res = run_lattice2d(args, world, rank, local)
     else:
         res = run_mine(args, world, rank, local)
