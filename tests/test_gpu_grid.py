@@ -163,8 +163,8 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 256 threads (96, 192, 384 or 512)
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
-    for flags, threads in ((GP, 192), (GP | mcinv.MCINV_F_GRID_NOPAIR, 384), (GR | mcinv.MCINV_F_GRID_PAIR, 384)):
-        with pytest.raises(mcinv.McinvError) as e:  # the pair shapes: 512, 384 or 256 threads, bulk staging
+    for flags, threads in ((GP, 96), (GP | mcinv.MCINV_F_GRID_NOPAIR, 384), (GR | mcinv.MCINV_F_GRID_PAIR, 384)):
+        with pytest.raises(mcinv.McinvError) as e:  # the pair shapes: 512, 384, 256 or 192 threads, bulk staging
             mcinv.create_from_csr(wl.pedigree(500, 1.2, 1), K=64, threads_per_cta=threads, flags=flags)
         assert e.value.status == mcinv.MCINV_E_ARG
     with pytest.raises(mcinv.McinvError) as e:  # the pair layout of a matrix that is not structurally symmetric
