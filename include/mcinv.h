@@ -127,10 +127,8 @@ typedef struct {
                               layout.  Same values, bit for bit. */
 #define MCINV_F_GRID_PAIR 128 /* with MCINV_F_GRID_BULK: the pair layout with the shape that
                               threads_per_cta names: 512 (16 warps, one block a warp, 12 slots of
-                              1 KB), 384 (the default), 256 (8 warps, two blocks a warp, 13 slots
-                              of 2 KB) or 192 (6 warps, two blocks a warp, 16 slots of 2 KB: two
-                              rows of 8 neighbours in flight a warp).  MCINV_E_UNSUPPORTED when C
-                              is not structurally symmetric;
+                              1 KB), 384 (the default) or 256 (8 warps, two blocks a warp, 13 slots
+                              of 2 KB).  MCINV_E_UNSUPPORTED when C is not structurally symmetric;
                               MCINV_E_ARG with MCINV_F_GRID_NOPAIR or another thread count. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns

@@ -372,12 +372,12 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 10; ++variant) {
+    for (int variant = 0; variant < 9; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
         // lane (12 warps of 32 slots) or 1 (16 warps of 24 slots); bulk-staged on the pair
         // layout (structurally symmetric matrices) with one vector a lane (16 warps) or two
-        // (12, 8 or 6 warps)
-        static const int kT[10] = {384, 512, 384, 192, 96, 512, 512, 384, 256, 192};
+        // (12 or 8 warps)
+        static const int kT[9] = {384, 512, 384, 192, 96, 512, 512, 384, 256};
         const int T = kT[variant];
         const bool bulk = variant >= 2;
         const bool pair = variant == 5 || variant >= 7;
@@ -585,8 +585,8 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         // (with bulk staging and no explicit shape, or MCINV_F_GRID_PAIR, the pair layout is
         // chosen below when it applies)
         const bool fpair = (h->flags & MCINV_F_GRID_PAIR) != 0;
-        if (fpair && ((h->flags & MCINV_F_GRID_NOPAIR) || (T != 512 && T != 384 && T != 256 && T != 192))) {
-            fail(h, MCINV_E_ARG, "MCINV_F_GRID_PAIR takes 512, 384, 256 or 192 threads per CTA, not MCINV_F_GRID_NOPAIR");
+        if (fpair && ((h->flags & MCINV_F_GRID_NOPAIR) || (T != 512 && T != 384 && T != 256))) {
+            fail(h, MCINV_E_ARG, "MCINV_F_GRID_PAIR takes 512, 384 or 256 threads per CTA, not MCINV_F_GRID_NOPAIR");
             return bail(MCINV_E_ARG);
         }
         const int ctas = grid_supported(cplx, vmax, opt.K, fpair ? 512 : T, bulk) ? grid_ctas(cplx, T, bulk, fpair) : 0;

@@ -69,11 +69,11 @@ constexpr int PAIR_THREADS = 512;
 // slots of one warp's ring.  Separate z and w buffers: RING with 12 / G warps
 // a CTA, RING16 with 16 warps.  The pair layout: PAIR_RN slots of 1 KB with 16
 // warps (G = 1); with G = 2 (two adjacent blocks a warp, 2 KB slots) 9 slots
-// with 12 warps, 13 with 8, or 16 with 6 (two rows of 8 neighbours in flight).
+// with 12 warps or 13 with 8.
 template <int NT, int G, bool PAIR>
 constexpr int ring_slots()
 {
-    return PAIR ? (G == 1 ? PAIR_RN : NT == 384 ? 9 : NT == 256 ? 13 : 16) : NT == 512 ? RING16 : RING;
+    return PAIR ? (G == 1 ? PAIR_RN : NT == 384 ? 9 : 13) : NT == 512 ? RING16 : RING;
 }
 // ring bytes of one warp: slots of G x 512 bytes, or of G x 1 KB on the pair layout
 template <int NT, int G, bool PAIR>
@@ -276,8 +276,6 @@ int grid_ctas(int cplx, int threads, bool bulk, bool pair)
             per_sm = cplx ? grid_blocks_per_sm<true, 2, 384, true, 2, true>() : grid_blocks_per_sm<false, 4, 384, true, 2, true>();
         else if (threads == 256)
             per_sm = cplx ? grid_blocks_per_sm<true, 2, 256, true, 2, true>() : grid_blocks_per_sm<false, 4, 256, true, 2, true>();
-        else if (threads == 192)
-            per_sm = cplx ? grid_blocks_per_sm<true, 2, 192, true, 2, true>() : grid_blocks_per_sm<false, 4, 192, true, 2, true>();
     } else if (bulk) {
         if (threads == PAIR_THREADS)  // the pair and the 16-warp separate forms: the same 12 KB rings
             per_sm = cplx ? grid_blocks_per_sm<true, 2, PAIR_THREADS, true, 1, true>()
@@ -318,9 +316,6 @@ cudaError_t launch_sweep_grid(const SweepArgs &a, const GridArgs &g, int cplx, i
             if (threads == 256)
                 return cplx ? launch_grid_v<true, 2, 256, true, 2, true>(a, g, ctas, s)
                             : launch_grid_v<false, 4, 256, true, 2, true>(a, g, ctas, s);
-            if (threads == 192)
-                return cplx ? launch_grid_v<true, 2, 192, true, 2, true>(a, g, ctas, s)
-                            : launch_grid_v<false, 4, 192, true, 2, true>(a, g, ctas, s);
             if (threads != PAIR_THREADS) return cudaErrorInvalidValue;
             return cplx ? launch_grid_v<true, 2, PAIR_THREADS, true, 1, true>(a, g, ctas, s)
                         : launch_grid_v<false, 4, PAIR_THREADS, true, 1, true>(a, g, ctas, s);

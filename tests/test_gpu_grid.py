@@ -54,7 +54,7 @@ def _pair(c, K, flags=0, cycles=(1, 7, 25), threads=384, grid=GR, **kw):
                                             (1024, 192, GB), (520, 192, GB), (1024, 96, GB), (900, 96, GB),
                                             (36, 96, GB), (256, 512, GB), (200, 512, GBS), (36, 512, GBS),
                                             (256, 512, GP), (200, 384, GP), (36, 384, GP), (1024, 384, GP),
-                                            (520, 256, GP), (900, 256, GP), (1024, 192, GP), (520, 192, GP)])
+                                            (520, 256, GP), (900, 256, GP)])
 def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
     c = wl.pedigree(6000, 1.2, 3)  # long rows (pieces), 60-odd levels in the given order
     hg, hr = _pair(c, K, flags=flags, threads=threads, grid=grid)
@@ -63,7 +63,7 @@ def test_grid_equals_chain_sliced_kernel_real(flags, K, threads, grid):
 
 
 @pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
-                                          (GP, 384), (GP, 256), (GP, 192)])
+                                          (GP, 384), (GP, 256)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
     c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=2)
@@ -72,9 +72,9 @@ def test_grid_equals_chain_sliced_kernel_complex(flags, grid, threads):
         mcinv.mcinv_destroy(h)
 
 
-@pytest.mark.parametrize("threads", [384, 256, 192])
+@pytest.mark.parametrize("threads", [384, 256])
 def test_pair_shapes_on_a_4d_lattice(threads):
-    # 8 neighbours a row: one row in flight a warp with 9 or 13 slots, two with 16
+    # 8 neighbours a row: one row in flight a warp (9 or 13 slots)
     c = wl.u1_lattice((4, 6, 4, 4), 0.06, 0.04, seed=3)
     hg, hr = _pair(c, 520, flags=CO, cycles=(2, 9), grid=GP, threads=threads)
     for h in (hg, hr):
@@ -90,7 +90,7 @@ def test_grid_equals_chain_sliced_kernel_wilson_dirac(grid, threads):
 
 
 @pytest.mark.parametrize("grid,threads", [(GR, 384), (GB, 0), (GBS, 0), (GB, 192), (GB, 96), (GBS, 512), (GP, 512),
-                                          (GP, 256), (GP, 192)])
+                                          (GP, 256)])
 @pytest.mark.parametrize("flags", [0, CO])
 def test_grid_estimates_equal_chain_sliced_kernel(flags, grid, threads):
     c = wl.pedigree(3000, 1.2, 7)
@@ -163,8 +163,8 @@ def test_grid_rejections():
     with pytest.raises(mcinv.McinvError) as e:  # bulk staging with 256 threads (96, 192, 384 or 512)
         mcinv.create_from_csr(c, K=64, threads_per_cta=256, flags=GB)
     assert e.value.status == mcinv.MCINV_E_UNSUPPORTED
-    for flags, threads in ((GP, 96), (GP | mcinv.MCINV_F_GRID_NOPAIR, 384), (GR | mcinv.MCINV_F_GRID_PAIR, 384)):
-        with pytest.raises(mcinv.McinvError) as e:  # the pair shapes: 512, 384, 256 or 192 threads, bulk staging
+    for flags, threads in ((GP, 192), (GP | mcinv.MCINV_F_GRID_NOPAIR, 384), (GR | mcinv.MCINV_F_GRID_PAIR, 384)):
+        with pytest.raises(mcinv.McinvError) as e:  # the pair shapes: 512, 384 or 256 threads, bulk staging
             mcinv.create_from_csr(wl.pedigree(500, 1.2, 1), K=64, threads_per_cta=threads, flags=flags)
         assert e.value.status == mcinv.MCINV_E_ARG
     with pytest.raises(mcinv.McinvError) as e:  # the pair layout of a matrix that is not structurally symmetric
