@@ -741,7 +741,7 @@ def run_lattice2d(args, world, rank, local):
     name = "lattice4d16" if args.workload == "lattice4d16-rate" else "lattice2d128"
     w = wl.WORKLOADS[name]
     csr = w.build()
-    K = w.K
+    K = args.lattice_chains or w.K  # fewer chains: a smaller case of the same kernel (for ncu)
     h = mcinv.create_from_csr(csr, K=K, seed=args.seed, chain_base=rank * K, acc=mcinv.MCINV_ACC_FP32_SIMT,
                               batch_cycles=args.batch, flags=kernel_flags(args)[0] | order_flag(args),
                               **shape_kw(args))
@@ -1083,6 +1083,7 @@ def main():
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--lattice-batches", type=int, default=6)
+    ap.add_argument("--lattice-chains", type=int, default=0, help="chains of the lattice rate runs (0: the workload's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("BENCH_ALLOW_SHORT"), "warmup >= 3"
