@@ -137,6 +137,8 @@ SWEEP_KERNELS = {
         "cc_sweep_grid_bulk_pedigree50k.txt"),
     4: ("cc_sweep_grid_kernel (bulk-staged gathers, pair layout)",
         ("sweep_grid.cu", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), "cc_sweep_grid_pair_pedigree50k.txt"),
+    5: ("cc_sweep_tiled_kernel (tile-staged neighbours, pair layout)",
+        ("sweep_tiled.cu", "sweep_tiled.h", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), None),
 }
 
 
@@ -182,6 +184,8 @@ def kernel_flags(args):
         return mcinv.MCINV_F_GRID, {"threads_per_cta": 512}
     if args.kernel == "bulk":
         return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_NOPAIR, {}
+    if args.kernel == "tile":
+        return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_TILE, {}
     # the pair layout in the shape --threads names (384 by default)
     return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_PAIR, {}
 
@@ -783,7 +787,7 @@ def run_lattice2d(args, world, rank, local):
     t_launch = sw_ms / sw_launches / 1e3 if sw_launches else None
     achieved = alg_bytes / t_launch / 1e9 if t_launch else None
     kname, ksrc, kprof = SWEEP_KERNELS[info0["sweep_kernel"]]
-    kprof = {4: f"cc_sweep_grid_pair_{name}.txt"}.get(info0["sweep_kernel"])
+    kprof = {4: f"cc_sweep_grid_pair_{name}.txt", 5: f"cc_sweep_tiled_{name}.txt"}.get(info0["sweep_kernel"])
     return {
         "metric": METRIC, "value": float(csr.nnz) * K * cycles * world / (ms_max / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -1079,7 +1083,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--order", default="colour", choices=["natural", "colour"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair", "tile"])
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--lattice-batches", type=int, default=6)

@@ -130,6 +130,16 @@ typedef struct {
                               1 KB), 384 (the default) or 256 (8 warps, two blocks a warp, 13 slots
                               of 2 KB).  MCINV_E_UNSUPPORTED when C is not structurally symmetric;
                               MCINV_E_ARG with MCINV_F_GRID_NOPAIR or another thread count. */
+#define MCINV_F_GRID_TILE 256 /* with MCINV_F_GRID_BULK: the tile-staged sweep.  The positions of every
+                              dependency level are cut into tiles of 64, 32, 16 or 8 consecutive
+                              positions (the largest that fits); a CTA copies a tile's distinct
+                              neighbours (at most 104 rows' 32-vector blocks of z and w, pair
+                              layout) into shared memory once and its 16 warps update the tile's
+                              rows from there, the next tile's copies in flight.  For lattices in
+                              the colour order.  MCINV_E_UNSUPPORTED when C is not structurally
+                              symmetric, a row is cut into pieces, or a tile would name more
+                              neighbours; MCINV_E_ARG with MCINV_F_GRID_NOPAIR.  Same values, bit
+                              for bit.  MCINV_F_AUTOTUNE times it where it applies. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.

@@ -18,6 +18,7 @@
 #include "internal.h"
 #include "partition.h"
 #include "prepare.h"
+#include "sweep_tiled.h"
 #include "tc_gemm.h"
 
 using namespace mcinv;
@@ -53,6 +54,11 @@ struct mcinv_ctx {
     uint8_t *d_gpzent[2] = {nullptr, nullptr}, *d_gpwent[2] = {nullptr, nullptr};
     void *d_x = nullptr;
     uint32_t gpnkv = 0;
+    // the tiled form (sweep_tiled.cu): tiles of positions and their staged neighbours
+    bool tile_able = false, gtile = false;
+    int *d_tptr = nullptr, *d_levtile = nullptr, *d_sptr = nullptr, *d_srow = nullptr;
+    uint16_t *d_slot = nullptr;
+    int tile_size = 0;
     int *d_levptr = nullptr;
     unsigned *d_gbar = nullptr;
     int nchunks = 0, blob_max = 0, seg = 1, units = 0;
@@ -270,6 +276,10 @@ static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
         b.w[0] = b.z[0];
         b.w[1] = b.z[1];
         h->canon_ok = false;
+        if (h->gtile) {
+            TileArgs t{h->d_tptr, h->d_levtile, h->d_sptr, h->d_srow, h->d_slot};
+            return launch_sweep_tiled(b, grid_args(h), t, h->cplx, h->gctas, h->stream);
+        }
         return launch_sweep_grid(b, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
     }
     if (h->grid) return launch_sweep_grid(a, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
@@ -287,6 +297,7 @@ struct TunedShape {
     bool grid = false;
     bool gbulk = false;
     bool gpair = false;
+    bool gtile = false;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -298,13 +309,14 @@ static mcinv_status autotune(mcinv_ctx *h)
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         // (a shape on the pair layout is for handles that hold the pair buffers)
-        if (it != g_tune_cache.end() && (!it->second.gpair || h->d_x)) {
+        if (it != g_tune_cache.end() && (!it->second.gpair || h->d_x) && (!it->second.gtile || h->tile_able)) {
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->grid = it->second.grid;
             h->gbulk = it->second.gbulk;
             h->gpair = it->second.gpair;
-            if (h->grid) h->gctas = grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair);
+            h->gtile = it->second.gtile;
+            if (h->grid) h->gctas = h->gtile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -317,7 +329,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk, h->gpair};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk, h->gpair, h->gtile};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -372,23 +384,26 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 9; ++variant) {
+    for (int variant = 0; variant < 10; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
         // lane (12 warps of 32 slots) or 1 (16 warps of 24 slots); bulk-staged on the pair
         // layout (structurally symmetric matrices) with one vector a lane (16 warps) or two
-        // (12 or 8 warps)
-        static const int kT[9] = {384, 512, 384, 192, 96, 512, 512, 384, 256};
+        // (12 or 8 warps); the tile-staged sweep (pair layout, 16 warps) where C has a tiled form
+        static const int kT[10] = {384, 512, 384, 192, 96, 512, 512, 384, 256, 512};
         const int T = kT[variant];
         const bool bulk = variant >= 2;
         const bool pair = variant == 5 || variant >= 7;
+        const bool tile = variant == 9;
         if (pair && !h->d_x) continue;
-        const int ctas = grid_ctas(h->cplx, T, bulk, pair);
+        if (tile && !h->tile_able) continue;
+        const int ctas = tile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, T, bulk, pair);
         if (!grid_supported(h->cplx, vmax, h->K, pair ? 512 : T, bulk) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
-        const bool sG = h->grid, sB = h->gbulk, sP = h->gpair;
+        const bool sG = h->grid, sB = h->gbulk, sP = h->gpair, sI = h->gtile;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
         h->gbulk = bulk;
         h->gpair = pair;
+        h->gtile = tile;
         h->slices = (int)((h->K + h->W - 1) / h->W);
         SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
         float ms = 1e30f;
@@ -401,10 +416,11 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
         if (e != cudaSuccess) cudaGetLastError();
         h->launches += 2;
-        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk, pair}; }
+        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk, pair, tile}; }
         h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS; h->gctas = sC; h->grid = sG;
         h->gbulk = sB;
         h->gpair = sP;
+        h->gtile = sI;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -412,7 +428,8 @@ static mcinv_status autotune(mcinv_ctx *h)
     h->grid = best.grid;
     h->gbulk = best.gbulk;
     h->gpair = best.gpair;
-    h->gctas = h->grid ? grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair) : 0;
+    h->gtile = best.gtile;
+    h->gctas = h->grid ? (h->gtile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair)) : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -687,6 +704,23 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
             for (int64_t p = 0; p < n; ++p) growp[p].row = (int)((uint32_t)P.grow[p].row * 2u * kvp);
             SETUP(upload(h, &h->d_grow_p, growp));
             h->pair_able = true;
+            // the tiled form: the largest tiles whose staged neighbours fit the stage
+            // buffers (lattices in the colour order; a random pattern has none)
+            {
+                std::vector<int> tptr, levtile, sptr, srow;
+                std::vector<uint16_t> slot;
+                for (int ts : {64, 32, 16, 8}) {
+                    if (!build_tiles(P.grow, P.gzent, esz_ent, P.lev_ptr, ts, tptr, levtile, sptr, srow, slot)) continue;
+                    SETUP(upload(h, &h->d_tptr, tptr));
+                    SETUP(upload(h, &h->d_levtile, levtile));
+                    SETUP(upload(h, &h->d_sptr, sptr));
+                    SETUP(upload(h, &h->d_srow, srow.empty() ? std::vector<int>(1, 0) : srow));
+                    SETUP(upload(h, &h->d_slot, slot.empty() ? std::vector<uint16_t>(1, 0) : slot));
+                    h->tile_able = true;
+                    h->tile_size = ts;
+                    break;
+                }
+            }
         }
         SETUP(upload(h, &h->d_levptr, P.lev_ptr));
         SETUP(dalloc(h, &h->d_gbar, 1));
@@ -738,6 +772,23 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
             fail(h, MCINV_E_UNSUPPORTED, "the pair-layout sweep with %d threads per CTA has no resident CTA", pt);
             return bail(MCINV_E_UNSUPPORTED);
         }
+    }
+    if (h->flags & MCINV_F_GRID_TILE) {
+        if (!(h->flags & MCINV_F_GRID) || !(h->flags & MCINV_F_GRID_BULK) || (h->flags & MCINV_F_GRID_NOPAIR)) {
+            fail(h, MCINV_E_ARG, "MCINV_F_GRID_TILE needs MCINV_F_GRID and MCINV_F_GRID_BULK, not MCINV_F_GRID_NOPAIR");
+            return bail(MCINV_E_ARG);
+        }
+        const int tc = tiled_ctas(cplx);
+        if (!h->tile_able || !h->d_x || tc < 1) {
+            fail(h, MCINV_E_UNSUPPORTED, "C has no tiled form (it needs a structurally symmetric C, no row cut into "
+                                         "pieces, and tiles of consecutive positions naming at most %d neighbours)",
+                 TILE_CAP);
+            return bail(MCINV_E_UNSUPPORTED);
+        }
+        h->gpair = true;
+        h->gtile = true;
+        h->threads = 512;
+        h->gctas = tc;
     }
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
@@ -1422,7 +1473,7 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
     info->kernel_launches = h->launches; info->device_bytes = h->bytes;
-    info->sweep_kernel = h->grid ? (h->gbulk ? (h->gpair ? 4 : 3) : 2) : h->staged ? 1 : 0;
+    info->sweep_kernel = h->grid ? (h->gtile ? 5 : h->gbulk ? (h->gpair ? 4 : 3) : 2) : h->staged ? 1 : 0;
     info->grid_ctas = h->grid ? h->gctas : 0;
     return MCINV_OK;
 }

@@ -1,0 +1,292 @@
+// sweep_tiled.cu -- the coupled sweep (Eqs. 4 and 5) of a structurally symmetric
+// matrix whose dependency levels cut into short tiles of positions that name few
+// distinct neighbours: the lattice operators in the colour order.
+//
+// The row pipeline of sweep_ring.cuh copies every row's neighbours for itself
+// (one bulk copy a neighbour, a ring slot, a queue of rows in flight): on a
+// stencil each site is copied again for each of its 4 or 8 neighbours, and the
+// per-row bookkeeping makes the sweep issue-bound.  Here a CTA takes a tile of
+// consecutive positions of one level and one 32-vector chain block, copies the
+// tile's distinct neighbours (the staged list, at most TILE_CAP slabs of 1 KB:
+// the block's z and w vectors of one row, pair layout) into shared memory once,
+// and its 16 warps update the tile's rows from there: an entry is a slot index,
+// a coefficient and two shared-memory loads.  Two stage buffers alternate, so
+// the next tile's copies run while this one is computed.  The rows' sums take
+// the entries in their order and the epilogue is the ring path's `finish`, so
+// the values are the same bits as every other sweep kernel's.  A grid barrier
+// ends each level; every wait is bounded (2 s of globaltimer).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "sweep_core.cuh"
+#include "sweep_ring.cuh"
+#include "sweep_tiled.h"
+
+namespace mcinv {
+
+bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &zent, size_t ent_bytes,
+                 const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr, std::vector<int> &lev_tile,
+                 std::vector<int> &stage_ptr, std::vector<int> &stage_row, std::vector<uint16_t> &slot)
+{
+    const int nlev = (int)lev_ptr.size() - 1;
+    tile_ptr.assign(1, 0);
+    lev_tile.assign(1, 0);
+    stage_ptr.assign(1, 0);
+    stage_row.clear();
+    slot.assign(zent.size() / ent_bytes, 0);
+    std::vector<long long> keys;
+    for (int l = 0; l < nlev; ++l) {
+        for (int p0 = lev_ptr[l]; p0 < lev_ptr[l + 1]; p0 += tile) {
+            const int p1 = std::min(p0 + tile, (int)lev_ptr[l + 1]);
+            // the tile's neighbours: (row j, read from this cycle's buffer), sorted
+            keys.clear();
+            for (int p = p0; p < p1; ++p) {
+                if (rows[p].info & 3) return false;  // a row cut into pieces
+                const int i = rows[p].row;
+                for (int e = rows[p].zb; e < rows[p + 1].zb; ++e) {
+                    const int j = *(const int *)(zent.data() + (size_t)e * ent_bytes);
+                    keys.push_back(((long long)j << 1) | (j < i ? 1 : 0));
+                }
+            }
+            std::sort(keys.begin(), keys.end());
+            keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+            if ((int)keys.size() > TILE_CAP) return false;
+            for (long long k : keys) stage_row.push_back((int)(k >> 1) | ((k & 1) ? (int)0x80000000u : 0));
+            for (int p = p0; p < p1; ++p) {
+                const int i = rows[p].row;
+                for (int e = rows[p].zb; e < rows[p + 1].zb; ++e) {
+                    const int j = *(const int *)(zent.data() + (size_t)e * ent_bytes);
+                    const long long k = ((long long)j << 1) | (j < i ? 1 : 0);
+                    slot[e] = (uint16_t)(std::lower_bound(keys.begin(), keys.end(), k) - keys.begin());
+                }
+            }
+            tile_ptr.push_back(p1);
+            stage_ptr.push_back((int)stage_row.size());
+        }
+        lev_tile.push_back((int)tile_ptr.size() - 1);
+    }
+    return true;
+}
+
+namespace {
+
+using namespace ring;
+
+constexpr int TILE_THREADS = 512;         // 16 warps, one CTA an SM
+constexpr int TNW = TILE_THREADS / 32;
+constexpr int SLAB = 2 * SEGB;            // a row's z and w vectors of one 32-vector block: 1 KB
+constexpr size_t TILE_SMEM = 2 * (size_t)TILE_CAP * SLAB + 2 * sizeof(uint64_t);
+
+// Arrive at the next grid barrier and wait until every CTA of the grid has (the
+// counter was zeroed before the launch; target = barriers so far x CTAs).
+// Thread 0 releases the CTA's writes and acquires everyone else's; the closing
+// CTA barrier passes that on to the whole CTA.  Bounded: 2 s.
+__device__ __forceinline__ void tile_grid_barrier(unsigned *bar, unsigned target, volatile int *abort_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*abort_flag) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        const uint64_t t0 = gtimer();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (gtimer() - t0 > 2000000000ull) {
+                *abort_flag = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    __syncthreads();
+}
+
+template <bool CPLX, int V>
+__global__ void __launch_bounds__(TILE_THREADS, 1)
+    cc_sweep_tiled_kernel(const SweepArgs a, const GridArgs g, const TileArgs t)
+{
+    using P = Prec<CPLX>;
+    using L = Lane<CPLX, V>;
+    using T = typename L::T;
+    using S = typename L::S;
+    using Ent = typename P::Ent;
+    using Cst = typename P::Cst;
+    extern __shared__ __align__(128) uint8_t tsm[];
+    __shared__ int abort_s;
+    volatile int *abort_flag = &abort_s;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t stage0 = smem_addr(tsm);
+    const uint32_t bar0 = stage0 + 2u * TILE_CAP * SLAB;  // one mbarrier per stage buffer
+    const uint32_t row_vecs = 64u * (uint32_t)g.nblk;    // vectors of one row in the pair layout
+    Lanes<CPLX, V, 1> w;
+    w.init(lane, 0, g.kv, a.K, a.n, a.seg, a.diag_part, a.noise, 0u, 0u, true);
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        mbar_init1(bar0);
+        mbar_init1(bar0 + 8u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    Mat<CPLX> m;
+    m.rows = g.rows;
+    m.cst = (const Cst *)g.cst;
+    m.z0 = a.z[0];
+    m.w0 = a.z[0];  // the pair layout holds w beside z
+    m.has_noise = a.noise != nullptr;
+    m.rpos = a.rpos;
+    m.spos = a.spos;
+    m.zsh = a.zsh;
+    m.wsh = a.wsh;
+    m.ldsh = a.ldsh;
+    m.kp = a.kp;
+    m.tq = a.tq;
+    // the coefficients (the same in both parities' entries; .col is not used here)
+    const Ent *zent = (const Ent *)g.zent[0];
+    const Ent *went = (const Ent *)g.went[0];
+    const float4 *x0 = (const float4 *)a.z[0];
+    bool diverged = false;
+    unsigned target = 0;
+    uint32_t uses = 0;  // tiles this CTA has staged: buffer uses & 1, its phase (uses >> 1) & 1
+    for (int cyc = 0; cyc < a.ncyc; ++cyc) {
+        const int cur = a.cur ^ (cyc & 1);
+        m.zn_off = cur ? 0u : g.nkv;                  // this cycle's buffer: the other one
+        const uint32_t old_off = cur ? g.nkv : 0u;    // last cycle's
+        m.noise_cyc = (size_t)cyc * a.nw * (size_t)a.n;
+        m.shcol = a.cyc0_in_batch + cyc;
+        m.check_div = cyc == a.ncyc - 1;
+        float tsum = 0.f;
+        for (int l = 0; l < g.nlev; ++l) {
+            const int t0 = __ldg(&t.lev_tile[l]);
+            const int nitems = (__ldg(&t.lev_tile[l + 1]) - t0) * g.nblk;
+            // stage item it (tile, chain block) into buffer b: warp 0 issues one bulk copy a
+            // staged neighbour, all completing on the buffer's mbarrier
+            auto issue = [&](int it, uint32_t b) {
+                if (warp != 0) return;
+                const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
+                const int s0 = __ldg(&t.stage_ptr[tile]);
+                const int ns = min(__ldg(&t.stage_ptr[tile + 1]) - s0, TILE_CAP);  // (the host keeps it <= TILE_CAP)
+                const uint32_t bar = bar0 + 8u * b;
+                // the slots' earlier generic-proxy reads before these async-proxy writes
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (lane == 0) mbar_expect(bar, (uint32_t)ns * SLAB);
+                __syncwarp();
+                for (int s = lane; s < ns; s += 32) {
+                    const int code = __ldg(&t.stage_row[s0 + s]);
+                    const uint32_t j = (uint32_t)code & 0x7fffffffu;
+                    const uint32_t off = (code < 0 ? m.zn_off : old_off) + j * row_vecs + (uint32_t)blk * 64u;
+                    bulk_g2s(stage0 + (b * TILE_CAP + (uint32_t)s) * SLAB, x0 + off, SLAB, bar);
+                }
+            };
+            if (!*abort_flag && nitems > 0) {
+                // the copies read rows that other CTAs wrote before the grid barrier
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                int it = blockIdx.x;
+                if (it < nitems) issue(it, uses & 1u);
+                for (; it < nitems; it += gridDim.x) {
+                    const uint32_t b = uses & 1u;
+                    const int nxt = it + gridDim.x;
+                    if (nxt < nitems) issue(nxt, b ^ 1u);  // that buffer was released at the last CTA barrier
+                    if (!ring_wait(bar0 + 8u * b, (uses >> 1) & 1u)) *abort_flag = 1;
+                    ++uses;
+                    const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
+                    w.set_block(blk, g.kv, a.K, a.n, a.diag_part, a.noise, true);
+                    const uint32_t base = stage0 + b * TILE_CAP * SLAB + (uint32_t)lane * 16u;
+                    const int p1 = __ldg(&t.tile_ptr[tile + 1]);
+                    for (int p = __ldg(&t.tile_ptr[tile]) + warp; p < p1; p += TNW) {
+                        const int4 rec = ldnc4(&m.rows[p]);
+                        const int d = (rec.w >> 2) & 0x7fff;  // entries a side (the same columns)
+                        const Cst k = ldg_cst(&m.cst[p]);
+                        const uint32_t bits = w.bits(0, p, m.noise_cyc);
+                        S dold = P::zero();
+                        if (w.dlead[0]) dold = w.dpart[0][p];
+                        int rp = -1, sp = -1;
+                        if (m.rpos) { rp = __ldg(&m.rpos[p]); sp = __ldg(&m.spos[p]); }
+                        T sz = L::zero(), sw = L::zero();
+                        for (int u = 0; u < d; ++u) {
+                            const uint32_t sl = __ldg(&t.slot[rec.y + u]);
+                            const Ent ez = ldg_ent(&zent[rec.y + u]);
+                            const Ent ew = ldg_ent(&went[rec.z + u]);
+                            L::fma(sz, ez, lds_vec<T>(base + sl * SLAB));
+                            L::fma(sw, ew, lds_vec<T>(base + sl * SLAB + SEGB));
+                        }
+                        const S pr = finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp, tsum,
+                                                         diverged);
+                        diag_one(w, 0, p, pr, dold);
+                    }
+                    // every warp is done with buffer b before it is staged again; an expired wait
+                    // ends the level's items for the whole CTA at once (the same answer in every thread)
+                    if (__syncthreads_or(*abort_flag)) break;
+                }
+            }
+            // the level's rows are written before any CTA reads them (none after the last)
+            if (!(cyc == a.ncyc - 1 && l == g.nlev - 1)) {
+                target += gridDim.x;
+                tile_grid_barrier(g.bar, target, abort_flag);
+            }
+        }
+        if (a.tpart && !*abort_flag) {
+            // this warp's partial of the cycle's trace series, reduced in a fixed order
+            float v = tsum;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) a.tpart[((size_t)cyc * gridDim.x + blockIdx.x) * TNW + warp] = v;
+        }
+    }
+    if (diverged) atomicOr(a.status, 1);
+    if (threadIdx.x == 0 && *abort_flag) {
+        atomicOr(a.status, 4);
+        const uint64_t t0 = gtimer();  // let copies still in flight land before exit
+        while (gtimer() - t0 < 10000000ull) {
+        }
+    }
+}
+
+}  // namespace
+
+int tiled_ctas(int cplx)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    auto kern = cplx ? cc_sweep_tiled_kernel<true, 2> : cc_sweep_tiled_kernel<false, 4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_THREADS, TILE_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+cudaError_t launch_sweep_tiled(const SweepArgs &a, const GridArgs &g, const TileArgs &t, int cplx, int ctas,
+                               cudaStream_t s)
+{
+    if (ctas < 1 || !g.pair) return cudaErrorInvalidConfiguration;
+    if ((long long)a.n + (long long)ctas >= (1LL << 31) || 2ull * g.nkv >= (1ull << 32)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(g.bar, 0, sizeof(unsigned), s);  // the barrier counter starts at zero
+    if (e != cudaSuccess) return e;
+    auto kern = cplx ? cc_sweep_tiled_kernel<true, 2> : cc_sweep_tiled_kernel<false, 4>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3((unsigned)TILE_THREADS);
+    cfg.dynamicSmemBytes = TILE_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a, g, t);
+}
+
+}  // namespace mcinv

@@ -33,6 +33,7 @@ MCINV_F_GRID = 16
 MCINV_F_GRID_BULK = 32
 MCINV_F_GRID_NOPAIR = 64
 MCINV_F_GRID_PAIR = 128
+MCINV_F_GRID_TILE = 256
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",
