@@ -44,7 +44,8 @@ bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &z
             // the tile's neighbours: (row j, read from this cycle's buffer), sorted
             keys.clear();
             for (int p = p0; p < p1; ++p) {
-                if (rows[p].info & 3) return false;  // a row cut into pieces
+                if (rows[p].info & 3) return false;                              // a row cut into pieces
+                if (rows[p + 1].zb - rows[p].zb > SPLIT_ENTRIES) return false;  // (implied by the above)
                 const int i = rows[p].row;
                 for (int e = rows[p].zb; e < rows[p + 1].zb; ++e) {
                     const int j = *(const int *)(zent.data() + (size_t)e * ent_bytes);
@@ -199,8 +200,11 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     w.set_block(blk, g.kv, a.K, a.n, a.diag_part, a.noise, true);
                     const uint32_t base = stage0 + b * TILE_CAP * SLAB + (uint32_t)lane * 16u;
                     const int p1 = __ldg(&t.tile_ptr[tile + 1]);
-                    for (int p = __ldg(&t.tile_ptr[tile]) + warp; p < p1; p += TNW) {
-                        const int4 rec = ldnc4(&m.rows[p]);
+                    int p = __ldg(&t.tile_ptr[tile]) + warp;
+                    int4 rec = p < p1 ? ldnc4(&m.rows[p]) : make_int4(0, 0, 0, 0);
+                    for (; p < p1; p += TNW) {
+                        // the warp's next row's record, loaded while this row is computed
+                        const int4 nrec = p + TNW < p1 ? ldnc4(&m.rows[p + TNW]) : make_int4(0, 0, 0, 0);
                         const int d = (rec.w >> 2) & 0x7fff;  // entries a side (the same columns)
                         const Cst k = ldg_cst(&m.cst[p]);
                         const uint32_t bits = w.bits(0, p, m.noise_cyc);
@@ -208,17 +212,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                         if (w.dlead[0]) dold = w.dpart[0][p];
                         int rp = -1, sp = -1;
                         if (m.rpos) { rp = __ldg(&m.rpos[p]); sp = __ldg(&m.spos[p]); }
+                        // the row's slots and coefficients all loaded at once (rows of the tiled
+                        // form have at most SPLIT_ENTRIES entries), then the sums in entry order
+                        uint32_t sl[SPLIT_ENTRIES];
+                        Ent ez[SPLIT_ENTRIES], ew[SPLIT_ENTRIES];
+#pragma unroll
+                        for (int u = 0; u < SPLIT_ENTRIES; ++u) {
+                            if (u < d) {
+                                sl[u] = __ldg(&t.slot[rec.y + u]);
+                                ez[u] = ldg_ent(&zent[rec.y + u]);
+                                ew[u] = ldg_ent(&went[rec.z + u]);
+                            }
+                        }
                         T sz = L::zero(), sw = L::zero();
-                        for (int u = 0; u < d; ++u) {
-                            const uint32_t sl = __ldg(&t.slot[rec.y + u]);
-                            const Ent ez = ldg_ent(&zent[rec.y + u]);
-                            const Ent ew = ldg_ent(&went[rec.z + u]);
-                            L::fma(sz, ez, lds_vec<T>(base + sl * SLAB));
-                            L::fma(sw, ew, lds_vec<T>(base + sl * SLAB + SEGB));
+#pragma unroll
+                        for (int u = 0; u < SPLIT_ENTRIES; ++u) {
+                            if (u < d) {
+                                L::fma(sz, ez[u], lds_vec<T>(base + sl[u] * SLAB));
+                                L::fma(sw, ew[u], lds_vec<T>(base + sl[u] * SLAB + SEGB));
+                            }
                         }
                         const S pr = finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp, tsum,
                                                          diverged);
                         diag_one(w, 0, p, pr, dold);
+                        rec = nrec;
                     }
                     // every warp is done with buffer b before it is staged again; an expired wait
                     // ends the level's items for the whole CTA at once (the same answer in every thread)
