@@ -56,9 +56,12 @@ struct mcinv_ctx {
     uint32_t gpnkv = 0;
     // the tiled form (sweep_tiled.cu): tiles of positions and their staged neighbours
     bool tile_able = false, gtile = false;
-    int *d_tptr = nullptr, *d_levtile = nullptr, *d_sptr = nullptr, *d_srow = nullptr;
+    GridRow *d_grow_t = nullptr;  // records with .row = i x 64 (block-major pair layout)
+    int *d_tptr = nullptr, *d_tslots = nullptr, *d_levtile = nullptr, *d_rptr = nullptr, *d_rrow = nullptr,
+        *d_rlen = nullptr;
     uint16_t *d_slot = nullptr;
     int tile_size = 0;
+    int x_layout = 0;  // the layout of d_x when pair_ok: 0 the pair layout, 1 block-major (tiled sweep)
     int *d_levptr = nullptr;
     unsigned *d_gbar = nullptr;
     int nchunks = 0, blob_max = 0, seg = 1, units = 0;
@@ -253,8 +256,11 @@ static cudaError_t ensure_canonical(mcinv_ctx *h)
 {
     if (h->canon_ok) return cudaSuccess;
     const size_t nx = (size_t)h->gpnkv * 16;  // bytes of one pair-layout buffer
-    cudaError_t e = launch_pair_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
-                                     (int)(h->K * (h->cplx ? 8 : 4) / 16), 1, h->stream);
+    const int kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
+    cudaError_t e = h->x_layout ? launch_tile_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
+                                                   kv, 1, h->stream)
+                                : launch_pair_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
+                                                   kv, 1, h->stream);
     if (e == cudaSuccess) h->canon_ok = true;
     return e;
 }
@@ -262,13 +268,24 @@ static cudaError_t ensure_canonical(mcinv_ctx *h)
 static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 {
     if (h->grid && h->gbulk && h->gpair) {
-        // the pair layout: packed from the canonical state when that is the newer
+        // the pair layout (block-major for the tiled sweep): packed from the canonical
+        // state when that is the newer, after unpacking the other pair layout if it held it
         const size_t nx = (size_t)h->gpnkv * 16;
+        const int layout = h->gtile ? 1 : 0;
+        if (h->pair_ok && h->x_layout != layout) {
+            cudaError_t e = ensure_canonical(h);
+            if (e != cudaSuccess) return e;
+            h->pair_ok = false;
+        }
         if (!h->pair_ok) {
-            cudaError_t e = launch_pair_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n,
-                                             (int)(h->K * (h->cplx ? 8 : 4) / 16), 0, h->stream);
+            const int kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
+            cudaError_t e = layout ? launch_tile_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n, kv, 0,
+                                                      h->stream)
+                                   : launch_pair_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n, kv, 0,
+                                                      h->stream);
             if (e != cudaSuccess) return e;
             h->pair_ok = true;
+            h->x_layout = layout;
         }
         SweepArgs b = a;
         b.z[0] = h->d_x;
@@ -277,7 +294,7 @@ static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
         b.w[1] = b.z[1];
         h->canon_ok = false;
         if (h->gtile) {
-            TileArgs t{h->d_tptr, h->d_levtile, h->d_sptr, h->d_srow, h->d_slot};
+            TileArgs t{h->d_grow_t, h->d_tptr, h->d_tslots, h->d_levtile, h->d_rptr, h->d_rrow, h->d_rlen, h->d_slot};
             return launch_sweep_tiled(b, grid_args(h), t, h->cplx, h->gctas, h->stream);
         }
         return launch_sweep_grid(b, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
@@ -707,14 +724,21 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
             // the tiled form: the largest tiles whose staged neighbours fit the stage
             // buffers (lattices in the colour order; a random pattern has none)
             {
-                std::vector<int> tptr, levtile, sptr, srow;
+                std::vector<int> tptr, tslots, levtile, rptr, rrow, rlen;
                 std::vector<uint16_t> slot;
                 for (int ts : {64, 32, 16, 8}) {
-                    if (!build_tiles(P.grow, P.gzent, esz_ent, P.lev_ptr, ts, tptr, levtile, sptr, srow, slot)) continue;
+                    if (!build_tiles(P.grow, P.gzent, esz_ent, P.lev_ptr, ts, tptr, tslots, levtile, rptr, rrow, rlen,
+                                     slot))
+                        continue;
+                    std::vector<GridRow> growt = P.grow;
+                    for (int64_t p = 0; p < n; ++p) growt[p].row = P.grow[p].row * 64;
+                    SETUP(upload(h, &h->d_grow_t, growt));
                     SETUP(upload(h, &h->d_tptr, tptr));
+                    SETUP(upload(h, &h->d_tslots, tslots.empty() ? std::vector<int>(1, 0) : tslots));
                     SETUP(upload(h, &h->d_levtile, levtile));
-                    SETUP(upload(h, &h->d_sptr, sptr));
-                    SETUP(upload(h, &h->d_srow, srow.empty() ? std::vector<int>(1, 0) : srow));
+                    SETUP(upload(h, &h->d_rptr, rptr));
+                    SETUP(upload(h, &h->d_rrow, rrow.empty() ? std::vector<int>(1, 0) : rrow));
+                    SETUP(upload(h, &h->d_rlen, rlen.empty() ? std::vector<int>(1, 0) : rlen));
                     SETUP(upload(h, &h->d_slot, slot.empty() ? std::vector<uint16_t>(1, 0) : slot));
                     h->tile_able = true;
                     h->tile_size = ts;

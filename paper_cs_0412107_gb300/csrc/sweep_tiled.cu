@@ -7,14 +7,17 @@
 // stencil each site is copied again for each of its 4 or 8 neighbours, and the
 // per-row bookkeeping makes the sweep issue-bound.  Here a CTA takes a tile of
 // consecutive positions of one level and one 32-vector chain block, copies the
-// tile's distinct neighbours (the staged list, at most TILE_CAP slabs of 1 KB:
-// the block's z and w vectors of one row, pair layout) into shared memory once,
-// and its 16 warps update the tile's rows from there: an entry is a slot index,
-// a coefficient and two shared-memory loads.  Two stage buffers alternate, so
-// the next tile's copies run while this one is computed.  The rows' sums take
-// the entries in their order and the epilogue is the ring path's `finish`, so
-// the values are the same bits as every other sweep kernel's.  A grid barrier
-// ends each level; every wait is bounded (2 s of globaltimer).
+// tile's distinct neighbours (its staged list, at most TILE_CAP slabs of 1 KB:
+// the block's z and w vectors of one row) into shared memory once, and its 16
+// warps update the tile's rows from there: an entry is a slot index, a
+// coefficient and two shared-memory loads.  The state is kept block-major
+// (block, row, z and w), so each run of consecutive staged rows is one bulk
+// copy: a tile of a 2D lattice stages about 97 rows in 3 or 4 copies.  Two
+// stage buffers alternate, so the next tile's copies run while this one is
+// computed.  The rows' sums take the entries in their order and the epilogue
+// is the ring path's `finish`, so the values are the same bits as every other
+// sweep kernel's.  A grid barrier ends each level; every wait is bounded (2 s
+// of globaltimer).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,44 +31,54 @@
 namespace mcinv {
 
 bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &zent, size_t ent_bytes,
-                 const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr, std::vector<int> &lev_tile,
-                 std::vector<int> &stage_ptr, std::vector<int> &stage_row, std::vector<uint16_t> &slot)
+                 const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr,
+                 std::vector<int> &tile_slots, std::vector<int> &lev_tile, std::vector<int> &run_ptr,
+                 std::vector<int> &run_row, std::vector<int> &run_len, std::vector<uint16_t> &slot)
 {
     const int nlev = (int)lev_ptr.size() - 1;
     tile_ptr.assign(1, 0);
+    tile_slots.clear();
     lev_tile.assign(1, 0);
-    stage_ptr.assign(1, 0);
-    stage_row.clear();
+    run_ptr.assign(1, 0);
+    run_row.clear();
+    run_len.clear();
     slot.assign(zent.size() / ent_bytes, 0);
     std::vector<long long> keys;
+    // key: (read from this cycle's buffer, row j): the rows of one buffer ascending
+    auto key_of = [](int i, int j) { return ((long long)(j < i ? 1 : 0) << 32) | (long long)(uint32_t)j; };
     for (int l = 0; l < nlev; ++l) {
         for (int p0 = lev_ptr[l]; p0 < lev_ptr[l + 1]; p0 += tile) {
             const int p1 = std::min(p0 + tile, (int)lev_ptr[l + 1]);
-            // the tile's neighbours: (row j, read from this cycle's buffer), sorted
             keys.clear();
             for (int p = p0; p < p1; ++p) {
                 if (rows[p].info & 3) return false;                              // a row cut into pieces
                 if (rows[p + 1].zb - rows[p].zb > SPLIT_ENTRIES) return false;  // (implied by the above)
                 const int i = rows[p].row;
-                for (int e = rows[p].zb; e < rows[p + 1].zb; ++e) {
-                    const int j = *(const int *)(zent.data() + (size_t)e * ent_bytes);
-                    keys.push_back(((long long)j << 1) | (j < i ? 1 : 0));
-                }
+                for (int e = rows[p].zb; e < rows[p + 1].zb; ++e)
+                    keys.push_back(key_of(i, *(const int *)(zent.data() + (size_t)e * ent_bytes)));
             }
             std::sort(keys.begin(), keys.end());
             keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
             if ((int)keys.size() > TILE_CAP) return false;
-            for (long long k : keys) stage_row.push_back((int)(k >> 1) | ((k & 1) ? (int)0x80000000u : 0));
+            // runs of consecutive rows of one buffer; a key's slot is its rank in `keys`
+            for (size_t k = 0; k < keys.size();) {
+                size_t e = k + 1;
+                while (e < keys.size() && keys[e] == keys[e - 1] + 1) ++e;  // same buffer, next row
+                const int j0 = (int)(uint32_t)keys[k];
+                run_row.push_back(j0 | ((keys[k] >> 32) ? (int)0x80000000u : 0));
+                run_len.push_back((int)(e - k) | ((int)k << 16));
+                k = e;
+            }
             for (int p = p0; p < p1; ++p) {
                 const int i = rows[p].row;
                 for (int e = rows[p].zb; e < rows[p + 1].zb; ++e) {
-                    const int j = *(const int *)(zent.data() + (size_t)e * ent_bytes);
-                    const long long k = ((long long)j << 1) | (j < i ? 1 : 0);
+                    const long long k = key_of(i, *(const int *)(zent.data() + (size_t)e * ent_bytes));
                     slot[e] = (uint16_t)(std::lower_bound(keys.begin(), keys.end(), k) - keys.begin());
                 }
             }
             tile_ptr.push_back(p1);
-            stage_ptr.push_back((int)stage_row.size());
+            tile_slots.push_back((int)keys.size());
+            run_ptr.push_back((int)run_row.size());
         }
         lev_tile.push_back((int)tile_ptr.size() - 1);
     }
@@ -124,7 +137,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     const int warp = threadIdx.x >> 5;
     const uint32_t stage0 = smem_addr(tsm);
     const uint32_t bar0 = stage0 + 2u * TILE_CAP * SLAB;  // one mbarrier per stage buffer
-    const uint32_t row_vecs = 64u * (uint32_t)g.nblk;    // vectors of one row in the pair layout
+    const uint32_t bstride = 64u * (uint32_t)a.n;        // vectors of one chain block, block-major
     Lanes<CPLX, V, 1> w;
     w.init(lane, 0, g.kv, a.K, a.n, a.seg, a.diag_part, a.noise, 0u, 0u, true);
     if (threadIdx.x == 0) {
@@ -136,7 +149,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     __syncthreads();
 
     Mat<CPLX> m;
-    m.rows = g.rows;
+    m.rows = t.rows;
     m.cst = (const Cst *)g.cst;
     m.z0 = a.z[0];
     m.w0 = a.z[0];  // the pair layout holds w beside z
@@ -167,22 +180,26 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
             const int t0 = __ldg(&t.lev_tile[l]);
             const int nitems = (__ldg(&t.lev_tile[l + 1]) - t0) * g.nblk;
             // stage item it (tile, chain block) into buffer b: warp 0 issues one bulk copy a
-            // staged neighbour, all completing on the buffer's mbarrier
+            // run of the tile's staged rows (contiguous in the block-major layout), all
+            // completing on the buffer's mbarrier
             auto issue = [&](int it, uint32_t b) {
                 if (warp != 0) return;
                 const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
-                const int s0 = __ldg(&t.stage_ptr[tile]);
-                const int ns = min(__ldg(&t.stage_ptr[tile + 1]) - s0, TILE_CAP);  // (the host keeps it <= TILE_CAP)
+                const int r0 = __ldg(&t.run_ptr[tile]), nr = __ldg(&t.run_ptr[tile + 1]) - r0;
+                const int ns = min(__ldg(&t.tile_slots[tile]), TILE_CAP);  // (the host keeps it <= TILE_CAP)
                 const uint32_t bar = bar0 + 8u * b;
                 // the slots' earlier generic-proxy reads before these async-proxy writes
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 if (lane == 0) mbar_expect(bar, (uint32_t)ns * SLAB);
                 __syncwarp();
-                for (int s = lane; s < ns; s += 32) {
-                    const int code = __ldg(&t.stage_row[s0 + s]);
-                    const uint32_t j = (uint32_t)code & 0x7fffffffu;
-                    const uint32_t off = (code < 0 ? m.zn_off : old_off) + j * row_vecs + (uint32_t)blk * 64u;
-                    bulk_g2s(stage0 + (b * TILE_CAP + (uint32_t)s) * SLAB, x0 + off, SLAB, bar);
+                for (int r = lane; r < nr; r += 32) {
+                    const int code = __ldg(&t.run_row[r0 + r]);
+                    const int ls = __ldg(&t.run_len[r0 + r]);
+                    const uint32_t len = (uint32_t)ls & 0xffffu, s0 = (uint32_t)ls >> 16;
+                    const uint32_t j0 = (uint32_t)code & 0x7fffffffu;
+                    const uint32_t off = (code < 0 ? m.zn_off : old_off) + (uint32_t)blk * bstride + j0 * 64u;
+                    if (s0 + len <= (uint32_t)TILE_CAP)
+                        bulk_g2s(stage0 + (b * TILE_CAP + s0) * SLAB, x0 + off, len * SLAB, bar);
                 }
             };
             if (!*abort_flag && nitems > 0) {
@@ -198,6 +215,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     ++uses;
                     const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
                     w.set_block(blk, g.kv, a.K, a.n, a.diag_part, a.noise, true);
+                    w.zo[0] = (uint32_t)blk * bstride + (uint32_t)lane;  // the block-major layout
+                    w.wo[0] = w.zo[0] + 32u;
                     const uint32_t base = stage0 + b * TILE_CAP * SLAB + (uint32_t)lane * 16u;
                     const int p1 = __ldg(&t.tile_ptr[tile + 1]);
                     int p = __ldg(&t.tile_ptr[tile]) + warp;
@@ -265,7 +284,37 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     }
 }
 
+// canonical z, w ([n][kv] vectors each) <-> the block-major pair layout x: block b,
+// row j at vector b n 64 + j 64 (z), + 32 (w); vectors past kv are zero
+__global__ void tile_pack_kernel(const float4 *__restrict__ z, const float4 *__restrict__ w, float4 *__restrict__ x,
+                                 long long n, int kv, int kvp, int unpack)
+{
+    const long long total = n * (long long)kvp;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const long long j = t / kvp;
+        const int v = (int)(t - j * kvp);
+        const long long xo = (long long)(v >> 5) * n * 64 + j * 64 + (v & 31);
+        if (!unpack) {
+            x[xo] = v < kv ? z[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[xo + 32] = v < kv ? w[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (v < kv) {
+            ((float4 *)z)[j * kv + v] = x[xo];
+            ((float4 *)w)[j * kv + v] = x[xo + 32];
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s)
+{
+    const int kvp = (kv + 31) / 32 * 32;
+    long long blocks = (n * kvp + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (blocks < 1) blocks = 1;
+    tile_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)z, (const float4 *)w, (float4 *)x, n, kv, kvp, unpack);
+    return cudaGetLastError();
+}
 
 int tiled_ctas(int cplx)
 {

@@ -17,13 +17,22 @@ constexpr int TILE_CAP = 104;
 // name the same columns in the same order).  The positions of every dependency
 // level are cut into tiles of at most `tile` consecutive positions; a tile's rows
 // name at most TILE_CAP distinct neighbours (row j, and whether the row reads
-// this cycle's buffer, j < i, or last cycle's, j > i), its staged list.
+// this cycle's buffer, j < i, or last cycle's, j > i), its staged list, kept as
+// runs of consecutive rows read from one buffer.
+//
+// The tiled sweep keeps the state in the block-major pair layout: chain block b
+// (32 vectors of 16 bytes), row j holds the block's z vectors then its w vectors
+// at vector b n 64 + j 64, so a run of consecutive rows of one block is one
+// contiguous copy.
 struct TileArgs {
+    const GridRow *rows;      // by position; .row holds i * 64 (the row's first vector in a block)
     const int *tile_ptr;      // [ntiles + 1]: first position of each tile
+    const int *tile_slots;    // [ntiles]: rows the tile stages
     const int *lev_tile;      // [nlev + 1]: first tile of each level
-    const int *stage_ptr;     // [ntiles + 1]: first staged entry of each tile
-    const int *stage_row;     // staged neighbours: row j, bit 31 set when read from this cycle's buffer
-    const uint16_t *slot;     // by C entry index (flat form): the entry's neighbour in its tile's staged list
+    const int *run_ptr;       // [ntiles + 1]: first run of each tile
+    const int *run_row;       // per run: its first row j, bit 31 set when read from this cycle's buffer
+    const int *run_len;       // per run: rows (bits 0-15) and first slot in the tile's stage (bits 16-31)
+    const uint16_t *slot;     // by C entry index (flat form): the entry's neighbour in its tile's stage
 };
 
 // Host: the tiled form from the flat form (rows by position with their row index
@@ -31,13 +40,19 @@ struct TileArgs {
 // some row is cut into pieces or some tile would stage more than TILE_CAP
 // neighbours.  Tiles of `tile` positions (the caller tries 64, 32, 16, 8).
 bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &zent, size_t ent_bytes,
-                 const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr, std::vector<int> &lev_tile,
-                 std::vector<int> &stage_ptr, std::vector<int> &stage_row, std::vector<uint16_t> &slot);
+                 const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr,
+                 std::vector<int> &tile_slots, std::vector<int> &lev_tile, std::vector<int> &run_ptr,
+                 std::vector<int> &run_row, std::vector<int> &run_len, std::vector<uint16_t> &slot);
+
+// The state between the canonical layout (z, w: [n][kv] vectors each) and the
+// block-major pair layout x (2 x 32 x ceil(kv / 32) vectors a row); unpack = 1: x -> z, w.
+cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s);
 
 // CTAs of the tiled sweep resident at once on the device (one per SM); 0: not launchable.
 int tiled_ctas(int cplx);
-// One launch of a.ncyc cycles on the pair layout (a.z[0]: its two buffers; g: the
-// pair form of the rows and entries).  Cooperative: a grid barrier ends each level.
+// One launch of a.ncyc cycles on the block-major pair layout (a.z[0]: its two
+// buffers; g: the pair form's entries, cycle count and levels; t: the tiled form).
+// Cooperative: a grid barrier ends each level.
 cudaError_t launch_sweep_tiled(const SweepArgs &a, const GridArgs &g, const TileArgs &t, int cplx, int ctas,
                                cudaStream_t s);
 
