@@ -56,10 +56,9 @@ struct mcinv_ctx {
     uint32_t gpnkv = 0;
     // the tiled form (sweep_tiled.cu): tiles of positions and their staged neighbours
     bool tile_able = false, gtile = false;
-    GridRow *d_grow_t = nullptr;  // records with .row = i x 64 (block-major pair layout)
+    uint8_t *d_trow = nullptr;  // TileRow records by position
     int *d_tptr = nullptr, *d_tslots = nullptr, *d_levtile = nullptr, *d_rptr = nullptr, *d_rrow = nullptr,
         *d_rlen = nullptr;
-    uint16_t *d_slot = nullptr;
     int tile_size = 0;
     int x_layout = 0;  // the layout of d_x when pair_ok: 0 the pair layout, 1 block-major (tiled sweep)
     int *d_levptr = nullptr;
@@ -294,7 +293,7 @@ static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
         b.w[1] = b.z[1];
         h->canon_ok = false;
         if (h->gtile) {
-            TileArgs t{h->d_grow_t, h->d_tptr, h->d_tslots, h->d_levtile, h->d_rptr, h->d_rrow, h->d_rlen, h->d_slot};
+            TileArgs t{h->d_trow, h->d_tptr, h->d_tslots, h->d_levtile, h->d_rptr, h->d_rrow, h->d_rlen};
             return launch_sweep_tiled(b, grid_args(h), t, h->cplx, h->gctas, h->stream);
         }
         return launch_sweep_grid(b, grid_args(h), h->cplx, h->gctas, h->threads, h->gbulk, h->stream);
@@ -730,16 +729,13 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
                     if (!build_tiles(P.grow, P.gzent, esz_ent, P.lev_ptr, ts, tptr, tslots, levtile, rptr, rrow, rlen,
                                      slot))
                         continue;
-                    std::vector<GridRow> growt = P.grow;
-                    for (int64_t p = 0; p < n; ++p) growt[p].row = P.grow[p].row * 64;
-                    SETUP(upload(h, &h->d_grow_t, growt));
+                    SETUP(upload(h, &h->d_trow, build_tile_rows(P.grow, P.gzent, P.gwent, slot, cplx)));
                     SETUP(upload(h, &h->d_tptr, tptr));
                     SETUP(upload(h, &h->d_tslots, tslots.empty() ? std::vector<int>(1, 0) : tslots));
                     SETUP(upload(h, &h->d_levtile, levtile));
                     SETUP(upload(h, &h->d_rptr, rptr));
                     SETUP(upload(h, &h->d_rrow, rrow.empty() ? std::vector<int>(1, 0) : rrow));
                     SETUP(upload(h, &h->d_rlen, rlen.empty() ? std::vector<int>(1, 0) : rlen));
-                    SETUP(upload(h, &h->d_slot, slot.empty() ? std::vector<uint16_t>(1, 0) : slot));
                     h->tile_able = true;
                     h->tile_size = ts;
                     break;

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 #include "sweep_core.cuh"
@@ -85,9 +86,63 @@ bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &z
     return true;
 }
 
+std::vector<uint8_t> build_tile_rows(const std::vector<GridRow> &rows, const std::vector<uint8_t> &zent,
+                                     const std::vector<uint8_t> &went, const std::vector<uint16_t> &slot, int cplx)
+{
+    const size_t n = rows.size() - 1;
+    const size_t rb = cplx ? sizeof(TileRow<true>) : sizeof(TileRow<false>);
+    const size_t eb = cplx ? sizeof(EntC) : sizeof(EntR);
+    std::vector<uint8_t> out(n * rb, 0);
+    for (size_t p = 0; p < n; ++p) {
+        const int d = rows[p + 1].zb - rows[p].zb;
+        uint8_t *r = out.data() + p * rb;
+        if (cplx) {
+            TileRow<true> t{};
+            t.iv = rows[p].row * 64;
+            t.d = d;
+            for (int u = 0; u < d && u < 8; ++u) {
+                const EntC ez = *(const EntC *)(zent.data() + (size_t)(rows[p].zb + u) * eb);
+                const EntC ew = *(const EntC *)(went.data() + (size_t)(rows[p].wb + u) * eb);
+                t.slot[u] = slot[rows[p].zb + u];
+                t.zc[u] = make_float2(ez.re, ez.im);
+                t.wc[u] = make_float2(ew.re, ew.im);
+            }
+            std::memcpy(r, &t, rb);
+        } else {
+            TileRow<false> t{};
+            t.iv = rows[p].row * 64;
+            t.d = d;
+            for (int u = 0; u < d && u < 8; ++u) {
+                const EntR ez = *(const EntR *)(zent.data() + (size_t)(rows[p].zb + u) * eb);
+                const EntR ew = *(const EntR *)(went.data() + (size_t)(rows[p].wb + u) * eb);
+                t.slot[u] = slot[rows[p].zb + u];
+                t.zc[u] = ez.val;
+                t.wc[u] = ew.val;
+            }
+            std::memcpy(r, &t, rb);
+        }
+    }
+    return out;
+}
+
 namespace {
 
 using namespace ring;
+
+static_assert(SPLIT_ENTRIES == 8, "a tiled row record holds the entries of an unsplit row");
+
+// The row's record: four (real) or six (complex) 16-byte words of coefficients after
+// the head and the slots, every load independent of the others.
+template <bool CPLX>
+__device__ __forceinline__ TileRow<CPLX> load_tile_row(const TileRow<CPLX> *p)
+{
+    TileRow<CPLX> r;
+    const int4 *src = (const int4 *)p;
+    int4 *dst = (int4 *)&r;
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(TileRow<CPLX>) / 16); ++k) dst[k] = __ldg(src + k);
+    return r;
+}
 
 constexpr int TILE_THREADS = 512;         // 16 warps, one CTA an SM
 constexpr int TNW = TILE_THREADS / 32;
@@ -149,7 +204,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     __syncthreads();
 
     Mat<CPLX> m;
-    m.rows = t.rows;
+    m.rows = g.rows;  // (not read: the tiled records carry what a row needs)
     m.cst = (const Cst *)g.cst;
     m.z0 = a.z[0];
     m.w0 = a.z[0];  // the pair layout holds w beside z
@@ -161,9 +216,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     m.ldsh = a.ldsh;
     m.kp = a.kp;
     m.tq = a.tq;
-    // the coefficients (the same in both parities' entries; .col is not used here)
-    const Ent *zent = (const Ent *)g.zent[0];
-    const Ent *went = (const Ent *)g.went[0];
     const float4 *x0 = (const float4 *)a.z[0];
     bool diverged = false;
     unsigned target = 0;
@@ -219,42 +271,39 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     w.wo[0] = w.zo[0] + 32u;
                     const uint32_t base = stage0 + b * TILE_CAP * SLAB + (uint32_t)lane * 16u;
                     const int p1 = __ldg(&t.tile_ptr[tile + 1]);
-                    int p = __ldg(&t.tile_ptr[tile]) + warp;
-                    int4 rec = p < p1 ? ldnc4(&m.rows[p]) : make_int4(0, 0, 0, 0);
-                    for (; p < p1; p += TNW) {
-                        // the warp's next row's record, loaded while this row is computed
-                        const int4 nrec = p + TNW < p1 ? ldnc4(&m.rows[p + TNW]) : make_int4(0, 0, 0, 0);
-                        const int d = (rec.w >> 2) & 0x7fff;  // entries a side (the same columns)
+                    const TileRow<CPLX> *trow = (const TileRow<CPLX> *)t.trow;
+                    for (int p = __ldg(&t.tile_ptr[tile]) + warp; p < p1; p += TNW) {
+                        // the row's record, constants, noise word, diagonal partial and shadow
+                        // indices: independent loads, one round trip
+                        const TileRow<CPLX> r = load_tile_row<CPLX>(trow + p);
                         const Cst k = ldg_cst(&m.cst[p]);
                         const uint32_t bits = w.bits(0, p, m.noise_cyc);
                         S dold = P::zero();
                         if (w.dlead[0]) dold = w.dpart[0][p];
                         int rp = -1, sp = -1;
                         if (m.rpos) { rp = __ldg(&m.rpos[p]); sp = __ldg(&m.spos[p]); }
-                        // the row's slots and coefficients all loaded at once (rows of the tiled
-                        // form have at most SPLIT_ENTRIES entries), then the sums in entry order
-                        uint32_t sl[SPLIT_ENTRIES];
-                        Ent ez[SPLIT_ENTRIES], ew[SPLIT_ENTRIES];
-#pragma unroll
-                        for (int u = 0; u < SPLIT_ENTRIES; ++u) {
-                            if (u < d) {
-                                sl[u] = __ldg(&t.slot[rec.y + u]);
-                                ez[u] = ldg_ent(&zent[rec.y + u]);
-                                ew[u] = ldg_ent(&went[rec.z + u]);
-                            }
-                        }
+                        // the sums in entry order (rows of the tiled form have at most 8 entries)
                         T sz = L::zero(), sw = L::zero();
 #pragma unroll
                         for (int u = 0; u < SPLIT_ENTRIES; ++u) {
-                            if (u < d) {
-                                L::fma(sz, ez[u], lds_vec<T>(base + sl[u] * SLAB));
-                                L::fma(sw, ew[u], lds_vec<T>(base + sl[u] * SLAB + SEGB));
+                            if (u < r.d) {
+                                Ent ez, ew;
+                                ez.col = ew.col = 0;
+                                if constexpr (CPLX) {
+                                    ez.re = r.zc[u].x; ez.im = r.zc[u].y; ez.pad = 0;
+                                    ew.re = r.wc[u].x; ew.im = r.wc[u].y; ew.pad = 0;
+                                } else {
+                                    ez.val = r.zc[u];
+                                    ew.val = r.wc[u];
+                                }
+                                const uint32_t sl = r.slot[u];
+                                L::fma(sz, ez, lds_vec<T>(base + sl * SLAB));
+                                L::fma(sw, ew, lds_vec<T>(base + sl * SLAB + SEGB));
                             }
                         }
-                        const S pr = finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)rec.x, sz, sw, k, bits, dold, rp, sp, tsum,
+                        const S pr = finish<CPLX, V, 1>(w, m, 0, p, (uint32_t)r.iv, sz, sw, k, bits, dold, rp, sp, tsum,
                                                          diverged);
                         diag_one(w, 0, p, pr, dold);
-                        rec = nrec;
                     }
                     // every warp is done with buffer b before it is staged again; an expired wait
                     // ends the level's items for the whole CTA at once (the same answer in every thread)

@@ -24,15 +24,31 @@ constexpr int TILE_CAP = 104;
 // (32 vectors of 16 bytes), row j holds the block's z vectors then its w vectors
 // at vector b n 64 + j 64, so a run of consecutive rows of one block is one
 // contiguous copy.
+// One position's row in the tiled form, everything a row reads to sum its entries
+// in one record of independent loads: its first vector (i x 64, block-major), its
+// entry count d, the entries' slots in the tile's stage, and the coefficients of
+// C (z side) and of C^dagger (w side), entry u at index u (u >= d: zero).
+template <bool CPLX> struct TileRow;
+template <> struct __align__(16) TileRow<false> {
+    int iv, d, pad0, pad1;
+    uint16_t slot[8];
+    float zc[8], wc[8];
+};
+template <> struct __align__(16) TileRow<true> {
+    int iv, d, pad0, pad1;
+    uint16_t slot[8];
+    float2 zc[8], wc[8];
+};
+static_assert(sizeof(TileRow<false>) == 96 && sizeof(TileRow<true>) == 160, "whole 16-byte loads");
+
 struct TileArgs {
-    const GridRow *rows;      // by position; .row holds i * 64 (the row's first vector in a block)
+    const void *trow;         // [n] TileRow by position
     const int *tile_ptr;      // [ntiles + 1]: first position of each tile
     const int *tile_slots;    // [ntiles]: rows the tile stages
     const int *lev_tile;      // [nlev + 1]: first tile of each level
     const int *run_ptr;       // [ntiles + 1]: first run of each tile
     const int *run_row;       // per run: its first row j, bit 31 set when read from this cycle's buffer
     const int *run_len;       // per run: rows (bits 0-15) and first slot in the tile's stage (bits 16-31)
-    const uint16_t *slot;     // by C entry index (flat form): the entry's neighbour in its tile's stage
 };
 
 // Host: the tiled form from the flat form (rows by position with their row index
@@ -43,6 +59,11 @@ bool build_tiles(const std::vector<GridRow> &rows, const std::vector<uint8_t> &z
                  const std::vector<int32_t> &lev_ptr, int tile, std::vector<int> &tile_ptr,
                  std::vector<int> &tile_slots, std::vector<int> &lev_tile, std::vector<int> &run_ptr,
                  std::vector<int> &run_row, std::vector<int> &run_len, std::vector<uint16_t> &slot);
+
+// Host: the TileRow records (bytes, n of them) from the flat form and the slots
+// build_tiles gave each entry.
+std::vector<uint8_t> build_tile_rows(const std::vector<GridRow> &rows, const std::vector<uint8_t> &zent,
+                                     const std::vector<uint8_t> &went, const std::vector<uint16_t> &slot, int cplx);
 
 // The state between the canonical layout (z, w: [n][kv] vectors each) and the
 // block-major pair layout x (2 x 32 x ceil(kv / 32) vectors a row); unpack = 1: x -> z, w.
