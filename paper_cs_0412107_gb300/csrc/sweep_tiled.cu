@@ -131,23 +131,13 @@ using namespace ring;
 
 static_assert(SPLIT_ENTRIES == 8, "a tiled row record holds the entries of an unsplit row");
 
-// The row's record: four (real) or six (complex) 16-byte words of coefficients after
-// the head and the slots, every load independent of the others.
-template <bool CPLX>
-__device__ __forceinline__ TileRow<CPLX> load_tile_row(const TileRow<CPLX> *p)
-{
-    TileRow<CPLX> r;
-    const int4 *src = (const int4 *)p;
-    int4 *dst = (int4 *)&r;
-#pragma unroll
-    for (int k = 0; k < (int)(sizeof(TileRow<CPLX>) / 16); ++k) dst[k] = __ldg(src + k);
-    return r;
-}
-
 constexpr int TILE_THREADS = 512;         // 16 warps, one CTA an SM
 constexpr int TNW = TILE_THREADS / 32;
 constexpr int SLAB = 2 * SEGB;            // a row's z and w vectors of one 32-vector block: 1 KB
-constexpr size_t TILE_SMEM = 2 * (size_t)TILE_CAP * SLAB + 2 * sizeof(uint64_t);
+// a stage buffer's tile metadata: the rows' records and constants (complex sizes)
+constexpr int META = TILE_MAX_ROWS * ((int)sizeof(TileRow<true>) + (int)sizeof(CstC));
+constexpr size_t TILE_SMEM = 2 * (size_t)TILE_CAP * SLAB + 2 * (size_t)META + 2 * sizeof(uint64_t);
+static_assert(TILE_SMEM <= 227u * 1024u, "two stage buffers fit the shared memory of a CTA");
 
 // Arrive at the next grid barrier and wait until every CTA of the grid has (the
 // counter was zeroed before the launch; target = barriers so far x CTAs).
@@ -191,7 +181,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t stage0 = smem_addr(tsm);
-    const uint32_t bar0 = stage0 + 2u * TILE_CAP * SLAB;  // one mbarrier per stage buffer
+    const uint32_t meta0 = stage0 + 2u * TILE_CAP * SLAB;  // the stage buffers' row records and constants
+    const uint32_t bar0 = meta0 + 2u * META;               // one mbarrier per stage buffer
+    constexpr uint32_t RB = sizeof(TileRow<CPLX>), CB = sizeof(Cst);
     const uint32_t bstride = 64u * (uint32_t)a.n;        // vectors of one chain block, block-major
     Lanes<CPLX, V, 1> w;
     w.init(lane, 0, g.kv, a.K, a.n, a.seg, a.diag_part, a.noise, 0u, 0u, true);
@@ -239,10 +231,18 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                 const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
                 const int r0 = __ldg(&t.run_ptr[tile]), nr = __ldg(&t.run_ptr[tile + 1]) - r0;
                 const int ns = min(__ldg(&t.tile_slots[tile]), TILE_CAP);  // (the host keeps it <= TILE_CAP)
+                const int p0 = __ldg(&t.tile_ptr[tile]);
+                const int np = min(__ldg(&t.tile_ptr[tile + 1]) - p0, TILE_MAX_ROWS);
                 const uint32_t bar = bar0 + 8u * b;
                 // the slots' earlier generic-proxy reads before these async-proxy writes
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (lane == 0) mbar_expect(bar, (uint32_t)ns * SLAB);
+                if (lane == 0) {
+                    mbar_expect(bar, (uint32_t)ns * SLAB + (uint32_t)np * (RB + CB));
+                    // the tile's row records and constants (contiguous by position)
+                    const uint32_t mb = meta0 + b * (uint32_t)META;
+                    bulk_g2s(mb, (const uint8_t *)t.trow + (size_t)p0 * RB, (uint32_t)np * RB, bar);
+                    bulk_g2s(mb + TILE_MAX_ROWS * RB, (const uint8_t *)g.cst + (size_t)p0 * CB, (uint32_t)np * CB, bar);
+                }
                 __syncwarp();
                 for (int r = lane; r < nr; r += 32) {
                     const int code = __ldg(&t.run_row[r0 + r]);
@@ -271,17 +271,32 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     w.wo[0] = w.zo[0] + 32u;
                     const uint32_t base = stage0 + b * TILE_CAP * SLAB + (uint32_t)lane * 16u;
                     const int p1 = __ldg(&t.tile_ptr[tile + 1]);
-                    const TileRow<CPLX> *trow = (const TileRow<CPLX> *)t.trow;
-                    for (int p = __ldg(&t.tile_ptr[tile]) + warp; p < p1; p += TNW) {
-                        // the row's record, constants, noise word, diagonal partial and shadow
-                        // indices: independent loads, one round trip
-                        const TileRow<CPLX> r = load_tile_row<CPLX>(trow + p);
-                        const Cst k = ldg_cst(&m.cst[p]);
-                        const uint32_t bits = w.bits(0, p, m.noise_cyc);
-                        S dold = P::zero();
-                        if (w.dlead[0]) dold = w.dpart[0][p];
-                        int rp = -1, sp = -1;
-                        if (m.rpos) { rp = __ldg(&m.rpos[p]); sp = __ldg(&m.spos[p]); }
+                    const int pb = __ldg(&t.tile_ptr[tile]);
+                    const uint32_t mb = meta0 + b * (uint32_t)META;
+                    // a row's noise word, diagonal partial and shadow indices, loaded one row ahead
+                    uint32_t nbits = 0u;
+                    S ndold = P::zero();
+                    int nrp = -1, nsp = -1;
+                    auto prefetch = [&](int q) {
+                        nbits = w.bits(0, q, m.noise_cyc);
+                        ndold = w.dlead[0] ? w.dpart[0][q] : P::zero();
+                        if (m.rpos) { nrp = __ldg(&m.rpos[q]); nsp = __ldg(&m.spos[q]); }
+                    };
+                    if (pb + warp < p1) prefetch(pb + warp);
+                    for (int p = pb + warp; p < p1; p += TNW) {
+                        const uint32_t bits = nbits;
+                        const S dold = ndold;
+                        const int rp = nrp, sp = nsp;
+                        if (p + TNW < p1) prefetch(p + TNW);
+                        // the row's record and constants, staged with the tile
+                        TileRow<CPLX> r;
+#pragma unroll
+                        for (int q = 0; q < (int)(RB / 16); ++q)
+                            ((float4 *)&r)[q] = lds_vec<float4>(mb + (uint32_t)(p - pb) * RB + 16u * q);
+                        Cst k;
+#pragma unroll
+                        for (int q = 0; q < (int)(CB / 16); ++q)
+                            ((float4 *)&k)[q] = lds_vec<float4>(mb + TILE_MAX_ROWS * RB + (uint32_t)(p - pb) * CB + 16u * q);
                         // the sums in entry order (rows of the tiled form have at most 8 entries)
                         T sz = L::zero(), sw = L::zero();
 #pragma unroll

@@ -10,8 +10,11 @@
 
 namespace mcinv {
 
-// Staged positions a tile may name: two buffers of this many 1 KB slabs fit a CTA.
-constexpr int TILE_CAP = 104;
+// Staged rows a tile may name: two buffers of this many 1 KB slabs, with the tiles'
+// row records and constants beside them, fit a CTA.
+constexpr int TILE_CAP = 100;
+// Positions a tile may hold (tiles of 64, 32, 16 or 8).
+constexpr int TILE_MAX_ROWS = 64;
 
 // The tiled form of a structurally symmetric matrix (row i of C and of C^dagger
 // name the same columns in the same order).  The positions of every dependency
