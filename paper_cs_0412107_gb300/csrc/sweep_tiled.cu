@@ -222,17 +222,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
         float tsum = 0.f;
         for (int l = 0; l < g.nlev; ++l) {
             const int t0 = __ldg(&t.lev_tile[l]);
-            const int ntl = __ldg(&t.lev_tile[l + 1]) - t0;  // the level's tiles
-            // items block-major: all of the level's tiles for chain block 0, then block 1, ...;
-            // a site's uses by distant neighbours (the 4D lattice's +-x3, 128 tiles apart) then
-            // fall within the tiles in flight, and L2 serves the second
-            const int nitems = ntl * g.nblk;
+            const int nitems = (__ldg(&t.lev_tile[l + 1]) - t0) * g.nblk;
             // stage item it (tile, chain block) into buffer b: warp 0 issues one bulk copy a
             // run of the tile's staged rows (contiguous in the block-major layout), all
             // completing on the buffer's mbarrier
             auto issue = [&](int it, uint32_t b) {
                 if (warp != 0) return;
-                const int blk = it / ntl, tile = t0 + (it - blk * ntl);
+                const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
                 const int r0 = __ldg(&t.run_ptr[tile]), nr = __ldg(&t.run_ptr[tile + 1]) - r0;
                 const int ns = min(__ldg(&t.tile_slots[tile]), TILE_CAP);  // (the host keeps it <= TILE_CAP)
                 const int p0 = __ldg(&t.tile_ptr[tile]);
@@ -269,7 +265,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     if (nxt < nitems) issue(nxt, b ^ 1u);  // that buffer was released at the last CTA barrier
                     if (!ring_wait(bar0 + 8u * b, (uses >> 1) & 1u)) *abort_flag = 1;
                     ++uses;
-                    const int blk = it / ntl, tile = t0 + (it - blk * ntl);
+                    const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
                     w.set_block(blk, g.kv, a.K, a.n, a.diag_part, a.noise, true);
                     w.zo[0] = (uint32_t)blk * bstride + (uint32_t)lane;  // the block-major layout
                     w.wo[0] = w.zo[0] + 32u;
