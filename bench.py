@@ -139,7 +139,15 @@ SWEEP_KERNELS = {
         ("sweep_grid.cu", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), "cc_sweep_grid_pair_pedigree50k.txt"),
     5: ("cc_sweep_tiled_kernel (tile-staged neighbours, pair layout)",
         ("sweep_tiled.cu", "sweep_tiled.h", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), None),
+    6: ("cc_sweep_wave_kernel (chain-sliced wavefront, sliced layout)",
+        ("sweep_wave.cu", "sweep_wave.h", "sweep_ring.cuh", "sweep_core.cuh", "internal.h"), None),
 }
+
+# bytes a cycle must move per (row, chain) of a complex64 sweep: z and w read and
+# written once (32), or, for the wavefront sweep, the black half read once and every
+# row written once (24: it keeps the red half in shared memory for the black rows)
+def kernel_bytes_per_unit(sweep_kernel):
+    return 24.0 if sweep_kernel == 6 else 32.0
 
 
 def traffic_from_profiles(kernel_file, units_per_launch, sources=("sweep.cu", "sweep_core.cuh", "internal.h"),
@@ -174,7 +182,8 @@ def kernel_flags(args):
     """The sweep kernel: timed on the matrix by the autotuner (auto), or fixed: the
     chain-sliced kernel in its default shape, the grid-wide kernel (register
     gathers, 512 threads), the grid-wide kernel with bulk-staged gathers on
-    separate z, w buffers (bulk) or on the pair layout (pair)."""
+    separate z, w buffers (bulk) or on the pair layout (pair), the tile-staged
+    sweep (tile) or the wavefront sweep (wave)."""
     from paper_cs_0412107_gb300 import mcinv
     if args.kernel == "auto":
         return (0 if args.no_autotune else mcinv.MCINV_F_AUTOTUNE), {}
@@ -186,6 +195,8 @@ def kernel_flags(args):
         return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_NOPAIR, {}
     if args.kernel == "tile":
         return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_TILE, {}
+    if args.kernel == "wave":
+        return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_WAVE, {}
     # the pair layout in the shape --threads names (384 by default)
     return mcinv.MCINV_F_GRID | mcinv.MCINV_F_GRID_BULK | mcinv.MCINV_F_GRID_PAIR, {}
 
@@ -787,7 +798,9 @@ def run_lattice2d(args, world, rank, local):
     t_launch = sw_ms / sw_launches / 1e3 if sw_launches else None
     achieved = alg_bytes / t_launch / 1e9 if t_launch else None
     kname, ksrc, kprof = SWEEP_KERNELS[info0["sweep_kernel"]]
-    kprof = {4: f"cc_sweep_grid_pair_{name}.txt", 5: f"cc_sweep_tiled_{name}.txt"}.get(info0["sweep_kernel"])
+    kprof = {4: f"cc_sweep_grid_pair_{name}.txt", 5: f"cc_sweep_tiled_{name}.txt",
+             6: f"cc_sweep_wave_{name}.txt"}.get(info0["sweep_kernel"])
+    own_bytes = kernel_bytes_per_unit(info0["sweep_kernel"]) * units_per_launch
     return {
         "metric": METRIC, "value": float(csr.nnz) * K * cycles * world / (ms_max / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -803,7 +816,9 @@ def run_lattice2d(args, world, rank, local):
                      "traffic": traffic_from_profiles(kprof, units_per_launch, ksrc, info0["threads_per_cta"]),
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_unit": alg_bytes / units_per_launch,
                      "units_per_launch": units_per_launch, "compulsory_bytes_per_launch": compulsory_bytes,
-                     "compulsory_frac": compulsory_bytes / t_launch / 1e9 / hbm if t_launch else None},
+                     "compulsory_frac": compulsory_bytes / t_launch / 1e9 / hbm if t_launch else None,
+                     "kernel_bytes_per_launch": own_bytes,
+                     "kernel_frac": own_bytes / t_launch / 1e9 / hbm if t_launch else None},
         "trace": {"re": float(np.real(tr)), "im": float(np.imag(tr)), "se_re": float(np.real(tse)),
                   "se_im": float(np.imag(tse)), "cycles": args.burnin + (args.warmup + args.steps) * B},
         "kernels_ms": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
@@ -1083,7 +1098,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128)
     ap.add_argument("--rms-samples", type=int, default=16)
     ap.add_argument("--order", default="colour", choices=["natural", "colour"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair", "tile"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "sliced", "grid", "bulk", "pair", "tile", "wave"])
     ap.add_argument("--no-natural", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-records")
     ap.add_argument("--lattice-batches", type=int, default=6)

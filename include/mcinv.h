@@ -133,13 +133,29 @@ typedef struct {
 #define MCINV_F_GRID_TILE 256 /* with MCINV_F_GRID_BULK: the tile-staged sweep.  The positions of every
                               dependency level are cut into tiles of 64, 32, 16 or 8 consecutive
                               positions (the largest that fits); a CTA copies a tile's distinct
-                              neighbours (at most 104 rows' 32-vector blocks of z and w, pair
+                              neighbours (at most 100 rows' 32-vector blocks of z and w, pair
                               layout) into shared memory once and its 16 warps update the tile's
                               rows from there, the next tile's copies in flight.  For lattices in
                               the colour order.  MCINV_E_UNSUPPORTED when C is not structurally
                               symmetric, a row is cut into pieces, or a tile would name more
                               neighbours; MCINV_E_ARG with MCINV_F_GRID_NOPAIR.  Same values, bit
                               for bit.  MCINV_F_AUTOTUNE times it where it applies. */
+#define MCINV_F_GRID_WAVE 512 /* with MCINV_F_GRID_BULK: the wavefront sweep, for a C whose order has
+                              two dependency levels of equal size (a lattice in the colour order:
+                              red, then black) that cut into chunks of S consecutive positions
+                              whose rows touch only the other level's chunks within B of their
+                              own, cyclically.  Each CTA owns a slice of the chains (16, 8 or 4
+                              vectors of 16 bytes) for whole cycles, with no grid barrier: it
+                              updates red chunk t from black chunks t-B .. t+B copied into
+                              shared memory once each, keeps the new red values there, then
+                              updates black chunk t-B; the B black chunks at each end of the
+                              cycle wait for its end.  A cycle reads the black half of the state
+                              once and writes all of it once.  MCINV_E_UNSUPPORTED when C has no
+                              such form (or its window does not fit a CTA's shared memory);
+                              MCINV_E_ARG with MCINV_F_GRID_NOPAIR or MCINV_F_GRID_TILE.  Same
+                              values, bit for bit, except the trace series' partial sums, which
+                              are grouped by warp in another way.  MCINV_F_AUTOTUNE times it
+                              where it applies. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.
@@ -304,8 +320,11 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the handle */
     int32_t sweep_kernel;    /* 0: chain-sliced (registers), 1: staged, 2: grid-wide (MCINV_F_GRID),
                                 3: grid-wide with bulk-staged gathers (MCINV_F_GRID_BULK),
-                                4: the same on the pair layout (structurally symmetric C) */
-    int32_t grid_ctas;       /* CTAs of the grid-wide sweep (0 for the others) */
+                                4: the same on the pair layout (structurally symmetric C),
+                                5: the tile-staged sweep (MCINV_F_GRID_TILE),
+                                6: the wavefront sweep (MCINV_F_GRID_WAVE) */
+    int32_t grid_ctas;       /* CTAs of the grid-wide sweep, or of the wavefront sweep (one a chain
+                                slice); 0 for the others */
 } mcinv_info_t;
 
 mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info);

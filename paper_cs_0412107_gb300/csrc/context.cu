@@ -19,6 +19,7 @@
 #include "partition.h"
 #include "prepare.h"
 #include "sweep_tiled.h"
+#include "sweep_wave.h"
 #include "tc_gemm.h"
 
 using namespace mcinv;
@@ -60,7 +61,13 @@ struct mcinv_ctx {
     int *d_tptr = nullptr, *d_tslots = nullptr, *d_levtile = nullptr, *d_rptr = nullptr, *d_rrow = nullptr,
         *d_rlen = nullptr;
     int tile_size = 0;
-    int x_layout = 0;  // the layout of d_x when pair_ok: 0 the pair layout, 1 block-major (tiled sweep)
+    // the wavefront form (sweep_wave.cu): chunk size, band, chunks a level, positions a
+    // level, slice width; records by position
+    bool wave_able = false, gwave = false;
+    uint8_t *d_wrow = nullptr;
+    int wave_S = 0, wave_B = 0, wave_m = 0, wave_h = 0, wave_sv = 0, wave_D = 0, wave_exact = 0;
+    int x_layout = 0;  // the layout of d_x when pair_ok: 0 the pair layout, 1 block-major (tiled
+                       // sweep), 2 sliced (block-major with blocks of wave_sv vectors: wavefront sweep)
     int *d_levptr = nullptr;
     unsigned *d_gbar = nullptr;
     int nchunks = 0, blob_max = 0, seg = 1, units = 0;
@@ -244,22 +251,47 @@ static GridArgs grid_args(mcinv_ctx *h)
     return g;
 }
 
+static WaveArgs wave_args(const mcinv_ctx *h)
+{
+    WaveArgs g{};
+    g.trow = h->d_wrow;
+    g.cst = h->d_gcst;
+    g.h = h->wave_h;
+    g.S = h->wave_S;
+    g.B = h->wave_B;
+    g.m = h->wave_m;
+    g.sv = h->wave_sv;
+    g.D = h->wave_D;
+    g.exact = h->wave_exact;
+    g.nb = 2 * h->wave_B + 2;
+    g.nr = 2 * h->wave_B + 2;
+    g.nkv = h->gpnkv;
+    return g;
+}
+static int wave_grid(const mcinv_ctx *h) { return wave_ctas((int)(h->K * (h->cplx ? 8 : 4) / 16), h->wave_sv); }
+
 // CTAs and warps per CTA of the sweep launch (the trace-series partials hold one
 // slot per cycle, CTA and warp)
 static int sweep_ctas(const mcinv_ctx *h) { return h->grid ? h->gctas : h->slices * h->Q; }
 static int sweep_warps(const mcinv_ctx *h) { return h->threads / 32; }
+
+// The state of buffer `buf` between the canonical layout and d_x in layout `layout`
+// (unpack = 1: d_x -> canonical).
+static cudaError_t pack_x(mcinv_ctx *h, int layout, int buf, int unpack)
+{
+    const size_t nx = (size_t)h->gpnkv * 16;  // bytes of one pair-layout buffer
+    const int kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
+    void *x = (char *)h->d_x + buf * nx;
+    if (layout == 0) return launch_pair_pack(h->d_z[buf], h->d_w[buf], x, h->n, kv, unpack, h->stream);
+    return launch_tile_pack(h->d_z[buf], h->d_w[buf], x, h->n, kv, unpack, h->stream, layout == 2 ? h->wave_sv : 32);
+}
 
 // The state in the canonical layout (z[n][K], w[n][K]) again, after sweeps on the
 // pair layout; every reader of the state calls this first.
 static cudaError_t ensure_canonical(mcinv_ctx *h)
 {
     if (h->canon_ok) return cudaSuccess;
-    const size_t nx = (size_t)h->gpnkv * 16;  // bytes of one pair-layout buffer
-    const int kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
-    cudaError_t e = h->x_layout ? launch_tile_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
-                                                   kv, 1, h->stream)
-                                : launch_pair_pack(h->d_z[h->cur], h->d_w[h->cur], (char *)h->d_x + h->cur * nx, h->n,
-                                                   kv, 1, h->stream);
+    cudaError_t e = pack_x(h, h->x_layout, h->cur, 1);
     if (e == cudaSuccess) h->canon_ok = true;
     return e;
 }
@@ -267,21 +299,18 @@ static cudaError_t ensure_canonical(mcinv_ctx *h)
 static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
 {
     if (h->grid && h->gbulk && h->gpair) {
-        // the pair layout (block-major for the tiled sweep): packed from the canonical
-        // state when that is the newer, after unpacking the other pair layout if it held it
+        // the pair layout (block-major for the tiled sweep, sliced for the wavefront
+        // sweep): packed from the canonical state when that is the newer, after
+        // unpacking another of these layouts if it held it
         const size_t nx = (size_t)h->gpnkv * 16;
-        const int layout = h->gtile ? 1 : 0;
+        const int layout = h->gwave ? 2 : h->gtile ? 1 : 0;
         if (h->pair_ok && h->x_layout != layout) {
             cudaError_t e = ensure_canonical(h);
             if (e != cudaSuccess) return e;
             h->pair_ok = false;
         }
         if (!h->pair_ok) {
-            const int kv = (int)(h->K * (h->cplx ? 8 : 4) / 16);
-            cudaError_t e = layout ? launch_tile_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n, kv, 0,
-                                                      h->stream)
-                                   : launch_pair_pack(h->d_z[a.cur], h->d_w[a.cur], (char *)h->d_x + a.cur * nx, h->n, kv, 0,
-                                                      h->stream);
+            cudaError_t e = pack_x(h, layout, a.cur, 0);
             if (e != cudaSuccess) return e;
             h->pair_ok = true;
             h->x_layout = layout;
@@ -292,6 +321,7 @@ static cudaError_t sweep_launch(mcinv_ctx *h, const SweepArgs &a)
         b.w[0] = b.z[0];
         b.w[1] = b.z[1];
         h->canon_ok = false;
+        if (h->gwave) return launch_sweep_wave(b, wave_args(h), h->cplx, h->stream);
         if (h->gtile) {
             TileArgs t{h->d_trow, h->d_tptr, h->d_tslots, h->d_levtile, h->d_rptr, h->d_rrow, h->d_rlen};
             return launch_sweep_tiled(b, grid_args(h), t, h->cplx, h->gctas, h->stream);
@@ -314,6 +344,7 @@ struct TunedShape {
     bool gbulk = false;
     bool gpair = false;
     bool gtile = false;
+    bool gwave = false;
 };
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int64_t, int64_t, int64_t, int>, TunedShape> g_tune_cache;
@@ -325,14 +356,17 @@ static mcinv_status autotune(mcinv_ctx *h)
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         // (a shape on the pair layout is for handles that hold the pair buffers)
-        if (it != g_tune_cache.end() && (!it->second.gpair || h->d_x) && (!it->second.gtile || h->tile_able)) {
+        if (it != g_tune_cache.end() && (!it->second.gpair || h->d_x) && (!it->second.gtile || h->tile_able) &&
+            (!it->second.gwave || h->wave_able)) {
             h->W = it->second.W; h->V = it->second.V; h->LPR = it->second.LPR;
             h->Q = it->second.Q; h->threads = it->second.T; h->staged = it->second.staged;
             h->grid = it->second.grid;
             h->gbulk = it->second.gbulk;
             h->gpair = it->second.gpair;
             h->gtile = it->second.gtile;
-            if (h->grid) h->gctas = h->gtile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair);
+            h->gwave = it->second.gwave;
+            if (h->grid) h->gctas = h->gwave ? wave_grid(h) : h->gtile ? tiled_ctas(h->cplx)
+                                                                     : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair);
             h->slices = (int)((h->K + h->W - 1) / h->W);
             return MCINV_OK;
         }
@@ -345,7 +379,7 @@ static mcinv_status autotune(mcinv_ctx *h)
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk, h->gpair, h->gtile};
+    TunedShape best{h->W, h->V, h->LPR, h->Q, h->threads, h->staged, h->grid, h->gbulk, h->gpair, h->gtile, h->gwave};
     float best_ms = 1e30f;
     for (int lpr = 1; lpr <= 32; lpr *= 2) {
         const int W = lpr * vmax;
@@ -400,26 +434,30 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
     }
     // the grid-wide kernel: one warp per (row, 32 x V chains), all SMs per level
-    for (int variant = 0; variant < 10; ++variant) {
+    for (int variant = 0; variant < 11; ++variant) {
         // register gathers with 384 or 512 threads; bulk-staged with 1, 2 or 4 vectors per
         // lane (12 warps of 32 slots) or 1 (16 warps of 24 slots); bulk-staged on the pair
         // layout (structurally symmetric matrices) with one vector a lane (16 warps) or two
-        // (12 or 8 warps); the tile-staged sweep (pair layout, 16 warps) where C has a tiled form
-        static const int kT[10] = {384, 512, 384, 192, 96, 512, 512, 384, 256, 512};
+        // (12 or 8 warps); the tile-staged sweep (pair layout, 16 warps) where C has a tiled
+        // form; the wavefront sweep (sliced layout, 16 warps) where C has a wavefront form
+        static const int kT[11] = {384, 512, 384, 192, 96, 512, 512, 384, 256, 512, 512};
         const int T = kT[variant];
         const bool bulk = variant >= 2;
         const bool pair = variant == 5 || variant >= 7;
         const bool tile = variant == 9;
+        const bool wave = variant == 10;
         if (pair && !h->d_x) continue;
         if (tile && !h->tile_able) continue;
-        const int ctas = tile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, T, bulk, pair);
+        if (wave && !h->wave_able) continue;
+        const int ctas = wave ? wave_grid(h) : tile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, T, bulk, pair);
         if (!grid_supported(h->cplx, vmax, h->K, pair ? 512 : T, bulk) || ctas < 1 || h->gnkv == 0) continue;
         const int sW = h->W, sV = h->V, sL = h->LPR, sQ = h->Q, sT = h->threads, sS = h->slices, sC = h->gctas;
-        const bool sG = h->grid, sB = h->gbulk, sP = h->gpair, sI = h->gtile;
+        const bool sG = h->grid, sB = h->gbulk, sP = h->gpair, sI = h->gtile, sX = h->gwave;
         h->V = vmax; h->W = 32 * vmax; h->LPR = 32; h->Q = 1; h->threads = T; h->gctas = ctas; h->grid = true;
         h->gbulk = bulk;
         h->gpair = pair;
         h->gtile = tile;
+        h->gwave = wave;
         h->slices = (int)((h->K + h->W - 1) / h->W);
         SweepArgs a = sweep_args(h, ncyc, 0, false, 0);
         float ms = 1e30f;
@@ -432,11 +470,15 @@ static mcinv_status autotune(mcinv_ctx *h)
         }
         if (e != cudaSuccess) cudaGetLastError();
         h->launches += 2;
-        if (ms < best_ms) { best_ms = ms; best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk, pair, tile}; }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = TunedShape{32 * vmax, vmax, 32, 1, T, false, true, bulk, pair, tile, wave};
+        }
         h->W = sW; h->V = sV; h->LPR = sL; h->Q = sQ; h->threads = sT; h->slices = sS; h->gctas = sC; h->grid = sG;
         h->gbulk = sB;
         h->gpair = sP;
         h->gtile = sI;
+        h->gwave = sX;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -445,7 +487,10 @@ static mcinv_status autotune(mcinv_ctx *h)
     h->gbulk = best.gbulk;
     h->gpair = best.gpair;
     h->gtile = best.gtile;
-    h->gctas = h->grid ? (h->gtile ? tiled_ctas(h->cplx) : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair)) : 0;
+    h->gwave = best.gwave;
+    h->gctas = h->grid ? (h->gwave ? wave_grid(h) : h->gtile ? tiled_ctas(h->cplx)
+                                                             : grid_ctas(h->cplx, h->threads, h->gbulk, h->gpair))
+                       : 0;
     h->slices = (int)((h->K + h->W - 1) / h->W);
     // back to Algorithm 1 step 1: z = w = 0, nothing run yet
     const size_t bytes = (size_t)h->n * (size_t)h->K * (h->cplx ? 8 : 4);
@@ -741,6 +786,22 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
                     break;
                 }
             }
+            // the wavefront form: two colours whose chunks touch only nearby chunks (lattices
+            // in the colour order)
+            {
+                WaveForm wf;
+                if (build_wave(P.grow, P.gzent, P.gwent, esz_ent, P.lev_ptr, cplx, (int)kv, sm_count(), wf)) {
+                    SETUP(upload(h, &h->d_wrow, wf.trow));
+                    h->wave_able = true;
+                    h->wave_S = wf.S;
+                    h->wave_B = wf.B;
+                    h->wave_m = wf.m;
+                    h->wave_h = wf.h;
+                    h->wave_sv = wf.sv;
+                    h->wave_D = wf.D;
+                    h->wave_exact = wf.exact ? 1 : 0;
+                }
+            }
         }
         SETUP(upload(h, &h->d_levptr, P.lev_ptr));
         SETUP(dalloc(h, &h->d_gbar, 1));
@@ -810,6 +871,24 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         h->threads = 512;
         h->gctas = tc;
     }
+    if (h->flags & MCINV_F_GRID_WAVE) {
+        if (!(h->flags & MCINV_F_GRID) || !(h->flags & MCINV_F_GRID_BULK) || (h->flags & MCINV_F_GRID_NOPAIR) ||
+            (h->flags & MCINV_F_GRID_TILE)) {
+            fail(h, MCINV_E_ARG, "MCINV_F_GRID_WAVE needs MCINV_F_GRID and MCINV_F_GRID_BULK, not MCINV_F_GRID_NOPAIR "
+                                 "or MCINV_F_GRID_TILE");
+            return bail(MCINV_E_ARG);
+        }
+        if (!h->wave_able || !h->d_x) {
+            fail(h, MCINV_E_UNSUPPORTED, "C has no wavefront form (it needs a structurally symmetric C in an order "
+                                         "with two dependency levels of equal size, no row cut into pieces, and each "
+                                         "level cut into chunks whose rows touch only nearby chunks of the other)");
+            return bail(MCINV_E_UNSUPPORTED);
+        }
+        h->gpair = true;
+        h->gwave = true;
+        h->threads = 512;
+        h->gctas = wave_grid(h);
+    }
     SETUP(dalloc(h, &h->d_noise, (size_t)h->B * h->nw * (size_t)n));
     SETUP(dalloc(h, &h->d_status, 1));
     SETUP(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
@@ -822,8 +901,10 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
     //      chains, a power of two dividing the slice); G groups of whole units
     {
         const int Greq = opt.groups > 0 ? opt.groups : 32;
+        // (at most a wavefront slice: the wavefront sweep sums a row's units in its slice)
+        const int segmax = h->wave_able ? std::min(h->LPR, h->wave_sv) : h->LPR;
         int seg = 1;
-        while (seg * 2 <= h->LPR && (int64_t)seg * 2 * h->V * Greq <= opt.K) seg *= 2;
+        while (seg * 2 <= segmax && (int64_t)seg * 2 * h->V * Greq <= opt.K) seg *= 2;
         h->seg = seg;
         const int64_t u = (int64_t)seg * h->V;
         h->units = (int)((opt.K + u - 1) / u);
@@ -1493,7 +1574,7 @@ extern "C" mcinv_status mcinv_info(mcinv_t h, mcinv_info_t *info)
     info->batch_cycles = h->B; info->acc = h->acc;
     info->cycle = h->cycle; info->samples = h->samples; info->block_batches = h->block_batches;
     info->kernel_launches = h->launches; info->device_bytes = h->bytes;
-    info->sweep_kernel = h->grid ? (h->gtile ? 5 : h->gbulk ? (h->gpair ? 4 : 3) : 2) : h->staged ? 1 : 0;
+    info->sweep_kernel = h->grid ? (h->gwave ? 6 : h->gtile ? 5 : h->gbulk ? (h->gpair ? 4 : 3) : 2) : h->staged ? 1 : 0;
     info->grid_ctas = h->grid ? h->gctas : 0;
     return MCINV_OK;
 }

@@ -316,12 +316,14 @@ struct Mat {
 
 // Eqs. 4/5 for the V chains of the lane's vector q from the sums over the row's
 // entries, the stores, the shadows and the trace term; returns the lane's
-// z_i conj(w_i) partial for the diagonal (diag_one / diag_pair).
+// z_i conj(w_i) partial for the diagonal (diag_one / diag_pair) and leaves the
+// new values in zv, wv (unset when the lane's chains are past K).
 template <bool CPLX, int V, int G>
-__device__ __forceinline__ typename Prec<CPLX>::T finish(const Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int q, int p, uint32_t iv,
-                                       const typename Lane<CPLX, V>::T &sz, const typename Lane<CPLX, V>::T &sw,
-                                       const typename Prec<CPLX>::Cst &k, uint32_t bits, typename Prec<CPLX>::T dold,
-                                       int rp, int sp, float &tsum, bool &diverged)
+__device__ __forceinline__ typename Prec<CPLX>::T finish_keep(const Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int q, int p,
+                                            uint32_t iv, const typename Lane<CPLX, V>::T &sz,
+                                            const typename Lane<CPLX, V>::T &sw, const typename Prec<CPLX>::Cst &k,
+                                            uint32_t bits, typename Prec<CPLX>::T dold, int rp, int sp, float &tsum,
+                                            bool &diverged, typename Lane<CPLX, V>::T &zv, typename Lane<CPLX, V>::T &wv)
 {
     using P = Prec<CPLX>;
     using L = Lane<CPLX, V>;
@@ -332,7 +334,6 @@ __device__ __forceinline__ typename Prec<CPLX>::T finish(const Lanes<CPLX, V, G>
         // phi alpha and phi beta (Eq. 5): phi = +-1 flips the sign bit; no noise: phi = +0
         const S a0 = m.has_noise ? k.alpha : P::times_zero(k.alpha);
         const S b0 = m.has_noise ? k.beta : P::times_zero(k.beta);
-        T zv, wv;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const uint32_t sign = ((bits >> v) & 1u) << 31;
@@ -384,6 +385,16 @@ __device__ __forceinline__ typename Prec<CPLX>::T finish(const Lanes<CPLX, V, G>
         }
     }
     return prod;
+}
+
+template <bool CPLX, int V, int G>
+__device__ __forceinline__ typename Prec<CPLX>::T finish(const Lanes<CPLX, V, G> &w, const Mat<CPLX> &m, int q, int p, uint32_t iv,
+                                       const typename Lane<CPLX, V>::T &sz, const typename Lane<CPLX, V>::T &sw,
+                                       const typename Prec<CPLX>::Cst &k, uint32_t bits, typename Prec<CPLX>::T dold,
+                                       int rp, int sp, float &tsum, bool &diverged)
+{
+    typename Lane<CPLX, V>::T zv, wv;
+    return finish_keep<CPLX, V, G>(w, m, q, p, iv, sz, sw, k, bits, dold, rp, sp, tsum, diverged, zv, wv);
 }
 
 // The unit's sum of the lanes' z_i conj(w_i) over its seg lanes (xor butterfly:

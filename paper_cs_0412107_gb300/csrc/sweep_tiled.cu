@@ -348,35 +348,42 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
     }
 }
 
-// canonical z, w ([n][kv] vectors each) <-> the block-major pair layout x: block b,
-// row j at vector b n 64 + j 64 (z), + 32 (w); vectors past kv are zero
+// canonical z, w ([n][kv] vectors each) <-> the block-major pair layout x with
+// blocks of bw = 2^lg vectors: block b, row j at vector b n 2bw + j 2bw (z), + bw
+// (w); vectors past kv are zero
 __global__ void tile_pack_kernel(const float4 *__restrict__ z, const float4 *__restrict__ w, float4 *__restrict__ x,
-                                 long long n, int kv, int kvp, int unpack)
+                                 long long n, int kv, int kvp, int lg, int unpack)
 {
     const long long total = n * (long long)kvp;
+    const int bw = 1 << lg;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
         const long long j = t / kvp;
         const int v = (int)(t - j * kvp);
-        const long long xo = (long long)(v >> 5) * n * 64 + j * 64 + (v & 31);
+        const long long xo = ((long long)(v >> lg) * n + j) * 2 * bw + (v & (bw - 1));
         if (!unpack) {
             x[xo] = v < kv ? z[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
-            x[xo + 32] = v < kv ? w[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[xo + bw] = v < kv ? w[j * kv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
         } else if (v < kv) {
             ((float4 *)z)[j * kv + v] = x[xo];
-            ((float4 *)w)[j * kv + v] = x[xo + 32];
+            ((float4 *)w)[j * kv + v] = x[xo + bw];
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s)
+cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s,
+                             int bw)
 {
-    const int kvp = (kv + 31) / 32 * 32;
+    int lg = 0;
+    while ((1 << lg) < bw) ++lg;
+    if (bw < 1 || bw > 32 || (1 << lg) != bw) return cudaErrorInvalidValue;
+    const int kvp = (kv + bw - 1) / bw * bw;
     long long blocks = (n * kvp + 255) / 256;
     if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (blocks < 1) blocks = 1;
-    tile_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)z, (const float4 *)w, (float4 *)x, n, kv, kvp, unpack);
+    tile_pack_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)z, (const float4 *)w, (float4 *)x, n, kv, kvp, lg,
+                                                      unpack);
     return cudaGetLastError();
 }
 

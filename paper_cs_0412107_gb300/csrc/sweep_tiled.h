@@ -69,8 +69,11 @@ std::vector<uint8_t> build_tile_rows(const std::vector<GridRow> &rows, const std
                                      const std::vector<uint8_t> &went, const std::vector<uint16_t> &slot, int cplx);
 
 // The state between the canonical layout (z, w: [n][kv] vectors each) and the
-// block-major pair layout x (2 x 32 x ceil(kv / 32) vectors a row); unpack = 1: x -> z, w.
-cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s);
+// block-major pair layout x with blocks of bw vectors (a power of two up to 32: block
+// b, row j at vector (b n + j) 2 bw: the block's z vectors, then its w vectors; the
+// tiled sweep's bw = 32, the wavefront sweep's its slice width); unpack = 1: x -> z, w.
+cudaError_t launch_tile_pack(const void *z, const void *w, void *x, long long n, int kv, int unpack, cudaStream_t s,
+                             int bw = 32);
 
 // CTAs of the tiled sweep resident at once on the device (one per SM); 0: not launchable.
 int tiled_ctas(int cplx);
