@@ -264,6 +264,9 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
         usel[q] = diag ? vs / a.seg : 0;   // the unit among the slice's
     }
     const bool whole = diag && a.seg == SV;  // one unit a row: the two halves add at the last level
+    // with units of two or more vectors, vector j + hl's unit sum ends in lane j + 1 (odd),
+    // which stores it when the unit's first vector (j + hl - 1) has chains
+    const bool lead1 = diag && a.seg >= 2 && (j % a.seg) == 1 && w.c0[1] - V < a.K;
     if (threadIdx.x == 0) {
         abort_s = 0;
         mbar_init1(bar0);
@@ -396,28 +399,6 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
 #pragma unroll
                 for (int q = 0; q < (int)(RB / 16); ++q)
                     ((float4 *)&rec)[q] = lds_vec<float4>(rc + (uint32_t)r * RB + 16u * q);
-                Cst k;
-#pragma unroll
-                for (int q = 0; q < (int)(CB / 16); ++q)
-                    ((float4 *)&k)[q] = lds_vec<float4>(rc + (uint32_t)SC * RB + (uint32_t)r * CB + 16u * q);
-                uint32_t bits0 = 0u, bits1 = 0u;
-                if (noisy) {
-                    const uint32_t wd0 = lds_u32(rc + off_noise + (uint32_t)(wsel[0] * SC + r) * 4u);
-                    const uint32_t wd1 =
-                        wsel[1] == wsel[0] ? wd0 : lds_u32(rc + off_noise + (uint32_t)(wsel[1] * SC + r) * 4u);
-                    bits0 = wd0 >> w.cshift[0];
-                    bits1 = wd1 >> w.cshift[1];
-                }
-                S dold0 = P::zero(), dold1 = P::zero();
-                if (diag) {
-                    lds_s(rc + off_dold + (uint32_t)(usel[0] * SC + r) * ES, dold0);
-                    if (!whole) lds_s(rc + off_dold + (uint32_t)(usel[1] * SC + r) * ES, dold1);
-                }
-                int rp = -1, sp = -1;
-                if (m.rpos) {
-                    rp = __ldg(&m.rpos[p]);
-                    sp = __ldg(&m.spos[p]);
-                }
                 // the sums in entry order
                 T sz0 = L::zero(), sw0 = L::zero(), sz1 = L::zero(), sw1 = L::zero();
                 const int dmax = EXACT ? D : __reduce_max_sync(0xffffffffu, rec.d);
@@ -447,10 +428,29 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                         }
                     }
                 }
+                // the epilogue's operands: constants, noise words, diagonal partials, shadows
+                Cst k;
+#pragma unroll
+                for (int q = 0; q < (int)(CB / 16); ++q)
+                    ((float4 *)&k)[q] = lds_vec<float4>(rc + (uint32_t)SC * RB + (uint32_t)r * CB + 16u * q);
+                uint32_t bits0 = 0u, bits1 = 0u;
+                if (noisy) {
+                    const uint32_t wd0 = lds_u32(rc + off_noise + (uint32_t)(wsel[0] * SC + r) * 4u);
+                    const uint32_t wd1 =
+                        wsel[1] == wsel[0] ? wd0 : lds_u32(rc + off_noise + (uint32_t)(wsel[1] * SC + r) * 4u);
+                    bits0 = wd0 >> w.cshift[0];
+                    bits1 = wd1 >> w.cshift[1];
+                }
+                int rp = -1, sp = -1;
+                if (m.rpos) {
+                    rp = __ldg(&m.rpos[p]);
+                    sp = __ldg(&m.spos[p]);
+                }
                 T zv0 = L::zero(), wv0 = L::zero(), zv1 = L::zero(), wv1 = L::zero();
                 const uint32_t iv = sliceo + (uint32_t)p * 2u * (uint32_t)SV;
-                S pr0 = finish_keep<CPLX, V, 2>(w, m, 0, p, iv, sz0, sw0, k, bits0, dold0, rp, sp, tsum, diverged, zv0, wv0);
-                S pr1 = finish_keep<CPLX, V, 2>(w, m, 1, p, iv, sz1, sw1, k, bits1, dold1, rp, sp, tsum, diverged, zv1, wv1);
+                const S zero = P::zero();
+                S pr0 = finish_keep<CPLX, V, 2>(w, m, 0, p, iv, sz0, sw0, k, bits0, zero, rp, sp, tsum, diverged, zv0, wv0);
+                S pr1 = finish_keep<CPLX, V, 2>(w, m, 1, p, iv, sz1, sw1, k, bits1, zero, rp, sp, tsum, diverged, zv1, wv1);
                 if (wslot) {
                     const uint32_t o = wslot + (uint32_t)r * rowb + (uint32_t)j * 16u;
                     sts_vec(o, *(const float4 *)&zv0);
@@ -459,20 +459,33 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                     sts_vec(o + (uint32_t)(SV + hl) * 16u, *(const float4 *)&wv1);
                 }
                 if (diag) {
-                    // the butterfly of the other kernels over a unit's vectors: its levels below
-                    // hl on both halves here, its last level (seg = sv) as the halves' sum
-#pragma unroll
-                    for (int o = 1; o < 16; o <<= 1) {
-                        if (o < hl && o < a.seg) {
-                            pr0 = P::add(pr0, P::shfl_xor(pr0, o));
-                            pr1 = P::add(pr1, P::shfl_xor(pr1, o));
-                        }
-                    }
-                    if (whole) {
-                        if (w.dlead[0]) w.dpart[0][p] = P::add(dold0, P::add(pr0, pr1));
+                    const uint32_t dd = rc + off_dold + (uint32_t)r * ES;
+                    S d0, d1;
+                    lds_s(dd + (uint32_t)(usel[0] * SC) * ES, d0);
+                    if (whole) d1 = d0;
+                    else lds_s(dd + (uint32_t)(usel[1] * SC) * ES, d1);
+                    if (a.seg == 1) {
+                        if (w.dlead[0]) w.dpart[0][p] = P::add(d0, pr0);
+                        if (w.dlead[1]) w.dpart[1][p] = P::add(d1, pr1);
                     } else {
-                        if (w.dlead[0]) w.dpart[0][p] = P::add(dold0, pr0);
-                        if (w.dlead[1]) w.dpart[1][p] = P::add(dold1, pr1);
+                        // the butterfly of the other kernels over a unit's vectors: at its first
+                        // level even lanes keep vector j's pair sum and odd lanes vector j + hl's
+                        // (each sends the other), then its levels below hl run once for both
+                        // halves; a unit of SV vectors adds the halves at its last level
+                        const bool odd = (lane & 1) != 0;
+                        S keep = odd ? pr1 : pr0;
+                        keep = P::add(keep, P::shfl_xor(odd ? pr0 : pr1, 1));
+#pragma unroll
+                        for (int o = 2; o < hl; o <<= 1)
+                            if (o < a.seg) keep = P::add(keep, P::shfl_xor(keep, o));
+                        if (whole) {
+                            const S other = P::shfl_xor(keep, 1);
+                            if (w.dlead[0]) w.dpart[0][p] = P::add(d0, P::add(keep, other));
+                        } else {
+                            // lane j (j mod seg = 0): vector j's unit; lane j + 1: vector j + hl's
+                            if (w.dlead[0]) w.dpart[0][p] = P::add(d0, keep);
+                            if (lead1) w.dpart[1][p] = P::add(d1, keep);
+                        }
                     }
                 }
             }
