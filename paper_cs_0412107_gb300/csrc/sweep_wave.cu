@@ -50,16 +50,15 @@ size_t row_bytes(int cplx, int D)
 }
 
 // shared memory of one CTA: the black ring and the red ring (2B + 2 chunks each), two
-// stage buffers of two record chunks each (records, constants, noise words, diagonal
-// partials of S positions), two mbarriers
-size_t smem_for(int S, int B, int sv, int cplx, int D, int upu)
+// stage buffers of two record chunks each (records, constants and noise words of S
+// positions), two mbarriers
+size_t smem_for(int S, int B, int sv, int cplx, int D)
 {
     const int V = cplx ? 2 : 4;
     const size_t chb = (size_t)S * 2 * sv * 16;
     const size_t cb = cplx ? sizeof(CstC) : sizeof(CstR);
-    const size_t es = cplx ? 8 : 4;
     const size_t nws = std::max(1, sv * V / 32);
-    const size_t rcb = (size_t)S * (row_bytes(cplx, D) + cb) + nws * S * 4 + (size_t)upu * S * es;
+    const size_t rcb = (size_t)S * (row_bytes(cplx, D) + cb) + nws * S * 4;
     return (size_t)(4 * B + 4) * chb + 4 * rcb + 16;
 }
 
@@ -136,7 +135,7 @@ bool build_wave(const std::vector<GridRow> &rows, const std::vector<uint8_t> &ze
             if (h % s || s % (64 / c)) continue;
             const int b = band(s);
             if (h / s < 4 * b + 2 || b > 15) continue;
-            if (smem_for(s, b, c, cplx, D, c) > WAVE_SMEM_MAX) continue;  // (with units of one vector)
+            if (smem_for(s, b, c, cplx, D) > WAVE_SMEM_MAX) continue;
             S = s;
             B = b;
             break;
@@ -187,11 +186,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
     return v;
 }
-__device__ __forceinline__ void lds_s(uint32_t addr, float &v) { asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr)); }
-__device__ __forceinline__ void lds_s(uint32_t addr, float2 &v)
-{
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
-}
 __device__ __forceinline__ void sts_vec(uint32_t addr, const float4 &v)
 {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
@@ -213,7 +207,7 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
     extern __shared__ __align__(128) uint8_t wsm[];
     __shared__ int abort_s;
     volatile int *abort_flag = &abort_s;
-    constexpr uint32_t RB = sizeof(Row), CB = sizeof(Cst), ES = sizeof(S);
+    constexpr uint32_t RB = sizeof(Row), CB = sizeof(Cst);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -230,13 +224,8 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
     const int nws = max(1, (SV * V) >> 5);
     const int w0 = (sl * SV * V) >> 5;
     const int nws_here = min(nws, a.nw - w0);
-    const int upu = diag ? SV / a.seg : 0;
-    const int u0 = diag ? sl * SV / a.seg : 0;
-    const int units = diag ? (a.K + a.seg * V - 1) / (a.seg * V) : 0;
-    const int upu_here = diag ? min(upu, units - u0) : 0;
     const uint32_t off_noise = (uint32_t)SC * (RB + CB);
-    const uint32_t off_dold = off_noise + (uint32_t)(nws * SC) * 4u;
-    const uint32_t rcb = off_dold + (uint32_t)(upu * SC) * ES;  // one record chunk
+    const uint32_t rcb = off_noise + (uint32_t)(nws * SC) * 4u;  // one record chunk
     const uint32_t black0 = smem_addr(wsm);
     const uint32_t red0 = black0 + (uint32_t)NB * chb;
     const uint32_t stage0 = red0 + (uint32_t)NR * chb;
@@ -246,7 +235,7 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
     w.lane = lane;
     w.seg = a.seg;
     w.diag = diag;
-    int wsel[2], usel[2];
+    int wsel[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int vs = j + q * hl;  // the vector within the slice
@@ -261,7 +250,6 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
         w.zo[q] = (uint32_t)vs;
         w.wo[q] = (uint32_t)(SV + vs);
         wsel[q] = (w.c0[q] >> 5) - w0;     // the noise word among the slice's
-        usel[q] = diag ? vs / a.seg : 0;   // the unit among the slice's
     }
     const bool whole = diag && a.seg == SV;  // one unit a row: the two halves add at the last level
     // with units of two or more vectors, vector j + hl's unit sum ends in lane j + 1 (odd),
@@ -346,8 +334,8 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                 }
             }
             const int nnw = noisy ? nws_here : 0;
-            const int per = 2 + nnw + upu_here;
-            const uint32_t recb = (uint32_t)SC * (RB + CB) + (uint32_t)(nnw * SC) * 4u + (uint32_t)(upu_here * SC) * ES;
+            const int per = 2 + nnw;
+            const uint32_t recb = (uint32_t)SC * (RB + CB) + (uint32_t)(nnw * SC) * 4u;
             const uint32_t bar = bar0 + 8u * b;
             if (lane == 0) mbar_expect(bar, (uint32_t)ccnt * chb + (uint32_t)nrec * recb);
             __syncwarp();
@@ -376,14 +364,10 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                         bulk_g2s(dst, (const uint8_t *)g.trow + (size_t)p0 * RB, (uint32_t)SC * RB, bar);
                     } else if (jj == 1) {
                         bulk_g2s(dst + (uint32_t)SC * RB, (const uint8_t *)g.cst + (size_t)p0 * CB, (uint32_t)SC * CB, bar);
-                    } else if (jj < 2 + nnw) {
+                    } else {
                         const int wq = jj - 2;
                         bulk_g2s(dst + off_noise + (uint32_t)(wq * SC) * 4u,
                                  a.noise + m.noise_cyc + (size_t)(w0 + wq) * (size_t)a.n + (size_t)p0, (uint32_t)SC * 4u, bar);
-                    } else {
-                        const int uq = jj - 2 - nnw;
-                        bulk_g2s(dst + off_dold + (uint32_t)(uq * SC) * ES,
-                                 (const S *)a.diag_part + (size_t)(u0 + uq) * (size_t)a.n + (size_t)p0, (uint32_t)SC * ES, bar);
                     }
                 }
             }
@@ -402,6 +386,12 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                 // the sums in entry order
                 T sz0 = L::zero(), sw0 = L::zero(), sz1 = L::zero(), sw1 = L::zero();
                 const int dmax = EXACT ? D : __reduce_max_sync(0xffffffffu, rec.d);
+                // the running diagonal partials this lane adds to, loaded now for the epilogue
+                S d0 = P::zero(), d1 = P::zero();
+                if (diag) {
+                    if (w.dlead[0]) d0 = w.dpart[0][p];
+                    if (!whole && (a.seg == 1 ? w.dlead[1] : lead1)) d1 = w.dpart[1][p];
+                }
 #pragma unroll
                 for (int u = 0; u < D; ++u) {
                     if (EXACT || u < dmax) {
@@ -459,11 +449,6 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                     sts_vec(o + (uint32_t)(SV + hl) * 16u, *(const float4 *)&wv1);
                 }
                 if (diag) {
-                    const uint32_t dd = rc + off_dold + (uint32_t)r * ES;
-                    S d0, d1;
-                    lds_s(dd + (uint32_t)(usel[0] * SC) * ES, d0);
-                    if (whole) d1 = d0;
-                    else lds_s(dd + (uint32_t)(usel[1] * SC) * ES, d1);
                     if (a.seg == 1) {
                         if (w.dlead[0]) w.dpart[0][p] = P::add(d0, pr0);
                         if (w.dlead[1]) w.dpart[1][p] = P::add(d1, pr1);
@@ -585,7 +570,8 @@ int wave_ctas(int kv, int sv) { return sv > 0 ? (kv + sv - 1) / sv : 0; }
 
 size_t wave_smem(const WaveArgs &g, int cplx, int seg)
 {
-    return smem_for(g.S, g.B, g.sv, cplx, g.D, seg > 0 ? g.sv / seg : 0);
+    (void)seg;
+    return smem_for(g.S, g.B, g.sv, cplx, g.D);
 }
 
 cudaError_t launch_sweep_wave(const SweepArgs &a, const WaveArgs &g, int cplx, cudaStream_t s)
