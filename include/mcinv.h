@@ -496,9 +496,9 @@ void mcinv_server_destroy(mcinv_server_t s);
  * it keeps the last call's product (the product is overwritten whole, so
  * nothing needs clearing): calls whose work overlaps on the GPU -- different
  * streams or host threads -- race; calls on one stream do not.  The first call
- * on a device looks up the array's device address with that device current;
- * make that first call before any stream capture.  The address is kept until
- * the process exits, so do not use this entry point across a cudaDeviceReset.
+ * on a device looks up the array's device address with that device current.
+ * The address is kept until the process exits, so do not use this entry
+ * point across a cudaDeviceReset.
  * The call waits for its stream before returning.  No cudaMalloc, cudaFree or
  * other allocation.  On failure *error (when error is not NULL) points to a
  * static message.  MCINV_E_UNSUPPORTED off sm_103a; MCINV_E_TIMEOUT if a
