@@ -78,6 +78,9 @@ def test_wave_sweep_equals_chain_sliced_kernel(name, make, K, sv):
 
 @pytest.mark.parametrize("make,K", [(lambda: wl.u1_lattice((16, 16), 0.12, 0.08, seed=6), 512),
                                     (lambda: wl.u1_lattice((32, 32), 0.12, 0.08, seed=9), 3200),
+                                    # 64-site half-rows in 32-position chunks: band 2, slices of 16
+                                    # (the shape of the 128 x 128 lattice at K = 4096)
+                                    (lambda: wl.u1_lattice((128, 32), 0.12, 0.08, seed=13), 4096),
                                     (lambda: _real(wl.u1_lattice((16, 12), 0.12, 0.08, seed=7)), 512)])
 def test_wave_estimates_equal_chain_sliced_kernel(make, K):
     c = make()
