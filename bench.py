@@ -934,7 +934,8 @@ def run_configs(args, local):
     import copy
     out = {}
     a = copy.copy(args)
-    a.steps, a.warmup, a.batch, a.burnin = 20, 5, 8, 20
+    # a step is one sampling batch of 128 cycles, as on the headline line
+    a.steps, a.warmup, a.batch, a.burnin = 8, 3, 128, 20
     a.kernel, a.order, a.W, a.threads, a.no_autotune = "auto", "colour", 0, 0, False
     r = guarded(run_lattice2d, a, 1, 0, local)
     if "error" not in r:
