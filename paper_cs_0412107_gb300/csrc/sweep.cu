@@ -35,9 +35,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k)
 // Noise plane for cycles cycle0 .. cycle0+ncyc-1: out[cyc][cw][pos[row]] holds
 // the sign bits of chains 32cw .. 32cw+31 at `row`.  One Philox call yields
 // the 128 bits of rows 128rb .. 128rb+127 of one chain (row r -> bit r%32 of
-// word (r/32)%4); a warp of 32 chains transposes them with ballots so every
-// word is written once.  The plane is stored by position so the sweep reads
-// it coalesced.
+// word (r/32)%4); a warp of 32 chains transposes each of its four 32 x 32 bit
+// blocks (lane = chain, bit = row) so every word is written once.  The plane
+// is stored by position so the sweep reads it coalesced.
 __global__ void __launch_bounds__(128) noise_kernel(uint64_t seed, uint32_t matrix,
                                                     uint64_t chain_base, int K, int n, int nw,
                                                     uint32_t cycle0, const int *__restrict__ pos,
@@ -56,14 +56,19 @@ __global__ void __launch_bounds__(128) noise_kernel(uint64_t seed, uint32_t matr
     uint32_t *dst = out + ((size_t)cyc * nw + cw) * (size_t)n;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        uint32_t mine = 0;
+        // the 32 x 32 bit block (lane i, bit j) transposed by halving block swaps: at
+        // width s each lane trades the half of its word whose bit index has bit s unlike
+        // its own lane index with the lane s away; lane j ends with bit i = block (i, j)
+        uint32_t x = valid ? xs[q] : 0u;
 #pragma unroll
-        for (int b = 0; b < 32; ++b) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, valid && ((xs[q] >> b) & 1u));
-            if (lane == b) mine = bal;
+        for (int sw = 16; sw > 0; sw >>= 1) {
+            const uint32_t m = sw == 16 ? 0x0000ffffu : sw == 8 ? 0x00ff00ffu : sw == 4 ? 0x0f0f0f0fu
+                               : sw == 2 ? 0x33333333u : 0x55555555u;  // bits j with (j & sw) == 0
+            const uint32_t t = __shfl_xor_sync(0xffffffffu, x, sw);
+            x = (lane & sw) ? ((x & ~m) | ((t >> sw) & m)) : ((x & m) | ((t & m) << sw));
         }
         const int row = rb * 128 + q * 32 + lane;
-        if (row < n) dst[pos[row]] = mine;
+        if (row < n) dst[pos[row]] = x;
     }
 }
 
