@@ -66,6 +66,8 @@ CASES = [
     ("c32x32", lambda: wl.u1_lattice((32, 32), 0.12, 0.08, seed=4), 3100, 16),
     ("c128x16", lambda: wl.u1_lattice((128, 16), 0.12, 0.08, seed=5), 2000, 8),
     ("r32x32", lambda: _real(wl.u1_lattice((32, 32), 0.12, 0.08, seed=6)), 4000, 8),
+    # 64 real chains a slice: two noise words, one for each of a lane's two vectors
+    ("r32x32w", lambda: _real(wl.u1_lattice((32, 32), 0.12, 0.08, seed=14)), 6400, 16),
     ("r20x16", lambda: _real(wl.u1_lattice((20, 16), 0.12, 0.08, seed=7)), 132, 4),
     ("c8x8x8x8", lambda: wl.u1_lattice((8, 8, 8, 8), 0.06, 0.04, seed=8), 520, 4),  # band of 8 chunks
 ]
