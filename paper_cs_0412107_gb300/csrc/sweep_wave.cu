@@ -295,6 +295,10 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
         m.noise_cyc = (size_t)cyc * a.nw * (size_t)a.n;
         m.shcol = a.cyc0_in_batch + cyc;
         m.check_div = cyc == a.ncyc - 1;
+        // the epilogue's view: with the diagonal on, the caller adds the trace terms (the
+        // epilogue forms z conj(w) for the diagonal anyway); without it, the epilogue does
+        Mat<CPLX> mt = m;
+        if (diag) mt.tq = nullptr;
         float tsum = 0.f;
 
         // Stage t (< m): black chunk t + B (chunks -B .. B at t = 0) from last cycle's
@@ -386,12 +390,14 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                 // the sums in entry order
                 T sz0 = L::zero(), sw0 = L::zero(), sz1 = L::zero(), sw1 = L::zero();
                 const int dmax = EXACT ? D : __reduce_max_sync(0xffffffffu, rec.d);
-                // the running diagonal partials this lane adds to, loaded now for the epilogue
+                // the running diagonal partials this lane adds to and the row's trace weight,
+                // loaded now for the epilogue
                 S d0 = P::zero(), d1 = P::zero();
                 if (diag) {
                     if (w.dlead[0]) d0 = w.dpart[0][p];
                     if (!whole && (a.seg == 1 ? w.dlead[1] : lead1)) d1 = w.dpart[1][p];
                 }
+                const float qp = diag && a.tq ? __ldg(&a.tq[p]) : 0.f;
 #pragma unroll
                 for (int u = 0; u < D; ++u) {
                     if (EXACT || u < dmax) {
@@ -439,8 +445,18 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
                 T zv0 = L::zero(), wv0 = L::zero(), zv1 = L::zero(), wv1 = L::zero();
                 const uint32_t iv = sliceo + (uint32_t)p * 2u * (uint32_t)SV;
                 const S zero = P::zero();
-                S pr0 = finish_keep<CPLX, V, 2>(w, m, 0, p, iv, sz0, sw0, k, bits0, zero, rp, sp, tsum, diverged, zv0, wv0);
-                S pr1 = finish_keep<CPLX, V, 2>(w, m, 1, p, iv, sz1, sw1, k, bits1, zero, rp, sp, tsum, diverged, zv1, wv1);
+                // (the trace terms in the epilogue's order, vector 0 then 1)
+                S pr0 = finish_keep<CPLX, V, 2>(w, mt, 0, p, iv, sz0, sw0, k, bits0, zero, rp, sp, tsum, diverged, zv0, wv0);
+                S pr1 = finish_keep<CPLX, V, 2>(w, mt, 1, p, iv, sz1, sw1, k, bits1, zero, rp, sp, tsum, diverged, zv1, wv1);
+                if (diag && a.tq) {
+                    if constexpr (CPLX) {
+                        if (w.ok[0]) tsum = __fmaf_rn(qp, pr0.x, tsum);
+                        if (w.ok[1]) tsum = __fmaf_rn(qp, pr1.x, tsum);
+                    } else {
+                        if (w.ok[0]) tsum = __fmaf_rn(qp, pr0, tsum);
+                        if (w.ok[1]) tsum = __fmaf_rn(qp, pr1, tsum);
+                    }
+                }
                 if (wslot) {
                     const uint32_t o = wslot + (uint32_t)r * rowb + (uint32_t)j * 16u;
                     sts_vec(o, *(const float4 *)&zv0);

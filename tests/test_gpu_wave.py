@@ -165,3 +165,22 @@ def test_wave_rejections():
         with pytest.raises(mcinv.McinvError) as e:
             mcinv.create_from_csr(wl.u1_lattice((8, 8), 0.1, 0.1, seed=1), K=64, flags=WAVE | CO | extra)
         assert e.value.status == mcinv.MCINV_E_ARG
+
+
+def test_wave_trace_series_without_the_diagonal():
+    """Trace weights with MCINV_F_NO_DIAG: the epilogue forms z conj(w) for the trace alone."""
+    c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=15)
+    q = wl.q_diag(c.n, 2)
+    nd = mcinv.MCINV_F_NO_DIAG
+    series = []
+    for flags, kw in ((WAVE | CO | nd, {}), (CO | nd, dict(chains_per_cta=64, ctas_per_slice=1, threads_per_cta=256))):
+        h = mcinv.create_from_csr(c, K=512, seed=2, acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=8, flags=flags, **kw)
+        if flags & mcinv.MCINV_F_GRID_WAVE:
+            assert mcinv.mcinv_info(h)["sweep_kernel"] == 6
+        mcinv.mcinv_set_trace_weights(h, q)
+        mcinv.mcinv_burnin(h, 10)
+        mcinv.mcinv_sample(h, 32)
+        series.append(mcinv.mcinv_trace_series(h))
+        mcinv.mcinv_destroy(h)
+    tw, tr = series
+    assert len(tw) == 32 and np.abs(tw - tr).max() <= 1e-5 * np.abs(tr).max()
