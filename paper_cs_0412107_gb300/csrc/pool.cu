@@ -127,14 +127,18 @@ __global__ void __launch_bounds__(128) pool_noise_kernel(const PoolSlotDev *__re
                 uint32_t *dst = S.noise + ((size_t)cyc * nw + cw) * (size_t)S.n;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    uint32_t mine = 0;
+                    // the 32 x 32 bit block (lane = chain, bit = row) transposed by halving block
+                    // swaps, as in the single-matrix noise plane
+                    uint32_t x = valid ? xs[q] : 0u;
 #pragma unroll
-                    for (int b = 0; b < 32; ++b) {
-                        const uint32_t bal = __ballot_sync(0xffffffffu, valid && ((xs[q] >> b) & 1u));
-                        if (lane == b) mine = bal;
+                    for (int sw = 16; sw > 0; sw >>= 1) {
+                        const uint32_t m = sw == 16 ? 0x0000ffffu : sw == 8 ? 0x00ff00ffu : sw == 4 ? 0x0f0f0f0fu
+                                           : sw == 2 ? 0x33333333u : 0x55555555u;  // bits j with (j & sw) == 0
+                        const uint32_t t = __shfl_xor_sync(0xffffffffu, x, sw);
+                        x = (lane & sw) ? ((x & ~m) | ((t >> sw) & m)) : ((x & m) | ((t & m) << sw));
                     }
                     const int row = rb.rb * 128 + q * 32 + lane;
-                    if (row < S.n) dst[S.pos[row]] = mine;
+                    if (row < S.n) dst[S.pos[row]] = x;
                 }
             }
         }
