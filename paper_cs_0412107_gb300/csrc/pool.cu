@@ -58,7 +58,7 @@ struct PoolSlotDev {
     int nlev;
     uint32_t *noise;    // [B][nw][n] by position
     float *dpart;       // [units][n] by position
-    double *dacc;       // [G][n] by row
+    double *dacc;       // [G][n] by position
     uint16_t *zsh, *wsh;
     float *D;
     double *bsum, *bsq;
@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(NT, 1) pool_ring_kernel(const PoolSlotDev *__r
 
 // Folds after the contraction: block segments add the FP32 batch product to
 // the FP64 sums and batch-mean moments; diagonal segments add the units'
-// partials of each group to the FP64 group sums (by row) and clear them.
+// partials of each group to the FP64 group sums (by position, so that the
+// read-modify-writes are coalesced; the estimate maps positions to rows) and
+// clear them.
 __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__restrict__ slots,
                                                         const PoolSeg *__restrict__ segs, const PoolCounts *cnt,
                                                         int units, int G)
@@ -379,7 +381,6 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
             const int upg = units / G;
             for (long long k = threadIdx.x; k < sg.count; k += blockDim.x) {
                 const int p = (int)(sg.begin + k);
-                const int i = S.perm[p];
                 for (int gg = 0; gg < G; ++gg) {
                     double s = 0.0;
                     for (int u = 0; u < upg; ++u) {
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
                         s += (double)*src;
                         *src = 0.f;
                     }
-                    S.dacc[(size_t)gg * S.n + i] += s;
+                    S.dacc[(size_t)gg * S.n + p] += s;
                 }
             }
         }
@@ -535,6 +536,7 @@ struct HostSlot {
     int inverse = 0;
     int cur = 0;
     std::vector<int32_t> ord;  // MCINV_F_COLOR_ORDER: row k of the sampled P C P^T is row ord[k] of C
+    std::vector<int32_t> perm; // position p (level order) is row perm[p] of the sampled matrix
     std::vector<Alloc> allocs;
     PoolSlotDev dev{};
     CUtensorMap maps[2];
@@ -806,6 +808,7 @@ extern "C" mcinv_status mcinv_pool_submit(mcinv_pool_t p, int64_t n, const int64
     HostSlot &s = p->slots[si];
     s = HostSlot{};
     s.ord = std::move(ord);
+    s.perm = P.perm;
     for (size_t b : parts) {
         Alloc a;
         a.bytes = b;
@@ -1004,7 +1007,9 @@ static void build_tables(mcinv_pool_ctx *p, StepTables &T)
                     for (long long b = 0; b < el; b += 1 << 16)
                         T.segs.push_back(PoolSeg{si, 0, b, std::min<long long>(1 << 16, el - b)});
             }
-            for (long long b = 0; b < s.n; b += 4096) T.segs.push_back(PoolSeg{si, 1, b, std::min<long long>(4096, s.n - b)});
+            // diagonal segments of 256 positions (a position a thread): the fold of a large
+            // matrix spreads over many CTAs instead of one walking it
+            for (long long b = 0; b < s.n; b += 256) T.segs.push_back(PoolSeg{si, 1, b, std::min<long long>(256, s.n - b)});
         }
     }
     // most expensive matrices first, so the persistent sweep ends evenly
@@ -1220,10 +1225,14 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
         e = launch_diag_estimate(0, (int)n, p->G, p->d_counts, (double)s.sampled, s.dev.dacc, mean, se, str);
     } else if (kind == MCINV_EST_TRACE) {
         double *dq = se + elems;
+        // q by position (the diagonal's group sums are kept by position)
         std::vector<double> qk;
-        if (q && !s.ord.empty()) {
+        if (q) {
             qk.resize(n);
-            for (size_t k = 0; k < n; ++k) qk[k] = q[s.ord[k]];
+            for (size_t k = 0; k < n; ++k) {
+                const int32_t r = s.perm[k];
+                qk[k] = q[s.ord.empty() ? r : s.ord[r]];
+            }
             q = qk.data();
         }
         if (!q) st = pfail(p, MCINV_E_ARG, "q_diag is NULL");
@@ -1267,17 +1276,23 @@ extern "C" mcinv_status mcinv_pool_estimate(mcinv_pool_t p, int64_t ticket, mcin
     if (g.bytes) p->heap.release(g.off, g.bytes);
     if (st != MCINV_OK) return st;
     if (e != cudaSuccess) return pfail(p, MCINV_E_CUDA, "estimate: %s", cudaGetErrorString(e));
-    if (!s.ord.empty() && kind != MCINV_EST_TRACE && !unpermuted) {
-        // rows (and, for the inverse, columns) of P C^-1 P^T back to those of C^-1
+    if (kind == MCINV_EST_DIAG) {
+        // positions back to the rows of the sampled matrix, and those (colour order) to the rows of C
         for (double *x : {out, se_out}) {
             if (!x) continue;
             std::vector<double> t(x, x + elems);
-            if (kind == MCINV_EST_DIAG) {
-                for (size_t k = 0; k < n; ++k) x[s.ord[k]] = t[k];
-            } else {
-                for (size_t i = 0; i < n; ++i)
-                    for (size_t j = 0; j < n; ++j) x[(size_t)s.ord[i] * n + s.ord[j]] = t[i * n + j];
+            for (size_t k = 0; k < n; ++k) {
+                const int32_t r = s.perm[k];
+                x[s.ord.empty() ? r : s.ord[r]] = t[k];
             }
+        }
+    } else if (!s.ord.empty() && kind != MCINV_EST_TRACE && !unpermuted) {
+        // rows and columns of P C^-1 P^T back to those of C^-1
+        for (double *x : {out, se_out}) {
+            if (!x) continue;
+            std::vector<double> t(x, x + elems);
+            for (size_t i = 0; i < n; ++i)
+                for (size_t j = 0; j < n; ++j) x[(size_t)s.ord[i] * n + s.ord[j]] = t[i * n + j];
         }
     }
     return MCINV_OK;
