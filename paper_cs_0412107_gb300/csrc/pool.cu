@@ -379,16 +379,28 @@ __global__ void __launch_bounds__(256) pool_fold_kernel(const PoolSlotDev *__res
             }
         } else {
             const int upg = units / G;
+            const size_t n = (size_t)S.n;
             for (long long k = threadIdx.x; k < sg.count; k += blockDim.x) {
-                const int p = (int)(sg.begin + k);
-                for (int gg = 0; gg < G; ++gg) {
-                    double s = 0.0;
-                    for (int u = 0; u < upg; ++u) {
-                        float *src = S.dpart + (size_t)(gg * upg + u) * S.n + p;
-                        s += (double)*src;
-                        *src = 0.f;
+                float *__restrict__ dp = S.dpart + sg.begin + k;
+                double *__restrict__ da = S.dacc + sg.begin + k;
+                // eight groups at a time: their partials loaded together, then summed in unit
+                // order from zero, cleared, and added to the group sums
+                for (int g0 = 0; g0 < G; g0 += 8) {
+                    double sum[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        double s = 0.0;
+                        if (g0 + j < G)
+                            for (int u = 0; u < upg; ++u) s += (double)dp[(size_t)((g0 + j) * upg + u) * n];
+                        sum[j] = s;
                     }
-                    S.dacc[(size_t)gg * S.n + p] += s;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (g0 + j < G) {
+                            for (int u = 0; u < upg; ++u) dp[(size_t)((g0 + j) * upg + u) * n] = 0.f;
+                            da[(size_t)(g0 + j) * n] += sum[j];
+                        }
+                    }
                 }
             }
         }
