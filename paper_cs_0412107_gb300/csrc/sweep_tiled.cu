@@ -263,7 +263,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                     const uint32_t b = uses & 1u;
                     const int nxt = it + gridDim.x;
                     if (nxt < nitems) issue(nxt, b ^ 1u);  // that buffer was released at the last CTA barrier
-                    if (!ring_wait(bar0 + 8u * b, (uses >> 1) & 1u)) *abort_flag = 1;
+                    // a stage that did not land (an expired wait) leaves its rows alone: its records,
+                    // and so their slots, may never have been written
+                    const bool landed = __all_sync(0xffffffffu, ring_wait(bar0 + 8u * b, (uses >> 1) & 1u));
+                    if (!landed) *abort_flag = 1;
                     ++uses;
                     const int tile = t0 + it / g.nblk, blk = it - (it / g.nblk) * g.nblk;
                     w.set_block(blk, g.kv, a.K, a.n, a.diag_part, a.noise, true);
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1)
                         if (m.rpos) { nrp = __ldg(&m.rpos[q]); nsp = __ldg(&m.spos[q]); }
                     };
                     if (pb + warp < p1) prefetch(pb + warp);
-                    for (int p = pb + warp; p < p1; p += TNW) {
+                    for (int p = pb + warp; landed && p < p1; p += TNW) {
                         const uint32_t bits = nbits;
                         const S dold = ndold;
                         const int rp = nrp, sp = nsp;

@@ -504,10 +504,14 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
             // last CTA barrier (stage m waits for the whole black ring: issued below)
             if (t + 1 < nst && t + 1 != MC) issue(t + 1, b ^ 1u);
             if (++bslot_next == NB) bslot_next = 0;
-            if (!ring_wait(bar0 + 8u * b, (gst >> 1) & 1u)) *abort_flag = 1;
+            // a stage that did not land (an expired wait) leaves its rows alone: its records,
+            // and so their ring offsets, may never have been written
+            const bool landed = __all_sync(0xffffffffu, ring_wait(bar0 + 8u * b, (gst >> 1) & 1u));
+            if (!landed) *abort_flag = 1;
             ++gst;
             const uint32_t rc0 = stage0 + b * 2u * rcb, rc1 = rc0 + rcb;
-            if (t < MC) {
+            if (!landed) {
+            } else if (t < MC) {
                 if (grp == 0) {
                     // red chunk t from black chunks t-B .. t+B (last cycle's values)
                     uint32_t tb = 0u;
