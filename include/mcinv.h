@@ -156,6 +156,13 @@ typedef struct {
                               values, bit for bit, except the trace series' partial sums, which
                               are grouped by warp in another way.  MCINV_F_AUTOTUNE times it
                               where it applies. */
+#define MCINV_F_TEST_EXPIRE_WAIT 1024 /* testing the bounded waits, with MCINV_F_GRID_WAVE only:
+                              each launch's first stage is announced to its mbarrier but never
+                              copied, so every CTA's wait for it expires (after 2 s), the CTAs
+                              skip their rows and end the launch, and mcinv_sync reports
+                              MCINV_E_TIMEOUT.  The state is then meaningless; the context and
+                              other handles are unaffected.  MCINV_E_ARG without
+                              MCINV_F_GRID_WAVE. */
 #define MCINV_F_COLOR_ORDER 4 /* sweep the rows in the colour order of mcinv_color_order: the
                               handle samples C' = P C P^T (Sec. 4, reordering the rows and columns
                               of C), whose Gauss-Seidel sweep has one dependency level per colour.

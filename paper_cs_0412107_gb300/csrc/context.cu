@@ -871,6 +871,10 @@ static mcinv_status create_impl(mcinv_t *out, int64_t n, const int64_t *row_ptr,
         h->threads = 512;
         h->gctas = tc;
     }
+    if ((h->flags & MCINV_F_TEST_EXPIRE_WAIT) && !(h->flags & MCINV_F_GRID_WAVE)) {
+        fail(h, MCINV_E_ARG, "MCINV_F_TEST_EXPIRE_WAIT needs MCINV_F_GRID_WAVE");
+        return bail(MCINV_E_ARG);
+    }
     if (h->flags & MCINV_F_GRID_WAVE) {
         if (!(h->flags & MCINV_F_GRID) || !(h->flags & MCINV_F_GRID_BULK) || (h->flags & MCINV_F_GRID_NOPAIR) ||
             (h->flags & MCINV_F_GRID_TILE)) {
@@ -1048,6 +1052,7 @@ static SweepArgs sweep_args(mcinv_ctx *h, int ncyc, int noise_cyc, bool accumula
     a.cur = h->cur; a.ncyc = ncyc;
     a.diag_part = accumulate ? h->d_diag_part : nullptr;
     a.seg = h->seg;
+    a.test_expire = (h->flags & MCINV_F_TEST_EXPIRE_WAIT) ? 1 : 0;
     if (accumulate && h->gemm) {
         a.rpos = h->d_rpos; a.spos = h->d_spos;
         a.zsh = h->d_zsh; a.wsh = h->d_wsh; a.ldsh = h->ldsh; a.kp = h->kp;

@@ -99,6 +99,7 @@ struct SweepArgs {
     const float *tq;
     float *tpart;
     int *status;               // bit 0: a chain diverged; bit 2: a staging wait expired
+    int test_expire;           // the wavefront sweep's first stage is never copied (its waits expire)
 };
 
 // Launchers (sweep.cu)

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(WAVE_THREADS, 1) cc_sweep_wave_kernel(const Sw
             const uint32_t bar = bar0 + 8u * b;
             if (lane == 0) mbar_expect(bar, (uint32_t)ccnt * chb + (uint32_t)nrec * recb);
             __syncwarp();
+            if (t == 0 && a.test_expire) return;  // announced, never copied: the waits for it expire
             const int ncp = ccnt + nrec * per;
             for (int k = lane; k < ncp; k += 32) {
                 if (k < ccnt) {

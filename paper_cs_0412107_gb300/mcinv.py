@@ -35,6 +35,7 @@ MCINV_F_GRID_NOPAIR = 64
 MCINV_F_GRID_PAIR = 128
 MCINV_F_GRID_TILE = 256
 MCINV_F_GRID_WAVE = 512
+MCINV_F_TEST_EXPIRE_WAIT = 1024
 
 # every symbol include/mcinv.h declares
 EXPORTS = ("mcinv_default_options", "mcinv_create", "mcinv_create_partitioned", "mcinv_burnin", "mcinv_burnin_coupled", "mcinv_sample",

@@ -184,3 +184,24 @@ def test_wave_trace_series_without_the_diagonal():
         mcinv.mcinv_destroy(h)
     tw, tr = series
     assert len(tw) == 32 and np.abs(tw - tr).max() <= 1e-5 * np.abs(tr).max()
+
+
+def test_wave_expired_wait_ends_the_launch_and_the_context_stays_usable():
+    """MCINV_F_TEST_EXPIRE_WAIT: a stage announced to its mbarrier and never copied. Every
+    CTA's bounded wait (2 s) expires, the launch ends without touching shared memory it did
+    not fill, and mcinv_sync reports MCINV_E_TIMEOUT; kernels then run as before."""
+    import time
+    c = wl.u1_lattice((16, 16), 0.12, 0.08, seed=16)
+    h = mcinv.create_from_csr(c, K=64, seed=1, acc=mcinv.MCINV_ACC_FP32_SIMT, batch_cycles=2,
+                              flags=WAVE | CO | mcinv.MCINV_F_TEST_EXPIRE_WAIT)
+    t0 = time.time()
+    with pytest.raises(mcinv.McinvError) as e:
+        mcinv.mcinv_burnin(h, 2)
+        mcinv.mcinv_sync(h)
+    assert e.value.status == mcinv.MCINV_E_TIMEOUT
+    assert time.time() - t0 < 60
+    mcinv.mcinv_destroy(h)
+    _pair(c, 64, 4, cycles=(1, 3))
+    with pytest.raises(mcinv.McinvError) as e:  # the hook is for the wavefront sweep only
+        mcinv.create_from_csr(c, K=64, flags=CO | mcinv.MCINV_F_TEST_EXPIRE_WAIT)
+    assert e.value.status == mcinv.MCINV_E_ARG
